@@ -1,0 +1,173 @@
+/*
+ * qcd.h - C ABI of the GB300 nested-BiCGStab / SAP / ll-SSOR solver for the
+ * clover-preconditioned O(a)-improved Wilson-Dirac equation
+ *
+ *     D x = b,   D = 1 - kappa F H                                   (Eq. (1), Eq. (2))
+ *
+ * of T. Boku, K.-I. Ishikawa et al., "Multi-block/multi-core SSOR
+ * preconditioner for the QCD quark solver for K computer", Lattice 2012.
+ *
+ * H is the 8-neighbour hop with SU(3) links and (1 -/+ gamma_mu) spin
+ * projectors, F(n) the inverse clover term (Eq. (2) and the sentence after
+ * it).  The solver is the paper's nested BiCGStab (Sec. 2): an FP64 outer
+ * flexible BiCGStab whose preconditioner is an FP32 inner BiCGStab, right-
+ * preconditioned by Luescher's SAP, M_SAP = K sum_{j<N_SAP} (1 - D K)^j
+ * (Eq. (4), Alg. 1), whose block inverses A_EE / A_OO are SSOR sweeps in
+ * locally-lexicographic sub-block order (Sec. 3, "Inverse of block operator").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - dims = {Lx, Ly, Lz, Lt}; site n = x + Lx*(y + Ly*(z + Lz*t)).
+ *    mu = 0..3 is x, y, z, t (the paper's mu = 1..4, mu = 4 the time axis).
+ *  - Complex numbers are interleaved (re, im).  Canonical caller layouts:
+ *      links   U[n][mu][a][b]          complex128 (4 x 3 x 3 complex per site)
+ *      spinor  psi[rhs][n][spin][colour] complex128 (FP64) or complex64 (FP32)
+ *  - gamma matrices in the Dirac representation with gamma_4 diagonal
+ *    (Sec. 3, "Dirac representation"): gamma_k = [[0,-i s_k],[i s_k,0]],
+ *    gamma_4 = diag(1,1,-1,-1).  The basis is part of the ABI.
+ *  - Boundary conditions periodic; qcd_set_boundary(ctx, -1) makes the
+ *    fermion hops across the t edge antiperiodic.
+ *  - SAP blocks: block[mu] divides L_mu and L_mu/block[mu] is even and >= 2
+ *    (so the block checkerboard of Eq. (3) is consistent); subblock[mu]
+ *    divides block[mu].  Block colour = (sum_mu floor(n_mu/block_mu)) mod 2,
+ *    colour 0 is E.
+ *
+ * Ownership and streams
+ * ---------------------
+ *  - A context owns its copies of the links, the clover field and all work
+ *    vectors (device memory it allocates with cudaMalloc and frees in
+ *    qcd_destroy).  The caller owns every pointer it passes.
+ *  - Spinor pointers may be device pointers or host pointers (pageable or
+ *    pinned); host data is copied in and out inside the call on the context
+ *    stream.  Device pointers must stay valid until the work completes.
+ *  - All device work is enqueued on the stream given to qcd_create (NULL =
+ *    legacy default stream).  qcd_apply_D and qcd_sap_precondition with
+ *    device pointers are asynchronous; every call with host pointers, and
+ *    qcd_solve, synchronise the stream before returning.
+ *  - One context per host thread.
+ *
+ * Errors
+ * ------
+ *  Calls return QCD_OK or a negative status and never abort, exit or trap.
+ *  qcd_last_error gives a message.  A CUDA error poisons the context: every
+ *  later call returns QCD_ERR_STATE.
+ */
+#ifndef QCD_H
+#define QCD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qcd_ctx qcd_ctx;
+
+enum {
+    QCD_OK = 0,
+    QCD_ERR_ARG = -1,       /* invalid argument (sizes, geometry, parameters)          */
+    QCD_ERR_CUDA = -2,      /* a CUDA runtime call failed; the context is poisoned    */
+    QCD_ERR_OOM = -3,       /* device allocation failed                               */
+    QCD_ERR_SINGULAR = -4,  /* a chiral 6x6 block of the clover term is not invertible */
+    QCD_ERR_NOCONV = -5,    /* max_outer reached; x holds the last iterate            */
+    QCD_ERR_BREAKDOWN = -6, /* BiCGStab breakdown not cured by 5 restarts             */
+    QCD_ERR_TIMEOUT = -7,   /* a bounded device-side wait gave up                     */
+    QCD_ERR_STATE = -8      /* wrong call order, or context poisoned by a CUDA error  */
+};
+
+enum { QCD_F64 = 0, QCD_F32 = 1, QCD_F16 = 2, QCD_BF16 = 3 };
+
+/* Solver and SAP parameters (Sec. 2, Sec. 3, Eq. (4)). */
+typedef struct {
+    double kappa, csw;  /* must equal the values given to qcd_build_clover             */
+    int block[4];       /* SAP block extents (x, y, z, t)                              */
+    int subblock[4];    /* ll-ordering sub-block extents; subblock | block             */
+    double omega;       /* SSOR relaxation, 0 < omega < 2                              */
+    int nsweep;         /* SSOR sweeps (forward + backward pass) per block inverse     */
+    int nsap;           /* SAP cycles N_SAP                                            */
+    double tol;         /* outer: stop at ||b - D x|| <= tol ||b|| (true FP64 residual) */
+    double inner_tol;   /* inner: stop at ||r|| <= inner_tol ||q||                     */
+    int max_outer, max_inner;
+    int bc_t;           /* +1 periodic, -1 antiperiodic in t (must match qcd_set_boundary) */
+    int sap_storage;    /* QCD_F32 (plain) or QCD_F16 (half storage, FP32 arithmetic)    */
+    int learned;        /* reserved, 0                                                 */
+    int rhs_group;      /* reserved, 0                                                 */
+} qcd_params;
+
+typedef struct {
+    int status, outer_iters, inner_iters, restarts;
+    double true_rel_res; /* max over right-hand sides of ||b - D x|| / ||b|| (FP64)     */
+    double ms_total;     /* wall time of the call                                      */
+    double ms_dslash;    /* reserved (0 unless kernel profiling is on)                 */
+    double ms_sap;       /* reserved (0 unless kernel profiling is on)                 */
+} qcd_stats;
+
+/* Creates a context for a lattice of the given extents (each >= 2, even
+ * volume).  cuda_stream is a cudaStream_t (NULL = default stream).  The
+ * current CUDA device at this call is the context's device. */
+int qcd_create(qcd_ctx **ctx, const int dims[4], void *cuda_stream);
+void qcd_destroy(qcd_ctx *ctx);
+const char *qcd_last_error(const qcd_ctx *ctx);
+
+/* Fermion boundary condition in t: +1 periodic (default), -1 antiperiodic. */
+int qcd_set_boundary(qcd_ctx *ctx, int bc_t);
+
+/* Copies the links U (canonical complex128 [V][4][3][3]; host memory if
+ * on_device == 0, device memory otherwise) into the context's internal FP64
+ * and FP32 link fields (Eq. (2): U_mu(n)).  Invalidates the clover field. */
+int qcd_load_gauge(qcd_ctx *ctx, const double *U, int on_device);
+
+/* Builds F(n) = (1 - (c_SW kappa/2) sigma_{mu nu} F_{mu nu}(n))^{-1} (Eq. (2)),
+ * F_{mu nu} the clover-leaf field strength (Q - Q^dag)/(8i) of the loaded
+ * links, in FP64 and inverts it per chiral 6x6 block (Sec. 3: the clover term
+ * is stored in the chiral representation).  Requires qcd_load_gauge.
+ * Returns QCD_ERR_SINGULAR if some block has a pivot below 1e-300. */
+int qcd_build_clover(qcd_ctx *ctx, double kappa, double csw);
+
+/* out = D in for nrhs right-hand sides (Eq. (2)).  prec = QCD_F64: in/out are
+ * complex128 [nrhs][V][4][3]; QCD_F32: complex64.  in and out must not
+ * overlap.  Requires qcd_build_clover. */
+int qcd_apply_D(qcd_ctx *ctx, void *out, const void *in, int prec, int nrhs);
+
+/* out = M_SAP in (Eq. (4), Alg. 1) in FP32 for nrhs right-hand sides:
+ * complex64 [nrhs][V][4][3].  Uses p->block, p->subblock, p->omega,
+ * p->nsweep, p->nsap, p->sap_storage. */
+int qcd_sap_precondition(qcd_ctx *ctx, float *out, const float *in, const qcd_params *p, int nrhs);
+
+/* Solves D x = b (Eq. (1)) by the nested BiCGStab of Sec. 2 for nrhs
+ * right-hand sides (complex128 [nrhs][V][4][3]).  x holds the initial guess
+ * on entry (zero it for x0 = 0) and the solution on return.  Synchronises.
+ * st may be NULL.  Returns QCD_OK when every right-hand side reached the
+ * true relative residual p->tol. */
+int qcd_solve(qcd_ctx *ctx, double *x, const double *b, const qcd_params *p, int nrhs,
+              qcd_stats *st);
+
+/* ---- measurement hooks -------------------------------------------------- */
+
+/* Kernel classes timed when profiling is on. */
+enum {
+    QCD_K_DSLASH = 0,   /* full operator D (FP64 / FP32)             */
+    QCD_K_SSOR = 1,     /* SAP block SSOR (A_EE / A_OO)              */
+    QCD_K_SAPHOP = 2,   /* SAP block / cross-block hop updates       */
+    QCD_K_BLAS = 3,     /* BiCGStab vector updates and reductions    */
+    QCD_K_OTHER = 4,    /* layout conversion, clover build           */
+    QCD_K_COUNT = 5
+};
+
+/* on != 0: bracket every kernel launch with CUDA events on the context
+ * stream and accumulate per-class device time. */
+int qcd_set_profiling(qcd_ctx *ctx, int on);
+/* Launch count and device milliseconds per class since the last reset
+ * (synchronises the stream).  reset != 0 clears the counters afterwards. */
+int qcd_kernel_stats(qcd_ctx *ctx, int kclass, long *launches, double *ms, int reset);
+/* Total kernel launches made by this context since creation. */
+long qcd_launch_count(const qcd_ctx *ctx);
+
+/* D on internal-layout buffers only, repeated `iters` times (no layout
+ * conversion): the kernel the memory-bandwidth roofline is measured on.
+ * prec = QCD_F64 or QCD_F32; nrhs >= 1.  Work buffers are allocated on first
+ * use and kept. */
+int qcd_bench_dslash(qcd_ctx *ctx, int prec, int nrhs, int iters);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QCD_H */

@@ -1,0 +1,235 @@
+"""Python binding of libqcd.so, the GB300 nested-BiCGStab / SAP / ll-SSOR solver.
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels (``csrc/``).  The functions carry the C ABI's names
+(``include/qcd.h``); :class:`Solver` bundles them for convenience.  Spinors
+and links are passed as torch tensors (device memory, any CUDA stream) or
+numpy arrays (host memory, copied inside the call).  There is no CPU
+fallback: importing the binding without a built library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqcd.so")
+
+QCD_OK, QCD_ERR_ARG, QCD_ERR_CUDA, QCD_ERR_OOM = 0, -1, -2, -3
+QCD_ERR_SINGULAR, QCD_ERR_NOCONV, QCD_ERR_BREAKDOWN, QCD_ERR_TIMEOUT, QCD_ERR_STATE = -4, -5, -6, -7, -8
+QCD_F64, QCD_F32, QCD_F16, QCD_BF16 = 0, 1, 2, 3
+QCD_K_DSLASH, QCD_K_SSOR, QCD_K_SAPHOP, QCD_K_BLAS, QCD_K_OTHER = 0, 1, 2, 3, 4
+KERNEL_CLASSES = ("dslash", "ssor", "saphop", "blas", "other")
+
+EXPORTS = ("qcd_create", "qcd_destroy", "qcd_last_error", "qcd_set_boundary", "qcd_load_gauge",
+           "qcd_build_clover", "qcd_apply_D", "qcd_sap_precondition", "qcd_solve", "qcd_set_profiling",
+           "qcd_kernel_stats", "qcd_launch_count", "qcd_bench_dslash")
+
+
+class QcdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("qcd status %d: %s" % (code, msg))
+        self.code = code
+
+
+class qcd_params(ctypes.Structure):
+    _fields_ = [("kappa", ctypes.c_double), ("csw", ctypes.c_double),
+                ("block", ctypes.c_int * 4), ("subblock", ctypes.c_int * 4),
+                ("omega", ctypes.c_double), ("nsweep", ctypes.c_int), ("nsap", ctypes.c_int),
+                ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
+                ("max_outer", ctypes.c_int), ("max_inner", ctypes.c_int),
+                ("bc_t", ctypes.c_int), ("sap_storage", ctypes.c_int),
+                ("learned", ctypes.c_int), ("rhs_group", ctypes.c_int)]
+
+
+class qcd_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int),
+                ("restarts", ctypes.c_int), ("true_rel_res", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("ms_dslash", ctypes.c_double), ("ms_sap", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libqcd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libqcd.so not built: run `python -m paper_1210_7398_gb300.build` (needs nvcc)")
+    L = ctypes.CDLL(path)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "qcd_create": (I, [ctypes.POINTER(P), ctypes.POINTER(I), P]),
+        "qcd_destroy": (None, [P]),
+        "qcd_last_error": (ctypes.c_char_p, [P]),
+        "qcd_set_boundary": (I, [P, I]),
+        "qcd_load_gauge": (I, [P, P, I]),
+        "qcd_build_clover": (I, [P, D, D]),
+        "qcd_apply_D": (I, [P, P, P, I, I]),
+        "qcd_sap_precondition": (I, [P, P, P, ctypes.POINTER(qcd_params), I]),
+        "qcd_solve": (I, [P, P, P, ctypes.POINTER(qcd_params), I, ctypes.POINTER(qcd_stats)]),
+        "qcd_set_profiling": (I, [P, I]),
+        "qcd_kernel_stats": (I, [P, I, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(D), I]),
+        "qcd_launch_count": (ctypes.c_long, [P]),
+        "qcd_bench_dslash": (I, [P, I, I, I]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    """Device pointer of a torch tensor, or host pointer of a numpy array (contiguous)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data)
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    raise TypeError("expected a torch tensor or a numpy array")
+
+
+def _is_device(a) -> bool:
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+# ---- thin wrappers with the C names ------------------------------------------------
+
+def qcd_create(dims, stream=None):
+    L = load_library()
+    ctx = ctypes.c_void_p()
+    d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    rc = L.qcd_create(ctypes.byref(ctx), d, ctypes.c_void_p(stream or 0))
+    if rc != QCD_OK:
+        raise QcdError(rc, "qcd_create failed")
+    return ctx
+
+
+def qcd_destroy(ctx):
+    load_library().qcd_destroy(ctx)
+
+
+def qcd_last_error(ctx) -> str:
+    return (load_library().qcd_last_error(ctx) or b"").decode()
+
+
+def _check(ctx, rc):
+    if rc != QCD_OK:
+        raise QcdError(rc, qcd_last_error(ctx))
+    return rc
+
+
+def qcd_set_boundary(ctx, bc_t: int):
+    return _check(ctx, load_library().qcd_set_boundary(ctx, int(bc_t)))
+
+
+def qcd_load_gauge(ctx, U):
+    return _check(ctx, load_library().qcd_load_gauge(ctx, _ptr(U), 1 if _is_device(U) else 0))
+
+
+def qcd_build_clover(ctx, kappa: float, csw: float):
+    return _check(ctx, load_library().qcd_build_clover(ctx, float(kappa), float(csw)))
+
+
+def qcd_apply_D(ctx, out, inp, prec: int, nrhs: int = 1):
+    return _check(ctx, load_library().qcd_apply_D(ctx, _ptr(out), _ptr(inp), int(prec), int(nrhs)))
+
+
+def qcd_sap_precondition(ctx, out, inp, params: qcd_params, nrhs: int = 1):
+    return _check(ctx, load_library().qcd_sap_precondition(ctx, _ptr(out), _ptr(inp), ctypes.byref(params),
+                                                           int(nrhs)))
+
+
+def qcd_solve(ctx, x, b, params: qcd_params, nrhs: int = 1, check: bool = True):
+    st = qcd_stats()
+    rc = load_library().qcd_solve(ctx, _ptr(x), _ptr(b), ctypes.byref(params), int(nrhs), ctypes.byref(st))
+    if check:
+        _check(ctx, rc)
+    d = st.as_dict()
+    d["rc"] = rc
+    return d
+
+
+def qcd_set_profiling(ctx, on: bool):
+    return _check(ctx, load_library().qcd_set_profiling(ctx, 1 if on else 0))
+
+
+def qcd_kernel_stats(ctx, kclass: int, reset: bool = False):
+    n = ctypes.c_long()
+    ms = ctypes.c_double()
+    _check(ctx, load_library().qcd_kernel_stats(ctx, int(kclass), ctypes.byref(n), ctypes.byref(ms),
+                                                1 if reset else 0))
+    return n.value, ms.value
+
+
+def qcd_launch_count(ctx) -> int:
+    return int(load_library().qcd_launch_count(ctx))
+
+
+def qcd_bench_dslash(ctx, prec: int, nrhs: int, iters: int):
+    return _check(ctx, load_library().qcd_bench_dslash(ctx, int(prec), int(nrhs), int(iters)))
+
+
+def make_params(kappa, csw, block, subblock, omega=1.0, nsweep=4, nsap=4, tol=1e-10, inner_tol=1e-5,
+                max_outer=100, max_inner=500, bc_t=1, sap_storage=QCD_F32) -> qcd_params:
+    p = qcd_params()
+    p.kappa, p.csw = float(kappa), float(csw)
+    p.block = (ctypes.c_int * 4)(*block)
+    p.subblock = (ctypes.c_int * 4)(*subblock)
+    p.omega, p.nsweep, p.nsap = float(omega), int(nsweep), int(nsap)
+    p.tol, p.inner_tol = float(tol), float(inner_tol)
+    p.max_outer, p.max_inner = int(max_outer), int(max_inner)
+    p.bc_t, p.sap_storage, p.learned, p.rhs_group = int(bc_t), int(sap_storage), 0, 0
+    return p
+
+
+class Solver:
+    """One context on the current CUDA device and torch's current stream."""
+
+    def __init__(self, dims, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.dims = tuple(int(v) for v in dims)
+        self.ctx = qcd_create(self.dims, stream)
+
+    def close(self):
+        if self.ctx:
+            qcd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_boundary(self, bc_t):
+        qcd_set_boundary(self.ctx, bc_t)
+
+    def load_gauge(self, U):
+        qcd_load_gauge(self.ctx, U)
+
+    def build_clover(self, kappa, csw):
+        qcd_build_clover(self.ctx, kappa, csw)
+
+    def apply_D(self, out, inp, prec, nrhs=1):
+        qcd_apply_D(self.ctx, out, inp, prec, nrhs)
+
+    def sap_precondition(self, out, inp, params, nrhs=1):
+        qcd_sap_precondition(self.ctx, out, inp, params, nrhs)
+
+    def solve(self, x, b, params, nrhs=1, check=True):
+        return qcd_solve(self.ctx, x, b, params, nrhs, check)

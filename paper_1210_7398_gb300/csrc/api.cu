@@ -1,0 +1,431 @@
+// C ABI of the solver library (declared in include/qcd.h): argument checks,
+// context and memory management, host/device staging and the launch
+// bookkeeping used for measurement.
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "qcd_internal.h"
+
+namespace qcd {
+
+int fail(qcd_ctx *c, int code, const std::string &msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(qcd_ctx *c, cudaError_t e, const char *what) {
+    if (c) {
+        c->err = std::string(what) + ": " + cudaGetErrorString(e);
+        c->poisoned = true;
+    }
+    if (e == cudaErrorMemoryAllocation) return QCD_ERR_OOM;
+    return QCD_ERR_CUDA;
+}
+
+static cudaEvent_t ev_get(qcd_ctx *c) {
+    if (!c->prof.pool.empty()) {
+        cudaEvent_t e = c->prof.pool.back();
+        c->prof.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_begin(qcd_ctx *c, int kclass, cudaEvent_t *a) {
+    (void)kclass;
+    *a = nullptr;
+    if (c->prof.on) {
+        *a = ev_get(c);
+        cudaEventRecord(*a, c->stream);
+    }
+}
+
+int check_launch(qcd_ctx *c, const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, what);
+    return QCD_OK;
+}
+
+int prof_end(qcd_ctx *c, int kclass, cudaEvent_t a) {
+    c->total_launches++;
+    c->prof.launches[kclass]++;
+    int rc = check_launch(c, "kernel launch");
+    if (rc) return rc;
+    if (c->prof.on && a) {
+        cudaEvent_t b = ev_get(c);
+        cudaEventRecord(b, c->stream);
+        c->prof.pending.push_back({kclass, a, b});
+    }
+    return QCD_OK;
+}
+
+static int prof_collect(qcd_ctx *c) {
+    if (c->prof.pending.empty()) return QCD_OK;
+    QCD_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (auto &p : c->prof.pending) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, p.a, p.b);
+        c->prof.ms[p.kclass] += ms;
+        c->prof.pool.push_back(p.a);
+        c->prof.pool.push_back(p.b);
+    }
+    c->prof.pending.clear();
+    return QCD_OK;
+}
+
+int dev_alloc(qcd_ctx *c, void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(c, QCD_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    return QCD_OK;
+}
+
+void dev_free(qcd_ctx *c, void *p) {
+    (void)c;
+    if (p) cudaFree(p);
+}
+
+}  // namespace qcd
+
+using namespace qcd;
+
+namespace {
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int ready(qcd_ctx *c) {
+    if (!c) return QCD_ERR_ARG;
+    if (c->poisoned) return fail(c, QCD_ERR_STATE, "context poisoned by an earlier CUDA error: " + c->err);
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    return QCD_OK;
+}
+
+int need_clover(qcd_ctx *c) {
+    if (!c->have_clover) return fail(c, QCD_ERR_STATE, "qcd_build_clover must be called first");
+    return QCD_OK;
+}
+
+int ensure_io(qcd_ctx *c, size_t bytes) {
+    if (c->d_io_bytes >= bytes) return QCD_OK;
+    dev_free(c, c->d_io);
+    c->d_io = nullptr;
+    c->d_io_bytes = 0;
+    int rc = dev_alloc(c, &c->d_io, bytes);
+    if (rc) return rc;
+    c->d_io_bytes = bytes;
+    return QCD_OK;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+
+int check_params(qcd_ctx *c, const qcd_params *p) {
+    if (!p) return fail(c, QCD_ERR_ARG, "params is NULL");
+    if (!(p->omega > 0 && p->omega < 2)) return fail(c, QCD_ERR_ARG, "omega must lie in (0, 2)");
+    if (p->nsweep < 1 || p->nsap < 1) return fail(c, QCD_ERR_ARG, "nsweep and nsap must be >= 1");
+    if (p->sap_storage != QCD_F32) return fail(c, QCD_ERR_ARG, "sap_storage: only QCD_F32 is supported");
+    if (p->learned != 0) return fail(c, QCD_ERR_ARG, "learned correction not available");
+    if (p->bc_t != c->bc_t) return fail(c, QCD_ERR_ARG, "params.bc_t differs from the context boundary condition");
+    if (p->kappa != c->kappa || p->csw != c->csw)
+        return fail(c, QCD_ERR_ARG, "params.kappa/csw differ from the clover field built");
+    return QCD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qcd_create(qcd_ctx **out, const int dims[4], void *stream) {
+    if (!out || !dims) return QCD_ERR_ARG;
+    *out = nullptr;
+    long V = 1;
+    for (int m = 0; m < 4; m++) {
+        if (dims[m] < 2 || dims[m] > 4096) return QCD_ERR_ARG;
+        V *= dims[m];
+    }
+    if (V > (1L << 31)) return QCD_ERR_ARG;
+    qcd_ctx *c = new (std::nothrow) qcd_ctx();
+    if (!c) return QCD_ERR_OOM;
+    cudaGetDevice(&c->device);
+    c->stream = (cudaStream_t)stream;
+    for (int m = 0; m < 4; m++) c->lat.L[m] = dims[m];
+    c->lat.V = V;
+    int rc = QCD_OK;
+    if (!rc) rc = dev_alloc(c, (void **)&c->U64, sizeof(double2) * 36 * V);
+    if (!rc) rc = dev_alloc(c, (void **)&c->U32, sizeof(float2) * 36 * V);
+    if (!rc) rc = dev_alloc(c, (void **)&c->F64, sizeof(double2) * 36 * V);
+    if (!rc) rc = dev_alloc(c, (void **)&c->F32, sizeof(float4) * 18 * V);
+    if (!rc) rc = dev_alloc(c, (void **)&c->d_status, sizeof(int) * 16);
+    if (!rc) rc = dev_alloc(c, (void **)&c->d_red, sizeof(double) * 3 * 1216);
+    if (!rc) rc = dev_alloc(c, (void **)&c->d_scalars, sizeof(double) * 16);
+    if (!rc && cudaMallocHost((void **)&c->h_scalars, sizeof(double) * 16) != cudaSuccess) {
+        cudaGetLastError();
+        rc = QCD_ERR_OOM;
+    }
+    if (rc) {
+        qcd_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return QCD_OK;
+}
+
+void qcd_destroy(qcd_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    void *bufs[] = {c->U64, c->U32, c->F64, c->F32, c->d_status, c->d_red, c->d_scalars, c->ws64, c->ws32,
+                    c->d_io, c->bench_in, c->bench_out, c->plan.d_step_ptr, c->plan.d_step_site,
+                    c->plan.d_origin[0], c->plan.d_origin[1]};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    if (c->h_scalars) cudaFreeHost(c->h_scalars);
+    for (auto &p : c->prof.pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : c->prof.pool) cudaEventDestroy(e);
+    cudaGetLastError();
+    delete c;
+}
+
+const char *qcd_last_error(const qcd_ctx *c) {
+    if (!c) return "null context";
+    return c->err.c_str();
+}
+
+int qcd_set_boundary(qcd_ctx *c, int bc_t) {
+    int rc = ready(c);
+    if (rc) return rc;
+    if (bc_t != 1 && bc_t != -1) return fail(c, QCD_ERR_ARG, "bc_t must be +1 or -1");
+    c->bc_t = bc_t;
+    return QCD_OK;
+}
+
+int qcd_load_gauge(qcd_ctx *c, const double *U, int on_device) {
+    int rc = ready(c);
+    if (rc) return rc;
+    if (!U) return fail(c, QCD_ERR_ARG, "U is NULL");
+    const size_t bytes = sizeof(double2) * 36 * c->lat.V;
+    const double2 *src = (const double2 *)U;
+    if (!on_device) {
+        if ((rc = ensure_io(c, bytes))) return rc;
+        QCD_CUDA(c, cudaMemcpyAsync(c->d_io, U, bytes, cudaMemcpyHostToDevice, c->stream));
+        src = (const double2 *)c->d_io;
+    } else if (!aligned16(U)) {
+        return fail(c, QCD_ERR_ARG, "device U must be 16-byte aligned");
+    }
+    if ((rc = links_to_internal(c, src))) return rc;
+    QCD_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->have_gauge = true;
+    c->have_clover = false;
+    return QCD_OK;
+}
+
+int qcd_build_clover(qcd_ctx *c, double kappa, double csw) {
+    int rc = ready(c);
+    if (rc) return rc;
+    if (!c->have_gauge) return fail(c, QCD_ERR_STATE, "qcd_load_gauge must be called first");
+    if (!(kappa > 0 && kappa < 1) || !(csw >= 0 && csw < 100)) return fail(c, QCD_ERR_ARG, "kappa or csw out of range");
+    c->have_clover = false;
+    if ((rc = build_clover(c, kappa, csw))) return rc;
+    c->kappa = kappa;
+    c->csw = csw;
+    c->have_clover = true;
+    return QCD_OK;
+}
+
+int qcd_apply_D(qcd_ctx *c, void *out, const void *in, int prec, int nrhs) {
+    int rc = ready(c);
+    if (rc) return rc;
+    if ((rc = need_clover(c))) return rc;
+    if (!out || !in || nrhs < 1 || (prec != QCD_F64 && prec != QCD_F32))
+        return fail(c, QCD_ERR_ARG, "qcd_apply_D: bad pointer, nrhs or precision");
+    const long V = c->lat.V;
+    const size_t elem = (prec == QCD_F64) ? 16 : 8;
+    const size_t bytes = elem * 12 * V * nrhs;
+    const bool dev_in = is_device_ptr(in), dev_out = is_device_ptr(out);
+    if ((dev_in && !aligned16(in)) || (dev_out && !aligned16(out)))
+        return fail(c, QCD_ERR_ARG, "device spinors must be 16-byte aligned");
+    if ((rc = ensure_io(c, 3 * bytes))) return rc;
+    char *io = (char *)c->d_io;
+    const void *din = in;
+    void *dout = dev_out ? out : io + 2 * bytes;
+    if (!dev_in) {
+        QCD_CUDA(c, cudaMemcpyAsync(io + 2 * bytes, in, bytes, cudaMemcpyHostToDevice, c->stream));
+        din = io + 2 * bytes;
+    }
+    if (prec == QCD_F64) {
+        double2 *a = (double2 *)io, *b = (double2 *)(io + bytes);
+        if ((rc = spinor64_to_internal(c, a, (const double2 *)din, nrhs))) return rc;
+        if ((rc = dslash64(c, b, a, nrhs))) return rc;
+        if ((rc = spinor64_from_internal(c, (double2 *)dout, b, nrhs))) return rc;
+    } else {
+        float4 *a = (float4 *)io, *b = (float4 *)(io + bytes);
+        if ((rc = spinor32_to_internal(c, a, (const float2 *)din, nrhs))) return rc;
+        if ((rc = dslash32(c, b, a, nrhs))) return rc;
+        if ((rc = spinor32_from_internal(c, (float2 *)dout, b, nrhs))) return rc;
+    }
+    if (!dev_out) QCD_CUDA(c, cudaMemcpyAsync(out, dout, bytes, cudaMemcpyDeviceToHost, c->stream));
+    if (!dev_in || !dev_out) QCD_CUDA(c, cudaStreamSynchronize(c->stream));
+    return QCD_OK;
+}
+
+int qcd_sap_precondition(qcd_ctx *c, float *out, const float *in, const qcd_params *p, int nrhs) {
+    int rc = ready(c);
+    if (rc) return rc;
+    if ((rc = need_clover(c))) return rc;
+    if (!out || !in || nrhs < 1) return fail(c, QCD_ERR_ARG, "qcd_sap_precondition: bad pointer or nrhs");
+    if ((rc = check_params(c, p))) return rc;
+    if ((rc = sap_prepare(c, p->block, p->subblock))) return rc;
+    const long V = c->lat.V;
+    const size_t bytes = 8 * 12 * V;  // one complex64 right-hand side
+    const bool dev_in = is_device_ptr(in), dev_out = is_device_ptr(out);
+    if ((dev_in && !aligned16(in)) || (dev_out && !aligned16(out)))
+        return fail(c, QCD_ERR_ARG, "device spinors must be 16-byte aligned");
+    // io: v (internal), x (internal), work (2), staging (1)
+    if ((rc = ensure_io(c, 5 * bytes))) return rc;
+    char *io = (char *)c->d_io;
+    float4 *v = (float4 *)io, *x = (float4 *)(io + bytes), *work = (float4 *)(io + 2 * bytes);
+    char *stage = io + 4 * bytes;
+    for (int k = 0; k < nrhs; k++) {
+        const char *src = (const char *)in + k * bytes;
+        char *dst = (char *)out + k * bytes;
+        if (!dev_in) {
+            QCD_CUDA(c, cudaMemcpyAsync(stage, src, bytes, cudaMemcpyHostToDevice, c->stream));
+            src = stage;
+        }
+        if ((rc = spinor32_to_internal(c, v, (const float2 *)src, 1))) return rc;
+        if ((rc = sap_apply(c, x, v, work, p->omega, p->nsweep, p->nsap))) return rc;
+        if ((rc = spinor32_from_internal(c, (float2 *)(dev_out ? dst : stage), x, 1))) return rc;
+        if (!dev_out) {
+            QCD_CUDA(c, cudaMemcpyAsync(dst, stage, bytes, cudaMemcpyDeviceToHost, c->stream));
+            QCD_CUDA(c, cudaStreamSynchronize(c->stream));
+        }
+    }
+    if (!dev_in) QCD_CUDA(c, cudaStreamSynchronize(c->stream));
+    return QCD_OK;
+}
+
+int qcd_solve(qcd_ctx *c, double *x, const double *b, const qcd_params *p, int nrhs, qcd_stats *st) {
+    auto t0 = std::chrono::steady_clock::now();
+    int rc = ready(c);
+    if (rc) return rc;
+    if ((rc = need_clover(c))) return rc;
+    if (!x || !b || nrhs < 1) return fail(c, QCD_ERR_ARG, "qcd_solve: bad pointer or nrhs");
+    if ((rc = check_params(c, p))) return rc;
+    if (!(p->tol > 0) || !(p->inner_tol > 0) || p->max_outer < 1 || p->max_inner < 1)
+        return fail(c, QCD_ERR_ARG, "tol, inner_tol, max_outer, max_inner must be positive");
+    if ((rc = sap_prepare(c, p->block, p->subblock))) return rc;
+    qcd_stats local;
+    std::memset(&local, 0, sizeof(local));
+    local.status = QCD_OK;
+    const long V = c->lat.V;
+    const size_t bytes = 16 * 12 * V;
+    const bool dev_x = is_device_ptr(x), dev_b = is_device_ptr(b);
+    if ((dev_x && !aligned16(x)) || (dev_b && !aligned16(b)))
+        return fail(c, QCD_ERR_ARG, "device spinors must be 16-byte aligned");
+    if ((rc = ensure_io(c, 4 * bytes))) return rc;
+    char *io = (char *)c->d_io;
+    double2 *xi = (double2 *)io, *bi = (double2 *)(io + bytes);
+    char *sx = io + 2 * bytes, *sb = io + 3 * bytes;
+    int status = QCD_OK;
+    for (int k = 0; k < nrhs; k++) {
+        const char *bsrc = (const char *)b + k * bytes;
+        char *xdst = (char *)x + k * bytes;
+        if (!dev_b) {
+            QCD_CUDA(c, cudaMemcpyAsync(sb, bsrc, bytes, cudaMemcpyHostToDevice, c->stream));
+            bsrc = sb;
+        }
+        const char *xsrc = xdst;
+        if (!dev_x) {
+            QCD_CUDA(c, cudaMemcpyAsync(sx, xdst, bytes, cudaMemcpyHostToDevice, c->stream));
+            xsrc = sx;
+        }
+        if ((rc = spinor64_to_internal(c, bi, (const double2 *)bsrc, 1))) return rc;
+        if ((rc = spinor64_to_internal(c, xi, (const double2 *)xsrc, 1))) return rc;
+        int s = solve(c, xi, bi, p, &local);
+        if (s == QCD_ERR_CUDA || s == QCD_ERR_OOM || s == QCD_ERR_STATE || s == QCD_ERR_ARG) return s;
+        if (s != QCD_OK && status == QCD_OK) status = s;
+        if ((rc = spinor64_from_internal(c, (double2 *)(dev_x ? xdst : sx), xi, 1))) return rc;
+        if (!dev_x) QCD_CUDA(c, cudaMemcpyAsync(xdst, sx, bytes, cudaMemcpyDeviceToHost, c->stream));
+    }
+    QCD_CUDA(c, cudaStreamSynchronize(c->stream));
+    local.status = status;
+    local.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (st) *st = local;
+    if (status != QCD_OK) {
+        if (status == QCD_ERR_NOCONV) c->err = "not converged within max_outer";
+        else if (status == QCD_ERR_BREAKDOWN) c->err = "BiCGStab breakdown not cured by restarts";
+    }
+    return status;
+}
+
+int qcd_set_profiling(qcd_ctx *c, int on) {
+    int rc = ready(c);
+    if (rc) return rc;
+    if (!on && (rc = prof_collect(c))) return rc;
+    c->prof.on = on != 0;
+    return QCD_OK;
+}
+
+int qcd_kernel_stats(qcd_ctx *c, int kclass, long *launches, double *ms, int reset) {
+    int rc = ready(c);
+    if (rc) return rc;
+    if (kclass < 0 || kclass >= QCD_K_COUNT) return fail(c, QCD_ERR_ARG, "kernel class out of range");
+    if ((rc = prof_collect(c))) return rc;
+    if (launches) *launches = c->prof.launches[kclass];
+    if (ms) *ms = c->prof.ms[kclass];
+    if (reset) {
+        c->prof.launches[kclass] = 0;
+        c->prof.ms[kclass] = 0;
+    }
+    return QCD_OK;
+}
+
+long qcd_launch_count(const qcd_ctx *c) { return c ? c->total_launches : 0; }
+
+int qcd_bench_dslash(qcd_ctx *c, int prec, int nrhs, int iters) {
+    int rc = ready(c);
+    if (rc) return rc;
+    if ((rc = need_clover(c))) return rc;
+    if ((prec != QCD_F64 && prec != QCD_F32) || nrhs < 1 || iters < 1)
+        return fail(c, QCD_ERR_ARG, "qcd_bench_dslash: bad precision, nrhs or iters");
+    const size_t bytes = (prec == QCD_F64 ? 16 : 8) * 12 * c->lat.V * (size_t)nrhs;
+    if (c->bench_bytes < bytes) {
+        dev_free(c, c->bench_in);
+        dev_free(c, c->bench_out);
+        c->bench_in = c->bench_out = nullptr;
+        c->bench_bytes = 0;
+        if ((rc = dev_alloc(c, &c->bench_in, bytes))) return rc;
+        if ((rc = dev_alloc(c, &c->bench_out, bytes))) return rc;
+        c->bench_bytes = bytes;
+        // a deterministic non-trivial input: constant bytes
+        QCD_CUDA(c, cudaMemsetAsync(c->bench_in, 0x3c, bytes, c->stream));
+    }
+    for (int i = 0; i < iters; i++) {
+        if (prec == QCD_F64) rc = dslash64(c, (double2 *)c->bench_out, (const double2 *)c->bench_in, nrhs);
+        else rc = dslash32(c, (float4 *)c->bench_out, (const float4 *)c->bench_in, nrhs);
+        if (rc) return rc;
+    }
+    return QCD_OK;
+}
+
+}  // extern "C"

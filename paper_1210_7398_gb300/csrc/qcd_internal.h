@@ -1,0 +1,164 @@
+// Internal declarations of the GB300 solver library (not part of the C ABI).
+//
+// Internal field layouts (all in device memory, V sites, site order as the
+// canonical lexicographic order n = x + Lx*(y + Ly*(z + Lz*t))):
+//   FP64 spinor   [nrhs][12][V] double2   plane k = spin*3 + colour
+//   FP32 spinor   [nrhs][6][V]  float4    plane p holds components 2p, 2p+1
+//   FP64 links    [4][9][V]     double2   plane mu*9 + a*3 + b
+//   FP32 links    [4][9][V]     float2
+//   FP64 clover   [36][V]       double2   chiral blocks of F/2, packed (see clover.cu)
+//   FP32 clover   [18][V]       float4    the same 72 reals per site
+// Each plane is contiguous over sites, so a warp of consecutive sites reads
+// one contiguous segment per plane (coalesced 16-byte or 8-byte loads).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/qcd.h"
+
+namespace qcd {
+
+struct Lattice {
+    int L[4];
+    long V;
+};
+
+// SAP geometry: block decomposition (Eq. (3)) plus the ll-order schedule of
+// the SSOR passes, grouped into steps whose sites are pairwise non-adjacent.
+struct SapPlan {
+    int b[4] = {0, 0, 0, 0}, s[4] = {0, 0, 0, 0};
+    int nb[4] = {0, 0, 0, 0};
+    int vol = 0;        // sites per block
+    int nsteps = 0;     // parallel steps per pass
+    int max_step = 0;   // largest number of sites in one step
+    int nblk[2] = {0, 0};
+    int *d_step_ptr = nullptr;   // [nsteps + 1]
+    int *d_step_site = nullptr;  // [vol] block-local lexicographic site index
+    int *d_origin[2] = {nullptr, nullptr};  // [nblk[c]][4] block origins per colour
+    std::vector<int> h_step_ptr, h_step_site;
+};
+
+struct Profiler {
+    bool on = false;
+    long launches[QCD_K_COUNT] = {0, 0, 0, 0, 0};
+    double ms[QCD_K_COUNT] = {0, 0, 0, 0, 0};
+    struct Pending { int kclass; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+};
+
+}  // namespace qcd
+
+struct qcd_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    qcd::Lattice lat{};
+    int bc_t = 1;
+    std::string err;
+    bool poisoned = false;
+    long total_launches = 0;
+    qcd::Profiler prof;
+
+    // gauge and clover fields
+    bool have_gauge = false, have_clover = false;
+    double kappa = 0, csw = 0;
+    double2 *U64 = nullptr;
+    float2 *U32 = nullptr;
+    double2 *F64 = nullptr;
+    float4 *F32 = nullptr;
+    int *d_status = nullptr;  // device status word (clover singularity)
+
+    // SAP plan cache (one geometry at a time)
+    qcd::SapPlan plan;
+
+    // workspace, grown on demand
+    std::vector<void *> allocations;
+    void *ws64 = nullptr;
+    size_t ws64_bytes = 0;
+    void *ws32 = nullptr;
+    size_t ws32_bytes = 0;
+    double *d_red = nullptr;      // reduction partials
+    double *d_scalars = nullptr;  // reduction results (device)
+    double *h_scalars = nullptr;  // pinned host mirror
+    // host staging for host-pointer calls
+    void *d_io = nullptr;
+    size_t d_io_bytes = 0;
+    // bench buffers
+    void *bench_in = nullptr, *bench_out = nullptr;
+    size_t bench_bytes = 0;
+};
+
+namespace qcd {
+
+// ---- error handling --------------------------------------------------------
+int fail(qcd_ctx *c, int code, const std::string &msg);
+int cuda_fail(qcd_ctx *c, cudaError_t e, const char *what);
+#define QCD_CUDA(ctx, call)                                        \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return qcd::cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+// ---- launch bookkeeping ------------------------------------------------------
+void prof_begin(qcd_ctx *c, int kclass, cudaEvent_t *a);
+int prof_end(qcd_ctx *c, int kclass, cudaEvent_t a);
+int check_launch(qcd_ctx *c, const char *what);
+
+// ---- memory ------------------------------------------------------------------
+int dev_alloc(qcd_ctx *c, void **p, size_t bytes);
+void dev_free(qcd_ctx *c, void *p);
+
+// ---- kernels (launchers return QCD_OK or an error) ----------------------------
+// layout conversion (layout.cu)
+int spinor64_to_internal(qcd_ctx *c, double2 *dst, const double2 *canon, int nrhs);
+int spinor64_from_internal(qcd_ctx *c, double2 *canon, const double2 *src, int nrhs);
+int spinor32_to_internal(qcd_ctx *c, float4 *dst, const float2 *canon, int nrhs);
+int spinor32_from_internal(qcd_ctx *c, float2 *canon, const float4 *src, int nrhs);
+int spinor64_to_32(qcd_ctx *c, float4 *dst, const double2 *src, int nrhs);
+int spinor32_to_64(qcd_ctx *c, double2 *dst, const float4 *src, int nrhs);
+int links_to_internal(qcd_ctx *c, const double2 *canon);
+
+// clover (clover.cu)
+int build_clover(qcd_ctx *c, double kappa, double csw);
+
+// operator D (dslash.cu)
+int dslash64(qcd_ctx *c, double2 *out, const double2 *in, int nrhs);
+int dslash32(qcd_ctx *c, float4 *out, const float4 *in, int nrhs);
+
+// SAP (sap.cu)
+int sap_prepare(qcd_ctx *c, const int b[4], const int s[4]);
+// x = M_SAP v (FP32 internal layout, one right-hand side); work = 3 spinors
+int sap_apply(qcd_ctx *c, float4 *x, const float4 *v, float4 *work, double omega, int nsweep,
+              int nsap);
+
+// BLAS (blas.cu) over complex vectors of n elements (double2 or float2)
+enum { RED_DOT = 0, RED_DOT_NORM = 1, RED_NORM = 2 };
+// results: cdot(a,b) -> res[0], res[1]; ||b||^2 (DOT_NORM) or ||a||^2 (NORM) -> res[2]
+int reduce64(qcd_ctx *c, int kind, const double2 *a, const double2 *b, long n, double res[3]);
+int reduce32(qcd_ctx *c, int kind, const float2 *a, const float2 *b, long n, double res[3]);
+int blas_zero(qcd_ctx *c, void *p, size_t bytes);
+int blas_copy(qcd_ctx *c, void *dst, const void *src, size_t bytes);
+// p = r + beta (p - om v)
+int blas_p_update64(qcd_ctx *c, double2 *p, const double2 *r, const double2 *v, double2 beta,
+                    double2 om, long n);
+int blas_p_update32(qcd_ctx *c, float2 *p, const float2 *r, const float2 *v, double2 beta,
+                    double2 om, long n);
+// s = r - alpha v
+int blas_s_update64(qcd_ctx *c, double2 *s, const double2 *r, const double2 *v, double2 alpha, long n);
+int blas_s_update32(qcd_ctx *c, float2 *s, const float2 *r, const float2 *v, double2 alpha, long n);
+// x += alpha ph + om sh;  r = s - om t
+int blas_xr_update64(qcd_ctx *c, double2 *x, double2 *r, const double2 *ph, const double2 *sh,
+                     const double2 *s, const double2 *t, double2 alpha, double2 om, long n);
+int blas_xr_update32(qcd_ctx *c, float2 *x, float2 *r, const float2 *ph, const float2 *sh,
+                     const float2 *s, const float2 *t, double2 alpha, double2 om, long n);
+// r = b - w
+int blas_sub64(qcd_ctx *c, double2 *r, const double2 *b, const double2 *w, long n);
+
+// solver (solver.cu)
+int solve(qcd_ctx *c, double2 *x, const double2 *b, const qcd_params *p, qcd_stats *st);
+
+}  // namespace qcd

@@ -1,0 +1,48 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+that include/qcd.h declares (no GPU needed; no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1210_7398_gb300 as q
+from paper_1210_7398_gb300 import build as qbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(qcd_[A-Za-z0-9_]+)\s*\(", text))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = qbuild.build()
+    return ctypes.CDLL(path)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    syms = declared_symbols()
+    assert len(syms) >= 13
+    for s in sorted(syms):
+        assert hasattr(lib, s), "missing export %s" % s
+    assert set(q.EXPORTS) <= syms
+
+
+def test_binding_structs_match_header():
+    # qcd_params: 2 doubles, 8 ints, 1 double, 2 ints, 2 doubles, 6 ints (with padding)
+    assert ctypes.sizeof(q.qcd_params) == 104
+    assert ctypes.sizeof(q.qcd_stats) == 48
+
+
+def test_null_context_is_rejected(lib):
+    q.load_library()
+    assert q.load_library().qcd_set_boundary(None, 1) == q.QCD_ERR_ARG
+    assert q.load_library().qcd_launch_count(None) == 0

@@ -1,0 +1,179 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Tolerances: FP64 D <= 1e-13 relative (max abs error / max abs value), FP32 D
+<= 2e-6 relative in norm, SAP output <= 1e-5 relative in norm, solutions at a
+true relative residual <= 1e-10 under the oracle's D.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import qcd_inputs as qi
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1210_7398_gb300 as q  # noqa: E402
+
+CSW = 1.6
+
+
+def rel_max(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def rel_norm(a, b):
+    return np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())
+
+
+def make_solver(dims, kappa, seed, bc_t=1, eps=0.3):
+    U = qi.gauge_field(dims, eps, seed=seed)
+    s = q.Solver(dims)
+    if bc_t != 1:
+        s.set_boundary(bc_t)
+    s.load_gauge(torch.from_numpy(U).cuda())
+    s.build_clover(kappa, CSW)
+    _, F = oracle.clover(dims, U, CSW, kappa)
+    return s, U, F
+
+
+@pytest.mark.parametrize("dims,bc_t", [((4, 4, 4, 4), 1), ((6, 4, 4, 6), -1), ((8, 8, 8, 16), 1),
+                                       ((2, 6, 4, 2), -1)])
+def test_dslash_fp64_fp32_vs_oracle(dims, bc_t):
+    kappa = 0.12
+    s, U, F = make_solver(dims, kappa, seed=1000, bc_t=bc_t)
+    psi = qi.gaussian_spinor(dims, seed=2000, nrhs=2)
+    ref = np.stack([oracle.apply_D(dims, U, F, kappa, psi[k], bc_t=bc_t) for k in range(2)])
+    dev = torch.from_numpy(psi).cuda()
+    out = torch.empty_like(dev)
+    s.apply_D(out, dev, q.QCD_F64, nrhs=2)
+    torch.cuda.synchronize()
+    assert rel_max(out.cpu().numpy(), ref) <= 1e-13
+    dev32 = dev.to(torch.complex64)
+    out32 = torch.empty_like(dev32)
+    s.apply_D(out32, dev32, q.QCD_F32, nrhs=2)
+    torch.cuda.synchronize()
+    assert rel_norm(out32.cpu().numpy().astype(np.complex128), ref) <= 2e-6
+    # host buffers through the same entry point
+    host_out = np.empty_like(psi)
+    s.apply_D(host_out, psi, q.QCD_F64, nrhs=2)
+    assert rel_max(host_out, ref) <= 1e-13
+    s.close()
+
+
+def test_dslash_free_field_plane_wave():
+    """U = 1: D e^{ipn} u = [1 - kappa sum(2cos p - 2i gamma sin p)] e^{ipn} u (closed form)."""
+    dims, kappa = (8, 4, 4, 8), 0.11
+    s = q.Solver(dims)
+    s.load_gauge(torch.from_numpy(qi.unit_gauge(dims)).cuda())
+    s.build_clover(kappa, CSW)
+    p = 2 * np.pi * np.array([1, 1, 0, 3]) / np.array(dims)
+    x = np.array(np.unravel_index(np.arange(qi.volume(dims)), dims, order="F")).T
+    rng = np.random.default_rng(3)
+    u = rng.normal(size=(4, 3)) + 1j * rng.normal(size=(4, 3))
+    ph = np.exp(1j * x @ p)
+    psi = (ph[:, None, None] * u[None])[None]
+    g = [oracle.gamma(m) for m in range(4)]
+    Mp = np.eye(4) * (1 - kappa * np.sum(2 * np.cos(p))) + sum(kappa * 2j * np.sin(p[m]) * g[m] for m in range(4))
+    expect = ph[:, None, None] * (Mp @ u)[None]
+    out = np.empty_like(psi)
+    s.apply_D(out, psi, q.QCD_F64)
+    assert rel_max(out[0], expect) <= 1e-14
+    s.close()
+
+
+SAP_CASES = [
+    # dims, block, subblock, omega, nsweep, nsap
+    ((4, 4, 4, 4), (2, 2, 2, 2), (1, 1, 1, 1), 1.0, 4, 4),   # the 4^4 configuration
+    ((8, 4, 4, 8), (4, 2, 2, 4), (2, 1, 2, 2), 1.2, 2, 3),
+    ((8, 8, 8, 8), (4, 4, 4, 4), (2, 2, 2, 2), 1.0, 3, 2),
+    ((12, 12, 12, 24), (6, 6, 6, 12), (3, 3, 3, 6), 1.0, 4, 4),  # the 12^3 x 24 configuration
+]
+
+
+@pytest.mark.parametrize("case", SAP_CASES, ids=lambda c: "x".join(map(str, c[0])))
+def test_sap_vs_oracle(case):
+    dims, b, sb, omega, nsweep, nsap = case
+    kappa = 0.12
+    s, U, F = make_solver(dims, kappa, seed=1001)
+    v = qi.gaussian_spinor(dims, seed=2001)[0]
+    ref = oracle.sap(dims, U, F, kappa, b, sb, omega, nsweep, nsap, v)
+    prm = q.make_params(kappa, CSW, b, sb, omega=omega, nsweep=nsweep, nsap=nsap)
+    vin = torch.from_numpy(v.astype(np.complex64)).cuda()
+    out = torch.empty_like(vin)
+    s.sap_precondition(out, vin, prm)
+    torch.cuda.synchronize()
+    assert rel_norm(out.cpu().numpy().astype(np.complex128), ref) <= 1e-5
+    s.close()
+
+
+def test_solve_4x4_matches_oracle_and_dense_lu():
+    dims, kappa = (4, 4, 4, 4), 0.12
+    s, U, F = make_solver(dims, kappa, seed=1000)
+    b = qi.gaussian_spinor(dims, seed=2000)
+    prm = q.make_params(kappa, CSW, (2, 2, 2, 2), (1, 1, 1, 1), omega=1.0, nsweep=4, nsap=4, tol=1e-10)
+    x = torch.zeros(b.shape, dtype=torch.complex128, device="cuda")
+    st = s.solve(x, torch.from_numpy(b).cuda(), prm)
+    xg = x.cpu().numpy()[0]
+    r = b[0] - oracle.apply_D(dims, U, F, kappa, xg)
+    assert np.linalg.norm(r) / np.linalg.norm(b[0]) <= 1e-10
+    assert st["true_rel_res"] <= 1e-10
+    xo, status, _ = oracle.solve(dims, U, F, kappa, (2, 2, 2, 2), (1, 1, 1, 1), 1.0, 4, 4, b[0], tol=1e-10)
+    assert status == 0
+    assert rel_norm(xg, xo) <= 1e-8
+    s.close()
+
+
+@pytest.mark.parametrize("dims,block,sub", [((12, 12, 12, 24), (6, 6, 6, 12), (3, 3, 3, 6)),
+                                            ((8, 8, 8, 16), (4, 4, 4, 4), (2, 2, 2, 2))])
+def test_solve_true_residual_under_oracle(dims, block, sub):
+    kappa = 0.12
+    s, U, F = make_solver(dims, kappa, seed=1001)
+    b = qi.gaussian_spinor(dims, seed=2001)
+    prm = q.make_params(kappa, CSW, block, sub, omega=1.0, nsweep=4, nsap=4, tol=1e-10)
+    x = np.zeros_like(b)
+    st = s.solve(x, b, prm)  # host buffers
+    r = b[0] - oracle.apply_D(dims, U, F, kappa, x[0])
+    rel = np.linalg.norm(r) / np.linalg.norm(b[0])
+    assert rel <= 1e-10, (rel, st)
+    assert st["outer_iters"] >= 1 and st["inner_iters"] >= 1
+    s.close()
+
+
+def test_solve_is_deterministic():
+    dims, kappa = (8, 8, 8, 8), 0.12
+    s, U, F = make_solver(dims, kappa, seed=1002)
+    b = torch.from_numpy(qi.gaussian_spinor(dims, seed=2002)).cuda()
+    prm = q.make_params(kappa, CSW, (4, 4, 4, 4), (2, 2, 2, 2), tol=1e-10)
+    x1 = torch.zeros_like(b)
+    x2 = torch.zeros_like(b)
+    s.solve(x1, b, prm)
+    s.solve(x2, b, prm)
+    assert torch.equal(x1, x2)
+    s.close()
+
+
+def test_errors_are_reported_not_fatal():
+    dims = (4, 4, 4, 4)
+    s = q.Solver(dims)
+    psi = torch.zeros((1, 256, 4, 3), dtype=torch.complex128, device="cuda")
+    with pytest.raises(q.QcdError) as e:
+        s.apply_D(torch.empty_like(psi), psi, q.QCD_F64)
+    assert e.value.code == q.QCD_ERR_STATE
+    s.load_gauge(torch.from_numpy(qi.gauge_field(dims, 0.3, seed=5)).cuda())
+    s.build_clover(0.12, CSW)
+    bad = q.make_params(0.12, CSW, (4, 2, 2, 2), (1, 1, 1, 1))  # one block along x
+    with pytest.raises(q.QcdError) as e:
+        s.solve(torch.zeros_like(psi), psi, bad)
+    assert e.value.code == q.QCD_ERR_ARG
+    # misaligned device pointer
+    flat = torch.zeros(256 * 12 + 1, dtype=torch.complex64, device="cuda")
+    with pytest.raises(q.QcdError) as e:
+        s.apply_D(flat[1:], flat[:-1], q.QCD_F32)
+    assert e.value.code == q.QCD_ERR_ARG
+    # the context is still usable
+    out = torch.empty_like(psi)
+    s.apply_D(out, psi, q.QCD_F64)
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(out) == 0
+    s.close()
