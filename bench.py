@@ -1,0 +1,369 @@
+"""Benchmark: time to solve D x = b to a true relative residual of 1e-10 on
+the 12^3 x 24 lattice (plain method: FP64 outer / FP32 inner nested BiCGStab,
+SAP blocks 6^3 x 12, ll sub-blocks 3^3 x 6, SSOR omega = 1, 4 sweeps, 4 SAP
+cycles), plus the bandwidth of the operator D on lattices larger than L2.
+
+One step = one full solve from x0 = 0 (every kernel of the solver runs in
+the step).  Prints one JSON line.  ``--impl reference`` times the FP64 CPU
+oracle instead: each step is one full oracle solve of the same workload on
+the host cores (10-20 s of CPU work).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solve time to rel. residual 1e-10, chosen vs plain; D GB/s vs HBM peak"
+WORKLOAD = dict(name="12^3x24 plain nested BiCGStab + SAP(6^3x12 blocks, 3^3x6 ll sub-blocks)",
+                dims=(12, 12, 12, 24), kappa=0.12, csw=1.6, eps=0.3, gauge_seed=1001, source_seed=2001,
+                block=(6, 6, 6, 12), subblock=(3, 3, 3, 6), omega=1.0, nsweep=4, nsap=4, tol=1e-10,
+                inner_tol=1e-5)
+TABLE1_FLOP_PER_SITE = 1896  # flop per site of the clover hopping matrix without SU(3) reconstruction (Table 1)
+D_BYTES_PER_SITE = {"f32": 768, "f64": 1536}  # in + out spinor, 4 links (each shared by 2 sites), clover
+L2_FLUSH_BYTES = 512 << 20
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return dict(hbm_gbs=float(p["hbm_gbs"]), sm_max_mhz=float(p.get("sm_max_mhz", 2070.0)), source="measured")
+    except Exception:
+        return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smmax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smmax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smmax) if smmax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (cpu_baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+
+def oracle_setup():
+    import oracle
+    import qcd_inputs as qi
+    w = WORKLOAD
+    U = qi.gauge_field(w["dims"], w["eps"], seed=w["gauge_seed"])
+    _, F = oracle.clover(w["dims"], U, w["csw"], w["kappa"])
+    b = qi.gaussian_spinor(w["dims"], seed=w["source_seed"])[0]
+    return U, F, b
+
+
+def oracle_solve_seconds(U, F, b):
+    """Wall seconds of one full oracle solve of the workload (FP64 outer and inner)."""
+    import oracle
+    w = WORKLOAD
+    t0 = time.perf_counter()
+    _, status, st = oracle.solve(w["dims"], U, F, w["kappa"], w["block"], w["subblock"], w["omega"], w["nsweep"],
+                                 w["nsap"], b, tol=w["tol"], inner_tol=w["inner_tol"])
+    return time.perf_counter() - t0, status, st
+
+
+def cores_used():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    U, F, b = oracle_setup()
+    for _ in range(args.warmup):
+        oracle_solve_seconds(U, F, b)
+    vals = []
+    for _ in range(args.steps):
+        t, status, st = oracle_solve_seconds(U, F, b)
+        vals.append(t)
+    v = statistics.mean(vals)
+    sample = ("per step: one full FP64 oracle solve of the 12^3x24 workload from x0 = 0 to 1e-10 "
+              "(outer %d, inner %d iterations, true rel. residual %.1e)" % (st["outer"], st["inner"],
+                                                                             st["true_rel_res"]))
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1000 * v, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD["name"], "lattice": "12x12x12x24", "kappa": WORKLOAD["kappa"],
+                      "csw": WORKLOAD["csw"], "tol": WORKLOAD["tol"]},
+           "cpu_baseline": {"value": v, "unit": "s", "cores": cores_used(), "kind": "oracle", "sample": sample},
+           "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def kernel_model(cls, V, nrhs_steps, prm, peaks):
+    """(bound, algorithmic units per launch, unit, peak) for a kernel class."""
+    fp32_tflops = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+    if cls == "dslash32":
+        return "hbm", V * D_BYTES_PER_SITE["f32"] / 1e9, "GB/s", peaks["hbm_gbs"]
+    if cls == "dslash64":
+        return "hbm", V * D_BYTES_PER_SITE["f64"] / 1e9, "GB/s", peaks["hbm_gbs"]
+    if cls == "ssor":
+        # one launch: the V/2 sites of one colour, 2 passes per sweep, Table-1 flops per site update
+        return "alu", (V / 2) * 2 * prm["nsweep"] * TABLE1_FLOP_PER_SITE / 1e12, "TFLOP/s", fp32_tflops
+    if cls == "saphop":
+        return "hbm", V * D_BYTES_PER_SITE["f32"] / 1e9, "GB/s", peaks["hbm_gbs"]
+    return None
+
+
+def dslash_bandwidth(q, torch, dims, iters, peaks, seed=1002):
+    """GB/s of the FP32 operator D (K1) on internal-layout buffers, CUDA events on the context stream."""
+    import qcd_inputs as qi
+    V = qi.volume(dims)
+    U = qi.gauge_field(dims, 0.3, seed=seed, device="cuda")
+    s = q.Solver(dims)
+    s.load_gauge(U)
+    del U
+    s.build_clover(0.12, 1.6)
+    stream = torch.cuda.current_stream()
+    q.qcd_bench_dslash(s.ctx, q.QCD_F32, 1, 3)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    times = []
+    for _ in range(iters):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        q.qcd_bench_dslash(s.ctx, q.QCD_F32, 1, 1)
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    s.close()
+    del flush
+    torch.cuda.empty_cache()
+    ms = statistics.median(times)
+    gbs = V * D_BYTES_PER_SITE["f32"] / (ms * 1e-3) / 1e9
+    return {"lattice": "x".join(map(str, dims)), "V": V, "prec": "f32", "ms": ms, "GB_s": gbs,
+            "GFLOP_s": V * TABLE1_FLOP_PER_SITE / (ms * 1e-3) / 1e9, "frac_measured": gbs / peaks["hbm_gbs"],
+            "frac_nominal_8TBs": gbs / 8000.0, "bytes_per_site": D_BYTES_PER_SITE["f32"],
+            "timing": "median of %d launches, L2 flushed before each" % iters}
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1210_7398_gb300 import build as qbuild
+    if not os.path.exists(qbuild.LIB):
+        qbuild.build()
+    import paper_1210_7398_gb300 as q
+    import qcd_inputs as qi
+
+    peaks = read_peaks()
+    w = WORKLOAD
+    dims = w["dims"]
+    V = qi.volume(dims)
+    U = qi.gauge_field(dims, w["eps"], seed=w["gauge_seed"])
+    b = qi.gaussian_spinor(dims, seed=w["source_seed"])
+    s = q.Solver(dims)
+    s.load_gauge(torch.from_numpy(U).cuda())
+    s.build_clover(w["kappa"], w["csw"])
+    prm = q.make_params(w["kappa"], w["csw"], w["block"], w["subblock"], omega=w["omega"], nsweep=w["nsweep"],
+                        nsap=w["nsap"], tol=w["tol"], inner_tol=w["inner_tol"])
+    stream = torch.cuda.current_stream()
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        x.zero_()
+        s.solve(x, bd, prm)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K solves, L2 flushed between them ----
+    q.qcd_set_profiling(s.ctx, True)
+    for k in range(len(q.KERNEL_CLASSES)):
+        q.qcd_kernel_stats(s.ctx, k, reset=True)
+    launches0 = q.qcd_launch_count(s.ctx)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    step_ms, stats = [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        x.zero_()
+        ev_a = torch.cuda.Event(enable_timing=True)
+        ev_b = torch.cuda.Event(enable_timing=True)
+        ev_a.record(stream)
+        st = s.solve(x, bd, prm)
+        ev_b.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(ev_a.elapsed_time(ev_b))
+        stats.append(st)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    launches = q.qcd_launch_count(s.ctx) - launches0
+    kstats = {}
+    for k, nm in enumerate(q.KERNEL_CLASSES):
+        n, ms = q.qcd_kernel_stats(s.ctx, k, reset=True)
+        kstats[nm] = {"launches": n, "ms": ms}
+    q.qcd_set_profiling(s.ctx, False)
+    ms_step = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([ms_step], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+
+    # true residual of the last solve, checked with the library's FP64 D
+    xr = x.cpu().numpy()
+
+    # ---- end to end: host buffers through the C ABI, copies inside the timed region ----
+    b_host = torch.from_numpy(b).pin_memory().numpy()
+    x_host = torch.zeros(b.shape, dtype=torch.complex128).pin_memory().numpy()
+    e2e = []
+    for _ in range(max(1, min(args.steps, 3))):
+        x_host[...] = 0
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.solve(x_host, b_host, prm)
+        e2e.append(time.perf_counter() - t0)
+    s.close()
+    del flush
+    torch.cuda.empty_cache()
+
+    out = None
+    if rank == 0:
+        # dominant kernel and its roofline
+        dom = max((nm for nm in kstats if kstats[nm]["launches"]), key=lambda nm: kstats[nm]["ms"])
+        model = kernel_model(dom, V, 1, w, peaks)
+        roof = None
+        if model:
+            bound, units, unit, peak = model
+            avg_ms = kstats[dom]["ms"] / kstats[dom]["launches"]
+            achieved = units / (avg_ms * 1e-3)
+            roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                    "frac": achieved / peak, "traffic": None, "avg_launch_ms": avg_ms,
+                    "peak_source": peaks["source"] if bound == "hbm" else "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+        tot_k = sum(v["ms"] for v in kstats.values())
+        for v in kstats.values():
+            v["share"] = v["ms"] / tot_k if tot_k else 0.0
+        dsl = []
+        if not args.skip_dslash:
+            for dd in ((24, 24, 24, 48), (48, 48, 48, 96)):
+                dsl.append(dslash_bandwidth(q, torch, dd, 20, peaks))
+        cpu = None
+        if world == 1 and not args.skip_cpu:
+            try:
+                Uo, Fo, bo = oracle_setup()
+                t, status, st_o = oracle_solve_seconds(Uo, Fo, bo)
+                cpu = {"value": t, "unit": "s", "cores": cores_used(), "kind": "oracle",
+                       "sample": "one full FP64 oracle solve of the same workload (outer %d, inner %d, "
+                                 "true rel. residual %.1e)" % (st_o["outer"], st_o["inner"], st_o["true_rel_res"])}
+            except Exception as e:  # the baseline is reported, not required
+                cpu = {"value": None, "unit": "s", "cores": cores_used(), "kind": "oracle", "sample": "failed: %s" % e}
+        last = stats[-1]
+        out = {"metric": METRIC, "value": ms_step / 1000.0, "unit": "s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+               "config": {"workload": WORKLOAD["name"], "lattice": "12x12x12x24", "kappa": w["kappa"],
+                          "csw": w["csw"], "omega": w["omega"], "nsweep": w["nsweep"], "nsap": w["nsap"],
+                          "tol": w["tol"], "inner_tol": w["inner_tol"], "l2": "flushed (512 MiB write) between steps",
+                          "parallelism": "replicas" if world > 1 else "single GPU"},
+               "solve": {"outer_iters": last["outer_iters"], "inner_iters": last["inner_iters"],
+                         "restarts": last["restarts"], "true_rel_res": last["true_rel_res"],
+                         "solves_per_s_all_gpus": world / (ms_step / 1000.0), "wall_s_timed_region": wall},
+               "e2e": {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": 2 * 16 * 12 * V,
+                       "d2h_bytes_per_step": 16 * 12 * V,
+                       "note": "qcd_solve with pinned host x and b; copies inside the call"},
+               "gpu_launches": launches, "kernels": kstats, "clocks": clk, "roofline": roof,
+               "dslash": dsl, "cpu_baseline": cpu}
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--skip-dslash", action="store_true", help="skip the D bandwidth measurement")
+    ap.add_argument("--skip-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

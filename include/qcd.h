@@ -144,12 +144,13 @@ int qcd_solve(qcd_ctx *ctx, double *x, const double *b, const qcd_params *p, int
 
 /* Kernel classes timed when profiling is on. */
 enum {
-    QCD_K_DSLASH = 0,   /* full operator D (FP64 / FP32)             */
-    QCD_K_SSOR = 1,     /* SAP block SSOR (A_EE / A_OO)              */
-    QCD_K_SAPHOP = 2,   /* SAP block / cross-block hop updates       */
-    QCD_K_BLAS = 3,     /* BiCGStab vector updates and reductions    */
-    QCD_K_OTHER = 4,    /* layout conversion, clover build           */
-    QCD_K_COUNT = 5
+    QCD_K_DSLASH32 = 0, /* full operator D in FP32 (inner solver)     */
+    QCD_K_DSLASH64 = 1, /* full operator D in FP64 (outer solver)     */
+    QCD_K_SSOR = 2,     /* SAP block SSOR (A_EE / A_OO)              */
+    QCD_K_SAPHOP = 3,   /* SAP block / cross-block hop updates       */
+    QCD_K_BLAS = 4,     /* BiCGStab vector updates and reductions    */
+    QCD_K_OTHER = 5,    /* layout conversion, clover build           */
+    QCD_K_COUNT = 6
 };
 
 /* on != 0: bracket every kernel launch with CUDA events on the context

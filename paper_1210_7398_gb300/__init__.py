@@ -20,8 +20,8 @@ LIB_PATH = os.path.join(_HERE, "libqcd.so")
 QCD_OK, QCD_ERR_ARG, QCD_ERR_CUDA, QCD_ERR_OOM = 0, -1, -2, -3
 QCD_ERR_SINGULAR, QCD_ERR_NOCONV, QCD_ERR_BREAKDOWN, QCD_ERR_TIMEOUT, QCD_ERR_STATE = -4, -5, -6, -7, -8
 QCD_F64, QCD_F32, QCD_F16, QCD_BF16 = 0, 1, 2, 3
-QCD_K_DSLASH, QCD_K_SSOR, QCD_K_SAPHOP, QCD_K_BLAS, QCD_K_OTHER = 0, 1, 2, 3, 4
-KERNEL_CLASSES = ("dslash", "ssor", "saphop", "blas", "other")
+QCD_K_DSLASH32, QCD_K_DSLASH64, QCD_K_SSOR, QCD_K_SAPHOP, QCD_K_BLAS, QCD_K_OTHER = 0, 1, 2, 3, 4, 5
+KERNEL_CLASSES = ("dslash32", "dslash64", "ssor", "saphop", "blas", "other")
 
 EXPORTS = ("qcd_create", "qcd_destroy", "qcd_last_error", "qcd_set_boundary", "qcd_load_gauge",
            "qcd_build_clover", "qcd_apply_D", "qcd_sap_precondition", "qcd_solve", "qcd_set_profiling",

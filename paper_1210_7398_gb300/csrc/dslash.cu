@@ -65,20 +65,20 @@ int dslash64(qcd_ctx *c, double2 *out, const double2 *in, int nrhs) {
     Geo g = geo_of(c);
     dim3 grid((unsigned)((g.V + 127) / 128), nrhs);
     cudaEvent_t ev;
-    prof_begin(c, QCD_K_DSLASH, &ev);
+    prof_begin(c, QCD_K_DSLASH64, &ev);
     dslash_kernel<double, double2, double2, double2><<<grid, 128, 0, c->stream>>>(out, in, c->U64, c->F64,
                                                                                   c->kappa, g, nrhs);
-    return prof_end(c, QCD_K_DSLASH, ev);
+    return prof_end(c, QCD_K_DSLASH64, ev);
 }
 
 int dslash32(qcd_ctx *c, float4 *out, const float4 *in, int nrhs) {
     Geo g = geo_of(c);
     dim3 grid((unsigned)((g.V + 127) / 128), nrhs);
     cudaEvent_t ev;
-    prof_begin(c, QCD_K_DSLASH, &ev);
+    prof_begin(c, QCD_K_DSLASH32, &ev);
     dslash_kernel<float, float4, float2, float4><<<grid, 128, 0, c->stream>>>(out, in, c->U32, c->F32,
                                                                               (float)c->kappa, g, nrhs);
-    return prof_end(c, QCD_K_DSLASH, ev);
+    return prof_end(c, QCD_K_DSLASH32, ev);
 }
 
 }  // namespace qcd

@@ -44,8 +44,8 @@ struct SapPlan {
 
 struct Profiler {
     bool on = false;
-    long launches[QCD_K_COUNT] = {0, 0, 0, 0, 0};
-    double ms[QCD_K_COUNT] = {0, 0, 0, 0, 0};
+    long launches[QCD_K_COUNT] = {};
+    double ms[QCD_K_COUNT] = {};
     struct Pending { int kclass; cudaEvent_t a, b; };
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> pool;
