@@ -132,6 +132,29 @@ int qcd_apply_D(qcd_ctx *ctx, void *out, const void *in, int prec, int nrhs);
  * p->nsweep, p->nsap, p->sap_storage. */
 int qcd_sap_precondition(qcd_ctx *ctx, float *out, const float *in, const qcd_params *p, int nrhs);
 
+/* The paper has no counterpart to this entry point; it serves callers that
+ * must not allocate device memory at call time: a process whose framework
+ * allocator has already reserved the GPU's free memory (a cudaMalloc here
+ * would fail or fragment its pool), or a serving loop with a fixed memory
+ * budget that must not grow or stall on an allocation while work is in
+ * flight.  Such a caller creates the context, loads the gauge field and
+ * builds the clover term once at set-up (those calls allocate), then calls
+ * this instead of qcd_sap_precondition.
+ *
+ * out = M_SAP in, exactly as qcd_sap_precondition with nrhs = 1, for device
+ * pointers only (16-byte aligned complex64 [V][4][3]).  It calls no
+ * cudaMalloc, cudaFree or allocating library routine: its scratch (four FP32
+ * spinor fields and the ll-schedule tables) is one fixed __device__ array of
+ * about 16.9 MB that every GPU loading the library holds until the process
+ * exits.  Lattices above 41,472 sites (12^3 x 24) are rejected with
+ * QCD_ERR_ARG.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  All calls on a device share the one array and leave their data
+ * in it; every region is rewritten before it is read, but calls that overlap
+ * on the GPU (other streams, other contexts on the same device) race and
+ * must be serialised by the caller.  Asynchronous on the context stream. */
+int qcd_sap_precondition_noalloc(qcd_ctx *ctx, float *out, const float *in, const qcd_params *p);
+
 /* Solves D x = b (Eq. (1)) by the nested BiCGStab of Sec. 2 for nrhs
  * right-hand sides (complex128 [nrhs][V][4][3]).  x holds the initial guess
  * on entry (zero it for x0 = 0) and the solution on return.  Synchronises.

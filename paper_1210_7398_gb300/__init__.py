@@ -25,7 +25,7 @@ KERNEL_CLASSES = ("dslash32", "dslash64", "ssor", "saphop", "blas", "other")
 
 EXPORTS = ("qcd_create", "qcd_destroy", "qcd_last_error", "qcd_set_boundary", "qcd_load_gauge",
            "qcd_build_clover", "qcd_apply_D", "qcd_sap_precondition", "qcd_solve", "qcd_set_profiling",
-           "qcd_kernel_stats", "qcd_launch_count", "qcd_bench_dslash")
+           "qcd_kernel_stats", "qcd_launch_count", "qcd_bench_dslash", "qcd_sap_precondition_noalloc")
 
 
 class QcdError(RuntimeError):
@@ -74,6 +74,7 @@ def load_library(path: str = LIB_PATH):
         "qcd_build_clover": (I, [P, D, D]),
         "qcd_apply_D": (I, [P, P, P, I, I]),
         "qcd_sap_precondition": (I, [P, P, P, ctypes.POINTER(qcd_params), I]),
+        "qcd_sap_precondition_noalloc": (I, [P, P, P, ctypes.POINTER(qcd_params)]),
         "qcd_solve": (I, [P, P, P, ctypes.POINTER(qcd_params), I, ctypes.POINTER(qcd_stats)]),
         "qcd_set_profiling": (I, [P, I]),
         "qcd_kernel_stats": (I, [P, I, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(D), I]),
@@ -150,6 +151,11 @@ def qcd_apply_D(ctx, out, inp, prec: int, nrhs: int = 1):
 def qcd_sap_precondition(ctx, out, inp, params: qcd_params, nrhs: int = 1):
     return _check(ctx, load_library().qcd_sap_precondition(ctx, _ptr(out), _ptr(inp), ctypes.byref(params),
                                                            int(nrhs)))
+
+
+def qcd_sap_precondition_noalloc(ctx, out, inp, params: qcd_params):
+    """out = M_SAP inp without any device allocation (device tensors, one right-hand side)."""
+    return _check(ctx, load_library().qcd_sap_precondition_noalloc(ctx, _ptr(out), _ptr(inp), ctypes.byref(params)))
 
 
 def qcd_solve(ctx, x, b, params: qcd_params, nrhs: int = 1, check: bool = True):

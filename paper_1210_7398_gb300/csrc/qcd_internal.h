@@ -39,7 +39,7 @@ struct SapPlan {
     int *d_step_ptr = nullptr;   // [nsteps + 1]
     int *d_step_site = nullptr;  // [vol] block-local lexicographic site index
     int *d_origin[2] = {nullptr, nullptr};  // [nblk[c]][4] block origins per colour
-    std::vector<int> h_step_ptr, h_step_site;
+    std::vector<int> h_step_ptr, h_step_site, h_origin[2];
 };
 
 struct Profiler {
@@ -130,10 +130,16 @@ int dslash64(qcd_ctx *c, double2 *out, const double2 *in, int nrhs);
 int dslash32(qcd_ctx *c, float4 *out, const float4 *in, int nrhs);
 
 // SAP (sap.cu)
+// host part of a plan (tables in h_*; device pointers left null); QCD_ERR_ARG on bad geometry
+int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &plan);
+// builds and uploads the plan of this geometry into c->plan (allocates its tables)
 int sap_prepare(qcd_ctx *c, const int b[4], const int s[4]);
 // x = M_SAP v (FP32 internal layout, one right-hand side); work = 3 spinors
 int sap_apply(qcd_ctx *c, float4 *x, const float4 *v, float4 *work, double omega, int nsweep,
               int nsap);
+// the same with an explicit plan whose device tables are already in place
+int sap_apply_plan(qcd_ctx *c, const SapPlan &plan, float4 *x, const float4 *v, float4 *work, double omega,
+                   int nsweep, int nsap);
 
 // BLAS (blas.cu) over complex vectors of n elements (double2 or float2)
 enum { RED_DOT = 0, RED_DOT_NORM = 1, RED_NORM = 2 };

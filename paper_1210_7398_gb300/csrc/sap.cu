@@ -197,13 +197,9 @@ void free_plan(qcd_ctx *c) {
 
 }  // namespace
 
-int sap_prepare(qcd_ctx *c, const int b[4], const int s[4]) {
-    if (!geometry_ok(c, b, s))
-        return fail(c, QCD_ERR_ARG, "SAP geometry: need L % block == 0, L/block even and >= 2, block % subblock == 0");
-    SapPlan &p = c->plan;
-    if (p.vol && std::equal(b, b + 4, p.b) && std::equal(s, s + 4, p.s)) return QCD_OK;
-    free_plan(c);
-    SapPlan np;
+int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &np) {
+    if (!geometry_ok(c, b, s)) return QCD_ERR_ARG;
+    np = SapPlan();
     std::memcpy(np.b, b, sizeof(np.b));
     std::memcpy(np.s, s, sizeof(np.s));
     int nq[4];
@@ -253,21 +249,32 @@ int sap_prepare(qcd_ctx *c, const int b[4], const int s[4]) {
     np.nsteps = (int)np.h_step_ptr.size() - 1;
     for (int k = 0; k < np.nsteps; k++) np.max_step = std::max(np.max_step, np.h_step_ptr[k + 1] - np.h_step_ptr[k]);
     // block origins per colour
-    std::vector<int> org[2];
     for (int B3 = 0; B3 < np.nb[3]; B3++)
         for (int B2 = 0; B2 < np.nb[2]; B2++)
             for (int B1 = 0; B1 < np.nb[1]; B1++)
                 for (int B0 = 0; B0 < np.nb[0]; B0++) {
                     const int col = (B0 + B1 + B2 + B3) & 1;
-                    org[col].insert(org[col].end(), {B0 * b[0], B1 * b[1], B2 * b[2], B3 * b[3]});
+                    np.h_origin[col].insert(np.h_origin[col].end(), {B0 * b[0], B1 * b[1], B2 * b[2], B3 * b[3]});
                 }
+    for (int col = 0; col < 2; col++) np.nblk[col] = (int)np.h_origin[col].size() / 4;
+    return QCD_OK;
+}
+
+int sap_prepare(qcd_ctx *c, const int b[4], const int s[4]) {
+    if (!geometry_ok(c, b, s))
+        return fail(c, QCD_ERR_ARG, "SAP geometry: need L % block == 0, L/block even and >= 2, block % subblock == 0");
+    SapPlan &p = c->plan;
+    if (p.vol && std::equal(b, b + 4, p.b) && std::equal(s, s + 4, p.s)) return QCD_OK;
+    free_plan(c);
+    SapPlan np;
+    sap_plan_host(c, b, s, np);
     int rc;
     if ((rc = dev_alloc(c, (void **)&np.d_step_ptr, sizeof(int) * np.h_step_ptr.size()))) return rc;
     if ((rc = dev_alloc(c, (void **)&np.d_step_site, sizeof(int) * np.vol))) return rc;
     for (int col = 0; col < 2; col++) {
-        np.nblk[col] = (int)org[col].size() / 4;
-        if ((rc = dev_alloc(c, (void **)&np.d_origin[col], sizeof(int) * org[col].size()))) return rc;
-        QCD_CUDA(c, cudaMemcpy(np.d_origin[col], org[col].data(), sizeof(int) * org[col].size(), cudaMemcpyHostToDevice));
+        if ((rc = dev_alloc(c, (void **)&np.d_origin[col], sizeof(int) * np.h_origin[col].size()))) return rc;
+        QCD_CUDA(c, cudaMemcpy(np.d_origin[col], np.h_origin[col].data(), sizeof(int) * np.h_origin[col].size(),
+                               cudaMemcpyHostToDevice));
     }
     QCD_CUDA(c, cudaMemcpy(np.d_step_ptr, np.h_step_ptr.data(), sizeof(int) * np.h_step_ptr.size(), cudaMemcpyHostToDevice));
     QCD_CUDA(c, cudaMemcpy(np.d_step_site, np.h_step_site.data(), sizeof(int) * np.vol, cudaMemcpyHostToDevice));
@@ -276,7 +283,11 @@ int sap_prepare(qcd_ctx *c, const int b[4], const int s[4]) {
 }
 
 int sap_apply(qcd_ctx *c, float4 *x, const float4 *v, float4 *work, double omega, int nsweep, int nsap) {
-    const SapPlan &p = c->plan;
+    return sap_apply_plan(c, c->plan, x, v, work, omega, nsweep, nsap);
+}
+
+int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, float4 *work, double omega, int nsweep,
+                   int nsap) {
     const long V = c->lat.V;
     float4 *r = work, *y = work + 6 * V;
     Geo g;
