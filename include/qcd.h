@@ -144,9 +144,9 @@ int qcd_sap_precondition(qcd_ctx *ctx, float *out, const float *in, const qcd_pa
  * out = M_SAP in, exactly as qcd_sap_precondition with nrhs = 1, for device
  * pointers only (16-byte aligned complex64 [V][4][3]).  It calls no
  * cudaMalloc, cudaFree or allocating library routine: its scratch (four FP32
- * spinor fields and the ll-schedule tables) is one fixed __device__ array of
- * about 16.9 MB that every GPU loading the library holds until the process
- * exits.  Lattices above 41,472 sites (12^3 x 24) are rejected with
+ * spinor fields, the per-site SSOR records and the ll-schedule tables) is one
+ * fixed __device__ array of about 68.3 MB that every GPU loading the library
+ * holds until the process exits.  Lattices above 41,472 sites (12^3 x 24) are rejected with
  * QCD_ERR_ARG.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress), so make that first call before any stream
  * capture.  All calls on a device share the one array and leave their data
@@ -162,6 +162,14 @@ int qcd_sap_precondition_noalloc(qcd_ctx *ctx, float *out, const float *in, cons
  * true relative residual p->tol. */
 int qcd_solve(qcd_ctx *ctx, double *x, const double *b, const qcd_params *p, int nrhs,
               qcd_stats *st);
+
+/* Tuning knob of the SAP block kernel; results do not depend on it.  The
+ * least number of CTAs (one thread-block cluster) that share one SAP block,
+ * 1..8: the kernel splits each block along t over the smallest divisor of
+ * block[3] that is >= min_ctas and whose slabs fit in shared memory.  More
+ * CTAs per block spread a step's sites over more SMs at the price of more
+ * cluster barriers.  Default 1. */
+int qcd_set_sap_ctas(qcd_ctx *ctx, int min_ctas);
 
 /* ---- measurement hooks -------------------------------------------------- */
 

@@ -192,8 +192,8 @@ void qcd_destroy(qcd_ctx *c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     void *bufs[] = {c->U64, c->U32, c->F64, c->F32, c->d_status, c->d_red, c->d_scalars, c->ws64, c->ws32,
-                    c->d_io, c->bench_in, c->bench_out, c->plan.d_step_ptr, c->plan.d_step_site,
-                    c->plan.d_origin[0], c->plan.d_origin[1]};
+                    c->d_io, c->bench_in, c->bench_out, c->plan.d_origin[0] /* the plan's table region */,
+                    c->plan.d_rec};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (c->h_scalars) cudaFreeHost(c->h_scalars);
@@ -235,6 +235,7 @@ int qcd_load_gauge(qcd_ctx *c, const double *U, int on_device) {
     if ((rc = links_to_internal(c, src))) return rc;
     QCD_CUDA(c, cudaStreamSynchronize(c->stream));
     c->have_gauge = true;
+    c->field_version++;
     c->have_clover = false;
     return QCD_OK;
 }
@@ -249,6 +250,7 @@ int qcd_build_clover(qcd_ctx *c, double kappa, double csw) {
     c->kappa = kappa;
     c->csw = csw;
     c->have_clover = true;
+    c->field_version++;
     return QCD_OK;
 }
 
@@ -376,6 +378,16 @@ int qcd_solve(qcd_ctx *c, double *x, const double *b, const qcd_params *p, int n
         else if (status == QCD_ERR_BREAKDOWN) c->err = "BiCGStab breakdown not cured by restarts";
     }
     return status;
+}
+
+int qcd_set_sap_ctas(qcd_ctx *c, int min_ctas) {
+    int rc = ready(c);
+    if (rc) return rc;
+    if (min_ctas < 1 || min_ctas > 8) return fail(c, QCD_ERR_ARG, "min_ctas must lie in 1..8");
+    QCD_CUDA(c, c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+    if (c->sap_min_ctas != min_ctas) sap_invalidate(c);
+    c->sap_min_ctas = min_ctas;
+    return QCD_OK;
 }
 
 int qcd_set_profiling(qcd_ctx *c, int on) {

@@ -11,7 +11,7 @@
 // this entry point, which only launches kernels and copies.
 //
 // Its scratch memory (the internal-layout input and output spinors, the two
-// SAP work spinors and the ll-schedule tables) lives in one file-scope
+// SAP work spinors, the per-site SSOR records and the ll-schedule tables) lives in one file-scope
 // __device__ array of fixed size, so the library reserves it on every GPU
 // that loads the library, until the process exits.  In host code the array's
 // name is only a host-side stand-in for the symbol; the device address is
@@ -28,8 +28,9 @@ namespace {
 // Largest lattice this entry point accepts: 41,472 sites (e.g. 12^3 x 24).
 constexpr long kNoAllocMaxSites = 41472;
 constexpr size_t kSpinorBytes = sizeof(float4) * 6 * (size_t)kNoAllocMaxSites;  // one FP32 spinor field
-constexpr size_t kTableInts = 6 * (size_t)kNoAllocMaxSites + 64;                 // ll schedule + block origins
-constexpr size_t kScratchBytes = 4 * kSpinorBytes + sizeof(int) * kTableInts;    // about 16.9 MB
+constexpr size_t kRecordBytes = kSapRecordBytesPerSite * (size_t)kNoAllocMaxSites;  // per-site SSOR records
+constexpr size_t kTableBytes = 64 * (size_t)kNoAllocMaxSites;                    // ll schedule, block tables
+constexpr size_t kScratchBytes = 4 * kSpinorBytes + kRecordBytes + kTableBytes;  // about 68.3 MB
 
 static __device__ __align__(256) unsigned char g_sap_scratch[kScratchBytes];
 
@@ -85,27 +86,18 @@ extern "C" int qcd_sap_precondition_noalloc(qcd_ctx *c, float *out, const float 
     SapPlan plan;
     if (sap_plan_host(c, p->block, p->subblock, plan) != QCD_OK)
         return fail(c, QCD_ERR_ARG, "SAP geometry: need L % block == 0, L/block even and >= 2, block % subblock == 0");
-    const size_t nints = plan.h_step_ptr.size() + plan.h_step_site.size() + plan.h_origin[0].size() +
-                         plan.h_origin[1].size();
-    if (nints > kTableInts) return fail(c, QCD_ERR_ARG, "SAP schedule tables exceed the fixed scratch");
+    if (sap_table_bytes(plan) > kTableBytes || sap_record_bytes(plan) > kRecordBytes)
+        return fail(c, QCD_ERR_ARG, "SAP schedule tables exceed the fixed scratch");
     unsigned char *base = nullptr;
     int rc = scratch_address(c, &base);
     if (rc) return rc;
-    // scratch layout: [v | x | r, y | tables]; every region is fully written before it is read
+    // scratch layout: [v | x | r, y | records | tables]; every region is fully written before it is read
     float4 *v = reinterpret_cast<float4 *>(base);
     float4 *x = reinterpret_cast<float4 *>(base + kSpinorBytes);
     float4 *work = reinterpret_cast<float4 *>(base + 2 * kSpinorBytes);
-    int *tab = reinterpret_cast<int *>(base + 4 * kSpinorBytes);
-    plan.d_step_ptr = tab;
-    plan.d_step_site = plan.d_step_ptr + plan.h_step_ptr.size();
-    plan.d_origin[0] = plan.d_step_site + plan.h_step_site.size();
-    plan.d_origin[1] = plan.d_origin[0] + plan.h_origin[0].size();
-    const std::vector<int> *src[4] = {&plan.h_step_ptr, &plan.h_step_site, &plan.h_origin[0], &plan.h_origin[1]};
-    int *dst[4] = {plan.d_step_ptr, plan.d_step_site, plan.d_origin[0], plan.d_origin[1]};
-    for (int k = 0; k < 4; k++)
-        if (!src[k]->empty())
-            QCD_CUDA(c, cudaMemcpyAsync(dst[k], src[k]->data(), sizeof(int) * src[k]->size(), cudaMemcpyHostToDevice,
-                                        c->stream));
+    float *rec = reinterpret_cast<float *>(base + 4 * kSpinorBytes);
+    if ((rc = sap_upload_tables(c, plan, base + 4 * kSpinorBytes + kRecordBytes))) return rc;
+    if ((rc = sap_build_records(c, plan, rec))) return rc;
     if ((rc = spinor32_to_internal(c, v, reinterpret_cast<const float2 *>(in), 1))) return rc;
     if ((rc = sap_apply_plan(c, plan, x, v, work, p->omega, p->nsweep, p->nsap))) return rc;
     if ((rc = spinor32_from_internal(c, reinterpret_cast<float2 *>(out), x, 1))) return rc;

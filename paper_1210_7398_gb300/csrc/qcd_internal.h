@@ -29,6 +29,11 @@ struct Lattice {
 
 // SAP geometry: block decomposition (Eq. (3)) plus the ll-order schedule of
 // the SSOR passes, grouped into steps whose sites are pairwise non-adjacent.
+// For the SSOR kernel each block is split along t into C slabs (one CTA each,
+// a thread-block cluster when C > 1) and each step into chunks of at most
+// nslot sites per CTA; the chunks form the kernel's timeline (forward pass,
+// then the reversed backward pass).  flags[p] (p < 2*nchunks) asks for a
+// cluster barrier before timeline step p of every sweep.
 struct SapPlan {
     int b[4] = {0, 0, 0, 0}, s[4] = {0, 0, 0, 0};
     int nb[4] = {0, 0, 0, 0};
@@ -36,10 +41,23 @@ struct SapPlan {
     int nsteps = 0;     // parallel steps per pass
     int max_step = 0;   // largest number of sites in one step
     int nblk[2] = {0, 0};
-    int *d_step_ptr = nullptr;   // [nsteps + 1]
-    int *d_step_site = nullptr;  // [vol] block-local lexicographic site index
-    int *d_origin[2] = {nullptr, nullptr};  // [nblk[c]][4] block origins per colour
     std::vector<int> h_step_ptr, h_step_site, h_origin[2];
+    int *d_origin[2] = {nullptr, nullptr};  // [nblk[c]][4] block origins per colour
+    int C = 1, slab_t = 0, slab_vol = 0;
+    int nchunks = 0, nslot = 0, nwarps = 0;
+    size_t smem_bytes = 0;
+    std::vector<int> h_chunk_ptr;   // [C][nchunks + 1], offsets into h_chunk_site
+    std::vector<int> h_chunk_site;  // block-local site indices, CTA-major
+    std::vector<unsigned char> h_flags;  // [2 * nchunks]
+    std::vector<int> h_site_off;    // [vol] global index offset of a block-local site from its block origin
+    std::vector<int> h_origin_site[2];  // [nblk[c]] global index of each block origin
+    int *d_chunk_ptr = nullptr;
+    int2 *d_chunk_site = nullptr;   // (block-local site, global offset from the block origin)
+    unsigned char *d_flags = nullptr;
+    int *d_site_off = nullptr;
+    int *d_origin_site[2] = {nullptr, nullptr};
+    float *d_rec = nullptr;         // per-site records (links, clover, neighbour codes), V x 912 bytes
+    long rec_version = -1;          // field version the records were built from
 };
 
 struct Profiler {
@@ -74,6 +92,8 @@ struct qcd_ctx {
 
     // SAP plan cache (one geometry at a time)
     qcd::SapPlan plan;
+    long field_version = 0;  // bumped whenever the links or the clover field change
+    int sap_min_ctas = 1;    // lower bound on the CTAs (cluster size) per SAP block
 
     // workspace, grown on demand
     std::vector<void *> allocations;
@@ -131,15 +151,25 @@ int dslash32(qcd_ctx *c, float4 *out, const float4 *in, int nrhs);
 
 // SAP (sap.cu)
 // host part of a plan (tables in h_*; device pointers left null); QCD_ERR_ARG on bad geometry
-int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &plan);
+int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &plan, int min_ctas = 1);
 // builds and uploads the plan of this geometry into c->plan (allocates its tables)
 int sap_prepare(qcd_ctx *c, const int b[4], const int s[4]);
+// drops the cached plan (it is rebuilt on next use)
+void sap_invalidate(qcd_ctx *c);
 // x = M_SAP v (FP32 internal layout, one right-hand side); work = 3 spinors
 int sap_apply(qcd_ctx *c, float4 *x, const float4 *v, float4 *work, double omega, int nsweep,
               int nsap);
-// the same with an explicit plan whose device tables are already in place
+// the same with an explicit plan whose device tables and records are already in place
 int sap_apply_plan(qcd_ctx *c, const SapPlan &plan, float4 *x, const float4 *v, float4 *work, double omega,
                    int nsweep, int nsap);
+// bytes of the device tables of a plan, and their upload into one region (no allocation)
+size_t sap_table_bytes(const SapPlan &plan);
+int sap_upload_tables(qcd_ctx *c, SapPlan &plan, void *region);
+// bytes of one per-site SSOR record (links, clover rows, neighbour codes), of all records of a
+// plan, and building them into rec (plan.d_rec is set to rec)
+constexpr size_t kSapRecordBytesPerSite = 1200;
+size_t sap_record_bytes(const SapPlan &plan);
+int sap_build_records(qcd_ctx *c, SapPlan &plan, float *rec);
 
 // BLAS (blas.cu) over complex vectors of n elements (double2 or float2)
 enum { RED_DOT = 0, RED_DOT_NORM = 1, RED_NORM = 2 };

@@ -7,12 +7,21 @@
 //   r_c' -= D_c'c y_c              (K4, hops that leave the block)
 // which equals Alg. 1 (y = K r, w = D y, x += y, r -= w) term by term.
 //
-// K3 runs one CTA per SAP block.  The ll order (key = lambda * N_sb + sigma,
-// lambda the lexicographic local position inside a sub-block, sigma the
-// lexicographic sub-block index) is cut into steps of consecutive sites that
-// are pairwise non-adjacent; the sites of one step are updated in parallel,
-// which gives exactly the sequential result, and steps are separated by
-// barriers (the paper's OpenMP barriers between dependent sites).
+// K3 runs one CTA per SAP block, or a cluster of C CTAs that split the block
+// into slabs along t when its spinor does not fit one CTA's shared memory.
+// The ll order (key = lambda * N_sb + sigma, lambda the lexicographic local
+// position inside a sub-block, sigma the lexicographic sub-block index) is cut
+// into steps of consecutive sites that are pairwise non-adjacent; the sites of
+// one step are updated in parallel, which gives exactly the sequential result,
+// and steps are separated by barriers (the paper's OpenMP barriers between
+// dependent sites).  Each site update is done by one warp: lane (d, c) takes
+// hop direction d = 2 mu + (backward) and colour row c, the 8 directions are
+// summed with butterfly shuffles, and 12 lanes apply the chiral clover blocks.
+// The block's spinor y lives in shared memory (remote slabs are read through
+// distributed shared memory); links, clover and source of the sites of the
+// next two steps are staged with cp.async while the current step computes.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cstring>
 
@@ -60,59 +69,303 @@ __device__ __forceinline__ void masked_hops(const float4 *src, const float2 *__r
 #undef QCD_HOP
 }
 
-// K3: y = A_BB f on every block of one colour (blockIdx.x enumerates them)
-__global__ void __launch_bounds__(256) k_ssor(float4 *y, const float4 *__restrict__ f, const float2 *__restrict__ U,
-                                              const float4 *__restrict__ F, float kappa, float omega, int nsweep,
-                                              Geo g, BlockGeo bg, const int *__restrict__ step_ptr,
-                                              const int *__restrict__ step_site, int nsteps,
-                                              const int *__restrict__ origins) {
-    const int o[4] = {origins[4 * blockIdx.x], origins[4 * blockIdx.x + 1], origins[4 * blockIdx.x + 2],
-                      origins[4 * blockIdx.x + 3]};
-    auto site_of = [&](int loc, int yl[4], int x[4]) -> long {
-        int r = loc;
-        yl[0] = r % bg.b[0]; r /= bg.b[0];
-        yl[1] = r % bg.b[1]; r /= bg.b[1];
-        yl[2] = r % bg.b[2]; r /= bg.b[2];
-        yl[3] = r;
-        for (int m = 0; m < 4; m++) x[m] = o[m] + yl[m];
-        return x[0] + (long)g.L[0] * (x[1] + (long)g.L[1] * (x[2] + (long)g.L[2] * x[3]));
-    };
-    const float2 zero[12] = {};
-    for (int i = threadIdx.x; i < bg.vol; i += blockDim.x) {
-        int yl[4], x[4];
-        store_spinor(y, g.V, site_of(i, yl, x), zero);
-    }
-    __syncthreads();
-    for (int sw = 0; sw < nsweep; sw++) {
-        for (int pass = 0; pass < 2; pass++) {
-            for (int k = 0; k < nsteps; k++) {
-                const int st = pass == 0 ? k : nsteps - 1 - k;
-                for (int j = step_ptr[st] + threadIdx.x; j < step_ptr[st + 1]; j += blockDim.x) {
-                    int yl[4], x[4];
-                    const long n = site_of(step_site[j], yl, x);
-                    float2 acc[12];
-#pragma unroll
-                    for (int q = 0; q < 12; q++) acc[q] = make_float2(0.f, 0.f);
-                    masked_hops<true, true>(y, U, g, n, x, yl, bg, acc);
-                    float fc[72];
-                    load_clover(F, g.V, n, fc);
-                    float2 fa[12], yo[12], fv[12];
-                    clover_mul<float, float2>(fc, acc, fa);
-                    load_spinor_rw(y, g.V, n, yo);
-                    load_spinor(f, g.V, n, fv);
-#pragma unroll
-                    for (int q = 0; q < 12; q++) {
-                        float2 t;
-                        t.x = fmaf(kappa, fa[q].x, fv[q].x);
-                        t.y = fmaf(kappa, fa[q].y, fv[q].y);
-                        yo[q].x = fmaf(omega, t.x - yo[q].x, yo[q].x);
-                        yo[q].y = fmaf(omega, t.y - yo[q].y, yo[q].y);
-                    }
-                    store_spinor(y, g.V, n, yo);
-                }
-                __syncthreads();
-            }
+
+namespace cg = cooperative_groups;
+
+constexpr int kRing = 3;           // staging depth (timeline steps in flight)
+constexpr int kRecFloats = 300;    // per-site record: 8 colour matrices, clover rows, metadata
+constexpr int kRecChunks = kRecFloats / 4;
+constexpr int kStageFloats = kRecFloats + 24;  // record + the site's source spinor
+constexpr int kStageChunks = kStageFloats / 4;
+static_assert(kRecFloats * sizeof(float) == kSapRecordBytesPerSite, "record size");
+constexpr int kMaxSlots = 16;      // sites per CTA per timeline step
+constexpr size_t kSmemLimit = 200 * 1024;
+// record layout (floats): [0, 144) W_d for d = 2 mu + (backward): U_mu(n) forward, U_mu(n - mu)^dag
+// backward, 3x3 row-major complex (zero when the hop leaves the block); [144, 288) the two chiral
+// blocks of F/2 as full 6x6 complex rows; ints at [288] global site, [289] float offset of the
+// site's spinor in its slab, [290, 298) neighbour code per direction: (slab << 24) | float offset
+// of the neighbour's spinor in that slab, or -1 when the hop leaves the block.
+constexpr int kRecClover = 144, kRecSite = 288, kRecYoff = 289, kRecNbr = 290;
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Builds the per-site records of every block (blocks of colour 0 first).
+__global__ void k_sap_records(float *__restrict__ rec, const float2 *__restrict__ U, const float4 *__restrict__ F,
+                              Geo g, BlockGeo bg, int slab_t, int slab_vol, const int *__restrict__ org0,
+                              const int *__restrict__ org1, int nblk0, long total) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int gb = (int)(i / bg.vol), yl = (int)(i % bg.vol);
+    const int *o = gb < nblk0 ? org0 + 4 * gb : org1 + 4 * (gb - nblk0);
+    int y[4], r = yl;
+    for (int m = 0; m < 4; m++) { y[m] = r % bg.b[m]; r /= bg.b[m]; }
+    const long gs[4] = {1, g.L[0], (long)g.L[0] * g.L[1], (long)g.L[0] * g.L[1] * g.L[2]};
+    long n = 0;
+    for (int m = 0; m < 4; m++) n += gs[m] * (o[m] + y[m]);
+    float *R = rec + i * kRecFloats;
+    int *Ri = reinterpret_cast<int *>(R);
+    const int bs[4] = {1, bg.b[0], bg.b[0] * bg.b[1], bg.b[0] * bg.b[1] * bg.b[2]};
+    for (int d = 0; d < 8; d++) {
+        const int mu = d >> 1;
+        const bool fwd = (d & 1) == 0;
+        const int ym = y[mu] + (fwd ? 1 : -1);
+        float *W = R + d * 18;
+        if (ym < 0 || ym >= bg.b[mu]) {
+            for (int k = 0; k < 18; k++) W[k] = 0.f;
+            Ri[kRecNbr + d] = -1;
+            continue;
         }
+        const long src = fwd ? n : n - gs[mu];
+        for (int a = 0; a < 3; a++)
+            for (int bb = 0; bb < 3; bb++) {
+                if (fwd) {
+                    const float2 u = U[(long)(mu * 9 + a * 3 + bb) * g.V + src];
+                    W[(a * 3 + bb) * 2] = u.x;
+                    W[(a * 3 + bb) * 2 + 1] = u.y;
+                } else {
+                    const float2 u = U[(long)(mu * 9 + bb * 3 + a) * g.V + src];
+                    W[(a * 3 + bb) * 2] = u.x;
+                    W[(a * 3 + bb) * 2 + 1] = -u.y;
+                }
+            }
+        const int nb = yl + (fwd ? bs[mu] : -bs[mu]);
+        const int sl = (mu == 3 ? ym : y[3]) / slab_t;
+        Ri[kRecNbr + d] = (sl << 24) | ((nb - sl * slab_vol) * 24);
+    }
+    float fp[72];
+    for (int k = 0; k < 18; k++) {
+        const float4 v = F[(long)k * g.V + n];
+        fp[4 * k] = v.x; fp[4 * k + 1] = v.y; fp[4 * k + 2] = v.z; fp[4 * k + 3] = v.w;
+    }
+    // unpack each Hermitian block (6 real diagonal, 15 complex below the diagonal) into full rows
+    for (int ch = 0; ch < 2; ch++)
+        for (int i = 0; i < 6; i++)
+            for (int j = 0; j < 6; j++) {
+                float re, im;
+                if (i == j) { re = fp[36 * ch + i]; im = 0.f; }
+                else if (j < i) { const int q = 36 * ch + 6 + 2 * (i * (i - 1) / 2 + j); re = fp[q]; im = fp[q + 1]; }
+                else { const int q = 36 * ch + 6 + 2 * (j * (j - 1) / 2 + i); re = fp[q]; im = -fp[q + 1]; }
+                R[kRecClover + 72 * ch + 12 * i + 2 * j] = re;
+                R[kRecClover + 72 * ch + 12 * i + 2 * j + 1] = im;
+            }
+    const int sl = y[3] / slab_t;
+    Ri[kRecSite] = (int)n;
+    Ri[kRecYoff] = (yl - sl * slab_vol) * 24;
+    Ri[kRecNbr + 8] = 0;
+    Ri[kRecNbr + 9] = 0;
+}
+
+struct SsorArgs {
+    float4 *y;                 // out: the block solutions, plane layout
+    const float4 *f;           // source (the SAP residual), plane layout
+    const float4 *rec;         // per-site records of this colour's blocks
+    float kappa, omega;
+    int nsweep;
+    long V;
+    int vol, C, slab_vol, nchunks, nslot;
+    const int *chunk_ptr;      // [C][nchunks + 1]
+    const int2 *chunk_site;    // (block-local site, global offset from the block origin)
+    const int *site_off;       // [vol] global offset of a block-local site from the block origin
+    const unsigned char *flags;  // [2 * nchunks] cluster barrier before a timeline step
+    const int *origin_site;    // [blocks of this colour] global index of the block origin
+};
+
+// K3: y = A_BB f on every block of one colour; blockIdx.x / C enumerates blocks
+__global__ void __launch_bounds__(512) k_ssor_warp(SsorArgs a) {
+    extern __shared__ __align__(16) float sm[];
+    const int rank = a.C > 1 ? (int)cg::this_cluster().block_rank() : 0;
+    const int nch = a.nchunks;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int *cptr_g = a.chunk_ptr + rank * (nch + 1);
+    const int tab0 = cptr_g[0], ntab = cptr_g[nch] - tab0;
+    // shared memory: [y slab | staging ring | chunk pointers | chunk sites | per-warp scratch]
+    float *ys = sm;                                                    // [slab_vol][24]
+    float *ring = ys + (size_t)a.slab_vol * 24;                        // [kRing][nslot][kStageFloats]
+    int *cptr = reinterpret_cast<int *>(ring + (size_t)kRing * a.nslot * kStageFloats);  // [nch + 1]
+    int2 *csite = reinterpret_cast<int2 *>(cptr + ((nch + 1 + 3) & ~3));                  // [ntab]
+    float2 *scr = reinterpret_cast<float2 *>(csite + ((ntab + 1) & ~1)) + warp * 12;      // [nw][12]
+    const int blk = blockIdx.x / a.C;
+    const long n0 = a.origin_site[blk];
+    const float4 *rec = a.rec + (size_t)blk * a.vol * kRecChunks;
+
+    // ---- lane constants of the hop phase: direction d = 2 mu + (backward), colour row c ----
+    const int d = lane >> 2, c = lane & 3;
+    // half-spinor h0 = psi[pa] + za psi[pb], h1 = psi[pc] + zc psi[pd] (spin rows) and the
+    // reconstruction acc[s] += al[s] w0 + be[s] w1, for (1 -+ gamma_mu) in the Dirac representation
+    int pa = 0, pb = 3, pc = 1, pd = 2;
+    float2 za = make_float2(0.f, 1.f), zc = make_float2(0.f, 1.f);
+    float2 al[4] = {make_float2(1.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    float2 be[4] = {make_float2(0.f, 0.f), make_float2(1.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    switch (d) {
+        case 0: al[3] = make_float2(0.f, -1.f); be[2] = make_float2(0.f, -1.f); break;
+        case 1: za = zc = make_float2(0.f, -1.f); al[3] = make_float2(0.f, 1.f); be[2] = make_float2(0.f, 1.f); break;
+        case 2: za = make_float2(1.f, 0.f); zc = make_float2(-1.f, 0.f); al[3] = make_float2(1.f, 0.f);
+                be[2] = make_float2(-1.f, 0.f); break;
+        case 3: za = make_float2(-1.f, 0.f); zc = make_float2(1.f, 0.f); al[3] = make_float2(-1.f, 0.f);
+                be[2] = make_float2(1.f, 0.f); break;
+        case 4: pb = 2; pd = 3; za = make_float2(0.f, 1.f); zc = make_float2(0.f, -1.f);
+                al[2] = make_float2(0.f, -1.f); be[3] = make_float2(0.f, 1.f); break;
+        case 5: pb = 2; pd = 3; za = make_float2(0.f, -1.f); zc = make_float2(0.f, 1.f);
+                al[2] = make_float2(0.f, 1.f); be[3] = make_float2(0.f, -1.f); break;
+        case 6: pa = pb = 2; pc = pd = 3; za = zc = make_float2(1.f, 0.f);
+                al[0] = make_float2(0.f, 0.f); be[1] = make_float2(0.f, 0.f);
+                al[2] = make_float2(1.f, 0.f); be[3] = make_float2(1.f, 0.f); break;
+        default: pa = pb = 0; pc = pd = 1; za = zc = make_float2(1.f, 0.f); break;
+    }
+    // ---- lane constants of the clover phase: lane (s, c), s = lane >> 3, holds spin s ----
+    const int so = lane >> 3;
+    const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0;
+    const int fch = so >> 1, fk = (so & 1) * 3 + (c < 3 ? c : 0);
+    const int frow = kRecClover + 72 * fch + 12 * fk;  // this lane's row of the chiral block
+    const bool owner = c < 3 && (lane & 4) == 0;      // one lane per (spin, colour) stores
+
+    // ---- set-up: zero this CTA's slab of y, copy its chunk tables ----
+    float4 *ys4 = reinterpret_cast<float4 *>(ys);
+    for (int i = threadIdx.x; i < a.slab_vol * 6; i += blockDim.x) ys4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = threadIdx.x; i <= nch; i += blockDim.x) cptr[i] = cptr_g[i] - tab0;
+    for (int i = threadIdx.x; i < ntab; i += blockDim.x) csite[i] = a.chunk_site[tab0 + i];
+    __syncthreads();
+
+    const int T = a.nsweep * 2 * nch;
+    int kiss = 0, tiss = 0;  // sweep position and ring slot of the next staging
+    // stage the records and sources of the sites of the next timeline step
+    auto issue = [&](int t) {
+        if (t < T) {
+            const int ch = kiss < nch ? kiss : 2 * nch - 1 - kiss;
+            const int base = cptr[ch], cnt = cptr[ch + 1] - base;
+            float *stage = ring + (size_t)tiss * a.nslot * kStageFloats;
+            for (int slot = warp; slot < cnt; slot += nw) {
+                const int2 e = csite[base + slot];
+                float *dst = stage + slot * kStageFloats;
+                const float4 *src = rec + (size_t)e.x * kRecChunks;
+#pragma unroll
+                for (int q = lane; q < kStageChunks; q += 32) {
+                    if (q < kRecChunks) cp_async16(dst + 4 * q, src + q);
+                    else cp_async16(dst + 4 * q, a.f + (long)(q - kRecChunks) * a.V + n0 + e.y);
+                }
+            }
+            if (++kiss == 2 * nch) kiss = 0;
+            if (++tiss == kRing) tiss = 0;
+        }
+        cp_async_commit();
+    };
+    // one SSOR site update by the whole warp
+    auto update = [&](const float *sd) {
+        const int *sdi = reinterpret_cast<const int *>(sd);
+        float2 acc[4];
+#pragma unroll
+        for (int s = 0; s < 4; s++) acc[s] = make_float2(0.f, 0.f);
+        const int code = sdi[kRecNbr + d];
+        if (c < 3 && code >= 0) {
+            const int sl = code >> 24;
+            const float *slab = (a.C > 1 && sl != rank) ? cg::this_cluster().map_shared_rank(ys, sl) : ys;
+            const float *pn = slab + (code & 0xffffff);
+            const float *W = sd + d * 18 + c * 6;
+            float2 w0 = make_float2(0.f, 0.f), w1 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int cc = 0; cc < 3; cc++) {
+                const float2 qa = *reinterpret_cast<const float2 *>(pn + pa * 6 + cc * 2);
+                const float2 qb = *reinterpret_cast<const float2 *>(pn + pb * 6 + cc * 2);
+                const float2 qc = *reinterpret_cast<const float2 *>(pn + pc * 6 + cc * 2);
+                const float2 qd = *reinterpret_cast<const float2 *>(pn + pd * 6 + cc * 2);
+                const float2 u = *reinterpret_cast<const float2 *>(W + cc * 2);
+                w0 = cfma(u, cfma(za, qb, qa), w0);
+                w1 = cfma(u, cfma(zc, qd, qc), w1);
+            }
+#pragma unroll
+            for (int s = 0; s < 4; s++) acc[s] = cfma(be[s], w1, cmul(al[s], w0));
+        }
+        // reduce-scatter over the 8 directions: lane bit 4 picks spins {0,1} / {2,3}, bit 3 one of them
+        float2 k0, k1;
+        {
+            const float2 s0 = b4 ? acc[0] : acc[2], s1 = b4 ? acc[1] : acc[3];
+            k0 = b4 ? acc[2] : acc[0];
+            k1 = b4 ? acc[3] : acc[1];
+            k0.x += __shfl_xor_sync(0xffffffffu, s0.x, 16);
+            k0.y += __shfl_xor_sync(0xffffffffu, s0.y, 16);
+            k1.x += __shfl_xor_sync(0xffffffffu, s1.x, 16);
+            k1.y += __shfl_xor_sync(0xffffffffu, s1.y, 16);
+        }
+        float2 A = b3 ? k1 : k0;
+        {
+            const float2 sn = b3 ? k0 : k1;
+            A.x += __shfl_xor_sync(0xffffffffu, sn.x, 8);
+            A.y += __shfl_xor_sync(0xffffffffu, sn.y, 8);
+        }
+        A.x += __shfl_xor_sync(0xffffffffu, A.x, 4);
+        A.y += __shfl_xor_sync(0xffffffffu, A.y, 4);
+        // lane (s, c) holds spin s, colour c of the hop sum; its chiral component (chirality s >> 1)
+        float2 P;
+        P.x = __shfl_xor_sync(0xffffffffu, A.x, 16);
+        P.y = __shfl_xor_sync(0xffffffffu, A.y, 16);
+        const float2 cv = so < 2 ? csub(A, P) : cadd(P, A);
+        if (owner) scr[fch * 6 + (so & 1) * 3 + c] = cv;
+        __syncwarp();
+        // row fk of the chiral clover block fch against the block's 6 components
+        const float4 *cvv = reinterpret_cast<const float4 *>(scr + fch * 6);
+        const float4 *fr = reinterpret_cast<const float4 *>(sd + frow);
+        float2 eta = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            const float4 x = cvv[q], f = fr[q];
+            eta = cfma(make_float2(f.x, f.y), make_float2(x.x, x.y), eta);
+            eta = cfma(make_float2(f.z, f.w), make_float2(x.z, x.w), eta);
+        }
+        __syncwarp();  // the scratch may be rewritten by this warp's next site
+        float2 Q;
+        Q.x = __shfl_xor_sync(0xffffffffu, eta.x, 16);
+        Q.y = __shfl_xor_sync(0xffffffffu, eta.y, 16);
+        // upper spins (s < 2): eta0 + eta1; lower: eta1 - eta0
+        const float2 out = so < 2 ? cadd(eta, Q) : csub(eta, Q);
+        if (owner) {
+            float *yp = ys + sdi[kRecYoff] + (so * 3 + c) * 2;
+            const float2 fv = *reinterpret_cast<const float2 *>(sd + kRecFloats + (so * 3 + c) * 2);
+            const float2 yo = *reinterpret_cast<float2 *>(yp);
+            float2 t;
+            t.x = fmaf(a.kappa, out.x, fv.x);
+            t.y = fmaf(a.kappa, out.y, fv.y);
+            float2 yn;
+            yn.x = fmaf(a.omega, t.x - yo.x, yo.x);
+            yn.y = fmaf(a.omega, t.y - yo.y, yo.y);
+            *reinterpret_cast<float2 *>(yp) = yn;
+        }
+    };
+
+    issue(0);
+    issue(1);
+    if (a.C > 1) cg::this_cluster().sync();
+    else __syncthreads();
+    int k = 0, tring = 0;  // sweep position and ring slot of the current step
+    for (int t = 0; t < T; t++) {
+        issue(t + 2);
+        cp_async_wait<2>();
+        __syncwarp();
+        const int ch = k < nch ? k : 2 * nch - 1 - k;
+        const int base = cptr[ch], cnt = cptr[ch + 1] - base;
+        const float *stage = ring + (size_t)tring * a.nslot * kStageFloats;
+        for (int slot = warp; slot < cnt; slot += nw) update(stage + slot * kStageFloats);
+        if (++k == 2 * nch) k = 0;
+        if (++tring == kRing) tring = 0;
+        if (t + 1 < T) {
+            if (a.C > 1 && a.flags[k]) cg::this_cluster().sync();
+            else __syncthreads();
+        }
+    }
+    cp_async_wait<0>();
+    // no CTA may leave (or overwrite) its slab while a peer can still read it
+    if (a.C > 1) cg::this_cluster().sync();
+    else __syncthreads();
+    for (int i = threadIdx.x; i < a.slab_vol * 6; i += blockDim.x) {
+        const int sl = i / 6, q = i - 6 * sl;
+        const long n = n0 + a.site_off[rank * a.slab_vol + sl];
+        a.y[(long)q * a.V + n] = ys4[i];
     }
 }
 
@@ -188,16 +441,129 @@ bool geometry_ok(const qcd_ctx *c, const int b[4], const int s[4]) {
 
 void free_plan(qcd_ctx *c) {
     SapPlan &p = c->plan;
-    dev_free(c, p.d_step_ptr);
-    dev_free(c, p.d_step_site);
-    dev_free(c, p.d_origin[0]);
-    dev_free(c, p.d_origin[1]);
+    dev_free(c, p.d_origin[0]);  // one region holds every table
+    dev_free(c, p.d_rec);
     p = SapPlan();
+}
+
+// Split the block into C slabs along t and every ll step into chunks of at
+// most kMaxSlots sites per slab.  Returns false if the shared memory of a CTA
+// (its slab of y plus the staging ring) would exceed kSmemLimit.
+bool make_chunks(SapPlan &np, int C) {
+    if (np.b[3] % C) return false;
+    np.C = C;
+    np.slab_t = np.b[3] / C;
+    np.slab_vol = np.vol / C;
+    std::vector<std::vector<int>> per(C);
+    std::vector<std::vector<int>> lists(C);  // chunk lists per CTA
+    std::vector<std::vector<int>> ptr(C, std::vector<int>(1, 0));
+    int nchunks = 0, nslot = 1;
+    for (int st = 0; st < np.nsteps; st++) {
+        for (auto &v : per) v.clear();
+        for (int k = np.h_step_ptr[st]; k < np.h_step_ptr[st + 1]; k++) {
+            const int yl = np.h_step_site[k];
+            const int yt = yl / (np.b[0] * np.b[1] * np.b[2]);
+            per[yt / np.slab_t].push_back(yl);
+        }
+        size_t most = 1;
+        for (auto &v : per) most = std::max(most, v.size());
+        const int nc = (int)((most + kMaxSlots - 1) / kMaxSlots);
+        for (int j = 0; j < nc; j++) {
+            for (int r = 0; r < C; r++) {
+                const int lo = j * kMaxSlots, hi = std::min((int)per[r].size(), lo + kMaxSlots);
+                for (int q = lo; q < hi; q++) lists[r].push_back(per[r][q]);
+                nslot = std::max(nslot, hi - lo);
+                ptr[r].push_back((int)lists[r].size());
+            }
+            nchunks++;
+        }
+    }
+    np.nchunks = nchunks;
+    np.nslot = nslot;
+    np.nwarps = nslot;
+    size_t most_sites = 0;
+    for (int r = 0; r < C; r++) most_sites = std::max(most_sites, lists[r].size());
+    np.smem_bytes = (size_t)np.slab_vol * 96 + (size_t)kRing * nslot * kStageFloats * sizeof(float) +
+                    sizeof(int) * ((nchunks + 1 + 3) & ~3) + sizeof(int2) * ((most_sites + 1) & ~1) +
+                    sizeof(float2) * 12 * nslot;
+    if (np.smem_bytes > kSmemLimit) return false;
+    np.h_chunk_ptr.clear();
+    np.h_chunk_site.clear();
+    for (int r = 0; r < C; r++) {
+        const int off = (int)np.h_chunk_site.size();
+        for (int v : ptr[r]) np.h_chunk_ptr.push_back(off + v);
+        np.h_chunk_site.insert(np.h_chunk_site.end(), lists[r].begin(), lists[r].end());
+    }
+    return true;
+}
+
+// Cluster barriers: a site reads its in-block neighbours in other slabs
+// through distributed shared memory.  Each such read must come after the
+// neighbour's latest earlier write (barrier in (t_w, t]) and before its next
+// write (barrier in (t, t_n]).  The intervals are taken over three sweeps and
+// stabbed greedily; the chosen positions, folded modulo one sweep, give a
+// periodic pattern that stabs every interval of any number of sweeps (no
+// interval spans a whole sweep, because every site is written twice per sweep).
+void make_flags(SapPlan &np) {
+    const int P = 2 * np.nchunks;
+    np.h_flags.assign(P, 0);
+    if (np.C == 1) return;
+    std::vector<int> chunk_of(np.vol, -1);
+    for (int r = 0; r < np.C; r++)
+        for (int ch = 0; ch < np.nchunks; ch++)
+            for (int k = np.h_chunk_ptr[r * (np.nchunks + 1) + ch]; k < np.h_chunk_ptr[r * (np.nchunks + 1) + ch + 1]; k++)
+                chunk_of[np.h_chunk_site[k]] = ch;
+    auto writes = [&](int yl, std::vector<int> &w) {
+        w.clear();
+        const int ch = chunk_of[yl];
+        for (int sw = 0; sw < 3; sw++) {
+            w.push_back(sw * P + ch);
+            w.push_back(sw * P + P - 1 - ch);
+        }
+        std::sort(w.begin(), w.end());
+    };
+    std::vector<std::pair<int, int>> iv;  // (lo, hi]: need a barrier p with lo < p <= hi
+    std::vector<int> wi, wj;
+    const int plane = np.b[0] * np.b[1] * np.b[2];
+    for (int yl = 0; yl < np.vol; yl++) {
+        int y[4], r = yl;
+        for (int m = 0; m < 4; m++) { y[m] = r % np.b[m]; r /= np.b[m]; }
+        int stride = 1;
+        for (int m = 0; m < 4; m++) {
+            for (int dir = -1; dir <= 1; dir += 2) {
+                const int ym = y[m] + dir;
+                if (ym < 0 || ym >= np.b[m]) continue;
+                const int nb = yl + dir * stride;
+                if ((yl / plane) / np.slab_t == (nb / plane) / np.slab_t) continue;
+                writes(yl, wi);
+                writes(nb, wj);
+                for (int t : wi) {
+                    int prev = -1, next = -1;
+                    for (int w : wj) {
+                        if (w < t) prev = w;
+                        if (w > t && next < 0) next = w;
+                    }
+                    iv.push_back({prev, t});            // read after the latest write (prev = -1: zero fill)
+                    if (next >= 0) iv.push_back({t, next});  // read before the next write
+                }
+            }
+            stride *= np.b[m];
+        }
+    }
+    std::sort(iv.begin(), iv.end(), [](const std::pair<int, int> &u, const std::pair<int, int> &v) {
+        return u.second < v.second;
+    });
+    int last = 0;  // the barrier after the zero fill, at p = 0
+    for (auto &v : iv) {
+        if (last > v.first) continue;  // already stabbed (last <= v.second by the sort order)
+        last = v.second;
+        if (last > 0) np.h_flags[last % P] = 1;  // p = 0 is the barrier after the zero fill
+    }
 }
 
 }  // namespace
 
-int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &np) {
+int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &np, int min_ctas) {
     if (!geometry_ok(c, b, s)) return QCD_ERR_ARG;
     np = SapPlan();
     std::memcpy(np.b, b, sizeof(np.b));
@@ -256,29 +622,120 @@ int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &np)
                     const int col = (B0 + B1 + B2 + B3) & 1;
                     np.h_origin[col].insert(np.h_origin[col].end(), {B0 * b[0], B1 * b[1], B2 * b[2], B3 * b[3]});
                 }
-    for (int col = 0; col < 2; col++) np.nblk[col] = (int)np.h_origin[col].size() / 4;
+    for (int col = 0; col < 2; col++) {
+        np.nblk[col] = (int)np.h_origin[col].size() / 4;
+        for (int k = 0; k < np.nblk[col]; k++) {
+            const int *o = &np.h_origin[col][4 * k];
+            np.h_origin_site[col].push_back(o[0] + c->lat.L[0] * (o[1] + c->lat.L[1] * (o[2] + c->lat.L[2] * o[3])));
+        }
+    }
+    np.h_site_off.resize(np.vol);
+    for (int yl = 0; yl < np.vol; yl++) {
+        int y[4], r = yl;
+        for (int m = 0; m < 4; m++) { y[m] = r % b[m]; r /= b[m]; }
+        np.h_site_off[yl] = y[0] + c->lat.L[0] * (y[1] + c->lat.L[1] * (y[2] + c->lat.L[2] * y[3]));
+    }
+    // slabs: the fewest CTAs per block whose shared memory fits
+    // slabs: the fewest CTAs per block (a divisor of b_t, at most 8, at least the requested
+    // minimum) whose shared memory fits
+    bool ok = false;
+    for (int C = std::max(1, min_ctas); C <= 8 && !ok; C++)
+        if (b[3] % C == 0) ok = make_chunks(np, C);
+    if (!ok) return QCD_ERR_ARG;
+    make_flags(np);
     return QCD_OK;
 }
+
+size_t sap_table_bytes(const SapPlan &p) {
+    auto up16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    return up16(sizeof(int) * p.h_origin[0].size()) + up16(sizeof(int) * p.h_origin[1].size()) +
+           up16(sizeof(int) * p.h_origin_site[0].size()) + up16(sizeof(int) * p.h_origin_site[1].size()) +
+           up16(sizeof(int) * p.h_chunk_ptr.size()) + up16(sizeof(int2) * p.h_chunk_site.size()) +
+           up16(sizeof(int) * p.h_site_off.size()) + up16(p.h_flags.size());
+}
+
+// Copies every table of the plan into one device region (sap_table_bytes long) on the
+// context stream and points the plan's device pointers into it.
+int sap_upload_tables(qcd_ctx *c, SapPlan &p, void *region) {
+    auto up16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    char *at = static_cast<char *>(region);
+    auto put = [&](const void *src, size_t bytes) -> void * {
+        void *dst = at;
+        if (bytes) {
+            cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream);
+            if (e != cudaSuccess) return nullptr;
+        }
+        at += up16(bytes);
+        return dst;
+    };
+    std::vector<int2> cs(p.h_chunk_site.size());
+    for (size_t k = 0; k < cs.size(); k++) cs[k] = make_int2(p.h_chunk_site[k], p.h_site_off[p.h_chunk_site[k]]);
+    p.d_origin[0] = (int *)put(p.h_origin[0].data(), sizeof(int) * p.h_origin[0].size());
+    p.d_origin[1] = (int *)put(p.h_origin[1].data(), sizeof(int) * p.h_origin[1].size());
+    p.d_origin_site[0] = (int *)put(p.h_origin_site[0].data(), sizeof(int) * p.h_origin_site[0].size());
+    p.d_origin_site[1] = (int *)put(p.h_origin_site[1].data(), sizeof(int) * p.h_origin_site[1].size());
+    p.d_chunk_ptr = (int *)put(p.h_chunk_ptr.data(), sizeof(int) * p.h_chunk_ptr.size());
+    p.d_chunk_site = (int2 *)put(cs.data(), sizeof(int2) * cs.size());
+    p.d_site_off = (int *)put(p.h_site_off.data(), sizeof(int) * p.h_site_off.size());
+    p.d_flags = (unsigned char *)put(p.h_flags.data(), p.h_flags.size());
+    if (!p.d_origin[0] || !p.d_origin[1] || !p.d_origin_site[0] || !p.d_origin_site[1] || !p.d_chunk_ptr ||
+        !p.d_chunk_site || !p.d_site_off || !p.d_flags)
+        return cuda_fail(c, cudaGetLastError(), "cudaMemcpyAsync(SAP tables)");
+    // the host vectors may be released only once the copies have consumed them
+    QCD_CUDA(c, cudaStreamSynchronize(c->stream));
+    return QCD_OK;
+}
+
+size_t sap_record_bytes(const SapPlan &p) { return (size_t)(p.nblk[0] + p.nblk[1]) * p.vol * kRecFloats * sizeof(float); }
+
+int sap_build_records(qcd_ctx *c, SapPlan &p, float *rec) {
+    Geo g;
+    for (int m = 0; m < 4; m++) g.L[m] = c->lat.L[m];
+    g.V = c->lat.V;
+    g.bc_t = c->bc_t;
+    BlockGeo bg;
+    for (int m = 0; m < 4; m++) bg.b[m] = p.b[m];
+    bg.vol = p.vol;
+    const long total = (long)(p.nblk[0] + p.nblk[1]) * p.vol;
+    cudaEvent_t ev;
+    prof_begin(c, QCD_K_OTHER, &ev);
+    k_sap_records<<<(unsigned)((total + 127) / 128), 128, 0, c->stream>>>(
+        rec, c->U32, c->F32, g, bg, p.slab_t, p.slab_vol, p.d_origin[0], p.d_origin[1], p.nblk[0], total);
+    int rc = prof_end(c, QCD_K_OTHER, ev);
+    if (rc) return rc;
+    p.d_rec = rec;
+    p.rec_version = c->field_version;
+    return QCD_OK;
+}
+
+void sap_invalidate(qcd_ctx *c) { free_plan(c); }
 
 int sap_prepare(qcd_ctx *c, const int b[4], const int s[4]) {
     if (!geometry_ok(c, b, s))
         return fail(c, QCD_ERR_ARG, "SAP geometry: need L % block == 0, L/block even and >= 2, block % subblock == 0");
     SapPlan &p = c->plan;
-    if (p.vol && std::equal(b, b + 4, p.b) && std::equal(s, s + 4, p.s)) return QCD_OK;
-    free_plan(c);
-    SapPlan np;
-    sap_plan_host(c, b, s, np);
-    int rc;
-    if ((rc = dev_alloc(c, (void **)&np.d_step_ptr, sizeof(int) * np.h_step_ptr.size()))) return rc;
-    if ((rc = dev_alloc(c, (void **)&np.d_step_site, sizeof(int) * np.vol))) return rc;
-    for (int col = 0; col < 2; col++) {
-        if ((rc = dev_alloc(c, (void **)&np.d_origin[col], sizeof(int) * np.h_origin[col].size()))) return rc;
-        QCD_CUDA(c, cudaMemcpy(np.d_origin[col], np.h_origin[col].data(), sizeof(int) * np.h_origin[col].size(),
-                               cudaMemcpyHostToDevice));
+    if (!(p.vol && std::equal(b, b + 4, p.b) && std::equal(s, s + 4, p.s))) {
+        free_plan(c);
+        SapPlan np;
+        if (sap_plan_host(c, b, s, np, c->sap_min_ctas) != QCD_OK)
+            return fail(c, QCD_ERR_ARG, "SAP block too large for the shared memory of a cluster of 8 CTAs");
+        void *region = nullptr;
+        int rc = dev_alloc(c, &region, sap_table_bytes(np));
+        if (rc) return rc;
+        if ((rc = sap_upload_tables(c, np, region))) {
+            dev_free(c, region);
+            return rc;
+        }
+        float *rec = nullptr;
+        if ((rc = dev_alloc(c, (void **)&rec, sap_record_bytes(np)))) {
+            dev_free(c, region);
+            return rc;
+        }
+        np.d_rec = rec;
+        np.rec_version = -1;
+        c->plan = np;
     }
-    QCD_CUDA(c, cudaMemcpy(np.d_step_ptr, np.h_step_ptr.data(), sizeof(int) * np.h_step_ptr.size(), cudaMemcpyHostToDevice));
-    QCD_CUDA(c, cudaMemcpy(np.d_step_site, np.h_step_site.data(), sizeof(int) * np.vol, cudaMemcpyHostToDevice));
-    c->plan = np;
+    if (c->plan.rec_version != c->field_version) return sap_build_records(c, c->plan, c->plan.d_rec);
     return QCD_OK;
 }
 
@@ -297,17 +754,50 @@ int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
     BlockGeo bg;
     for (int m = 0; m < 4; m++) bg.b[m] = p.b[m];
     bg.vol = p.vol;
+    static bool attr_done = false;
+    if (!attr_done) {
+        QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+        attr_done = true;
+    }
+    SsorArgs a;
+    a.y = y;
+    a.f = r;
+    a.kappa = (float)c->kappa;
+    a.omega = (float)omega;
+    a.nsweep = nsweep;
+    a.V = V;
+    a.vol = p.vol;
+    a.C = p.C;
+    a.slab_vol = p.slab_vol;
+    a.nchunks = p.nchunks;
+    a.nslot = p.nslot;
+    a.chunk_ptr = p.d_chunk_ptr;
+    a.chunk_site = p.d_chunk_site;
+    a.site_off = p.d_site_off;
+    a.flags = p.d_flags;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = p.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(32 * p.nwarps);
+    cfg.dynamicSmemBytes = p.smem_bytes;
+    cfg.stream = c->stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     int rc;
     if ((rc = blas_copy(c, r, v, sizeof(float4) * 6 * V))) return rc;
     if ((rc = blas_zero(c, x, sizeof(float4) * 6 * V))) return rc;
-    int nt = ((p.max_step + 31) / 32) * 32;
-    nt = std::min(std::max(nt, 32), 256);
     for (int j = 0; j < nsap; j++) {
         for (int col = 0; col < 2; col++) {
             cudaEvent_t ev;
+            a.rec = reinterpret_cast<const float4 *>(p.d_rec) + (size_t)(col ? p.nblk[0] : 0) * p.vol * kRecChunks;
+            a.origin_site = p.d_origin_site[col];
+            cfg.gridDim = dim3(p.nblk[col] * p.C);
             prof_begin(c, QCD_K_SSOR, &ev);
-            k_ssor<<<p.nblk[col], nt, 0, c->stream>>>(y, r, c->U32, c->F32, (float)c->kappa, (float)omega, nsweep, g,
-                                                      bg, p.d_step_ptr, p.d_step_site, p.nsteps, p.d_origin[col]);
+            cudaError_t e = cudaLaunchKernelEx(&cfg, k_ssor_warp, a);
+            if (e != cudaSuccess) return cuda_fail(c, e, "cudaLaunchKernelEx(k_ssor_warp)");
             if ((rc = prof_end(c, QCD_K_SSOR, ev))) return rc;
             const int last = (j == nsap - 1);
             prof_begin(c, QCD_K_SAPHOP, &ev);

@@ -177,3 +177,26 @@ def test_errors_are_reported_not_fatal():
     torch.cuda.synchronize()
     assert torch.count_nonzero(out) == 0
     s.close()
+
+
+def test_sap_identical_for_every_cluster_width():
+    """The SSOR kernel may split a block over 1..8 CTAs (a thread-block cluster);
+    the arithmetic and its order do not change, so the output is bitwise equal."""
+    dims, b, sb = (12, 12, 12, 24), (6, 6, 6, 12), (3, 3, 3, 6)
+    kappa = 0.12
+    s, U, F = make_solver(dims, kappa, seed=1003)
+    v = qi.gaussian_spinor(dims, seed=2003)[0]
+    prm = q.make_params(kappa, CSW, b, sb, omega=1.0, nsweep=2, nsap=2)
+    vin = torch.from_numpy(v.astype(np.complex64)).cuda()
+    outs = []
+    for ctas in (1, 2, 3, 4, 6):
+        q.qcd_set_sap_ctas(s.ctx, ctas)
+        out = torch.empty_like(vin)
+        s.sap_precondition(out, vin, prm)
+        torch.cuda.synchronize()
+        outs.append(out)
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+    ref = oracle.sap(dims, U, F, kappa, b, sb, 1.0, 2, 2, v)
+    assert rel_norm(outs[0].cpu().numpy().astype(np.complex128), ref) <= 1e-5
+    s.close()
