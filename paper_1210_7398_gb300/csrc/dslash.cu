@@ -13,8 +13,12 @@
 
 namespace qcd {
 
-template <typename R, typename SP, typename LK, typename CL>
-__global__ void __launch_bounds__(128) dslash_kernel(SP *__restrict__ out, const SP *__restrict__ in,
+// MINB: resident blocks per SM requested from the register allocator.  The FP32
+// kernel is bound by memory latency, so it trades registers for occupancy
+// (7 blocks of 128 threads); the FP64 kernel is bound by GB300's FP64 rate and
+// keeps its registers.
+template <int MINB, typename R, typename SP, typename LK, typename CL>
+__global__ void __launch_bounds__(128, MINB) dslash_kernel(SP *__restrict__ out, const SP *__restrict__ in,
                                                      const LK *__restrict__ U, const CL *__restrict__ F,
                                                      R kappa, Geo g, int nrhs) {
     using C = typename CT<R>::C;
@@ -66,7 +70,7 @@ int dslash64(qcd_ctx *c, double2 *out, const double2 *in, int nrhs) {
     dim3 grid((unsigned)((g.V + 127) / 128), nrhs);
     cudaEvent_t ev;
     prof_begin(c, QCD_K_DSLASH64, &ev);
-    dslash_kernel<double, double2, double2, double2><<<grid, 128, 0, c->stream>>>(out, in, c->U64, c->F64,
+    dslash_kernel<3, double, double2, double2, double2><<<grid, 128, 0, c->stream>>>(out, in, c->U64, c->F64,
                                                                                   c->kappa, g, nrhs);
     return prof_end(c, QCD_K_DSLASH64, ev);
 }
@@ -76,7 +80,7 @@ int dslash32(qcd_ctx *c, float4 *out, const float4 *in, int nrhs) {
     dim3 grid((unsigned)((g.V + 127) / 128), nrhs);
     cudaEvent_t ev;
     prof_begin(c, QCD_K_DSLASH32, &ev);
-    dslash_kernel<float, float4, float2, float4><<<grid, 128, 0, c->stream>>>(out, in, c->U32, c->F32,
+    dslash_kernel<7, float, float4, float2, float4><<<grid, 128, 0, c->stream>>>(out, in, c->U32, c->F32,
                                                                               (float)c->kappa, g, nrhs);
     return prof_end(c, QCD_K_DSLASH32, ev);
 }
