@@ -139,7 +139,8 @@ int check_params(qcd_ctx *c, const qcd_params *p) {
     if (!p) return fail(c, QCD_ERR_ARG, "params is NULL");
     if (!(p->omega > 0 && p->omega < 2)) return fail(c, QCD_ERR_ARG, "omega must lie in (0, 2)");
     if (p->nsweep < 1 || p->nsap < 1) return fail(c, QCD_ERR_ARG, "nsweep and nsap must be >= 1");
-    if (p->sap_storage != QCD_F32) return fail(c, QCD_ERR_ARG, "sap_storage: only QCD_F32 is supported");
+    if (p->sap_storage != QCD_F32 && p->sap_storage != QCD_F16)
+        return fail(c, QCD_ERR_ARG, "sap_storage must be QCD_F32 or QCD_F16");
     if (p->learned != 0) return fail(c, QCD_ERR_ARG, "learned correction not available");
     if (p->bc_t != c->bc_t) return fail(c, QCD_ERR_ARG, "params.bc_t differs from the context boundary condition");
     if (p->kappa != c->kappa || p->csw != c->csw)
@@ -296,7 +297,7 @@ int qcd_sap_precondition(qcd_ctx *c, float *out, const float *in, const qcd_para
     if ((rc = need_clover(c))) return rc;
     if (!out || !in || nrhs < 1) return fail(c, QCD_ERR_ARG, "qcd_sap_precondition: bad pointer or nrhs");
     if ((rc = check_params(c, p))) return rc;
-    if ((rc = sap_prepare(c, p->block, p->subblock))) return rc;
+    if ((rc = sap_prepare(c, p->block, p->subblock, p->sap_storage == QCD_F16))) return rc;
     const long V = c->lat.V;
     const size_t bytes = 8 * 12 * V;  // one complex64 right-hand side
     const bool dev_in = is_device_ptr(in), dev_out = is_device_ptr(out);
@@ -335,7 +336,7 @@ int qcd_solve(qcd_ctx *c, double *x, const double *b, const qcd_params *p, int n
     if ((rc = check_params(c, p))) return rc;
     if (!(p->tol > 0) || !(p->inner_tol > 0) || p->max_outer < 1 || p->max_inner < 1)
         return fail(c, QCD_ERR_ARG, "tol, inner_tol, max_outer, max_inner must be positive");
-    if ((rc = sap_prepare(c, p->block, p->subblock))) return rc;
+    if ((rc = sap_prepare(c, p->block, p->subblock, p->sap_storage == QCD_F16))) return rc;
     qcd_stats local;
     std::memset(&local, 0, sizeof(local));
     local.status = QCD_OK;

@@ -21,6 +21,7 @@
 // distributed shared memory); links, clover and source of the sites of the
 // next two steps are staged with cp.async while the current step computes.
 #include <cooperative_groups.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <cstring>
@@ -73,19 +74,28 @@ __device__ __forceinline__ void masked_hops(const float4 *src, const float2 *__r
 namespace cg = cooperative_groups;
 
 constexpr int kRing = 3;           // staging depth (timeline steps in flight)
-constexpr int kRecFloats = 300;    // per-site record: 8 colour matrices, clover rows, metadata
-constexpr int kRecChunks = kRecFloats / 4;
-constexpr int kStageFloats = kRecFloats + 24;  // record + the site's source spinor
-constexpr int kStageChunks = kStageFloats / 4;
-static_assert(kRecFloats * sizeof(float) == kSapRecordBytesPerSite, "record size");
 constexpr int kMaxSlots = 16;      // sites per CTA per timeline step
 constexpr size_t kSmemLimit = 200 * 1024;
-// record layout (floats): [0, 144) W_d for d = 2 mu + (backward): U_mu(n) forward, U_mu(n - mu)^dag
-// backward, 3x3 row-major complex (zero when the hop leaves the block); [144, 288) the two chiral
-// blocks of F/2 as full 6x6 complex rows; ints at [288] global site, [289] float offset of the
-// site's spinor in its slab, [290, 298) neighbour code per direction: (slab << 24) | float offset
-// of the neighbour's spinor in that slab, or -1 when the hop leaves the block.
-constexpr int kRecClover = 144, kRecSite = 288, kRecYoff = 289, kRecNbr = 290;
+
+// Per-site record of the SSOR kernel, in 4-byte words.  W_d for d = 2 mu + (backward):
+// U_mu(n) forward, U_mu(n - mu)^dag backward, 3x3 row-major complex (zero when the hop leaves
+// the block); then the two chiral blocks of F/2 as full 6x6 complex rows; then ints: global
+// site, offset (words) of the site's spinor in its slab, and per direction the neighbour code
+// (slab << 24) | offset (words) of the neighbour's spinor in that slab, or -1 when the hop
+// leaves the block.  FP32 storage keeps complex numbers as float2 (2 words), FP16 storage as
+// half2 (1 word) with the block spinor scaled by one FP32 factor per slab.
+template <bool HALF> struct Rec {
+    static constexpr int cw = HALF ? 1 : 2;        // words per complex
+    static constexpr int W = 0, F = 72 * cw;       // colour matrices, clover rows
+    static constexpr int site = 144 * cw, yoff = site + 1, nbr = site + 2;
+    static constexpr int words = site + 12;        // 300 (FP32) or 156 (FP16)
+    static constexpr int chunks = words / 4;
+    static constexpr int stage = words + 24;       // + the site's FP32 source spinor
+    static constexpr int stage_chunks = stage / 4;
+    static constexpr int ywords = 12 * cw;         // words of one site's spinor in shared memory
+};
+static_assert(Rec<false>::words * 4 == kSapRecordBytesPerSite, "record size");
+static_assert(Rec<true>::words % 4 == 0 && Rec<false>::words % 4 == 0, "records are 16-byte chunks");
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -96,10 +106,22 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// complex load / store in the storage format (w points at the number's first word)
+template <bool HALF> __device__ __forceinline__ float2 ld_c(const float *w) {
+    if constexpr (HALF) return __half22float2(*reinterpret_cast<const __half2 *>(w));
+    else return *reinterpret_cast<const float2 *>(w);
+}
+template <bool HALF> __device__ __forceinline__ void st_c(float *w, float2 v) {
+    if constexpr (HALF) *reinterpret_cast<__half2 *>(w) = __float22half2_rn(v);
+    else *reinterpret_cast<float2 *>(w) = v;
+}
+
 // Builds the per-site records of every block (blocks of colour 0 first).
+template <bool HALF>
 __global__ void k_sap_records(float *__restrict__ rec, const float2 *__restrict__ U, const float4 *__restrict__ F,
                               Geo g, BlockGeo bg, int slab_t, int slab_vol, const int *__restrict__ org0,
                               const int *__restrict__ org1, int nblk0, long total) {
+    using L = Rec<HALF>;
     const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i >= total) return;
     const int gb = (int)(i / bg.vol), yl = (int)(i % bg.vol);
@@ -109,35 +131,34 @@ __global__ void k_sap_records(float *__restrict__ rec, const float2 *__restrict_
     const long gs[4] = {1, g.L[0], (long)g.L[0] * g.L[1], (long)g.L[0] * g.L[1] * g.L[2]};
     long n = 0;
     for (int m = 0; m < 4; m++) n += gs[m] * (o[m] + y[m]);
-    float *R = rec + i * kRecFloats;
+    float *R = rec + i * L::words;
     int *Ri = reinterpret_cast<int *>(R);
     const int bs[4] = {1, bg.b[0], bg.b[0] * bg.b[1], bg.b[0] * bg.b[1] * bg.b[2]};
     for (int d = 0; d < 8; d++) {
         const int mu = d >> 1;
         const bool fwd = (d & 1) == 0;
         const int ym = y[mu] + (fwd ? 1 : -1);
-        float *W = R + d * 18;
+        float *W = R + L::W + d * 9 * L::cw;
         if (ym < 0 || ym >= bg.b[mu]) {
-            for (int k = 0; k < 18; k++) W[k] = 0.f;
-            Ri[kRecNbr + d] = -1;
+            for (int k = 0; k < 9; k++) st_c<HALF>(W + k * L::cw, make_float2(0.f, 0.f));
+            Ri[L::nbr + d] = -1;
             continue;
         }
         const long src = fwd ? n : n - gs[mu];
         for (int a = 0; a < 3; a++)
             for (int bb = 0; bb < 3; bb++) {
+                float2 u;
                 if (fwd) {
-                    const float2 u = U[(long)(mu * 9 + a * 3 + bb) * g.V + src];
-                    W[(a * 3 + bb) * 2] = u.x;
-                    W[(a * 3 + bb) * 2 + 1] = u.y;
+                    u = U[(long)(mu * 9 + a * 3 + bb) * g.V + src];
                 } else {
-                    const float2 u = U[(long)(mu * 9 + bb * 3 + a) * g.V + src];
-                    W[(a * 3 + bb) * 2] = u.x;
-                    W[(a * 3 + bb) * 2 + 1] = -u.y;
+                    u = U[(long)(mu * 9 + bb * 3 + a) * g.V + src];
+                    u.y = -u.y;
                 }
+                st_c<HALF>(W + (a * 3 + bb) * L::cw, u);
             }
         const int nb = yl + (fwd ? bs[mu] : -bs[mu]);
         const int sl = (mu == 3 ? ym : y[3]) / slab_t;
-        Ri[kRecNbr + d] = (sl << 24) | ((nb - sl * slab_vol) * 24);
+        Ri[L::nbr + d] = (sl << 24) | ((nb - sl * slab_vol) * L::ywords);
     }
     float fp[72];
     for (int k = 0; k < 18; k++) {
@@ -146,20 +167,18 @@ __global__ void k_sap_records(float *__restrict__ rec, const float2 *__restrict_
     }
     // unpack each Hermitian block (6 real diagonal, 15 complex below the diagonal) into full rows
     for (int ch = 0; ch < 2; ch++)
-        for (int i = 0; i < 6; i++)
+        for (int ii = 0; ii < 6; ii++)
             for (int j = 0; j < 6; j++) {
-                float re, im;
-                if (i == j) { re = fp[36 * ch + i]; im = 0.f; }
-                else if (j < i) { const int q = 36 * ch + 6 + 2 * (i * (i - 1) / 2 + j); re = fp[q]; im = fp[q + 1]; }
-                else { const int q = 36 * ch + 6 + 2 * (j * (j - 1) / 2 + i); re = fp[q]; im = -fp[q + 1]; }
-                R[kRecClover + 72 * ch + 12 * i + 2 * j] = re;
-                R[kRecClover + 72 * ch + 12 * i + 2 * j + 1] = im;
+                float2 e;
+                if (ii == j) e = make_float2(fp[36 * ch + ii], 0.f);
+                else if (j < ii) { const int q = 36 * ch + 6 + 2 * (ii * (ii - 1) / 2 + j); e = make_float2(fp[q], fp[q + 1]); }
+                else { const int q = 36 * ch + 6 + 2 * (j * (j - 1) / 2 + ii); e = make_float2(fp[q], -fp[q + 1]); }
+                st_c<HALF>(R + L::F + (36 * ch + 6 * ii + j) * L::cw, e);
             }
     const int sl = y[3] / slab_t;
-    Ri[kRecSite] = (int)n;
-    Ri[kRecYoff] = (yl - sl * slab_vol) * 24;
-    Ri[kRecNbr + 8] = 0;
-    Ri[kRecNbr + 9] = 0;
+    Ri[L::site] = (int)n;
+    Ri[L::yoff] = (yl - sl * slab_vol) * L::ywords;
+    for (int k = L::nbr + 8; k < L::words; k++) Ri[k] = 0;
 }
 
 struct SsorArgs {
@@ -178,22 +197,26 @@ struct SsorArgs {
 };
 
 // K3: y = A_BB f on every block of one colour; blockIdx.x / C enumerates blocks
+template <bool HALF>
 __global__ void __launch_bounds__(512) k_ssor_warp(SsorArgs a) {
+    using L = Rec<HALF>;
     extern __shared__ __align__(16) float sm[];
     const int rank = a.C > 1 ? (int)cg::this_cluster().block_rank() : 0;
     const int nch = a.nchunks;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int *cptr_g = a.chunk_ptr + rank * (nch + 1);
     const int tab0 = cptr_g[0], ntab = cptr_g[nch] - tab0;
-    // shared memory: [y slab | staging ring | chunk pointers | chunk sites | per-warp scratch]
-    float *ys = sm;                                                    // [slab_vol][24]
-    float *ring = ys + (size_t)a.slab_vol * 24;                        // [kRing][nslot][kStageFloats]
-    int *cptr = reinterpret_cast<int *>(ring + (size_t)kRing * a.nslot * kStageFloats);  // [nch + 1]
+    // shared memory: [y slab | staging ring | chunk pointers | chunk sites | per-warp scratch | scale]
+    float *ys = sm;                                                    // [slab_vol][ywords]
+    float *ring = ys + (size_t)a.slab_vol * L::ywords;                 // [kRing][nslot][stage]
+    int *cptr = reinterpret_cast<int *>(ring + (size_t)kRing * a.nslot * L::stage);      // [nch + 1]
     int2 *csite = reinterpret_cast<int2 *>(cptr + ((nch + 1 + 3) & ~3));                  // [ntab]
-    float2 *scr = reinterpret_cast<float2 *>(csite + ((ntab + 1) & ~1)) + warp * 12;      // [nw][12]
+    float2 *scr0 = reinterpret_cast<float2 *>(csite + ((ntab + 1) & ~1));                 // [nw][12]
+    float2 *scr = scr0 + warp * 12;
+    float *yscale = reinterpret_cast<float *>(scr0 + nw * 12);                             // [4]
     const int blk = blockIdx.x / a.C;
     const long n0 = a.origin_site[blk];
-    const float4 *rec = a.rec + (size_t)blk * a.vol * kRecChunks;
+    const float4 *rec = a.rec + (size_t)blk * a.vol * L::chunks;
 
     // ---- lane constants of the hop phase: direction d = 2 mu + (backward), colour row c ----
     const int d = lane >> 2, c = lane & 3;
@@ -223,14 +246,33 @@ __global__ void __launch_bounds__(512) k_ssor_warp(SsorArgs a) {
     const int so = lane >> 3;
     const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0;
     const int fch = so >> 1, fk = (so & 1) * 3 + (c < 3 ? c : 0);
-    const int frow = kRecClover + 72 * fch + 12 * fk;  // this lane's row of the chiral block
-    const bool owner = c < 3 && (lane & 4) == 0;      // one lane per (spin, colour) stores
+    const int frow = L::F + (36 * fch + 6 * fk) * L::cw;  // this lane's row of the chiral block
+    const bool owner = c < 3 && (lane & 4) == 0;         // one lane per (spin, colour) stores
 
-    // ---- set-up: zero this CTA's slab of y, copy its chunk tables ----
+    // ---- set-up: zero this CTA's slab of y, copy its chunk tables, FP16: the slab's scale ----
     float4 *ys4 = reinterpret_cast<float4 *>(ys);
-    for (int i = threadIdx.x; i < a.slab_vol * 6; i += blockDim.x) ys4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = threadIdx.x; i < a.slab_vol * L::ywords / 4; i += blockDim.x) ys4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int i = threadIdx.x; i <= nch; i += blockDim.x) cptr[i] = cptr_g[i] - tab0;
     for (int i = threadIdx.x; i < ntab; i += blockDim.x) csite[i] = a.chunk_site[tab0 + i];
+    float inv_scale = 1.f, my_scale = 1.f;
+    if constexpr (HALF) {
+        // scale = largest |component| of the source on this slab (the block solve is O(1) in it)
+        float m = 0.f;
+        for (int i = threadIdx.x; i < a.slab_vol * 6; i += blockDim.x) {
+            const int sl = i / 6, q = i - 6 * sl;
+            const float4 v = a.f[(long)q * a.V + n0 + a.site_off[rank * a.slab_vol + sl]];
+            m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+        }
+        for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+        if (threadIdx.x == 0) yscale[0] = 0.f;
+        __syncthreads();
+        if (lane == 0) atomicMax(reinterpret_cast<int *>(yscale), __float_as_int(m));  // m >= 0: int order = float order
+        __syncthreads();
+        my_scale = yscale[0] > 0.f ? yscale[0] : 1.f;
+        inv_scale = 1.f / my_scale;
+        __syncthreads();
+        if (threadIdx.x == 0) yscale[0] = my_scale;
+    }
     __syncthreads();
 
     const int T = a.nsweep * 2 * nch;
@@ -240,15 +282,15 @@ __global__ void __launch_bounds__(512) k_ssor_warp(SsorArgs a) {
         if (t < T) {
             const int ch = kiss < nch ? kiss : 2 * nch - 1 - kiss;
             const int base = cptr[ch], cnt = cptr[ch + 1] - base;
-            float *stage = ring + (size_t)tiss * a.nslot * kStageFloats;
+            float *stage = ring + (size_t)tiss * a.nslot * L::stage;
             for (int slot = warp; slot < cnt; slot += nw) {
                 const int2 e = csite[base + slot];
-                float *dst = stage + slot * kStageFloats;
-                const float4 *src = rec + (size_t)e.x * kRecChunks;
+                float *dst = stage + slot * L::stage;
+                const float4 *src = rec + (size_t)e.x * L::chunks;
 #pragma unroll
-                for (int q = lane; q < kStageChunks; q += 32) {
-                    if (q < kRecChunks) cp_async16(dst + 4 * q, src + q);
-                    else cp_async16(dst + 4 * q, a.f + (long)(q - kRecChunks) * a.V + n0 + e.y);
+                for (int q = lane; q < L::stage_chunks; q += 32) {
+                    if (q < L::chunks) cp_async16(dst + 4 * q, src + q);
+                    else cp_async16(dst + 4 * q, a.f + (long)(q - L::chunks) * a.V + n0 + e.y);
                 }
             }
             if (++kiss == 2 * nch) kiss = 0;
@@ -262,23 +304,29 @@ __global__ void __launch_bounds__(512) k_ssor_warp(SsorArgs a) {
         float2 acc[4];
 #pragma unroll
         for (int s = 0; s < 4; s++) acc[s] = make_float2(0.f, 0.f);
-        const int code = sdi[kRecNbr + d];
+        const int code = sdi[L::nbr + d];
         if (c < 3 && code >= 0) {
             const int sl = code >> 24;
-            const float *slab = (a.C > 1 && sl != rank) ? cg::this_cluster().map_shared_rank(ys, sl) : ys;
+            const float *slab = ys;
+            float sc = my_scale;
+            if (a.C > 1 && sl != rank) {
+                slab = cg::this_cluster().map_shared_rank(ys, sl);
+                if constexpr (HALF) sc = *cg::this_cluster().map_shared_rank(yscale, sl);
+            }
             const float *pn = slab + (code & 0xffffff);
-            const float *W = sd + d * 18 + c * 6;
+            const float *W = sd + L::W + (d * 9 + c * 3) * L::cw;
             float2 w0 = make_float2(0.f, 0.f), w1 = make_float2(0.f, 0.f);
 #pragma unroll
             for (int cc = 0; cc < 3; cc++) {
-                const float2 qa = *reinterpret_cast<const float2 *>(pn + pa * 6 + cc * 2);
-                const float2 qb = *reinterpret_cast<const float2 *>(pn + pb * 6 + cc * 2);
-                const float2 qc = *reinterpret_cast<const float2 *>(pn + pc * 6 + cc * 2);
-                const float2 qd = *reinterpret_cast<const float2 *>(pn + pd * 6 + cc * 2);
-                const float2 u = *reinterpret_cast<const float2 *>(W + cc * 2);
+                const float2 qa = ld_c<HALF>(pn + (pa * 3 + cc) * L::cw);
+                const float2 qb = ld_c<HALF>(pn + (pb * 3 + cc) * L::cw);
+                const float2 qc = ld_c<HALF>(pn + (pc * 3 + cc) * L::cw);
+                const float2 qd = ld_c<HALF>(pn + (pd * 3 + cc) * L::cw);
+                const float2 u = ld_c<HALF>(W + cc * L::cw);
                 w0 = cfma(u, cfma(za, qb, qa), w0);
                 w1 = cfma(u, cfma(zc, qd, qc), w1);
             }
+            if constexpr (HALF) { w0 = cscale(w0, sc); w1 = cscale(w1, sc); }
 #pragma unroll
             for (int s = 0; s < 4; s++) acc[s] = cfma(be[s], w1, cmul(al[s], w0));
         }
@@ -310,13 +358,12 @@ __global__ void __launch_bounds__(512) k_ssor_warp(SsorArgs a) {
         __syncwarp();
         // row fk of the chiral clover block fch against the block's 6 components
         const float4 *cvv = reinterpret_cast<const float4 *>(scr + fch * 6);
-        const float4 *fr = reinterpret_cast<const float4 *>(sd + frow);
         float2 eta = make_float2(0.f, 0.f);
 #pragma unroll
         for (int q = 0; q < 3; q++) {
-            const float4 x = cvv[q], f = fr[q];
-            eta = cfma(make_float2(f.x, f.y), make_float2(x.x, x.y), eta);
-            eta = cfma(make_float2(f.z, f.w), make_float2(x.z, x.w), eta);
+            const float4 x = cvv[q];
+            eta = cfma(ld_c<HALF>(sd + frow + (2 * q) * L::cw), make_float2(x.x, x.y), eta);
+            eta = cfma(ld_c<HALF>(sd + frow + (2 * q + 1) * L::cw), make_float2(x.z, x.w), eta);
         }
         __syncwarp();  // the scratch may be rewritten by this warp's next site
         float2 Q;
@@ -325,16 +372,18 @@ __global__ void __launch_bounds__(512) k_ssor_warp(SsorArgs a) {
         // upper spins (s < 2): eta0 + eta1; lower: eta1 - eta0
         const float2 out = so < 2 ? cadd(eta, Q) : csub(eta, Q);
         if (owner) {
-            float *yp = ys + sdi[kRecYoff] + (so * 3 + c) * 2;
-            const float2 fv = *reinterpret_cast<const float2 *>(sd + kRecFloats + (so * 3 + c) * 2);
-            const float2 yo = *reinterpret_cast<float2 *>(yp);
+            float *yp = ys + sdi[L::yoff] + (so * 3 + c) * L::cw;
+            const float2 fv = *reinterpret_cast<const float2 *>(sd + L::words + (so * 3 + c) * 2);
+            float2 yo = ld_c<HALF>(yp);
+            if constexpr (HALF) yo = cscale(yo, my_scale);
             float2 t;
             t.x = fmaf(a.kappa, out.x, fv.x);
             t.y = fmaf(a.kappa, out.y, fv.y);
             float2 yn;
             yn.x = fmaf(a.omega, t.x - yo.x, yo.x);
             yn.y = fmaf(a.omega, t.y - yo.y, yo.y);
-            *reinterpret_cast<float2 *>(yp) = yn;
+            if constexpr (HALF) yn = cscale(yn, inv_scale);
+            st_c<HALF>(yp, yn);
         }
     };
 
@@ -349,8 +398,8 @@ __global__ void __launch_bounds__(512) k_ssor_warp(SsorArgs a) {
         __syncwarp();
         const int ch = k < nch ? k : 2 * nch - 1 - k;
         const int base = cptr[ch], cnt = cptr[ch + 1] - base;
-        const float *stage = ring + (size_t)tring * a.nslot * kStageFloats;
-        for (int slot = warp; slot < cnt; slot += nw) update(stage + slot * kStageFloats);
+        const float *stage = ring + (size_t)tring * a.nslot * L::stage;
+        for (int slot = warp; slot < cnt; slot += nw) update(stage + slot * L::stage);
         if (++k == 2 * nch) k = 0;
         if (++tring == kRing) tring = 0;
         if (t + 1 < T) {
@@ -365,7 +414,15 @@ __global__ void __launch_bounds__(512) k_ssor_warp(SsorArgs a) {
     for (int i = threadIdx.x; i < a.slab_vol * 6; i += blockDim.x) {
         const int sl = i / 6, q = i - 6 * sl;
         const long n = n0 + a.site_off[rank * a.slab_vol + sl];
-        a.y[(long)q * a.V + n] = ys4[i];
+        float4 v;
+        if constexpr (HALF) {
+            const float2 lo = cscale(ld_c<true>(ys + sl * 12 + 2 * q), my_scale);
+            const float2 hi = cscale(ld_c<true>(ys + sl * 12 + 2 * q + 1), my_scale);
+            v = make_float4(lo.x, lo.y, hi.x, hi.y);
+        } else {
+            v = ys4[i];
+        }
+        a.y[(long)q * a.V + n] = v;
     }
 }
 
@@ -483,9 +540,11 @@ bool make_chunks(SapPlan &np, int C) {
     np.nwarps = nslot;
     size_t most_sites = 0;
     for (int r = 0; r < C; r++) most_sites = std::max(most_sites, lists[r].size());
-    np.smem_bytes = (size_t)np.slab_vol * 96 + (size_t)kRing * nslot * kStageFloats * sizeof(float) +
+    const int ywords = np.half ? Rec<true>::ywords : Rec<false>::ywords;
+    const int stage = np.half ? Rec<true>::stage : Rec<false>::stage;
+    np.smem_bytes = (size_t)np.slab_vol * ywords * 4 + (size_t)kRing * nslot * stage * sizeof(float) +
                     sizeof(int) * ((nchunks + 1 + 3) & ~3) + sizeof(int2) * ((most_sites + 1) & ~1) +
-                    sizeof(float2) * 12 * nslot;
+                    sizeof(float2) * 12 * nslot + 16;
     if (np.smem_bytes > kSmemLimit) return false;
     np.h_chunk_ptr.clear();
     np.h_chunk_site.clear();
@@ -563,9 +622,10 @@ void make_flags(SapPlan &np) {
 
 }  // namespace
 
-int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &np, int min_ctas) {
+int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &np, int min_ctas, bool half) {
     if (!geometry_ok(c, b, s)) return QCD_ERR_ARG;
     np = SapPlan();
+    np.half = half;
     std::memcpy(np.b, b, sizeof(np.b));
     std::memcpy(np.s, s, sizeof(np.s));
     int nq[4];
@@ -686,7 +746,9 @@ int sap_upload_tables(qcd_ctx *c, SapPlan &p, void *region) {
     return QCD_OK;
 }
 
-size_t sap_record_bytes(const SapPlan &p) { return (size_t)(p.nblk[0] + p.nblk[1]) * p.vol * kRecFloats * sizeof(float); }
+size_t sap_record_bytes(const SapPlan &p) {
+    return (size_t)(p.nblk[0] + p.nblk[1]) * p.vol * (p.half ? Rec<true>::words : Rec<false>::words) * sizeof(float);
+}
 
 int sap_build_records(qcd_ctx *c, SapPlan &p, float *rec) {
     Geo g;
@@ -699,8 +761,12 @@ int sap_build_records(qcd_ctx *c, SapPlan &p, float *rec) {
     const long total = (long)(p.nblk[0] + p.nblk[1]) * p.vol;
     cudaEvent_t ev;
     prof_begin(c, QCD_K_OTHER, &ev);
-    k_sap_records<<<(unsigned)((total + 127) / 128), 128, 0, c->stream>>>(
-        rec, c->U32, c->F32, g, bg, p.slab_t, p.slab_vol, p.d_origin[0], p.d_origin[1], p.nblk[0], total);
+    if (p.half)
+        k_sap_records<true><<<(unsigned)((total + 127) / 128), 128, 0, c->stream>>>(
+            rec, c->U32, c->F32, g, bg, p.slab_t, p.slab_vol, p.d_origin[0], p.d_origin[1], p.nblk[0], total);
+    else
+        k_sap_records<false><<<(unsigned)((total + 127) / 128), 128, 0, c->stream>>>(
+            rec, c->U32, c->F32, g, bg, p.slab_t, p.slab_vol, p.d_origin[0], p.d_origin[1], p.nblk[0], total);
     int rc = prof_end(c, QCD_K_OTHER, ev);
     if (rc) return rc;
     p.d_rec = rec;
@@ -710,14 +776,14 @@ int sap_build_records(qcd_ctx *c, SapPlan &p, float *rec) {
 
 void sap_invalidate(qcd_ctx *c) { free_plan(c); }
 
-int sap_prepare(qcd_ctx *c, const int b[4], const int s[4]) {
+int sap_prepare(qcd_ctx *c, const int b[4], const int s[4], bool half) {
     if (!geometry_ok(c, b, s))
         return fail(c, QCD_ERR_ARG, "SAP geometry: need L % block == 0, L/block even and >= 2, block % subblock == 0");
     SapPlan &p = c->plan;
-    if (!(p.vol && std::equal(b, b + 4, p.b) && std::equal(s, s + 4, p.s))) {
+    if (!(p.vol && std::equal(b, b + 4, p.b) && std::equal(s, s + 4, p.s) && p.half == half)) {
         free_plan(c);
         SapPlan np;
-        if (sap_plan_host(c, b, s, np, c->sap_min_ctas) != QCD_OK)
+        if (sap_plan_host(c, b, s, np, c->sap_min_ctas, half) != QCD_OK)
             return fail(c, QCD_ERR_ARG, "SAP block too large for the shared memory of a cluster of 8 CTAs");
         void *region = nullptr;
         int rc = dev_alloc(c, &region, sap_table_bytes(np));
@@ -756,7 +822,8 @@ int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
     bg.vol = p.vol;
     static bool attr_done = false;
     if (!attr_done) {
-        QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+        QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_warp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+        QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_warp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
         attr_done = true;
     }
     SsorArgs a;
@@ -792,11 +859,13 @@ int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
     for (int j = 0; j < nsap; j++) {
         for (int col = 0; col < 2; col++) {
             cudaEvent_t ev;
-            a.rec = reinterpret_cast<const float4 *>(p.d_rec) + (size_t)(col ? p.nblk[0] : 0) * p.vol * kRecChunks;
+            a.rec = reinterpret_cast<const float4 *>(p.d_rec) +
+                    (size_t)(col ? p.nblk[0] : 0) * p.vol * (p.half ? Rec<true>::chunks : Rec<false>::chunks);
             a.origin_site = p.d_origin_site[col];
             cfg.gridDim = dim3(p.nblk[col] * p.C);
             prof_begin(c, QCD_K_SSOR, &ev);
-            cudaError_t e = cudaLaunchKernelEx(&cfg, k_ssor_warp, a);
+            cudaError_t e = p.half ? cudaLaunchKernelEx(&cfg, k_ssor_warp<true>, a)
+                                   : cudaLaunchKernelEx(&cfg, k_ssor_warp<false>, a);
             if (e != cudaSuccess) return cuda_fail(c, e, "cudaLaunchKernelEx(k_ssor_warp)");
             if ((rc = prof_end(c, QCD_K_SSOR, ev))) return rc;
             const int last = (j == nsap - 1);

@@ -200,3 +200,41 @@ def test_sap_identical_for_every_cluster_width():
     ref = oracle.sap(dims, U, F, kappa, b, sb, 1.0, 2, 2, v)
     assert rel_norm(outs[0].cpu().numpy().astype(np.complex128), ref) <= 1e-5
     s.close()
+
+
+# FP16 storage inside the SAP block solve (FP32 arithmetic): the block spinor is
+# kept as half2 scaled by the slab's largest source component, links and clover
+# rows as half2.  Unit roundoff 2^-11 = 4.9e-4 per stored value; a few sweeps
+# accumulate a few units, so the tolerance is 10 units in norm.
+SAP_F16_TOL = 5e-3
+
+
+@pytest.mark.parametrize("case", [SAP_CASES[0], SAP_CASES[2], SAP_CASES[3]], ids=lambda c: "x".join(map(str, c[0])))
+def test_sap_fp16_storage_vs_oracle(case):
+    dims, b, sb, omega, nsweep, nsap = case
+    kappa = 0.12
+    s, U, F = make_solver(dims, kappa, seed=1001)
+    v = qi.gaussian_spinor(dims, seed=2001)[0]
+    ref = oracle.sap(dims, U, F, kappa, b, sb, omega, nsweep, nsap, v)
+    prm = q.make_params(kappa, CSW, b, sb, omega=omega, nsweep=nsweep, nsap=nsap, sap_storage=q.QCD_F16)
+    vin = torch.from_numpy(v.astype(np.complex64)).cuda()
+    out = torch.empty_like(vin)
+    s.sap_precondition(out, vin, prm)
+    torch.cuda.synchronize()
+    err = rel_norm(out.cpu().numpy().astype(np.complex128), ref)
+    assert err <= SAP_F16_TOL
+    assert err > 1e-7  # really stored in half precision
+    s.close()
+
+
+def test_solve_with_fp16_sap_reaches_fp64_tolerance():
+    dims, block, sub = (12, 12, 12, 24), (6, 6, 6, 12), (3, 3, 3, 6)
+    kappa = 0.12
+    s, U, F = make_solver(dims, kappa, seed=1001)
+    b = qi.gaussian_spinor(dims, seed=2001)
+    prm = q.make_params(kappa, CSW, block, sub, tol=1e-10, sap_storage=q.QCD_F16)
+    x = torch.zeros(b.shape, dtype=torch.complex128, device="cuda")
+    st = s.solve(x, torch.from_numpy(b).cuda(), prm)
+    r = b[0] - oracle.apply_D(dims, U, F, kappa, x.cpu().numpy()[0])
+    assert np.linalg.norm(r) / np.linalg.norm(b[0]) <= 1e-10, st
+    s.close()
