@@ -156,12 +156,19 @@ int qcd_sap_precondition(qcd_ctx *ctx, float *out, const float *in, const qcd_pa
 int qcd_sap_precondition_noalloc(qcd_ctx *ctx, float *out, const float *in, const qcd_params *p);
 
 /* Solves D x = b (Eq. (1)) by the nested BiCGStab of Sec. 2 for nrhs
- * right-hand sides (complex128 [nrhs][V][4][3]).  x holds the initial guess
+ * right-hand sides (complex128 [nrhs][V][4][3]), all advancing together
+ * (batched kernels, per right-hand side scalars on the device; a converged
+ * right-hand side drops out).  x holds the initial guess
  * on entry (zero it for x0 = 0) and the solution on return.  Synchronises.
  * st may be NULL.  Returns QCD_OK when every right-hand side reached the
  * true relative residual p->tol. */
 int qcd_solve(qcd_ctx *ctx, double *x, const double *b, const qcd_params *p, int nrhs,
               qcd_stats *st);
+
+/* on != 0 (default): qcd_solve captures one inner BiCGStab iteration as a CUDA
+ * graph and replays it, when the context stream is not the legacy default
+ * stream and kernel profiling is off.  Results do not depend on it. */
+int qcd_set_graphs(qcd_ctx *ctx, int on);
 
 /* Tuning knob of the SAP block kernel; results do not depend on it.  The
  * least number of CTAs (one thread-block cluster) that share one SAP block,

@@ -26,7 +26,7 @@ KERNEL_CLASSES = ("dslash32", "dslash64", "ssor", "saphop", "blas", "other")
 EXPORTS = ("qcd_create", "qcd_destroy", "qcd_last_error", "qcd_set_boundary", "qcd_load_gauge",
            "qcd_build_clover", "qcd_apply_D", "qcd_sap_precondition", "qcd_solve", "qcd_set_profiling",
            "qcd_kernel_stats", "qcd_launch_count", "qcd_bench_dslash", "qcd_sap_precondition_noalloc",
-           "qcd_set_sap_ctas")
+           "qcd_set_sap_ctas", "qcd_set_graphs")
 
 
 class QcdError(RuntimeError):
@@ -79,6 +79,7 @@ def load_library(path: str = LIB_PATH):
         "qcd_solve": (I, [P, P, P, ctypes.POINTER(qcd_params), I, ctypes.POINTER(qcd_stats)]),
         "qcd_set_profiling": (I, [P, I]),
         "qcd_set_sap_ctas": (I, [P, I]),
+        "qcd_set_graphs": (I, [P, I]),
         "qcd_kernel_stats": (I, [P, I, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(D), I]),
         "qcd_launch_count": (ctypes.c_long, [P]),
         "qcd_bench_dslash": (I, [P, I, I, I]),
@@ -172,6 +173,10 @@ def qcd_solve(ctx, x, b, params: qcd_params, nrhs: int = 1, check: bool = True):
 
 def qcd_set_sap_ctas(ctx, min_ctas: int):
     return _check(ctx, load_library().qcd_set_sap_ctas(ctx, int(min_ctas)))
+
+
+def qcd_set_graphs(ctx, on: bool):
+    return _check(ctx, load_library().qcd_set_graphs(ctx, 1 if on else 0))
 
 
 def qcd_set_profiling(ctx, on: bool):

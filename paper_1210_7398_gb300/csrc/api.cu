@@ -173,8 +173,6 @@ int qcd_create(qcd_ctx **out, const int dims[4], void *stream) {
     if (!rc) rc = dev_alloc(c, (void **)&c->F64, sizeof(double2) * 36 * V);
     if (!rc) rc = dev_alloc(c, (void **)&c->F32, sizeof(float4) * 18 * V);
     if (!rc) rc = dev_alloc(c, (void **)&c->d_status, sizeof(int) * 16);
-    if (!rc) rc = dev_alloc(c, (void **)&c->d_red, sizeof(double) * 3 * 1216);
-    if (!rc) rc = dev_alloc(c, (void **)&c->d_scalars, sizeof(double) * 16);
     if (!rc && cudaMallocHost((void **)&c->h_scalars, sizeof(double) * 16) != cudaSuccess) {
         cudaGetLastError();
         rc = QCD_ERR_OOM;
@@ -192,12 +190,15 @@ void qcd_destroy(qcd_ctx *c) {
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
-    void *bufs[] = {c->U64, c->U32, c->F64, c->F32, c->d_status, c->d_red, c->d_scalars, c->ws64, c->ws32,
+    void *bufs[] = {c->U64, c->U32, c->F64, c->F32, c->d_status, c->d_red, c->d_scalars, c->d_bicg, c->d_mask,
+                    c->ws64, c->ws32,
                     c->d_io, c->bench_in, c->bench_out, c->plan.d_origin[0] /* the plan's table region */,
                     c->plan.d_rec};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (c->h_scalars) cudaFreeHost(c->h_scalars);
+    if (c->h_bicg) cudaFreeHost(c->h_bicg);
+    if (c->h_mask) cudaFreeHost(c->h_mask);
     for (auto &p : c->prof.pending) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
@@ -341,7 +342,7 @@ int qcd_solve(qcd_ctx *c, double *x, const double *b, const qcd_params *p, int n
     std::memset(&local, 0, sizeof(local));
     local.status = QCD_OK;
     const long V = c->lat.V;
-    const size_t bytes = 16 * 12 * V;
+    const size_t bytes = 16 * 12 * V * (size_t)nrhs;  // all right-hand sides, complex128
     const bool dev_x = is_device_ptr(x), dev_b = is_device_ptr(b);
     if ((dev_x && !aligned16(x)) || (dev_b && !aligned16(b)))
         return fail(c, QCD_ERR_ARG, "device spinors must be 16-byte aligned");
@@ -349,27 +350,22 @@ int qcd_solve(qcd_ctx *c, double *x, const double *b, const qcd_params *p, int n
     char *io = (char *)c->d_io;
     double2 *xi = (double2 *)io, *bi = (double2 *)(io + bytes);
     char *sx = io + 2 * bytes, *sb = io + 3 * bytes;
-    int status = QCD_OK;
-    for (int k = 0; k < nrhs; k++) {
-        const char *bsrc = (const char *)b + k * bytes;
-        char *xdst = (char *)x + k * bytes;
-        if (!dev_b) {
-            QCD_CUDA(c, cudaMemcpyAsync(sb, bsrc, bytes, cudaMemcpyHostToDevice, c->stream));
-            bsrc = sb;
-        }
-        const char *xsrc = xdst;
-        if (!dev_x) {
-            QCD_CUDA(c, cudaMemcpyAsync(sx, xdst, bytes, cudaMemcpyHostToDevice, c->stream));
-            xsrc = sx;
-        }
-        if ((rc = spinor64_to_internal(c, bi, (const double2 *)bsrc, 1))) return rc;
-        if ((rc = spinor64_to_internal(c, xi, (const double2 *)xsrc, 1))) return rc;
-        int s = solve(c, xi, bi, p, &local);
-        if (s == QCD_ERR_CUDA || s == QCD_ERR_OOM || s == QCD_ERR_STATE || s == QCD_ERR_ARG) return s;
-        if (s != QCD_OK && status == QCD_OK) status = s;
-        if ((rc = spinor64_from_internal(c, (double2 *)(dev_x ? xdst : sx), xi, 1))) return rc;
-        if (!dev_x) QCD_CUDA(c, cudaMemcpyAsync(xdst, sx, bytes, cudaMemcpyDeviceToHost, c->stream));
+    const char *bsrc = (const char *)b, *xsrc = (const char *)x;
+    if (!dev_b) {
+        QCD_CUDA(c, cudaMemcpyAsync(sb, b, bytes, cudaMemcpyHostToDevice, c->stream));
+        bsrc = sb;
     }
+    if (!dev_x) {
+        QCD_CUDA(c, cudaMemcpyAsync(sx, x, bytes, cudaMemcpyHostToDevice, c->stream));
+        xsrc = sx;
+    }
+    if ((rc = spinor64_to_internal(c, bi, (const double2 *)bsrc, nrhs))) return rc;
+    if ((rc = spinor64_to_internal(c, xi, (const double2 *)xsrc, nrhs))) return rc;
+    int status = solve(c, xi, bi, p, nrhs, &local);
+    if (status == QCD_ERR_CUDA || status == QCD_ERR_OOM || status == QCD_ERR_STATE || status == QCD_ERR_ARG)
+        return status;
+    if ((rc = spinor64_from_internal(c, (double2 *)(dev_x ? (char *)x : sx), xi, nrhs))) return rc;
+    if (!dev_x) QCD_CUDA(c, cudaMemcpyAsync(x, sx, bytes, cudaMemcpyDeviceToHost, c->stream));
     QCD_CUDA(c, cudaStreamSynchronize(c->stream));
     local.status = status;
     local.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -379,6 +375,13 @@ int qcd_solve(qcd_ctx *c, double *x, const double *b, const qcd_params *p, int n
         else if (status == QCD_ERR_BREAKDOWN) c->err = "BiCGStab breakdown not cured by restarts";
     }
     return status;
+}
+
+int qcd_set_graphs(qcd_ctx *c, int on) {
+    int rc = ready(c);
+    if (rc) return rc;
+    c->use_graphs = on != 0;
+    return QCD_OK;
 }
 
 int qcd_set_sap_ctas(qcd_ctx *c, int min_ctas) {

@@ -80,6 +80,7 @@ struct qcd_ctx {
     std::string err;
     bool poisoned = false;
     long total_launches = 0;
+    long graph_launches = 0;  // kernel launches inside one replay of the captured inner iteration
     qcd::Profiler prof;
 
     // gauge and clover fields
@@ -102,9 +103,15 @@ struct qcd_ctx {
     size_t ws64_bytes = 0;
     void *ws32 = nullptr;
     size_t ws32_bytes = 0;
-    double *d_red = nullptr;      // reduction partials
-    double *d_scalars = nullptr;  // reduction results (device)
+    double *d_red = nullptr;      // reduction partials [nrhs][3][kRedMaxBlocks]
+    double *d_scalars = nullptr;  // reduction results [nrhs][3]
     double *h_scalars = nullptr;  // pinned host mirror
+    int red_rhs = 0;              // right-hand sides d_red / d_scalars are sized for
+    void *d_bicg = nullptr;       // BiCGStab scalars: outer [nrhs] + inner [nrhs]
+    void *h_bicg = nullptr;       // pinned host mirror
+    int *d_mask = nullptr;        // per right-hand side masks [2][nrhs]
+    int *h_mask = nullptr;
+    bool use_graphs = true;       // replay the inner iteration as a CUDA graph when possible
     // host staging for host-pointer calls
     void *d_io = nullptr;
     size_t d_io_bytes = 0;
@@ -158,12 +165,14 @@ int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &pla
 int sap_prepare(qcd_ctx *c, const int b[4], const int s[4], bool half);
 // drops the cached plan (it is rebuilt on next use)
 void sap_invalidate(qcd_ctx *c);
-// x = M_SAP v (FP32 internal layout, one right-hand side); work = 3 spinors
-int sap_apply(qcd_ctx *c, float4 *x, const float4 *v, float4 *work, double omega, int nsweep,
-              int nsap);
+// x = M_SAP v (FP32 internal layout, nrhs right-hand sides); work = 2 nrhs spinors; right-hand
+// sides inactive in gate (may be null) are skipped
+struct BicgScalars;
+int sap_apply(qcd_ctx *c, float4 *x, const float4 *v, float4 *work, double omega, int nsweep, int nsap,
+              int nrhs = 1, const BicgScalars *gate = nullptr);
 // the same with an explicit plan whose device tables and records are already in place
 int sap_apply_plan(qcd_ctx *c, const SapPlan &plan, float4 *x, const float4 *v, float4 *work, double omega,
-                   int nsweep, int nsap);
+                   int nsweep, int nsap, int nrhs = 1, const BicgScalars *gate = nullptr);
 // bytes of the device tables of a plan, and their upload into one region (no allocation)
 size_t sap_table_bytes(const SapPlan &plan);
 int sap_upload_tables(qcd_ctx *c, SapPlan &plan, void *region);
@@ -173,30 +182,45 @@ constexpr size_t kSapRecordBytesPerSite = 1200;
 size_t sap_record_bytes(const SapPlan &plan);
 int sap_build_records(qcd_ctx *c, SapPlan &plan, float *rec);
 
-// BLAS (blas.cu) over complex vectors of n elements (double2 or float2)
-enum { RED_DOT = 0, RED_DOT_NORM = 1, RED_NORM = 2 };
-// results: cdot(a,b) -> res[0], res[1]; ||b||^2 (DOT_NORM) or ||a||^2 (NORM) -> res[2]
-int reduce64(qcd_ctx *c, int kind, const double2 *a, const double2 *b, long n, double res[3]);
-int reduce32(qcd_ctx *c, int kind, const float2 *a, const float2 *b, long n, double res[3]);
+// BLAS (blas.cu), batched: vectors [nrhs][n] complex (double2 or float2), scalars per
+// right-hand side in device memory.  A right-hand side whose scalars say inactive is skipped.
+struct BicgScalars {
+    double2 rho, rho0, alpha, omega, beta;
+    double rn2, rhn2, q2;  // |r|^2, |rhat|^2, |rhs|^2
+    int active, done, breakdown, iters;
+};
+enum { SC_INIT = 0, SC_BETA = 1, SC_ALPHA = 2, SC_OMEGA = 3, SC_RHO = 4 };
+enum { RED_DOT = 0, RED_DOT_NORM = 1, RED_NORM = 2, RED_DOT_NORMA = 3 };
+constexpr int kRedMaxBlocks = 1216;  // 8 x 152 SMs
+// out[rhs][3] = Re, Im <a,b> and |b|^2 (DOT_NORM), |a|^2 (NORM, DOT_NORMA); gate: skip inactive rhs
+int reduce64(qcd_ctx *c, int kind, const double2 *a, const double2 *b, long n, int nrhs, double *out,
+             const BicgScalars *gate);
+int reduce32(qcd_ctx *c, int kind, const float2 *a, const float2 *b, long n, int nrhs, double *out,
+             const BicgScalars *gate);
+// one scalar step of BiCGStab (SC_*) for every right-hand side; SC_INIT: gate (may be null)
+// deactivates right-hand sides that are inactive in the outer solver
+int scalars(qcd_ctx *c, int stage, BicgScalars *S, const double *red, int nrhs, double tol, const BicgScalars *gate);
 int blas_zero(qcd_ctx *c, void *p, size_t bytes);
 int blas_copy(qcd_ctx *c, void *dst, const void *src, size_t bytes);
 // p = r + beta (p - om v)
-int blas_p_update64(qcd_ctx *c, double2 *p, const double2 *r, const double2 *v, double2 beta,
-                    double2 om, long n);
-int blas_p_update32(qcd_ctx *c, float2 *p, const float2 *r, const float2 *v, double2 beta,
-                    double2 om, long n);
+int blas_p_update64(qcd_ctx *c, double2 *p, const double2 *r, const double2 *v, const BicgScalars *S, long n, int nrhs);
+int blas_p_update32(qcd_ctx *c, float2 *p, const float2 *r, const float2 *v, const BicgScalars *S, long n, int nrhs);
 // s = r - alpha v
-int blas_s_update64(qcd_ctx *c, double2 *s, const double2 *r, const double2 *v, double2 alpha, long n);
-int blas_s_update32(qcd_ctx *c, float2 *s, const float2 *r, const float2 *v, double2 alpha, long n);
+int blas_s_update64(qcd_ctx *c, double2 *s, const double2 *r, const double2 *v, const BicgScalars *S, long n, int nrhs);
+int blas_s_update32(qcd_ctx *c, float2 *s, const float2 *r, const float2 *v, const BicgScalars *S, long n, int nrhs);
 // x += alpha ph + om sh;  r = s - om t
-int blas_xr_update64(qcd_ctx *c, double2 *x, double2 *r, const double2 *ph, const double2 *sh,
-                     const double2 *s, const double2 *t, double2 alpha, double2 om, long n);
-int blas_xr_update32(qcd_ctx *c, float2 *x, float2 *r, const float2 *ph, const float2 *sh,
-                     const float2 *s, const float2 *t, double2 alpha, double2 om, long n);
-// r = b - w
-int blas_sub64(qcd_ctx *c, double2 *r, const double2 *b, const double2 *w, long n);
+int blas_xr_update64(qcd_ctx *c, double2 *x, double2 *r, const double2 *ph, const double2 *sh, const double2 *s,
+                     const double2 *t, const BicgScalars *S, long n, int nrhs);
+int blas_xr_update32(qcd_ctx *c, float2 *x, float2 *r, const float2 *ph, const float2 *sh, const float2 *s,
+                     const float2 *t, const BicgScalars *S, long n, int nrhs);
+// r = b - w where mask[rhs] (all when mask is null)
+int blas_sub64(qcd_ctx *c, double2 *r, const double2 *b, const double2 *w, const int *mask, long n, int nrhs);
+// rh = r, p = v = 0 where mask[rhs]
+int blas_restart64(qcd_ctx *c, double2 *rh, double2 *p, double2 *v, const double2 *r, const int *mask, long n,
+                   int nrhs);
 
 // solver (solver.cu)
-int solve(qcd_ctx *c, double2 *x, const double2 *b, const qcd_params *p, qcd_stats *st);
+// x, b: internal FP64 layout, nrhs right-hand sides
+int solve(qcd_ctx *c, double2 *x, const double2 *b, const qcd_params *p, int nrhs, qcd_stats *st);
 
 }  // namespace qcd

@@ -194,6 +194,7 @@ struct SsorArgs {
     const int *site_off;       // [vol] global offset of a block-local site from the block origin
     const unsigned char *flags;  // [2 * nchunks] cluster barrier before a timeline step
     const int *origin_site;    // [blocks of this colour] global index of the block origin
+    const BicgScalars *gate;   // blockIdx.y = right-hand side; skipped when inactive (null: all)
 };
 
 // K3: y = A_BB f on every block of one colour; blockIdx.x / C enumerates blocks
@@ -201,6 +202,10 @@ template <bool HALF>
 __global__ void __launch_bounds__(512) k_ssor_warp(SsorArgs a) {
     using L = Rec<HALF>;
     extern __shared__ __align__(16) float sm[];
+    // one right-hand side per blockIdx.y (the whole cluster shares it, so the early exit is uniform)
+    if (a.gate && !a.gate[blockIdx.y].active) return;
+    a.f += (size_t)blockIdx.y * 6 * a.V;
+    a.y += (size_t)blockIdx.y * 6 * a.V;
     const int rank = a.C > 1 ? (int)cg::this_cluster().block_rank() : 0;
     const int nch = a.nchunks;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -432,9 +437,14 @@ __global__ void __launch_bounds__(512) k_ssor_warp(SsorArgs a) {
 __global__ void __launch_bounds__(128) k_sap_hop(float4 *__restrict__ r, float4 *__restrict__ x,
                                                  const float4 *__restrict__ y, const float2 *__restrict__ U,
                                                  const float4 *__restrict__ F, float kappa, Geo g, BlockGeo bg,
-                                                 int colour, int upd_in, int upd_cross) {
+                                                 int colour, int upd_in, int upd_cross,
+                                                 const BicgScalars *__restrict__ gate) {
     const long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (n >= g.V) return;
+    if (gate && !gate[blockIdx.y].active) return;
+    r += (size_t)blockIdx.y * 6 * g.V;
+    x += (size_t)blockIdx.y * 6 * g.V;
+    y += (size_t)blockIdx.y * 6 * g.V;
     int xc[4], yl[4];
     site_coords(g, n, xc);
     int col = 0;
@@ -805,14 +815,15 @@ int sap_prepare(qcd_ctx *c, const int b[4], const int s[4], bool half) {
     return QCD_OK;
 }
 
-int sap_apply(qcd_ctx *c, float4 *x, const float4 *v, float4 *work, double omega, int nsweep, int nsap) {
-    return sap_apply_plan(c, c->plan, x, v, work, omega, nsweep, nsap);
+int sap_apply(qcd_ctx *c, float4 *x, const float4 *v, float4 *work, double omega, int nsweep, int nsap, int nrhs,
+              const BicgScalars *gate) {
+    return sap_apply_plan(c, c->plan, x, v, work, omega, nsweep, nsap, nrhs, gate);
 }
 
 int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, float4 *work, double omega, int nsweep,
-                   int nsap) {
+                   int nsap, int nrhs, const BicgScalars *gate) {
     const long V = c->lat.V;
-    float4 *r = work, *y = work + 6 * V;
+    float4 *r = work, *y = work + 6 * V * nrhs;
     Geo g;
     for (int m = 0; m < 4; m++) g.L[m] = c->lat.L[m];
     g.V = V;
@@ -842,6 +853,7 @@ int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
     a.chunk_site = p.d_chunk_site;
     a.site_off = p.d_site_off;
     a.flags = p.d_flags;
+    a.gate = gate;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -854,15 +866,15 @@ int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int rc;
-    if ((rc = blas_copy(c, r, v, sizeof(float4) * 6 * V))) return rc;
-    if ((rc = blas_zero(c, x, sizeof(float4) * 6 * V))) return rc;
+    if ((rc = blas_copy(c, r, v, sizeof(float4) * 6 * V * nrhs))) return rc;
+    if ((rc = blas_zero(c, x, sizeof(float4) * 6 * V * nrhs))) return rc;
     for (int j = 0; j < nsap; j++) {
         for (int col = 0; col < 2; col++) {
             cudaEvent_t ev;
             a.rec = reinterpret_cast<const float4 *>(p.d_rec) +
                     (size_t)(col ? p.nblk[0] : 0) * p.vol * (p.half ? Rec<true>::chunks : Rec<false>::chunks);
             a.origin_site = p.d_origin_site[col];
-            cfg.gridDim = dim3(p.nblk[col] * p.C);
+            cfg.gridDim = dim3(p.nblk[col] * p.C, nrhs);
             prof_begin(c, QCD_K_SSOR, &ev);
             cudaError_t e = p.half ? cudaLaunchKernelEx(&cfg, k_ssor_warp<true>, a)
                                    : cudaLaunchKernelEx(&cfg, k_ssor_warp<false>, a);
@@ -870,8 +882,8 @@ int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
             if ((rc = prof_end(c, QCD_K_SSOR, ev))) return rc;
             const int last = (j == nsap - 1);
             prof_begin(c, QCD_K_SAPHOP, &ev);
-            k_sap_hop<<<(unsigned)((V + 127) / 128), 128, 0, c->stream>>>(r, x, y, c->U32, c->F32, (float)c->kappa, g,
-                                                                           bg, col, !last, !(last && col == 1));
+            k_sap_hop<<<dim3((unsigned)((V + 127) / 128), nrhs), 128, 0, c->stream>>>(
+                r, x, y, c->U32, c->F32, (float)c->kappa, g, bg, col, !last, !(last && col == 1), gate);
             if ((rc = prof_end(c, QCD_K_SAPHOP, ev))) return rc;
         }
     }
