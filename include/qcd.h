@@ -89,7 +89,8 @@ typedef struct {
     int bc_t;           /* +1 periodic, -1 antiperiodic in t (must match qcd_set_boundary) */
     int sap_storage;    /* QCD_F32 (plain) or QCD_F16 (half storage, FP32 arithmetic)    */
     int learned;        /* reserved, 0                                                 */
-    int rhs_group;      /* reserved, 0                                                 */
+    int sap_ctas;       /* CTAs per SAP block in the SSOR kernel, 0 = context default
+                           (qcd_set_sap_ctas); results do not depend on it            */
 } qcd_params;
 
 typedef struct {
@@ -177,6 +178,19 @@ int qcd_set_graphs(qcd_ctx *ctx, int on);
  * CTAs per block spread a step's sites over more SMs at the price of more
  * cluster barriers.  Default 1. */
 int qcd_set_sap_ctas(qcd_ctx *ctx, int min_ctas);
+
+/* Autotuner (no counterpart in the paper, which fixes 6^4 blocks with 3^4
+ * sub-blocks).  Starting from *base (kappa, csw, tol, inner_tol, bc_t, limits),
+ * times complete solves of D x = b from x0 = 0 for candidate SAP set-ups and
+ * returns the fastest that converges in *best (block, subblock, sap_storage,
+ * sap_ctas, nsweep, nsap; omega from base) and its time in *best_ms.  Stage 1
+ * tries block splits (L_mu / block_mu in {2, 4, 6, 8}, spatial directions
+ * alike) with sub-blocks block/2, block/3 or block; stage 2 refines the three
+ * fastest over FP16 storage, 2 CTAs per block and (nsweep, nsap) in
+ * {2, 4} x {2, 4}.  At most max_candidates solves are timed (<= 0: 64).
+ * b: complex128 [nrhs][V][4][3], host or device.  Synchronises. */
+int qcd_autotune(qcd_ctx *ctx, const double *b, int nrhs, const qcd_params *base, qcd_params *best,
+                 double *best_ms, int max_candidates);
 
 /* ---- measurement hooks -------------------------------------------------- */
 

@@ -26,7 +26,7 @@ KERNEL_CLASSES = ("dslash32", "dslash64", "ssor", "saphop", "blas", "other")
 EXPORTS = ("qcd_create", "qcd_destroy", "qcd_last_error", "qcd_set_boundary", "qcd_load_gauge",
            "qcd_build_clover", "qcd_apply_D", "qcd_sap_precondition", "qcd_solve", "qcd_set_profiling",
            "qcd_kernel_stats", "qcd_launch_count", "qcd_bench_dslash", "qcd_sap_precondition_noalloc",
-           "qcd_set_sap_ctas", "qcd_set_graphs")
+           "qcd_set_sap_ctas", "qcd_set_graphs", "qcd_autotune")
 
 
 class QcdError(RuntimeError):
@@ -42,7 +42,7 @@ class qcd_params(ctypes.Structure):
                 ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
                 ("max_outer", ctypes.c_int), ("max_inner", ctypes.c_int),
                 ("bc_t", ctypes.c_int), ("sap_storage", ctypes.c_int),
-                ("learned", ctypes.c_int), ("rhs_group", ctypes.c_int)]
+                ("learned", ctypes.c_int), ("sap_ctas", ctypes.c_int)]
 
 
 class qcd_stats(ctypes.Structure):
@@ -80,6 +80,8 @@ def load_library(path: str = LIB_PATH):
         "qcd_set_profiling": (I, [P, I]),
         "qcd_set_sap_ctas": (I, [P, I]),
         "qcd_set_graphs": (I, [P, I]),
+        "qcd_autotune": (I, [P, P, I, ctypes.POINTER(qcd_params), ctypes.POINTER(qcd_params),
+                             ctypes.POINTER(D), I]),
         "qcd_kernel_stats": (I, [P, I, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(D), I]),
         "qcd_launch_count": (ctypes.c_long, [P]),
         "qcd_bench_dslash": (I, [P, I, I, I]),
@@ -175,6 +177,21 @@ def qcd_set_sap_ctas(ctx, min_ctas: int):
     return _check(ctx, load_library().qcd_set_sap_ctas(ctx, int(min_ctas)))
 
 
+def qcd_autotune(ctx, b, base: qcd_params, nrhs: int = 1, max_candidates: int = 0):
+    """Returns (best qcd_params, best time in ms) over the candidate SAP set-ups."""
+    best = qcd_params()
+    ms = ctypes.c_double()
+    _check(ctx, load_library().qcd_autotune(ctx, _ptr(b), int(nrhs), ctypes.byref(base), ctypes.byref(best),
+                                            ctypes.byref(ms), int(max_candidates)))
+    return best, ms.value
+
+
+def params_dict(p: qcd_params) -> dict:
+    return {"block": list(p.block), "subblock": list(p.subblock), "omega": p.omega, "nsweep": p.nsweep,
+            "nsap": p.nsap, "sap_storage": {QCD_F32: "f32", QCD_F16: "f16"}.get(p.sap_storage, p.sap_storage),
+            "sap_ctas": p.sap_ctas, "learned": p.learned}
+
+
 def qcd_set_graphs(ctx, on: bool):
     return _check(ctx, load_library().qcd_set_graphs(ctx, 1 if on else 0))
 
@@ -200,7 +217,7 @@ def qcd_bench_dslash(ctx, prec: int, nrhs: int, iters: int):
 
 
 def make_params(kappa, csw, block, subblock, omega=1.0, nsweep=4, nsap=4, tol=1e-10, inner_tol=1e-5,
-                max_outer=100, max_inner=500, bc_t=1, sap_storage=QCD_F32) -> qcd_params:
+                max_outer=100, max_inner=500, bc_t=1, sap_storage=QCD_F32, sap_ctas=0) -> qcd_params:
     p = qcd_params()
     p.kappa, p.csw = float(kappa), float(csw)
     p.block = (ctypes.c_int * 4)(*block)
@@ -208,7 +225,7 @@ def make_params(kappa, csw, block, subblock, omega=1.0, nsweep=4, nsap=4, tol=1e
     p.omega, p.nsweep, p.nsap = float(omega), int(nsweep), int(nsap)
     p.tol, p.inner_tol = float(tol), float(inner_tol)
     p.max_outer, p.max_inner = int(max_outer), int(max_inner)
-    p.bc_t, p.sap_storage, p.learned, p.rhs_group = int(bc_t), int(sap_storage), 0, 0
+    p.bc_t, p.sap_storage, p.learned, p.sap_ctas = int(bc_t), int(sap_storage), 0, int(sap_ctas)
     return p
 
 

@@ -145,6 +145,11 @@ int check_params(qcd_ctx *c, const qcd_params *p) {
     if (p->bc_t != c->bc_t) return fail(c, QCD_ERR_ARG, "params.bc_t differs from the context boundary condition");
     if (p->kappa != c->kappa || p->csw != c->csw)
         return fail(c, QCD_ERR_ARG, "params.kappa/csw differ from the clover field built");
+    if (p->sap_ctas < 0 || p->sap_ctas > 8) return fail(c, QCD_ERR_ARG, "sap_ctas must lie in 0..8");
+    if (p->sap_ctas > 0 && p->sap_ctas != c->sap_min_ctas) {
+        sap_invalidate(c);
+        c->sap_min_ctas = p->sap_ctas;
+    }
     return QCD_OK;
 }
 

@@ -1,0 +1,183 @@
+// S2: autotuner of the SAP set-up.  The paper fixes one geometry (6^4 blocks,
+// 3^4 sub-blocks per node); on a GPU the best block split trades the number of
+// dependent ll steps (block size) against SAP quality (outer/inner iteration
+// counts), so candidates are compared by measured time to solution.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "qcd_internal.h"
+
+namespace qcd {
+namespace {
+
+struct Cand {
+    qcd_params p;
+    double ms = 1e300;
+    bool ok = false;
+};
+
+bool valid_block(const qcd_ctx *c, const int b[4], const int s[4]) {
+    for (int m = 0; m < 4; m++) {
+        if (b[m] < 2 || s[m] < 1 || c->lat.L[m] % b[m] || b[m] % s[m]) return false;
+        const int nb = c->lat.L[m] / b[m];
+        if (nb < 2 || nb % 2) return false;
+    }
+    return true;
+}
+
+// time one complete solve (x0 = 0) of the internal-layout right-hand sides bi
+int time_solve(qcd_ctx *c, double2 *xi, const double2 *bi, int nrhs, const qcd_params *p, double *ms, bool *ok) {
+    *ok = false;
+    const int old_ctas = c->sap_min_ctas;
+    if (p->sap_ctas > 0 && p->sap_ctas != c->sap_min_ctas) {
+        sap_invalidate(c);
+        c->sap_min_ctas = p->sap_ctas;
+    }
+    int rc = sap_prepare(c, p->block, p->subblock, p->sap_storage == QCD_F16);
+    if (rc == QCD_ERR_ARG) {  // geometry does not fit: not a candidate
+        c->err.clear();
+        c->sap_min_ctas = old_ctas;
+        return QCD_OK;
+    }
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    QCD_CUDA(c, cudaEventCreate(&e0));
+    QCD_CUDA(c, cudaEventCreate(&e1));
+    const size_t bytes = sizeof(double2) * 12 * c->lat.V * nrhs;
+    QCD_CUDA(c, cudaMemsetAsync(xi, 0, bytes, c->stream));
+    QCD_CUDA(c, cudaEventRecord(e0, c->stream));
+    qcd_stats st;
+    std::memset(&st, 0, sizeof(st));
+    int s = solve(c, xi, bi, p, nrhs, &st);
+    QCD_CUDA(c, cudaEventRecord(e1, c->stream));
+    QCD_CUDA(c, cudaEventSynchronize(e1));
+    float t = 0;
+    cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s == QCD_ERR_CUDA || s == QCD_ERR_OOM || s == QCD_ERR_STATE) return s;
+    *ok = (s == QCD_OK);
+    *ms = t;
+    return QCD_OK;
+}
+
+}  // namespace
+}  // namespace qcd
+
+using namespace qcd;
+
+extern "C" int qcd_autotune(qcd_ctx *c, const double *b, int nrhs, const qcd_params *base, qcd_params *best,
+                            double *best_ms, int max_candidates) {
+    if (!c || !b || !base || !best || nrhs < 1) return QCD_ERR_ARG;
+    if (c->poisoned) return fail(c, QCD_ERR_STATE, "context poisoned by an earlier CUDA error: " + c->err);
+    QCD_CUDA(c, cudaSetDevice(c->device));
+    if (!c->have_clover) return fail(c, QCD_ERR_STATE, "qcd_build_clover must be called first");
+    if (base->kappa != c->kappa || base->csw != c->csw || base->bc_t != c->bc_t)
+        return fail(c, QCD_ERR_ARG, "params kappa/csw/bc_t differ from the context");
+    if (max_candidates <= 0) max_candidates = 64;
+    const long V = c->lat.V;
+    const size_t bytes = sizeof(double2) * 12 * V * nrhs;
+    // right-hand sides in the internal layout, solution buffer
+    void *buf = nullptr;
+    int rc = dev_alloc(c, &buf, 3 * bytes);
+    if (rc) return rc;
+    struct Free {
+        qcd_ctx *c;
+        void *p;
+        ~Free() { dev_free(c, p); }
+    } guard{c, buf};
+    double2 *bi = (double2 *)buf, *xi = bi + 12 * V * nrhs, *stage = xi + 12 * V * nrhs;
+    cudaPointerAttributes at;
+    const bool on_dev = cudaPointerGetAttributes(&at, b) == cudaSuccess &&
+                        (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    QCD_CUDA(c, cudaMemcpyAsync(stage, b, bytes, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    if ((rc = spinor64_to_internal(c, bi, stage, nrhs))) return rc;
+    const int old_ctas = c->sap_min_ctas;
+    const bool old_prof = c->prof.on;
+    c->prof.on = false;
+
+    // stage 1: block splits and sub-block splits, FP32 storage, base sweeps and cycles
+    std::vector<Cand> cands;
+    const int splits[4] = {2, 4, 6, 8};
+    for (int ks : splits)
+        for (int kt : splits) {
+            int blk[4];
+            for (int m = 0; m < 3; m++) blk[m] = c->lat.L[m] % ks ? 0 : c->lat.L[m] / ks;
+            blk[3] = c->lat.L[3] % kt ? 0 : c->lat.L[3] / kt;
+            if (!blk[0] || !blk[1] || !blk[2] || !blk[3]) continue;
+            const int vol = blk[0] * blk[1] * blk[2] * blk[3];
+            if (vol > 4096 || vol < 16) continue;
+            for (int div = 2; div <= 4; div++) {
+                int sub[4];
+                for (int m = 0; m < 4; m++) sub[m] = (div == 4) ? blk[m] : (blk[m] % div ? 0 : blk[m] / div);
+                if (!sub[0] || !sub[1] || !sub[2] || !sub[3]) continue;
+                if (!valid_block(c, blk, sub)) continue;
+                Cand cd;
+                cd.p = *base;
+                std::memcpy(cd.p.block, blk, sizeof(blk));
+                std::memcpy(cd.p.subblock, sub, sizeof(sub));
+                cd.p.sap_storage = QCD_F32;
+                cd.p.sap_ctas = 0;
+                cands.push_back(cd);
+            }
+        }
+    int tried = 0;
+    auto run = [&](Cand &cd) -> int {
+        if (tried >= max_candidates) return QCD_OK;
+        tried++;
+        double ms = 0;
+        bool ok = false;
+        // first solve builds the plan and records; the second is timed
+        int r2 = time_solve(c, xi, bi, nrhs, &cd.p, &ms, &ok);
+        if (r2) return r2;
+        if (ok) {
+            r2 = time_solve(c, xi, bi, nrhs, &cd.p, &ms, &ok);
+            if (r2) return r2;
+        }
+        cd.ok = ok;
+        cd.ms = ok ? ms : 1e300;
+        return QCD_OK;
+    };
+    for (auto &cd : cands)
+        if ((rc = run(cd))) break;
+    if (!rc) {
+        std::sort(cands.begin(), cands.end(), [](const Cand &u, const Cand &v) { return u.ms < v.ms; });
+        // stage 2: refine the three fastest
+        std::vector<Cand> more;
+        for (size_t i = 0; i < cands.size() && i < 3; i++) {
+            if (!cands[i].ok) continue;
+            for (int storage : {QCD_F32, QCD_F16})
+                for (int ctas : {0, 2})
+                    for (int ns : {2, 4})
+                        for (int np : {2, 4}) {
+                            Cand cd = cands[i];
+                            cd.p.sap_storage = storage;
+                            cd.p.sap_ctas = ctas;
+                            cd.p.nsweep = ns;
+                            cd.p.nsap = np;
+                            if (storage == cands[i].p.sap_storage && ctas == cands[i].p.sap_ctas &&
+                                ns == cands[i].p.nsweep && np == cands[i].p.nsap)
+                                continue;
+                            more.push_back(cd);
+                        }
+        }
+        for (auto &cd : more)
+            if ((rc = run(cd))) break;
+        cands.insert(cands.end(), more.begin(), more.end());
+    }
+    c->prof.on = old_prof;
+    if (c->sap_min_ctas != old_ctas) {
+        sap_invalidate(c);
+        c->sap_min_ctas = old_ctas;
+    }
+    if (rc) return rc;
+    const Cand *win = nullptr;
+    for (auto &cd : cands)
+        if (cd.ok && (!win || cd.ms < win->ms)) win = &cd;
+    if (!win) return fail(c, QCD_ERR_NOCONV, "autotune: no candidate converged");
+    *best = win->p;
+    if (best_ms) *best_ms = win->ms;
+    return QCD_OK;
+}

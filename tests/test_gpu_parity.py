@@ -280,3 +280,18 @@ def test_graph_replay_equals_direct_launches():
     assert torch.equal(xg, xd)
     assert q.qcd_launch_count(s.ctx) > l0
     s.close()
+
+
+def test_autotune_returns_a_converging_setup():
+    dims, kappa = (8, 8, 8, 16), 0.12
+    s, U, F = make_solver(dims, kappa, seed=1006)
+    b = torch.from_numpy(qi.gaussian_spinor(dims, seed=2006)).cuda()
+    base = q.make_params(kappa, CSW, (4, 4, 4, 4), (2, 2, 2, 2), tol=1e-10)
+    best, ms = q.qcd_autotune(s.ctx, b, base, max_candidates=12)
+    assert ms > 0
+    assert oracle.check_geometry(dims, tuple(best.block), tuple(best.subblock))
+    x = torch.zeros_like(b)
+    s.solve(x, b, best)
+    r = b.cpu().numpy()[0] - oracle.apply_D(dims, U, F, kappa, x.cpu().numpy()[0])
+    assert np.linalg.norm(r) / np.linalg.norm(b.cpu().numpy()[0]) <= 1e-10
+    s.close()
