@@ -64,6 +64,10 @@ def lib():
             L.orc_inner_bicgstab.restype = i
             L.orc_solve.argtypes = [P, i, P, P, d, P, P, d, i, i, d, d, i, i, P, P, P]
             L.orc_solve.restype = i
+            L.orc_learned_layer.argtypes = [P, i, P, i, i, P, P, P]
+            L.orc_learned_forward.argtypes = [P, i, P, i, P, P, P, P]
+            L.orc_learned_loss_grad.argtypes = [P, i, P, i, P, P, P, P, P]
+            L.orc_learned_loss_grad.restype = d
             _lib = L
     return _lib
 
@@ -242,3 +246,39 @@ def solve(dims, U, F, kappa, block, sub, omega, nsweep, nsap, b, tol=1e-10, inne
                              st.ctypes.data_as(ctypes.c_void_p))
     return x, status, dict(outer=int(st[0]), inner=int(st[1]), restarts=int(st[2]),
                            true_rel_res=float(st[3]))
+
+
+# ---------------------------------------------------------------------------
+# learned correction (a project addition): linear gauge-covariant network
+# ---------------------------------------------------------------------------
+
+def learned_weight_count(chans) -> int:
+    """Complex weights of a network with channel counts chans[0..nl]: 9 x cout x cin x 4 x 4 per layer."""
+    return sum(9 * chans[l + 1] * chans[l] * 16 for l in range(len(chans) - 1))
+
+
+def learned_forward(dims, U, chans, W, x, bc_t: int = 1):
+    """N(x): x complex [chans[0]][V][4][3], W complex (layer-concatenated [9][cout][cin][4][4])."""
+    Lk, Lp = _ivec(dims)
+    ck, cp = _ivec(chans)
+    U, Up = _c(U)
+    W, Wp = _c(W)
+    x, xp = _c(x)
+    V = _vol(dims)
+    y = np.empty((chans[-1], V, 4, 3), dtype=np.complex128)
+    lib().orc_learned_forward(Lp, bc_t, Up, len(chans) - 1, cp, Wp, xp, y.ctypes.data_as(ctypes.c_void_p))
+    return y
+
+
+def learned_loss_grad(dims, U, chans, W, rho, eps, bc_t: int = 1):
+    """(loss, grad) for one pair; grad is real [2 * nweights] = 2 (Re, Im) of dL/dW*."""
+    Lk, Lp = _ivec(dims)
+    ck, cp = _ivec(chans)
+    U, Up = _c(U)
+    W, Wp = _c(W)
+    rho, rp = _c(rho)
+    eps, ep = _c(eps)
+    g = np.empty(2 * learned_weight_count(chans))
+    loss = lib().orc_learned_loss_grad(Lp, bc_t, Up, len(chans) - 1, cp, Wp, rp, ep,
+                                       g.ctypes.data_as(ctypes.c_void_p))
+    return loss, g

@@ -747,3 +747,191 @@ done:
     free(r); free(rh); free(p); free(v); free(ph); free(sh); free(sv); free(t); free(tmp);
     return status;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Learned correction (a project addition; the paper has none).  A linear,  */
+/* gauge-covariant network of parallel-transport layers                     */
+/*   y_c(n) = sum_{d=0..8} sum_{c'} W_d[c][c'] (T_d x_{c'})(n)               */
+/* with 4x4 complex spin matrices W_d[c][c'] and transports                 */
+/*   T_0 = 1,  T_{2mu} x(n) = U_mu(n) x(n+mu),                               */
+/*   T_{2mu+1} x(n) = U_mu(n-mu)^dag x(n-mu)   (boundary sign as in D).       */
+/* Weights of a layer: complex [9][cout][cin][4][4]; fields [c][V][4][3].     */
+/* ------------------------------------------------------------------------ */
+
+/* z = T_d x for one site n (x: one channel [V][12]) */
+static void transport_site(const int *L, int bc_t, const cplx *U, int d, long n, const cplx *x, cplx z[12])
+{
+    if (d == 0) {
+        for (int k = 0; k < 12; k++) z[k] = x[n * 12 + k];
+        return;
+    }
+    int mu = (d - 1) / 2, dir = ((d - 1) % 2 == 0) ? +1 : -1;
+    long m = neighbour(L, n, mu, dir);
+    double sgn = hop_sign(L, n, mu, dir, bc_t);
+    const cplx *W = (dir > 0) ? link(U, n, mu) : link(U, m, mu);
+    for (int s = 0; s < 4; s++)
+        for (int a = 0; a < 3; a++) {
+            cplx acc = 0;
+            for (int b = 0; b < 3; b++) acc += ((dir > 0) ? W[a * 3 + b] : conj(W[b * 3 + a])) * x[m * 12 + s * 3 + b];
+            z[s * 3 + a] = sgn * acc;
+        }
+}
+
+/* adjoint transport z = T_d^dag x at site m:
+ * T_{2mu}^dag x(m) = U_mu(m-mu)^dag x(m-mu),  T_{2mu+1}^dag x(m) = U_mu(m) x(m+mu) */
+static void transport_adj_site(const int *L, int bc_t, const cplx *U, int d, long m, const cplx *x, cplx z[12])
+{
+    if (d == 0) {
+        for (int k = 0; k < 12; k++) z[k] = x[m * 12 + k];
+        return;
+    }
+    int mu = (d - 1) / 2, dir = ((d - 1) % 2 == 0) ? -1 : +1; /* the opposite hop */
+    long n = neighbour(L, m, mu, dir);
+    double sgn = hop_sign(L, m, mu, dir, bc_t);
+    const cplx *W = (dir > 0) ? link(U, m, mu) : link(U, n, mu);
+    for (int s = 0; s < 4; s++)
+        for (int a = 0; a < 3; a++) {
+            cplx acc = 0;
+            for (int b = 0; b < 3; b++) acc += ((dir > 0) ? W[a * 3 + b] : conj(W[b * 3 + a])) * x[n * 12 + s * 3 + b];
+            z[s * 3 + a] = sgn * acc;
+        }
+}
+
+/* one layer: y = sum_d W_d T_d x */
+void orc_learned_layer(const int *L, int bc_t, const double *Ud, int cin, int cout, const double *Wd,
+                       const double *xd, double *yd)
+{
+    const cplx *U = (const cplx *)Ud, *W = (const cplx *)Wd, *x = (const cplx *)xd;
+    cplx *y = (cplx *)yd;
+    long V = volume(L);
+#pragma omp parallel for schedule(static)
+    for (long n = 0; n < V; n++) {
+        cplx out[64][12];
+        for (int c = 0; c < cout; c++)
+            for (int k = 0; k < 12; k++) out[c][k] = 0;
+        for (int d = 0; d < 9; d++)
+            for (int cp = 0; cp < cin; cp++) {
+                cplx z[12];
+                transport_site(L, bc_t, U, d, n, x + (long)cp * V * 12, z);
+                for (int c = 0; c < cout; c++) {
+                    const cplx *w = W + (((long)d * cout + c) * cin + cp) * 16;
+                    for (int al = 0; al < 4; al++)
+                        for (int be = 0; be < 4; be++)
+                            for (int a = 0; a < 3; a++) out[c][al * 3 + a] += w[al * 4 + be] * z[be * 3 + a];
+                }
+            }
+        for (int c = 0; c < cout; c++)
+            for (int k = 0; k < 12; k++) y[((long)c * V + n) * 12 + k] = out[c][k];
+    }
+}
+
+/* whole network: chans[0..nl] channel counts, weights concatenated layer by layer */
+static long layer_wsize(int cin, int cout) { return 9L * cout * cin * 16; }
+
+void orc_learned_forward(const int *L, int bc_t, const double *U, int nl, const int *chans, const double *W,
+                         const double *x, double *y)
+{
+    long V = volume(L);
+    const double *in = x;
+    double *buf[2] = {malloc(sizeof(double) * 24 * V * 64), malloc(sizeof(double) * 24 * V * 64)};
+    long woff = 0;
+    for (int l = 0; l < nl; l++) {
+        double *out = (l == nl - 1) ? y : buf[l % 2];
+        orc_learned_layer(L, bc_t, U, chans[l], chans[l + 1], W + 2 * woff, in, out);
+        woff += layer_wsize(chans[l], chans[l + 1]);
+        in = out;
+    }
+    free(buf[0]);
+    free(buf[1]);
+}
+
+/* Loss L = |N(rho) - eps|^2 / |eps|^2 for one pair, and its gradient with
+ * respect to the real and imaginary parts of every weight:
+ * grad = 2 (Re, Im) of dL/dW*, dL/dW_d[c][c'] = sum_n g_c(n) (T_d a_{c'}(n))^dag
+ * with g = dL/dy* propagated back by the adjoint layers. */
+double orc_learned_loss_grad(const int *L, int bc_t, const double *Ud, int nl, const int *chans,
+                             const double *Wd, const double *rhod, const double *epsd, double *grad)
+{
+    const cplx *U = (const cplx *)Ud, *W = (const cplx *)Wd;
+    long V = volume(L);
+    /* activations a[0] = rho, a[l+1] = layer l output */
+    cplx *a[16];
+    a[0] = (cplx *)rhod;
+    long woffs[16];
+    long woff = 0;
+    for (int l = 0; l < nl; l++) {
+        woffs[l] = woff;
+        a[l + 1] = malloc(sizeof(cplx) * 12 * V * chans[l + 1]);
+        orc_learned_layer(L, bc_t, Ud, chans[l], chans[l + 1], Wd + 2 * woff, (double *)a[l], (double *)a[l + 1]);
+        woff += layer_wsize(chans[l], chans[l + 1]);
+    }
+    const cplx *eps = (const cplx *)epsd;
+    double en2 = 0, loss = 0;
+    for (long i = 0; i < 12 * V; i++) en2 += creal(eps[i] * conj(eps[i]));
+    cplx *g = malloc(sizeof(cplx) * 12 * V * chans[nl]);
+    for (long i = 0; i < 12 * V; i++) {
+        cplx r = a[nl][i] - eps[i];
+        loss += creal(r * conj(r)) / en2;
+        g[i] = r / en2;
+    }
+    cplx *gW = (cplx *)grad; /* written as complex, converted to 2 (Re, Im) at the end */
+    for (long i = 0; i < woff; i++) gW[i] = 0;
+    for (int l = nl - 1; l >= 0; l--) {
+        int cin = chans[l], cout = chans[l + 1];
+        const cplx *x = a[l];
+        /* weight gradient */
+        for (int d = 0; d < 9; d++)
+            for (int cp = 0; cp < cin; cp++) {
+                cplx acc[64][16];
+                for (int c = 0; c < cout; c++)
+                    for (int k = 0; k < 16; k++) acc[c][k] = 0;
+                for (long n = 0; n < V; n++) {
+                    cplx z[12];
+                    transport_site(L, bc_t, U, d, n, x + (long)cp * V * 12, z);
+                    for (int c = 0; c < cout; c++)
+                        for (int al = 0; al < 4; al++)
+                            for (int be = 0; be < 4; be++)
+                                for (int aa = 0; aa < 3; aa++)
+                                    acc[c][al * 4 + be] += g[((long)c * V + n) * 12 + al * 3 + aa] * conj(z[be * 3 + aa]);
+                }
+                for (int c = 0; c < cout; c++)
+                    for (int k = 0; k < 16; k++) gW[woffs[l] + (((long)d * cout + c) * cin + cp) * 16 + k] = acc[c][k];
+            }
+        if (l == 0) break;
+        /* g_prev(c') = sum_d T_d^dag sum_c W_d[c][c']^dag g_c */
+        cplx *gp = malloc(sizeof(cplx) * 12 * V * cin);
+        cplx *h = malloc(sizeof(cplx) * 12 * V);
+        for (int cp = 0; cp < cin; cp++) {
+            for (long i = 0; i < 12 * V; i++) gp[(long)cp * V * 12 + i] = 0;
+            for (int d = 0; d < 9; d++) {
+                for (long n = 0; n < V; n++)
+                    for (int be = 0; be < 4; be++)
+                        for (int aa = 0; aa < 3; aa++) {
+                            cplx s = 0;
+                            for (int c = 0; c < cout; c++) {
+                                const cplx *w = W + woffs[l] + (((long)d * cout + c) * cin + cp) * 16;
+                                for (int al = 0; al < 4; al++)
+                                    s += conj(w[al * 4 + be]) * g[((long)c * V + n) * 12 + al * 3 + aa];
+                            }
+                            h[n * 12 + be * 3 + aa] = s;
+                        }
+                for (long m = 0; m < V; m++) {
+                    cplx z[12];
+                    transport_adj_site(L, bc_t, U, d, m, h, z);
+                    for (int k = 0; k < 12; k++) gp[((long)cp * V + m) * 12 + k] += z[k];
+                }
+            }
+        }
+        free(h);
+        free(g);
+        g = gp;
+    }
+    free(g);
+    for (int l = 0; l < nl; l++) free(a[l + 1]);
+    for (long i = 0; i < woff; i++) {
+        cplx v = gW[i];
+        grad[2 * i] = 2 * creal(v);
+        grad[2 * i + 1] = 2 * cimag(v);
+    }
+    return loss;
+}
