@@ -88,7 +88,8 @@ typedef struct {
     int max_outer, max_inner;
     int bc_t;           /* +1 periodic, -1 antiperiodic in t (must match qcd_set_boundary) */
     int sap_storage;    /* QCD_F32 (plain) or QCD_F16 (half storage, FP32 arithmetic)    */
-    int learned;        /* reserved, 0                                                 */
+    int learned;        /* 1: precondition with M_SAP + N (1 - D M_SAP), N the learned
+                           correction (qcd_learned_*); 0: plain SAP                    */
     int sap_ctas;       /* CTAs per SAP block in the SSOR kernel, 0 = context default
                            (qcd_set_sap_ctas); results do not depend on it            */
 } qcd_params;
@@ -192,6 +193,36 @@ int qcd_set_sap_ctas(qcd_ctx *ctx, int min_ctas);
 int qcd_autotune(qcd_ctx *ctx, const double *b, int nrhs, const qcd_params *base, qcd_params *best,
                  double *best_ms, int max_candidates);
 
+/* ---- learned correction (no counterpart in the paper) -----------------------
+ * N is a linear, gauge-covariant network of 3 parallel-transport layers with
+ * 1 -> 8 -> 8 -> 1 channels: y_c(n) = sum_{d=0..8} sum_{c'} W_d[c][c'] (T_d x_c')(n),
+ * T_0 = 1, T_{2mu+1} x(n) = U_mu(n) x(n+mu), T_{2mu+2} x(n) = U_mu(n-mu)^dag x(n-mu)
+ * (the directions 1..8 are (mu, forward/backward)), W_d[c][c'] a 4x4 complex
+ * spin matrix.  Weights: complex64 [layer][9][cout][cin][4][4], concatenated.
+ * Layers run on the tensor cores in BF16 with FP32 accumulation.  Because N is
+ * linear, M_SAP + N (1 - D M_SAP) is a fixed preconditioner for the inner
+ * BiCGStab (qcd_params.learned = 1). */
+long qcd_learned_weight_count(void);
+/* w: complex64 [n], host or device; resets the optimiser state */
+int qcd_learned_set_weights(qcd_ctx *ctx, const float *w, long n);
+/* w: host complex64 [n] */
+int qcd_learned_get_weights(qcd_ctx *ctx, float *w, long n);
+/* out = N(in), complex64 [V][4][3], host or device */
+int qcd_learned_apply(qcd_ctx *ctx, float *out, const float *in);
+/* One training pair: loss = |N(rho) - eps|^2 / |eps|^2 and its gradient grad
+ * (host float [2n]: 2 (Re, Im) of dL/dW* per complex weight).  rho, eps:
+ * complex64 [V][4][3], host or device. */
+int qcd_learned_loss_grad(qcd_ctx *ctx, const float *rho, const float *eps, double *loss, float *grad);
+/* Trains N on npairs pairs made from the sources r_k (complex64
+ * [npairs][V][4][3], host or device) with the plain SAP of *p:
+ * rho_k = r_k - D M_SAP r_k, eps_k = D^{-1} rho_k (the error of M_SAP r_k,
+ * solved in FP64 to 1e-9), loss sum_k |N(rho_k) - eps_k|^2 / |eps_k|^2, Adam
+ * with learning rate lr over mini-batches of `batch` pairs for `epochs`
+ * epochs.  history (may be NULL): [epochs + 1] mean loss before training and
+ * after each epoch.  Requires qcd_learned_set_weights (the initial weights). */
+int qcd_learned_train(qcd_ctx *ctx, const float *sources, int npairs, const qcd_params *p, int epochs, int batch,
+                      float lr, double *history);
+
 /* ---- measurement hooks -------------------------------------------------- */
 
 /* Kernel classes timed when profiling is on. */
@@ -202,7 +233,8 @@ enum {
     QCD_K_SAPHOP = 3,   /* SAP block / cross-block hop updates       */
     QCD_K_BLAS = 4,     /* BiCGStab vector updates and reductions    */
     QCD_K_OTHER = 5,    /* layout conversion, clover build           */
-    QCD_K_COUNT = 6
+    QCD_K_LEARNED = 6,  /* learned correction (layers, gradients)    */
+    QCD_K_COUNT = 7
 };
 
 /* on != 0: bracket every kernel launch with CUDA events on the context

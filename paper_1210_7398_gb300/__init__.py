@@ -20,13 +20,15 @@ LIB_PATH = os.path.join(_HERE, "libqcd.so")
 QCD_OK, QCD_ERR_ARG, QCD_ERR_CUDA, QCD_ERR_OOM = 0, -1, -2, -3
 QCD_ERR_SINGULAR, QCD_ERR_NOCONV, QCD_ERR_BREAKDOWN, QCD_ERR_TIMEOUT, QCD_ERR_STATE = -4, -5, -6, -7, -8
 QCD_F64, QCD_F32, QCD_F16, QCD_BF16 = 0, 1, 2, 3
-QCD_K_DSLASH32, QCD_K_DSLASH64, QCD_K_SSOR, QCD_K_SAPHOP, QCD_K_BLAS, QCD_K_OTHER = 0, 1, 2, 3, 4, 5
-KERNEL_CLASSES = ("dslash32", "dslash64", "ssor", "saphop", "blas", "other")
+QCD_K_DSLASH32, QCD_K_DSLASH64, QCD_K_SSOR, QCD_K_SAPHOP, QCD_K_BLAS, QCD_K_OTHER, QCD_K_LEARNED = range(7)
+KERNEL_CLASSES = ("dslash32", "dslash64", "ssor", "saphop", "blas", "other", "learned")
 
 EXPORTS = ("qcd_create", "qcd_destroy", "qcd_last_error", "qcd_set_boundary", "qcd_load_gauge",
            "qcd_build_clover", "qcd_apply_D", "qcd_sap_precondition", "qcd_solve", "qcd_set_profiling",
            "qcd_kernel_stats", "qcd_launch_count", "qcd_bench_dslash", "qcd_sap_precondition_noalloc",
-           "qcd_set_sap_ctas", "qcd_set_graphs", "qcd_autotune")
+           "qcd_set_sap_ctas", "qcd_set_graphs", "qcd_autotune", "qcd_learned_weight_count",
+           "qcd_learned_set_weights", "qcd_learned_get_weights", "qcd_learned_apply", "qcd_learned_loss_grad",
+           "qcd_learned_train")
 
 
 class QcdError(RuntimeError):
@@ -80,6 +82,12 @@ def load_library(path: str = LIB_PATH):
         "qcd_set_profiling": (I, [P, I]),
         "qcd_set_sap_ctas": (I, [P, I]),
         "qcd_set_graphs": (I, [P, I]),
+        "qcd_learned_weight_count": (ctypes.c_long, []),
+        "qcd_learned_set_weights": (I, [P, P, ctypes.c_long]),
+        "qcd_learned_get_weights": (I, [P, P, ctypes.c_long]),
+        "qcd_learned_apply": (I, [P, P, P]),
+        "qcd_learned_loss_grad": (I, [P, P, P, ctypes.POINTER(D), P]),
+        "qcd_learned_train": (I, [P, P, I, ctypes.POINTER(qcd_params), I, I, ctypes.c_float, P]),
         "qcd_autotune": (I, [P, P, I, ctypes.POINTER(qcd_params), ctypes.POINTER(qcd_params),
                              ctypes.POINTER(D), I]),
         "qcd_kernel_stats": (I, [P, I, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(D), I]),
@@ -190,6 +198,60 @@ def params_dict(p: qcd_params) -> dict:
     return {"block": list(p.block), "subblock": list(p.subblock), "omega": p.omega, "nsweep": p.nsweep,
             "nsap": p.nsap, "sap_storage": {QCD_F32: "f32", QCD_F16: "f16"}.get(p.sap_storage, p.sap_storage),
             "sap_ctas": p.sap_ctas, "learned": p.learned}
+
+
+LEARNED_CHANS = (1, 8, 8, 1)
+
+
+def qcd_learned_weight_count() -> int:
+    return int(load_library().qcd_learned_weight_count())
+
+
+def qcd_learned_set_weights(ctx, w):
+    """w: complex64 array/tensor [qcd_learned_weight_count()] (layers concatenated, each [9][cout][cin][4][4])."""
+    return _check(ctx, load_library().qcd_learned_set_weights(ctx, _ptr(w), int(qcd_learned_weight_count())))
+
+
+def qcd_learned_get_weights(ctx):
+    w = np.empty(qcd_learned_weight_count(), dtype=np.complex64)
+    _check(ctx, load_library().qcd_learned_get_weights(ctx, _ptr(w), len(w)))
+    return w
+
+
+def qcd_learned_apply(ctx, out, inp):
+    return _check(ctx, load_library().qcd_learned_apply(ctx, _ptr(out), _ptr(inp)))
+
+
+def qcd_learned_loss_grad(ctx, rho, eps):
+    """(loss, grad): grad float32 [2 n] = 2 (Re, Im) of dL/dW* for one pair."""
+    loss = ctypes.c_double()
+    g = np.empty(2 * qcd_learned_weight_count(), dtype=np.float32)
+    _check(ctx, load_library().qcd_learned_loss_grad(ctx, _ptr(rho), _ptr(eps), ctypes.byref(loss), _ptr(g)))
+    return loss.value, g
+
+
+def qcd_learned_train(ctx, sources, npairs, params: qcd_params, epochs, batch, lr):
+    """Trains the correction on pairs made from ``sources``; returns the loss history [epochs + 1]."""
+    hist = np.zeros(epochs + 1)
+    _check(ctx, load_library().qcd_learned_train(ctx, _ptr(sources), int(npairs), ctypes.byref(params), int(epochs),
+                                                 int(batch), ctypes.c_float(lr), _ptr(hist)))
+    return hist
+
+
+def learned_init_weights(seed: int, scale_last: float = 0.01) -> np.ndarray:
+    """Seeded initial weights (complex64): N(0, 1/fan_in) per component, last layer scaled down
+    so the untrained correction starts near zero."""
+    import qcd_inputs as qi
+    parts = []
+    off = 0
+    for l in range(len(LEARNED_CHANS) - 1):
+        cin, cout = LEARNED_CHANS[l], LEARNED_CHANS[l + 1]
+        n = 9 * cout * cin * 16
+        r = qi.normals(seed + 7919 * l, 2 * n)
+        sc = (1.0 / np.sqrt(9 * cin * 4)) * (scale_last if l == len(LEARNED_CHANS) - 2 else 1.0)
+        parts.append(sc * (r[0::2] + 1j * r[1::2]))
+        off += n
+    return np.concatenate(parts).astype(np.complex64)
 
 
 def qcd_set_graphs(ctx, on: bool):

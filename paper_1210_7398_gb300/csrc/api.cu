@@ -1,6 +1,7 @@
 // C ABI of the solver library (declared in include/qcd.h): argument checks,
 // context and memory management, host/device staging and the launch
 // bookkeeping used for measurement.
+#include <algorithm>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
@@ -141,7 +142,8 @@ int check_params(qcd_ctx *c, const qcd_params *p) {
     if (p->nsweep < 1 || p->nsap < 1) return fail(c, QCD_ERR_ARG, "nsweep and nsap must be >= 1");
     if (p->sap_storage != QCD_F32 && p->sap_storage != QCD_F16)
         return fail(c, QCD_ERR_ARG, "sap_storage must be QCD_F32 or QCD_F16");
-    if (p->learned != 0) return fail(c, QCD_ERR_ARG, "learned correction not available");
+    if (p->learned != 0 && p->learned != 1) return fail(c, QCD_ERR_ARG, "learned must be 0 or 1");
+    if (p->learned == 1 && !c->net.ready) return fail(c, QCD_ERR_STATE, "learned = 1 needs qcd_learned_set_weights");
     if (p->bc_t != c->bc_t) return fail(c, QCD_ERR_ARG, "params.bc_t differs from the context boundary condition");
     if (p->kappa != c->kappa || p->csw != c->csw)
         return fail(c, QCD_ERR_ARG, "params.kappa/csw differ from the clover field built");
@@ -195,7 +197,9 @@ void qcd_destroy(qcd_ctx *c) {
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
-    void *bufs[] = {c->U64, c->U32, c->F64, c->F32, c->d_status, c->d_red, c->d_scalars, c->d_bicg, c->d_mask,
+    void *bufs[] = {c->net.W, c->net.grad, c->net.m, c->net.v, c->net.B, c->net.P, c->net.scal, c->net.act,
+                    c->net.pairs,
+                    c->U64, c->U32, c->F64, c->F32, c->d_status, c->d_red, c->d_scalars, c->d_bicg, c->d_mask,
                     c->ws64, c->ws32,
                     c->d_io, c->bench_in, c->bench_out, c->plan.d_origin[0] /* the plan's table region */,
                     c->plan.d_rec};
@@ -422,6 +426,176 @@ int qcd_kernel_stats(qcd_ctx *c, int kclass, long *launches, double *ms, int res
 }
 
 long qcd_launch_count(const qcd_ctx *c) { return c ? c->total_launches : 0; }
+
+long qcd_learned_weight_count(void) { return learned_weight_count(); }
+
+int qcd_learned_set_weights(qcd_ctx *c, const float *w, long n) {
+    int rc = ready(c);
+    if (rc) return rc;
+    if (!c->have_gauge) return fail(c, QCD_ERR_STATE, "qcd_load_gauge must be called first");
+    if (!w || n != learned_weight_count()) return fail(c, QCD_ERR_ARG, "weight count mismatch");
+    if ((rc = learned_set_weights(c, (const float2 *)w, is_device_ptr(w)))) return rc;
+    QCD_CUDA(c, cudaStreamSynchronize(c->stream));
+    return QCD_OK;
+}
+
+int qcd_learned_get_weights(qcd_ctx *c, float *w, long n) {
+    int rc = ready(c);
+    if (rc) return rc;
+    if (!w || n != learned_weight_count()) return fail(c, QCD_ERR_ARG, "weight count mismatch");
+    return learned_get_weights(c, (float2 *)w);
+}
+
+// stage a complex64 [k][V][12] field (host or device) into the internal plane layout
+static int stage_in32(qcd_ctx *c, float4 *dst, const float *src, int k, char *scratch) {
+    const size_t bytes = 8 * 12 * (size_t)c->lat.V * k;
+    const void *s = src;
+    if (!is_device_ptr(src)) {
+        QCD_CUDA(c, cudaMemcpyAsync(scratch, src, bytes, cudaMemcpyHostToDevice, c->stream));
+        s = scratch;
+    }
+    return spinor32_to_internal(c, dst, (const float2 *)s, k);
+}
+
+int qcd_learned_apply(qcd_ctx *c, float *out, const float *in) {
+    int rc = ready(c);
+    if (rc) return rc;
+    if (!c->net.ready) return fail(c, QCD_ERR_STATE, "qcd_learned_set_weights must be called first");
+    if (!out || !in) return fail(c, QCD_ERR_ARG, "NULL argument");
+    const size_t bytes = 8 * 12 * (size_t)c->lat.V;
+    if ((rc = ensure_io(c, 3 * bytes))) return rc;
+    char *io = (char *)c->d_io;
+    float4 *x = (float4 *)io, *y = (float4 *)(io + bytes);
+    if ((rc = stage_in32(c, x, in, 1, io + 2 * bytes))) return rc;
+    if ((rc = learned_forward(c, y, x))) return rc;
+    const bool dev_out = is_device_ptr(out);
+    if ((rc = spinor32_from_internal(c, (float2 *)(dev_out ? (char *)out : io + 2 * bytes), y, 1))) return rc;
+    if (!dev_out) QCD_CUDA(c, cudaMemcpyAsync(out, io + 2 * bytes, bytes, cudaMemcpyDeviceToHost, c->stream));
+    QCD_CUDA(c, cudaStreamSynchronize(c->stream));
+    return QCD_OK;
+}
+
+int qcd_learned_loss_grad(qcd_ctx *c, const float *rho, const float *eps, double *loss, float *grad) {
+    int rc = ready(c);
+    if (rc) return rc;
+    if (!c->net.ready) return fail(c, QCD_ERR_STATE, "qcd_learned_set_weights must be called first");
+    if (!rho || !eps) return fail(c, QCD_ERR_ARG, "NULL argument");
+    const size_t bytes = 8 * 12 * (size_t)c->lat.V;
+    if ((rc = ensure_io(c, 5 * bytes))) return rc;
+    char *io = (char *)c->d_io;
+    float4 *r = (float4 *)io, *e4 = (float4 *)(io + bytes), *y = (float4 *)(io + 2 * bytes);
+    float2 *es = (float2 *)(io + 3 * bytes);
+    if ((rc = stage_in32(c, r, rho, 1, io + 4 * bytes))) return rc;
+    if ((rc = stage_in32(c, e4, eps, 1, io + 4 * bytes))) return rc;
+    if ((rc = plane_to_site(c, es, e4))) return rc;
+    if ((rc = learned_zero_grad(c))) return rc;
+    double l = 0;
+    if ((rc = learned_loss_grad(c, r, es, &l, y))) return rc;
+    if (loss) *loss = l;
+    if (grad) {
+        QCD_CUDA(c, cudaMemcpyAsync(grad, c->net.grad, sizeof(float2) * learned_weight_count(),
+                                    cudaMemcpyDeviceToHost, c->stream));
+        QCD_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return QCD_OK;
+}
+
+int qcd_learned_train(qcd_ctx *c, const float *sources, int npairs, const qcd_params *p, int epochs, int batch,
+                      float lr, double *history) {
+    int rc = ready(c);
+    if (rc) return rc;
+    if ((rc = need_clover(c))) return rc;
+    if (!c->net.ready) return fail(c, QCD_ERR_STATE, "qcd_learned_set_weights must be called first");
+    if (!sources || npairs < 1 || epochs < 0 || batch < 1 || !(lr > 0)) return fail(c, QCD_ERR_ARG, "bad training arguments");
+    qcd_params pp = *p;
+    pp.learned = 0;  // the pairs measure the error of plain SAP
+    if ((rc = check_params(c, &pp))) return rc;
+    if ((rc = sap_prepare(c, pp.block, pp.subblock, pp.sap_storage == QCD_F16))) return rc;
+    const long V = c->lat.V;
+    const size_t f32 = 96 * (size_t)V, f64 = 192 * (size_t)V;
+    // pairs: rho (plane FP32) then eps (site FP32), per pair
+    const size_t need = 2 * f32 * (size_t)npairs;
+    if (c->net.pairs_bytes < need) {
+        dev_free(c, c->net.pairs);
+        c->net.pairs = nullptr;
+        c->net.pairs_bytes = 0;
+        if ((rc = dev_alloc(c, (void **)&c->net.pairs, need))) return rc;
+        c->net.pairs_bytes = need;
+    }
+    char *pairs = (char *)c->net.pairs;
+    const int chunk = npairs < 16 ? npairs : 16;
+    // chunk buffers: staging, r, x, Dx, SAP work (2), FP64 rhs and solution
+    void *tmpb = nullptr;
+    if ((rc = dev_alloc(c, &tmpb, (size_t)chunk * (6 * f32 + 2 * f64)))) return rc;
+    struct Free {
+        qcd_ctx *c;
+        void *p;
+        ~Free() { dev_free(c, p); }
+    } guard{c, tmpb};
+    char *tb = (char *)tmpb;
+    char *stg = tb;
+    float4 *r = (float4 *)(tb + chunk * f32), *x = (float4 *)(tb + 2 * chunk * f32);
+    float4 *dx = (float4 *)(tb + 3 * chunk * f32), *work = (float4 *)(tb + 4 * chunk * f32);
+    double2 *b64 = (double2 *)(tb + 6 * chunk * f32), *x64 = (double2 *)(tb + 6 * chunk * f32 + chunk * f64);
+    qcd_params ps = pp;
+    ps.tol = 1e-9;
+    const bool dev_src = is_device_ptr(sources);
+    for (int k0 = 0; k0 < npairs; k0 += chunk) {
+        const int k = std::min(chunk, npairs - k0);
+        const float *src = sources + (size_t)k0 * 24 * V;
+        if (!dev_src) {
+            QCD_CUDA(c, cudaMemcpyAsync(stg, src, (size_t)k * f32, cudaMemcpyHostToDevice, c->stream));
+            src = (const float *)stg;
+        }
+        if ((rc = spinor32_to_internal(c, r, (const float2 *)src, k))) return rc;
+        if ((rc = sap_apply(c, x, r, work, pp.omega, pp.nsweep, pp.nsap, k))) return rc;
+        if ((rc = dslash32(c, dx, x, k))) return rc;
+        if ((rc = sub_plane(c, dx, r, dx, k))) return rc;  // rho = r - D M_SAP r
+        for (int j = 0; j < k; j++)
+            QCD_CUDA(c, cudaMemcpyAsync(pairs + (size_t)(k0 + j) * 2 * f32, (char *)dx + j * f32, f32,
+                                        cudaMemcpyDeviceToDevice, c->stream));
+        // eps = D^{-1} rho in FP64
+        if ((rc = spinor32_to_64(c, b64, dx, k))) return rc;
+        QCD_CUDA(c, cudaMemsetAsync(x64, 0, (size_t)k * f64, c->stream));
+        qcd_stats st;
+        std::memset(&st, 0, sizeof(st));
+        int s = solve(c, x64, b64, &ps, k, &st);
+        if (s != QCD_OK) return s == QCD_ERR_NOCONV || s == QCD_ERR_BREAKDOWN ? fail(c, s, "training pairs: solve failed") : s;
+        if ((rc = spinor64_to_32(c, x, x64, k))) return rc;
+        for (int j = 0; j < k; j++)
+            if ((rc = plane_to_site(c, (float2 *)(pairs + (size_t)(k0 + j) * 2 * f32 + f32), x + j * 6 * V))) return rc;
+    }
+    // training
+    float4 *ybuf = dx;
+    auto pair_loss = [&](int k, bool grad, double *l) -> int {
+        const float4 *rho = (const float4 *)(pairs + (size_t)k * 2 * f32);
+        const float2 *eps = (const float2 *)(pairs + (size_t)k * 2 * f32 + f32);
+        if (!grad) QCD_CUDA(c, cudaMemsetAsync(c->net.grad, 0, sizeof(float2) * learned_weight_count(), c->stream));
+        return learned_loss_grad(c, rho, eps, l, ybuf);
+    };
+    double total = 0;
+    for (int k = 0; k < npairs; k++) {
+        double l = 0;
+        if ((rc = pair_loss(k, false, &l))) return rc;
+        total += l;
+    }
+    if (history) history[0] = total / npairs;
+    for (int e = 0; e < epochs; e++) {
+        total = 0;
+        for (int b0 = 0; b0 < npairs; b0 += batch) {
+            if ((rc = learned_zero_grad(c))) return rc;
+            for (int k = b0; k < std::min(npairs, b0 + batch); k++) {
+                double l = 0;
+                if ((rc = pair_loss(k, true, &l))) return rc;
+                total += l;
+            }
+            if ((rc = learned_adam(c, lr))) return rc;
+        }
+        if (history) history[e + 1] = total / npairs;
+    }
+    QCD_CUDA(c, cudaStreamSynchronize(c->stream));
+    return QCD_OK;
+}
 
 int qcd_bench_dslash(qcd_ctx *c, int prec, int nrhs, int iters) {
     int rc = ready(c);

@@ -1,0 +1,614 @@
+// K7: the learned correction (a project addition; the paper has none): a
+// linear, gauge-covariant network of parallel-transport layers
+//   y_c(n) = sum_{d=0..8} sum_{c'} W_d[c][c'] (T_d x_{c'})(n),
+// T_0 = 1, T_{2mu} x(n) = U_mu(n) x(n+mu), T_{2mu+1} x(n) = U_mu(n-mu)^dag x(n-mu),
+// W_d[c][c'] a 4x4 complex spin matrix.  Because W acts on spin and channel and
+// T on colour and site, a layer is, per direction, a dense contraction over
+// (input channel, spin) for every (site, colour) row: a GEMM with M = 3V rows,
+// K = 9 x Cin x 4 complex, N = Cout x 4 complex.  It runs on the tensor cores
+// in BF16 with FP32 accumulation (mma.sync m16n8k16): a CTA gathers and
+// transports the inputs of 32 sites for one direction into shared memory (the
+// A tile), loads that direction's weights as a real 2x2-block matrix (the B
+// tile), multiplies, and moves to the next direction with the accumulators
+// in registers.  The data gradient is the same kernel with the adjoint
+// weights (T_d^dag = T_{opposite d} and W commutes with T); the weight
+// gradient is sum over rows of A^T G, computed the same way with the
+// reduction over rows.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "fields.cuh"
+#include "qcd_internal.h"
+
+namespace qcd {
+namespace {
+
+constexpr int kTileSites = 32;             // sites per CTA tile
+constexpr int kTileRows = 3 * kTileSites;  // (site, colour) rows
+constexpr int kLayerThreads = 192;         // 6 warps, one 16-row MMA tile each
+
+// activation formats
+enum { PLANE32 = 0, SITE16 = 1, SITE32 = 2 };
+
+template <int FMT> __device__ __forceinline__ float2 act_ld(const void *base, long V, int ch, long n, int k) {
+    if constexpr (FMT == PLANE32) {
+        const float4 *p = static_cast<const float4 *>(base) + (long)ch * 6 * V + (long)(k >> 1) * V + n;
+        const float4 v = *p;
+        return (k & 1) ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
+    } else if constexpr (FMT == SITE16) {
+        return __bfloat1622float2(static_cast<const __nv_bfloat162 *>(base)[((long)ch * V + n) * 12 + k]);
+    } else {
+        return static_cast<const float2 *>(base)[((long)ch * V + n) * 12 + k];
+    }
+}
+template <int FMT> __device__ __forceinline__ void act_st(void *base, long V, int ch, long n, int k, float2 v) {
+    if constexpr (FMT == PLANE32) {
+        float2 *p = reinterpret_cast<float2 *>(static_cast<float4 *>(base) + (long)ch * 6 * V + (long)(k >> 1) * V + n);
+        p[k & 1] = v;
+    } else if constexpr (FMT == SITE16) {
+        static_cast<__nv_bfloat162 *>(base)[((long)ch * V + n) * 12 + k] = __float22bfloat162_rn(v);
+    } else {
+        static_cast<float2 *>(base)[((long)ch * V + n) * 12 + k] = v;
+    }
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+__device__ __forceinline__ void mma_bf16(float c[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// z = T_d x_ch (one site, 12 complex, FP32); returns false when n is outside the lattice
+template <int FMT>
+__device__ __forceinline__ void transport(const void *x, int ch, const float2 *__restrict__ U, const Geo &g, int d,
+                                          long n, float2 z[12]) {
+    if (d == 0) {
+#pragma unroll
+        for (int k = 0; k < 12; k++) z[k] = act_ld<FMT>(x, g.V, ch, n, k);
+        return;
+    }
+    const int mu = (d - 1) >> 1;
+    const bool fwd = ((d - 1) & 1) == 0;
+    int xc[4];
+    site_coords(g, n, xc);
+    long stride = 1;
+    for (int m = 0; m < mu; m++) stride *= g.L[m];
+    long m;
+    float sgn = 1.f;
+    if (fwd) {
+        m = (xc[mu] == g.L[mu] - 1) ? n - stride * (g.L[mu] - 1) : n + stride;
+        if (mu == 3 && xc[3] == g.L[3] - 1) sgn = (float)g.bc_t;
+    } else {
+        m = (xc[mu] == 0) ? n + stride * (g.L[mu] - 1) : n - stride;
+        if (mu == 3 && xc[3] == 0) sgn = (float)g.bc_t;
+    }
+    const long ls = fwd ? n : m;
+    float2 u[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) u[i] = __ldg(U + (long)(mu * 9 + i) * g.V + ls);
+    float2 xm[12];
+#pragma unroll
+    for (int k = 0; k < 12; k++) xm[k] = act_ld<FMT>(x, g.V, ch, m, k);
+#pragma unroll
+    for (int s = 0; s < 4; s++)
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int b = 0; b < 3; b++) acc = fwd ? cfma(u[a * 3 + b], xm[s * 3 + b], acc) : cfmac(u[b * 3 + a], xm[s * 3 + b], acc);
+            z[s * 3 + a] = cscale(acc, sgn);
+        }
+}
+
+// y = layer(x): CIN -> COUT channels.  Bt: [9][N][KDP] BF16, N = COUT*8, KDP = max(16, CIN*8).
+template <int CIN, int COUT, int FIN, int FOUT>
+__global__ void __launch_bounds__(kLayerThreads) k_layer(void *y, const void *x, const float2 *__restrict__ U,
+                                                         const __nv_bfloat16 *__restrict__ Bt, Geo g) {
+    constexpr int KD = CIN * 8, KDP = KD < 16 ? 16 : KD, N = COUT * 8, NT = N / 8;
+    constexpr int AS = KDP + 8;  // padded row strides (bank spread)
+    __shared__ __align__(16) __nv_bfloat16 A[kTileRows][AS];
+    __shared__ __align__(16) __nv_bfloat16 B[N][AS];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gq = lane >> 2, tq = lane & 3;
+    const long n0 = (long)blockIdx.x * kTileSites;
+    for (int i = tid; i < kTileRows * AS; i += kLayerThreads) (&A[0][0])[i] = __float2bfloat16(0.f);
+    float acc[NT][4];
+#pragma unroll
+    for (int j = 0; j < NT; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    for (int d = 0; d < 9; d++) {
+        __syncthreads();
+        // A tile: rows (site, colour), columns (input channel, spin, re/im)
+        for (int item = tid; item < kTileSites * CIN; item += kLayerThreads) {
+            const int s = item % kTileSites, ch = item / kTileSites;
+            const long n = n0 + s;
+            float2 z[12];
+            if (n < g.V) transport<FIN>(x, ch, U, g, d, n, z);
+            else
+#pragma unroll
+                for (int k = 0; k < 12; k++) z[k] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int be = 0; be < 4; be++)
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    const int col = (ch * 4 + be) * 2;
+                    *reinterpret_cast<uint32_t *>(&A[s * 3 + a][col]) = pack_bf16(z[be * 3 + a].x, z[be * 3 + a].y);
+                }
+        }
+        // B tile of direction d
+        const __nv_bfloat16 *Bd = Bt + (long)d * N * KDP;
+        for (int i = tid; i < N * KDP; i += kLayerThreads) B[i / KDP][i % KDP] = Bd[i];
+        __syncthreads();
+        const int r0 = warp * 16;
+#pragma unroll
+        for (int k0 = 0; k0 < KDP; k0 += 16) {
+            const uint32_t a0 = *reinterpret_cast<const uint32_t *>(&A[r0 + gq][k0 + 2 * tq]);
+            const uint32_t a1 = *reinterpret_cast<const uint32_t *>(&A[r0 + gq + 8][k0 + 2 * tq]);
+            const uint32_t a2 = *reinterpret_cast<const uint32_t *>(&A[r0 + gq][k0 + 2 * tq + 8]);
+            const uint32_t a3 = *reinterpret_cast<const uint32_t *>(&A[r0 + gq + 8][k0 + 2 * tq + 8]);
+#pragma unroll
+            for (int j = 0; j < NT; j++) {
+                const uint32_t b0 = *reinterpret_cast<const uint32_t *>(&B[j * 8 + gq][k0 + 2 * tq]);
+                const uint32_t b1 = *reinterpret_cast<const uint32_t *>(&B[j * 8 + gq][k0 + 2 * tq + 8]);
+                mma_bf16(acc[j], a0, a1, a2, a3, b0, b1);
+            }
+        }
+    }
+    // epilogue: accumulator (row, column pair) -> output channel, spin, colour (complex)
+#pragma unroll
+    for (int j = 0; j < NT; j++) {
+        const int col = j * 8 + 2 * tq;  // even: the (re, im) pair of one complex output
+        const int c = col / 8, al = (col % 8) / 2;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int r = warp * 16 + gq + 8 * h;
+            const long n = n0 + r / 3;
+            if (n < g.V) act_st<FOUT>(y, g.V, c, n, al * 3 + r % 3, make_float2(acc[j][2 * h], acc[j][2 * h + 1]));
+        }
+    }
+}
+
+// P[d][k][j] += sum over rows of A_d[row][k] G[row][j]  (real; A from x, G from the output gradient)
+template <int CIN, int COUT, int FIN>
+__global__ void __launch_bounds__(128) k_wgrad(float *__restrict__ P, const void *x, const float2 *__restrict__ G,
+                                               const float2 *__restrict__ U, Geo g, int ntiles) {
+    constexpr int KD = CIN * 8, KDP = KD < 16 ? 16 : KD, N = COUT * 8, NM = KDP / 16, NT = N / 8;
+    constexpr int PAIRS = NM * NT, PW = (PAIRS + 3) / 4;  // (m-tile, n-tile) pairs per warp
+    constexpr int RS = kTileRows + 8;
+    __shared__ __align__(16) __nv_bfloat16 At[KDP][RS];
+    __shared__ __align__(16) __nv_bfloat16 Gt[N][RS];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gq = lane >> 2, tq = lane & 3;
+    for (int i = tid; i < KDP * RS; i += 128) (&At[0][0])[i] = __float2bfloat16(0.f);
+    for (int d = 0; d < 9; d++) {
+        float acc[PW][4];
+#pragma unroll
+        for (int q = 0; q < PW; q++) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            const long n0 = (long)tile * kTileSites;
+            __syncthreads();
+            for (int item = tid; item < kTileSites * CIN; item += 128) {
+                const int s = item % kTileSites, ch = item / kTileSites;
+                const long n = n0 + s;
+                float2 z[12];
+                if (n < g.V) transport<FIN>(x, ch, U, g, d, n, z);
+                else
+#pragma unroll
+                    for (int k = 0; k < 12; k++) z[k] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int be = 0; be < 4; be++)
+#pragma unroll
+                    for (int a = 0; a < 3; a++) {
+                        const int col = (ch * 4 + be) * 2;
+                        At[col][s * 3 + a] = __float2bfloat16(z[be * 3 + a].x);
+                        At[col + 1][s * 3 + a] = __float2bfloat16(z[be * 3 + a].y);
+                    }
+            }
+            for (int item = tid; item < kTileSites * COUT * 12; item += 128) {
+                const int s = item % kTileSites, rest = item / kTileSites, k = rest % 12, c = rest / 12;
+                const long n = n0 + s;
+                const float2 v = n < g.V ? G[((long)c * g.V + n) * 12 + k] : make_float2(0.f, 0.f);
+                const int al = k / 3, a = k % 3, col = (c * 4 + al) * 2;
+                Gt[col][s * 3 + a] = __float2bfloat16(v.x);
+                Gt[col + 1][s * 3 + a] = __float2bfloat16(v.y);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r0 = 0; r0 < kTileRows; r0 += 16) {
+#pragma unroll
+                for (int q = 0; q < PW; q++) {
+                    const int pr = warp + 4 * q;
+                    if (pr >= PAIRS) break;
+                    const int m0 = (pr / NT) * 16, j0 = (pr % NT) * 8;
+                    const uint32_t a0 = *reinterpret_cast<const uint32_t *>(&At[m0 + gq][r0 + 2 * tq]);
+                    const uint32_t a1 = *reinterpret_cast<const uint32_t *>(&At[m0 + gq + 8][r0 + 2 * tq]);
+                    const uint32_t a2 = *reinterpret_cast<const uint32_t *>(&At[m0 + gq][r0 + 2 * tq + 8]);
+                    const uint32_t a3 = *reinterpret_cast<const uint32_t *>(&At[m0 + gq + 8][r0 + 2 * tq + 8]);
+                    const uint32_t b0 = *reinterpret_cast<const uint32_t *>(&Gt[j0 + gq][r0 + 2 * tq]);
+                    const uint32_t b1 = *reinterpret_cast<const uint32_t *>(&Gt[j0 + gq][r0 + 2 * tq + 8]);
+                    mma_bf16(acc[q], a0, a1, a2, a3, b0, b1);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < PW; q++) {
+            const int pr = warp + 4 * q;
+            if (pr >= PAIRS) break;
+            const int m0 = (pr / NT) * 16, j0 = (pr % NT) * 8;
+            float *Pd = P + (long)d * KDP * N;
+            atomicAdd(&Pd[(m0 + gq) * N + j0 + 2 * tq], acc[q][0]);
+            atomicAdd(&Pd[(m0 + gq) * N + j0 + 2 * tq + 1], acc[q][1]);
+            atomicAdd(&Pd[(m0 + gq + 8) * N + j0 + 2 * tq], acc[q][2]);
+            atomicAdd(&Pd[(m0 + gq + 8) * N + j0 + 2 * tq + 1], acc[q][3]);
+        }
+    }
+}
+
+// B matrices (BF16, [9][N][KDP]) of a layer from its complex weights W [9][cout][cin][4][4];
+// adjoint: the layer x -> sum_d W_d^dag T_{opposite d} x (cin and cout swap roles)
+__global__ void k_build_B(__nv_bfloat16 *__restrict__ Bt, const float2 *__restrict__ W, int cin, int cout,
+                          int adjoint) {
+    const int ci = adjoint ? cout : cin, co = adjoint ? cin : cout;  // channels of the layer being built
+    const int KD = ci * 8, KDP = KD < 16 ? 16 : KD, N = co * 8;
+    const long total = 9L * N * KDP;
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int e = (int)(i / ((long)N * KDP));
+    const int j = (int)((i / KDP) % N), k = (int)(i % KDP);
+    float v = 0.f;
+    if (k < KD) {
+        const int p = k & 1, be = (k >> 1) & 3, cp = k >> 3;   // input channel, spin, re/im
+        const int q = j & 1, al = (j >> 1) & 3, c = j >> 3;     // output channel, spin, re/im
+        float2 w;
+        if (!adjoint) {
+            w = W[(((long)e * cout + c) * cin + cp) * 16 + al * 4 + be];
+        } else {
+            const int d = e == 0 ? 0 : ((e - 1) ^ 1) + 1;  // W'_e = W_d^dag with d the opposite of e
+            const float2 o = W[(((long)d * cout + cp) * cin + c) * 16 + be * 4 + al];
+            w = make_float2(o.x, -o.y);
+        }
+        // complex out = w in as a real 2x2 block [[wr, -wi], [wi, wr]] (rows: out re/im, cols: in re/im)
+        v = (p == 0) ? (q == 0 ? w.x : w.y) : (q == 0 ? -w.y : w.x);
+    }
+    Bt[i] = __float2bfloat16(v);
+}
+
+// dW (complex) from P: (P[re][re] + P[im][im]) + i (P[re][im] - P[im][re]); grad += 2 (Re, Im)
+__global__ void k_wgrad_finish(float2 *__restrict__ grad, const float *__restrict__ P, int cin, int cout) {
+    const int KD = cin * 8, KDP = KD < 16 ? 16 : KD, N = cout * 8;
+    const long total = 9L * cout * cin * 16;
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int be = i % 4, al = (i / 4) % 4, cp = (int)((i / 16) % cin), c = (int)((i / 16 / cin) % cout);
+    const int d = (int)(i / 16 / cin / cout);
+    const float *Pd = P + (long)d * KDP * N;
+    const int kr = (cp * 4 + be) * 2, jr = (c * 4 + al) * 2;
+    const float rr = Pd[kr * N + jr], ii = Pd[(kr + 1) * N + jr + 1];
+    const float ri = Pd[kr * N + jr + 1], ir = Pd[(kr + 1) * N + jr];
+    grad[i].x += 2.f * (rr + ii);
+    grad[i].y += 2.f * (ri - ir);
+}
+
+// r = a - b (plane layout FP32, 6 float4 per site)
+__global__ void k_sub_plane(float4 *__restrict__ r, const float4 *__restrict__ a, const float4 *__restrict__ b, long n) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 x = a[i], y = b[i];
+    r[i] = make_float4(x.x - y.x, x.y - y.y, x.z - y.z, x.w - y.w);
+}
+// x += y (plane layout FP32)
+__global__ void k_add_plane(float4 *__restrict__ x, const float4 *__restrict__ y, long n) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 a = x[i], b = y[i];
+    x[i] = make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+// loss += |y - eps|^2 / en2 over one pair; g = (y - eps) / en2 (site layout, FP32)
+__global__ void k_loss(float2 *__restrict__ g, double *__restrict__ loss, const float4 *__restrict__ y,
+                       const float2 *__restrict__ eps, const double *__restrict__ en2, long V) {
+    __shared__ double sh[256];
+    const long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    double acc = 0;
+    if (n < V) {
+        const float inv = (float)(1.0 / *en2);
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+            const float4 v = y[(long)(k >> 1) * V + n];
+            const float2 yk = (k & 1) ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
+            const float2 e = eps[n * 12 + k];
+            const float2 r = make_float2(yk.x - e.x, yk.y - e.y);
+            acc += ((double)r.x * r.x + (double)r.y * r.y) * inv;
+            g[n * 12 + k] = make_float2(r.x * inv, r.y * inv);
+        }
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(loss, sh[0]);
+}
+
+// |eps|^2 of one pair (site layout)
+__global__ void k_norm2(double *__restrict__ out, const float2 *__restrict__ e, long n) {
+    __shared__ double sh[256];
+    double acc = 0;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        acc += (double)e[i].x * e[i].x + (double)e[i].y * e[i].y;
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(out, sh[0]);
+}
+
+// Adam on real parameters: w -= lr mhat / (sqrt(vhat) + eps)
+__global__ void k_adam(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
+                       long n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    m[i] = b1 * m[i] + (1.f - b1) * gi;
+    v[i] = b2 * v[i] + (1.f - b2) * gi * gi;
+    w[i] -= lr * (m[i] / c1) / (sqrtf(v[i] / c2) + eps);
+}
+
+// plane-layout FP32 spinor -> site layout FP32
+__global__ void k_plane_to_site(float2 *__restrict__ out, const float4 *__restrict__ in, long V) {
+    const long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (n >= V) return;
+#pragma unroll
+    for (int p = 0; p < 6; p++) {
+        const float4 v = in[(long)p * V + n];
+        out[n * 12 + 2 * p] = make_float2(v.x, v.y);
+        out[n * 12 + 2 * p + 1] = make_float2(v.z, v.w);
+    }
+}
+
+Geo geo(const qcd_ctx *c) {
+    Geo g;
+    for (int m = 0; m < 4; m++) g.L[m] = c->lat.L[m];
+    g.V = c->lat.V;
+    g.bc_t = c->bc_t;
+    return g;
+}
+
+template <int CIN, int COUT, int FIN, int FOUT>
+int launch_layer(qcd_ctx *c, void *y, const void *x, const __nv_bfloat16 *Bt) {
+    const long tiles = (c->lat.V + kTileSites - 1) / kTileSites;
+    cudaEvent_t ev;
+    prof_begin(c, QCD_K_LEARNED, &ev);
+    k_layer<CIN, COUT, FIN, FOUT><<<(unsigned)tiles, kLayerThreads, 0, c->stream>>>(y, x, c->U32, Bt, geo(c));
+    return prof_end(c, QCD_K_LEARNED, ev);
+}
+
+template <int CIN, int COUT, int FIN>
+int launch_wgrad(qcd_ctx *c, float *P, const void *x, const float2 *G) {
+    const int tiles = (int)((c->lat.V + kTileSites - 1) / kTileSites);
+    const int grid = tiles < 608 ? tiles : 608;
+    cudaEvent_t ev;
+    prof_begin(c, QCD_K_LEARNED, &ev);
+    k_wgrad<CIN, COUT, FIN><<<grid, 128, 0, c->stream>>>(P, x, G, c->U32, geo(c), tiles);
+    return prof_end(c, QCD_K_LEARNED, ev);
+}
+
+}  // namespace
+
+// ---- network state -----------------------------------------------------------------------
+
+long learned_weight_count() {
+    long n = 0;
+    for (int l = 0; l < kLearnedLayers; l++) n += 9L * kLearnedChans[l + 1] * kLearnedChans[l] * 16;
+    return n;
+}
+
+static long layer_woff(int l) {
+    long n = 0;
+    for (int k = 0; k < l; k++) n += 9L * kLearnedChans[k + 1] * kLearnedChans[k] * 16;
+    return n;
+}
+static long layer_boff(int l, bool adjoint) {
+    // B matrices of layers 0..l-1 (forward and adjoint interleaved)
+    long n = 0;
+    for (int k = 0; k <= l; k++)
+        for (int a = 0; a < 2; a++) {
+            if (k == l && a == (adjoint ? 1 : 0)) return n;
+            const int ci = a ? kLearnedChans[k + 1] : kLearnedChans[k], co = a ? kLearnedChans[k] : kLearnedChans[k + 1];
+            const int KD = ci * 8, KDP = KD < 16 ? 16 : KD;
+            n += 9L * co * 8 * KDP;
+        }
+    return n;
+}
+
+static int ensure_net(qcd_ctx *c) {
+    Learned &L = c->net;
+    const long V = c->lat.V;
+    if (!L.W) {
+        const long nw = learned_weight_count();
+        int rc;
+        if ((rc = dev_alloc(c, (void **)&L.W, sizeof(float2) * nw))) return rc;
+        if ((rc = dev_alloc(c, (void **)&L.grad, sizeof(float2) * nw))) return rc;
+        if ((rc = dev_alloc(c, (void **)&L.m, sizeof(float2) * nw))) return rc;
+        if ((rc = dev_alloc(c, (void **)&L.v, sizeof(float2) * nw))) return rc;
+        if ((rc = dev_alloc(c, (void **)&L.B, sizeof(__nv_bfloat16) * layer_boff(kLearnedLayers, false)))) return rc;
+        if ((rc = dev_alloc(c, (void **)&L.P, sizeof(float) * 9 * 64 * 64))) return rc;
+        if ((rc = dev_alloc(c, (void **)&L.scal, sizeof(double) * 4))) return rc;
+    }
+    if (L.V != V) {
+        dev_free(c, L.act);
+        L.act = nullptr;
+        // hidden activations (BF16, 8 channels each), gradients (FP32, 8 channels each), two site spinors
+        const size_t bytes = 2 * (sizeof(__nv_bfloat162) * 12 * 8 * V) + 2 * (sizeof(float2) * 12 * 8 * V) +
+                             2 * (sizeof(float2) * 12 * V);
+        int rc;
+        if ((rc = dev_alloc(c, &L.act, bytes))) return rc;
+        L.V = V;
+        char *p = (char *)L.act;
+        L.a1 = p; p += sizeof(__nv_bfloat162) * 12 * 8 * V;
+        L.a2 = p; p += sizeof(__nv_bfloat162) * 12 * 8 * V;
+        L.g1 = (float2 *)p; p += sizeof(float2) * 12 * 8 * V;
+        L.g2 = (float2 *)p; p += sizeof(float2) * 12 * 8 * V;
+        L.g3 = (float2 *)p; p += sizeof(float2) * 12 * V;
+        L.tmp = (float2 *)p;
+    }
+    return QCD_OK;
+}
+
+// rebuild the BF16 B matrices from the FP32 weights
+int learned_sync_B(qcd_ctx *c) {
+    Learned &L = c->net;
+    for (int l = 0; l < kLearnedLayers; l++)
+        for (int a = 0; a < 2; a++) {
+            const int ci = a ? kLearnedChans[l + 1] : kLearnedChans[l], co = a ? kLearnedChans[l] : kLearnedChans[l + 1];
+            const int KD = ci * 8, KDP = KD < 16 ? 16 : KD;
+            const long total = 9L * co * 8 * KDP;
+            cudaEvent_t ev;
+            prof_begin(c, QCD_K_LEARNED, &ev);
+            k_build_B<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(
+                L.B + layer_boff(l, a), L.W + layer_woff(l), kLearnedChans[l], kLearnedChans[l + 1], a);
+            int rc = prof_end(c, QCD_K_LEARNED, ev);
+            if (rc) return rc;
+        }
+    return QCD_OK;
+}
+
+int learned_set_weights(qcd_ctx *c, const float2 *w_host_or_dev, bool on_device) {
+    int rc = ensure_net(c);
+    if (rc) return rc;
+    const size_t bytes = sizeof(float2) * learned_weight_count();
+    QCD_CUDA(c, cudaMemcpyAsync(c->net.W, w_host_or_dev, bytes, on_device ? cudaMemcpyDeviceToDevice
+                                                                         : cudaMemcpyHostToDevice, c->stream));
+    QCD_CUDA(c, cudaMemsetAsync(c->net.m, 0, bytes, c->stream));
+    QCD_CUDA(c, cudaMemsetAsync(c->net.v, 0, bytes, c->stream));
+    c->net.step = 0;
+    c->net.ready = true;
+    return learned_sync_B(c);
+}
+
+int learned_get_weights(qcd_ctx *c, float2 *w_host) {
+    if (!c->net.ready) return fail(c, QCD_ERR_STATE, "no learned weights set");
+    QCD_CUDA(c, cudaMemcpyAsync(w_host, c->net.W, sizeof(float2) * learned_weight_count(), cudaMemcpyDeviceToHost,
+                                c->stream));
+    QCD_CUDA(c, cudaStreamSynchronize(c->stream));
+    return QCD_OK;
+}
+
+// y = N(x) for one right-hand side in the FP32 plane layout (layers 1 -> 8 -> 8 -> 1)
+int learned_forward(qcd_ctx *c, float4 *y, const float4 *x) {
+    Learned &L = c->net;
+    if (!L.ready) return fail(c, QCD_ERR_STATE, "no learned weights set");
+    int rc = ensure_net(c);
+    if (rc) return rc;
+    if ((rc = launch_layer<1, 8, PLANE32, SITE16>(c, L.a1, x, L.B + layer_boff(0, false)))) return rc;
+    if ((rc = launch_layer<8, 8, SITE16, SITE16>(c, L.a2, L.a1, L.B + layer_boff(1, false)))) return rc;
+    return launch_layer<8, 1, SITE16, PLANE32>(c, y, L.a2, L.B + layer_boff(2, false));
+}
+
+// loss of one pair (rho: plane layout FP32, eps: site layout FP32) and, with accumulate,
+// its gradient added to the running sum in L.grad (real pairs, 2 (Re, Im) of dL/dW*)
+int learned_loss_grad(qcd_ctx *c, const float4 *rho, const float2 *eps, double *loss_out, float4 *ybuf) {
+    Learned &L = c->net;
+    int rc = learned_forward(c, ybuf, rho);
+    if (rc) return rc;
+    const long V = c->lat.V;
+    QCD_CUDA(c, cudaMemsetAsync(L.scal, 0, sizeof(double) * 2, c->stream));
+    cudaEvent_t ev;
+    prof_begin(c, QCD_K_LEARNED, &ev);
+    k_norm2<<<256, 256, 0, c->stream>>>(L.scal + 1, eps, 12 * V);
+    if ((rc = prof_end(c, QCD_K_LEARNED, ev))) return rc;
+    prof_begin(c, QCD_K_LEARNED, &ev);
+    k_loss<<<(unsigned)((V + 255) / 256), 256, 0, c->stream>>>(L.g3, L.scal, ybuf, eps, L.scal + 1, V);
+    if ((rc = prof_end(c, QCD_K_LEARNED, ev))) return rc;
+    // backward: layer 3 (8 -> 1), layer 2 (8 -> 8), layer 1 (1 -> 8)
+    auto wgrad_layer = [&](int l, auto launcher) -> int {
+        QCD_CUDA(c, cudaMemsetAsync(L.P, 0, sizeof(float) * 9 * 64 * 64, c->stream));
+        int r = launcher();
+        if (r) return r;
+        const long cnt = 9L * kLearnedChans[l + 1] * kLearnedChans[l] * 16;
+        cudaEvent_t e2;
+        prof_begin(c, QCD_K_LEARNED, &e2);
+        k_wgrad_finish<<<(unsigned)((cnt + 255) / 256), 256, 0, c->stream>>>(L.grad + layer_woff(l), L.P,
+                                                                            kLearnedChans[l], kLearnedChans[l + 1]);
+        return prof_end(c, QCD_K_LEARNED, e2);
+    };
+    if ((rc = wgrad_layer(2, [&]() { return launch_wgrad<8, 1, SITE16>(c, L.P, L.a2, L.g3); }))) return rc;
+    if ((rc = launch_layer<1, 8, SITE32, SITE32>(c, L.g2, L.g3, L.B + layer_boff(2, true)))) return rc;
+    if ((rc = wgrad_layer(1, [&]() { return launch_wgrad<8, 8, SITE16>(c, L.P, L.a1, L.g2); }))) return rc;
+    if ((rc = launch_layer<8, 8, SITE32, SITE32>(c, L.g1, L.g2, L.B + layer_boff(1, true)))) return rc;
+    if ((rc = wgrad_layer(0, [&]() { return launch_wgrad<1, 8, PLANE32>(c, L.P, rho, L.g1); }))) return rc;
+    if (loss_out) {
+        double h = 0;
+        QCD_CUDA(c, cudaMemcpyAsync(&h, L.scal, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        QCD_CUDA(c, cudaStreamSynchronize(c->stream));
+        *loss_out = h;
+    }
+    return QCD_OK;
+}
+
+int learned_adam(qcd_ctx *c, float lr) {
+    Learned &L = c->net;
+    const long n = 2 * learned_weight_count();
+    L.step++;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)L.step), c2 = 1.f - powf(b2, (float)L.step);
+    cudaEvent_t ev;
+    prof_begin(c, QCD_K_LEARNED, &ev);
+    k_adam<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>((float *)L.W, (const float *)L.grad, (float *)L.m,
+                                                                (float *)L.v, n, lr, b1, b2, 1e-8f, c1, c2);
+    int rc = prof_end(c, QCD_K_LEARNED, ev);
+    if (rc) return rc;
+    return learned_sync_B(c);
+}
+
+int learned_zero_grad(qcd_ctx *c) {
+    QCD_CUDA(c, cudaMemsetAsync(c->net.grad, 0, sizeof(float2) * learned_weight_count(), c->stream));
+    return QCD_OK;
+}
+
+// out = out + N(v - D out) for nrhs right-hand sides (plane layout): the learned correction
+// applied after SAP; w1, w2: two scratch spinors of nrhs fields each
+int learned_correct(qcd_ctx *c, float4 *out, const float4 *v, float4 *w1, float4 *w2, int nrhs) {
+    const long n4 = 6 * c->lat.V;
+    int rc;
+    if ((rc = dslash32(c, w1, out, nrhs))) return rc;
+    for (int k = 0; k < nrhs; k++) {
+        cudaEvent_t ev;
+        prof_begin(c, QCD_K_LEARNED, &ev);
+        k_sub_plane<<<(unsigned)((n4 + 255) / 256), 256, 0, c->stream>>>(w1 + k * n4, v + k * n4, w1 + k * n4, n4);
+        if ((rc = prof_end(c, QCD_K_LEARNED, ev))) return rc;
+        if ((rc = learned_forward(c, w2, w1 + k * n4))) return rc;
+        prof_begin(c, QCD_K_LEARNED, &ev);
+        k_add_plane<<<(unsigned)((n4 + 255) / 256), 256, 0, c->stream>>>(out + k * n4, w2, n4);
+        if ((rc = prof_end(c, QCD_K_LEARNED, ev))) return rc;
+    }
+    return QCD_OK;
+}
+
+int sub_plane(qcd_ctx *c, float4 *r, const float4 *a, const float4 *b, int nrhs) {
+    const long n4 = 6 * c->lat.V * nrhs;
+    cudaEvent_t ev;
+    prof_begin(c, QCD_K_LEARNED, &ev);
+    k_sub_plane<<<(unsigned)((n4 + 255) / 256), 256, 0, c->stream>>>(r, a, b, n4);
+    return prof_end(c, QCD_K_LEARNED, ev);
+}
+
+int plane_to_site(qcd_ctx *c, float2 *out, const float4 *in) {
+    cudaEvent_t ev;
+    prof_begin(c, QCD_K_OTHER, &ev);
+    k_plane_to_site<<<(unsigned)((c->lat.V + 255) / 256), 256, 0, c->stream>>>(out, in, c->lat.V);
+    return prof_end(c, QCD_K_OTHER, ev);
+}
+
+}  // namespace qcd

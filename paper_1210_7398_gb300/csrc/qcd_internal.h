@@ -12,6 +12,7 @@
 // one contiguous segment per plane (coalesced 16-byte or 8-byte loads).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -61,6 +62,27 @@ struct SapPlan {
     long rec_version = -1;          // field version the records were built from
 };
 
+// learned correction: channels 1 -> 8 -> 8 -> 1, weights complex [9][cout][cin][4][4] per layer
+constexpr int kLearnedLayers = 3;
+constexpr int kLearnedChans[kLearnedLayers + 1] = {1, 8, 8, 1};
+
+struct Learned {
+    bool ready = false;
+    long step = 0;           // Adam steps taken
+    float2 *W = nullptr;     // FP32 master weights (complex)
+    float2 *grad = nullptr;  // accumulated gradient, real pairs 2 (Re, Im) of dL/dW*
+    float2 *m = nullptr, *v = nullptr;  // Adam moments
+    __nv_bfloat16 *B = nullptr;  // BF16 real-block weight matrices, forward and adjoint per layer
+    float *P = nullptr;      // weight-gradient accumulator of one layer [9][64][64]
+    double *scal = nullptr;  // loss, |eps|^2
+    long V = 0;              // lattice the activations are sized for
+    void *act = nullptr;     // one allocation for the buffers below
+    void *a1 = nullptr, *a2 = nullptr;   // hidden activations (BF16, 8 channels)
+    float2 *g1 = nullptr, *g2 = nullptr, *g3 = nullptr, *tmp = nullptr;
+    float4 *pairs = nullptr;  // training pairs: rho (plane FP32) then eps (site FP32) per pair
+    size_t pairs_bytes = 0;
+};
+
 struct Profiler {
     bool on = false;
     long launches[QCD_K_COUNT] = {};
@@ -94,6 +116,8 @@ struct qcd_ctx {
 
     // SAP plan cache (one geometry at a time)
     qcd::SapPlan plan;
+    // learned correction
+    qcd::Learned net;
     long field_version = 0;  // bumped whenever the links or the clover field change
     int sap_min_ctas = 1;    // lower bound on the CTAs (cluster size) per SAP block
 
@@ -218,6 +242,22 @@ int blas_sub64(qcd_ctx *c, double2 *r, const double2 *b, const double2 *w, const
 // rh = r, p = v = 0 where mask[rhs]
 int blas_restart64(qcd_ctx *c, double2 *rh, double2 *p, double2 *v, const double2 *r, const int *mask, long n,
                    int nrhs);
+
+// learned correction (learned.cu)
+long learned_weight_count();
+int learned_set_weights(qcd_ctx *c, const float2 *w, bool on_device);
+int learned_get_weights(qcd_ctx *c, float2 *w_host);
+int learned_sync_B(qcd_ctx *c);
+// y = N(x), one right-hand side, plane layout FP32
+int learned_forward(qcd_ctx *c, float4 *y, const float4 *x);
+// loss of one pair (rho plane layout, eps site layout FP32); gradient added to net.grad
+int learned_loss_grad(qcd_ctx *c, const float4 *rho, const float2 *eps, double *loss, float4 *ybuf);
+int learned_zero_grad(qcd_ctx *c);
+int learned_adam(qcd_ctx *c, float lr);
+// out += N(v - D out) per right-hand side; w1, w2 scratch of nrhs fields
+int learned_correct(qcd_ctx *c, float4 *out, const float4 *v, float4 *w1, float4 *w2, int nrhs);
+int sub_plane(qcd_ctx *c, float4 *r, const float4 *a, const float4 *b, int nrhs);
+int plane_to_site(qcd_ctx *c, float2 *out, const float4 *in);
 
 // solver (solver.cu)
 // x, b: internal FP64 layout, nrhs right-hand sides

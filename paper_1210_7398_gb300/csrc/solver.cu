@@ -49,11 +49,13 @@ int inner_iteration(qcd_ctx *c, const Ws &w, const qcd_params *p) {
     TRY(scalars(c, SC_BETA, w.Si, w.red, R, p->inner_tol, nullptr));
     TRY(blas_p_update32(c, f2(w.ip), f2(w.ir), f2(w.iv), w.Si, n, R));
     TRY(sap_apply(c, w.ipt, w.ip, w.sapw, p->omega, p->nsweep, p->nsap, R, w.Si));
+    if (p->learned) TRY(learned_correct(c, w.ipt, w.ip, w.iv, reinterpret_cast<float4 *>(c->net.tmp), R));
     TRY(dslash32(c, w.iv, w.ipt, R));
     TRY(reduce32(c, RED_DOT_NORM, f2(w.irh), f2(w.iv), n, R, w.red, w.Si));
     TRY(scalars(c, SC_ALPHA, w.Si, w.red, R, p->inner_tol, nullptr));
     TRY(blas_s_update32(c, f2(w.is), f2(w.ir), f2(w.iv), w.Si, n, R));
     TRY(sap_apply(c, w.ist, w.is, w.sapw, p->omega, p->nsweep, p->nsap, R, w.Si));
+    if (p->learned) TRY(learned_correct(c, w.ist, w.is, w.it, reinterpret_cast<float4 *>(c->net.tmp), R));
     TRY(dslash32(c, w.it, w.ist, R));
     TRY(reduce32(c, RED_DOT_NORMA, f2(w.it), f2(w.is), n, R, w.red, w.Si));
     TRY(scalars(c, SC_OMEGA, w.Si, w.red, R, p->inner_tol, nullptr));

@@ -1,0 +1,113 @@
+"""GPU learned correction against the FP64 oracle (a project addition, not in the paper).
+
+BF16 tensor-core layers with FP32 accumulation: forward <= 2e-2 relative in norm
+(BF16 unit roundoff 3.9e-3 times the square root of the ~9 x 8 x 4 terms summed,
+times a safety factor), gradients <= 5e-2.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import qcd_inputs as qi
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1210_7398_gb300 as q  # noqa: E402
+
+CSW, KAPPA = 1.6, 0.12
+CH = q.LEARNED_CHANS
+
+
+def rel_norm(a, b):
+    return np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())
+
+
+def setup(dims, seed=1007):
+    U = qi.gauge_field(dims, 0.3, seed=seed)
+    s = q.Solver(dims)
+    s.load_gauge(torch.from_numpy(U).cuda())
+    s.build_clover(KAPPA, CSW)
+    return s, U
+
+
+def test_weight_count_matches_oracle():
+    assert q.qcd_learned_weight_count() == oracle.learned_weight_count(CH)
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (8, 8, 8, 8), (6, 4, 4, 6)])
+def test_forward_vs_oracle(dims):
+    s, U = setup(dims)
+    W = q.learned_init_weights(11, scale_last=1.0)
+    q.qcd_learned_set_weights(s.ctx, W)
+    x = qi.gaussian_spinor(dims, seed=12)
+    out = np.empty((qi.volume(dims), 4, 3), dtype=np.complex64)
+    q.qcd_learned_apply(s.ctx, out, x[0].astype(np.complex64))
+    ref = oracle.learned_forward(dims, U, CH, W.astype(np.complex128), x)[0]
+    assert rel_norm(out.astype(np.complex128), ref) <= 2e-2
+    s.close()
+
+
+def test_hop_special_case():
+    """Layer weights (1 -+ gamma_mu) on the transports reproduce the Wilson hop; with
+    identity first and last layers the network is H itself."""
+    dims = (8, 4, 4, 8)
+    s, U = setup(dims)
+    W = np.zeros(q.qcd_learned_weight_count(), dtype=np.complex64)
+    n1 = 9 * 8 * 1 * 16
+    n2 = 9 * 8 * 8 * 16
+    W1 = W[:n1].reshape(9, 8, 1, 4, 4)
+    W2 = W[n1:n1 + n2].reshape(9, 8, 8, 4, 4)
+    W3 = W[n1 + n2:].reshape(9, 1, 8, 4, 4)
+    W1[0, 0, 0] = np.eye(4)   # channel 0 copies the input
+    for mu in range(4):
+        g = oracle.gamma(mu)
+        W2[1 + 2 * mu, 0, 0] = np.eye(4) - g
+        W2[2 + 2 * mu, 0, 0] = np.eye(4) + g
+    W3[0, 0, 0] = np.eye(4)
+    q.qcd_learned_set_weights(s.ctx, W)
+    x = qi.gaussian_spinor(dims, seed=13)[0]
+    out = np.empty_like(x, dtype=np.complex64)
+    q.qcd_learned_apply(s.ctx, out, x.astype(np.complex64))
+    ref = oracle.hop(dims, U, x)
+    assert rel_norm(out.astype(np.complex128), ref) <= 2e-2
+    s.close()
+
+
+def test_loss_and_gradient_vs_oracle():
+    dims = (4, 4, 4, 8)
+    s, U = setup(dims)
+    W = q.learned_init_weights(14, scale_last=0.5)
+    q.qcd_learned_set_weights(s.ctx, W)
+    rho = qi.gaussian_spinor(dims, seed=15)
+    eps = qi.gaussian_spinor(dims, seed=16)
+    loss, grad = q.qcd_learned_loss_grad(s.ctx, rho[0].astype(np.complex64), eps[0].astype(np.complex64))
+    rloss, rgrad = oracle.learned_loss_grad(dims, U, CH, W.astype(np.complex128), rho, eps)
+    assert abs(loss - rloss) <= 2e-2 * rloss
+    assert rel_norm(grad.astype(np.float64), rgrad) <= 5e-2
+    # per layer too (the small first and last layers are not hidden by the big middle one)
+    n1 = 2 * 9 * 8 * 16
+    n3 = 2 * 9 * 8 * 16
+    assert rel_norm(grad[:n1].astype(np.float64), rgrad[:n1]) <= 5e-2
+    assert rel_norm(grad[-n3:].astype(np.float64), rgrad[-n3:]) <= 5e-2
+    s.close()
+
+
+def test_training_reduces_loss_and_solver_converges():
+    dims = (8, 8, 8, 8)
+    s, U = setup(dims)
+    prm = q.make_params(KAPPA, CSW, (4, 4, 4, 4), (2, 2, 2, 2), nsweep=2, nsap=2, tol=1e-10)
+    q.qcd_learned_set_weights(s.ctx, q.learned_init_weights(17))
+    src = torch.from_numpy(qi.gaussian_spinor(dims, seed=18, nrhs=16).astype(np.complex64)).cuda()
+    hist = q.qcd_learned_train(s.ctx, src, 16, prm, epochs=6, batch=4, lr=3e-3)
+    assert np.all(np.isfinite(hist))
+    assert hist[-1] < hist[0]
+    b = torch.from_numpy(qi.gaussian_spinor(dims, seed=19)).cuda()
+    x = torch.zeros_like(b)
+    prm_l = q.make_params(KAPPA, CSW, (4, 4, 4, 4), (2, 2, 2, 2), nsweep=2, nsap=2, tol=1e-10)
+    prm_l.learned = 1
+    st = s.solve(x, b, prm_l)
+    F = oracle.clover(dims, U, CSW, KAPPA)[1]
+    r = b.cpu().numpy()[0] - oracle.apply_D(dims, U, F, KAPPA, x.cpu().numpy()[0])
+    assert np.linalg.norm(r) / np.linalg.norm(b.cpu().numpy()[0]) <= 1e-10, st
+    s.close()
