@@ -205,6 +205,25 @@ def dslash_bandwidth(q, torch, dims, iters, peaks, seed=1002):
             "timing": "median of %d launches, L2 flushed before each" % iters}
 
 
+def learned_section(q, qi, torch, s, dims, prm, b, nrhs, npairs, epochs, lr=3e-3, batch=8):
+    """Trains the learned correction on npairs (residual, error) pairs of the plain SAP set-up prm
+    (sources seed 3000, weights seed 4000), then lets qcd_learned_evaluate judge it on b."""
+    t0 = time.perf_counter()
+    q.qcd_learned_set_weights(s.ctx, q.learned_init_weights(4000))
+    src = qi.gaussian_spinor_torch(dims, 3000, npairs, "cuda").to(torch.complex64).contiguous()
+    hist = q.qcd_learned_train(s.ctx, src, npairs, prm, epochs=epochs, batch=batch, lr=lr)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del src
+    v = q.qcd_learned_evaluate(s.ctx, b, nrhs, prm)
+    return {"pairs": npairs, "epochs": epochs, "lr": lr, "batch": batch, "train_s": t_train,
+            "loss_first": float(hist[0]), "loss_last": float(hist[-1]), "params": q.params_dict(prm),
+            "nrhs": nrhs, "verdict": v,
+            "inner_iter_ratio": v["learned_inner"] / max(1, v["plain_inner"]),
+            "time_ratio": v["learned_ms"] / v["plain_ms"],
+            "fallback": "plain SAP" if not v["use_learned"] else None}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -334,6 +353,27 @@ def run_gpu(args):
         chosen["batched_12_point_sources"] = {"seconds": tb, "seconds_per_source": tb / 12,
                                               "outer_iters": bst["outer_iters"], "inner_iters": bst["inner_iters"],
                                               "true_rel_res_max": bst["true_rel_res"]}
+        # the learned correction on top of the chosen set-up; kept only when it is faster
+        lr_sec = learned_section(q, qi, torch, s, dims, best, bd, 1, 64, 8)
+        chosen["learned"] = lr_sec
+        if lr_sec["verdict"]["use_learned"]:
+            chosen["value"] = lr_sec["verdict"]["learned_ms"] / 1000.0
+            chosen["params"]["learned"] = 1
+            chosen["speedup_vs_plain"] = ms_step / lr_sec["verdict"]["learned_ms"]
+    learned_full = None
+    if args.learned_full:
+        # 24^3 x 48, kappa 0.122, 12 point sources, 256 training pairs, plain SAP with 4 sweeps
+        dl = (24, 24, 24, 48)
+        sl = q.Solver(dl)
+        sl.load_gauge(qi.gauge_field(dl, w["eps"], seed=1003, device="cuda"))
+        sl.build_clover(0.122, w["csw"])
+        pl = q.make_params(0.122, w["csw"], (4, 4, 4, 4), (2, 2, 2, 2), nsweep=4, nsap=4, tol=w["tol"],
+                           inner_tol=w["inner_tol"])
+        pts = torch.from_numpy(qi.point_sources(dl)).cuda()
+        learned_full = learned_section(q, qi, torch, sl, dl, pl, pts, 12, 256, 8)
+        learned_full["lattice"] = "24x24x24x48"
+        sl.close()
+        del pts
     s.close()
     del flush
     torch.cuda.empty_cache()
@@ -384,6 +424,8 @@ def run_gpu(args):
                        "note": "qcd_solve with pinned host x and b; copies inside the call"},
                "gpu_launches": launches, "kernels": kstats, "clocks": clk, "roofline": roof,
                "dslash": dsl, "chosen": chosen, "cpu_baseline": cpu}
+        if learned_full is not None:
+            out["learned_24x24x24x48"] = learned_full
         print(json.dumps(out))
     if world > 1:
         torch.distributed.barrier()
@@ -401,6 +443,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--skip-chosen", action="store_true", help="skip the autotuned (chosen) measurement")
     ap.add_argument("--tune-candidates", type=int, default=48, help="solves the autotuner may time")
+    ap.add_argument("--learned-full", action="store_true",
+                    help="also train and judge the learned correction on 24^3 x 48 with 12 point sources")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

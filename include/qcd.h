@@ -88,8 +88,11 @@ typedef struct {
     int max_outer, max_inner;
     int bc_t;           /* +1 periodic, -1 antiperiodic in t (must match qcd_set_boundary) */
     int sap_storage;    /* QCD_F32 (plain) or QCD_F16 (half storage, FP32 arithmetic)    */
-    int learned;        /* 1: precondition with M_SAP + N (1 - D M_SAP), N the learned
-                           correction (qcd_learned_*); 0: plain SAP                    */
+    int learned;        /* 0: plain SAP.  1: precondition with M_SAP + N (1 - D M_SAP),
+                           N the learned correction (qcd_learned_*), unless the last
+                           qcd_learned_evaluate found it slower than plain SAP, in
+                           which case plain SAP is used (the fallback).  2: always use
+                           the learned correction                                     */
     int sap_ctas;       /* CTAs per SAP block in the SSOR kernel, 0 = context default
                            (qcd_set_sap_ctas); results do not depend on it            */
 } qcd_params;
@@ -222,6 +225,25 @@ int qcd_learned_loss_grad(qcd_ctx *ctx, const float *rho, const float *eps, doub
  * after each epoch.  Requires qcd_learned_set_weights (the initial weights). */
 int qcd_learned_train(qcd_ctx *ctx, const float *sources, int npairs, const qcd_params *p, int epochs, int batch,
                       float lr, double *history);
+
+/* Result of qcd_learned_evaluate: the same right-hand sides solved from x = 0
+ * with plain SAP and with the learned correction (times are wall times of a
+ * second, warm qcd_solve call; relres the FP64 true relative residual). */
+typedef struct {
+    double plain_ms, learned_ms;
+    double plain_relres, learned_relres;
+    int plain_outer, plain_inner;
+    int learned_outer, learned_inner;
+    int use_learned; /* 1: learned converged and was faster; qcd_params.learned = 1 uses it */
+    int pad;
+} qcd_learned_verdict;
+
+/* Judges the trained correction on b (complex128 [nrhs][V][4][3], host or
+ * device) with the solver settings *p (p->learned ignored): solves with plain
+ * SAP and with the correction, compares time to solution, and records the
+ * verdict in the context; qcd_learned_set_weights and qcd_learned_train clear
+ * it.  Synchronises. */
+int qcd_learned_evaluate(qcd_ctx *ctx, const double *b, int nrhs, const qcd_params *p, qcd_learned_verdict *out);
 
 /* ---- measurement hooks -------------------------------------------------- */
 

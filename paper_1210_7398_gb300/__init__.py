@@ -28,7 +28,7 @@ EXPORTS = ("qcd_create", "qcd_destroy", "qcd_last_error", "qcd_set_boundary", "q
            "qcd_kernel_stats", "qcd_launch_count", "qcd_bench_dslash", "qcd_sap_precondition_noalloc",
            "qcd_set_sap_ctas", "qcd_set_graphs", "qcd_autotune", "qcd_learned_weight_count",
            "qcd_learned_set_weights", "qcd_learned_get_weights", "qcd_learned_apply", "qcd_learned_loss_grad",
-           "qcd_learned_train")
+           "qcd_learned_train", "qcd_learned_evaluate")
 
 
 class QcdError(RuntimeError):
@@ -45,6 +45,17 @@ class qcd_params(ctypes.Structure):
                 ("max_outer", ctypes.c_int), ("max_inner", ctypes.c_int),
                 ("bc_t", ctypes.c_int), ("sap_storage", ctypes.c_int),
                 ("learned", ctypes.c_int), ("sap_ctas", ctypes.c_int)]
+
+
+class qcd_learned_verdict(ctypes.Structure):
+    _fields_ = [("plain_ms", ctypes.c_double), ("learned_ms", ctypes.c_double),
+                ("plain_relres", ctypes.c_double), ("learned_relres", ctypes.c_double),
+                ("plain_outer", ctypes.c_int), ("plain_inner", ctypes.c_int),
+                ("learned_outer", ctypes.c_int), ("learned_inner", ctypes.c_int),
+                ("use_learned", ctypes.c_int), ("pad", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
 
 
 class qcd_stats(ctypes.Structure):
@@ -88,6 +99,7 @@ def load_library(path: str = LIB_PATH):
         "qcd_learned_apply": (I, [P, P, P]),
         "qcd_learned_loss_grad": (I, [P, P, P, ctypes.POINTER(D), P]),
         "qcd_learned_train": (I, [P, P, I, ctypes.POINTER(qcd_params), I, I, ctypes.c_float, P]),
+        "qcd_learned_evaluate": (I, [P, P, I, ctypes.POINTER(qcd_params), ctypes.POINTER(qcd_learned_verdict)]),
         "qcd_autotune": (I, [P, P, I, ctypes.POINTER(qcd_params), ctypes.POINTER(qcd_params),
                              ctypes.POINTER(D), I]),
         "qcd_kernel_stats": (I, [P, I, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(D), I]),
@@ -236,6 +248,14 @@ def qcd_learned_train(ctx, sources, npairs, params: qcd_params, epochs, batch, l
     _check(ctx, load_library().qcd_learned_train(ctx, _ptr(sources), int(npairs), ctypes.byref(params), int(epochs),
                                                  int(batch), ctypes.c_float(lr), _ptr(hist)))
     return hist
+
+
+def qcd_learned_evaluate(ctx, b, nrhs, params: qcd_params) -> dict:
+    """Solves b with plain SAP and with the learned correction; records and returns the verdict
+    (times, iterations, residuals, use_learned)."""
+    v = qcd_learned_verdict()
+    _check(ctx, load_library().qcd_learned_evaluate(ctx, _ptr(b), int(nrhs), ctypes.byref(params), ctypes.byref(v)))
+    return v.as_dict()
 
 
 def learned_init_weights(seed: int, scale_last: float = 0.01) -> np.ndarray:

@@ -142,8 +142,8 @@ int check_params(qcd_ctx *c, const qcd_params *p) {
     if (p->nsweep < 1 || p->nsap < 1) return fail(c, QCD_ERR_ARG, "nsweep and nsap must be >= 1");
     if (p->sap_storage != QCD_F32 && p->sap_storage != QCD_F16)
         return fail(c, QCD_ERR_ARG, "sap_storage must be QCD_F32 or QCD_F16");
-    if (p->learned != 0 && p->learned != 1) return fail(c, QCD_ERR_ARG, "learned must be 0 or 1");
-    if (p->learned == 1 && !c->net.ready) return fail(c, QCD_ERR_STATE, "learned = 1 needs qcd_learned_set_weights");
+    if (p->learned < 0 || p->learned > 2) return fail(c, QCD_ERR_ARG, "learned must be 0, 1 or 2");
+    if (p->learned && !c->net.ready) return fail(c, QCD_ERR_STATE, "learned != 0 needs qcd_learned_set_weights");
     if (p->bc_t != c->bc_t) return fail(c, QCD_ERR_ARG, "params.bc_t differs from the context boundary condition");
     if (p->kappa != c->kappa || p->csw != c->csw)
         return fail(c, QCD_ERR_ARG, "params.kappa/csw differ from the clover field built");
@@ -370,7 +370,10 @@ int qcd_solve(qcd_ctx *c, double *x, const double *b, const qcd_params *p, int n
     }
     if ((rc = spinor64_to_internal(c, bi, (const double2 *)bsrc, nrhs))) return rc;
     if ((rc = spinor64_to_internal(c, xi, (const double2 *)xsrc, nrhs))) return rc;
-    int status = solve(c, xi, bi, p, nrhs, &local);
+    // learned = 1 falls back to plain SAP when the last evaluation found the correction slower
+    qcd_params pe = *p;
+    pe.learned = (p->learned == 2 || (p->learned == 1 && c->net.verdict != 0)) ? 1 : 0;
+    int status = solve(c, xi, bi, &pe, nrhs, &local);
     if (status == QCD_ERR_CUDA || status == QCD_ERR_OOM || status == QCD_ERR_STATE || status == QCD_ERR_ARG)
         return status;
     if ((rc = spinor64_from_internal(c, (double2 *)(dev_x ? (char *)x : sx), xi, nrhs))) return rc;
@@ -435,6 +438,7 @@ int qcd_learned_set_weights(qcd_ctx *c, const float *w, long n) {
     if (!c->have_gauge) return fail(c, QCD_ERR_STATE, "qcd_load_gauge must be called first");
     if (!w || n != learned_weight_count()) return fail(c, QCD_ERR_ARG, "weight count mismatch");
     if ((rc = learned_set_weights(c, (const float2 *)w, is_device_ptr(w)))) return rc;
+    c->net.verdict = -1;
     QCD_CUDA(c, cudaStreamSynchronize(c->stream));
     return QCD_OK;
 }
@@ -509,6 +513,7 @@ int qcd_learned_train(qcd_ctx *c, const float *sources, int npairs, const qcd_pa
     if (!sources || npairs < 1 || epochs < 0 || batch < 1 || !(lr > 0)) return fail(c, QCD_ERR_ARG, "bad training arguments");
     qcd_params pp = *p;
     pp.learned = 0;  // the pairs measure the error of plain SAP
+    c->net.verdict = -1;
     if ((rc = check_params(c, &pp))) return rc;
     if ((rc = sap_prepare(c, pp.block, pp.subblock, pp.sap_storage == QCD_F16))) return rc;
     const long V = c->lat.V;
@@ -594,6 +599,49 @@ int qcd_learned_train(qcd_ctx *c, const float *sources, int npairs, const qcd_pa
         if (history) history[e + 1] = total / npairs;
     }
     QCD_CUDA(c, cudaStreamSynchronize(c->stream));
+    return QCD_OK;
+}
+
+int qcd_learned_evaluate(qcd_ctx *c, const double *b, int nrhs, const qcd_params *p, qcd_learned_verdict *out) {
+    int rc = ready(c);
+    if (rc) return rc;
+    if ((rc = need_clover(c))) return rc;
+    if (!c->net.ready) return fail(c, QCD_ERR_STATE, "qcd_learned_set_weights must be called first");
+    if (!b || nrhs < 1 || !p) return fail(c, QCD_ERR_ARG, "qcd_learned_evaluate: bad b, nrhs or params");
+    const size_t bytes = 16 * 12 * (size_t)c->lat.V * nrhs;
+    void *xb = nullptr;
+    if ((rc = dev_alloc(c, &xb, bytes))) return rc;
+    struct Free {
+        qcd_ctx *c;
+        void *p;
+        ~Free() { dev_free(c, p); }
+    } guard{c, xb};
+    qcd_learned_verdict v;
+    std::memset(&v, 0, sizeof(v));
+    // each variant: one warm solve, then the timed one
+    auto run = [&](int learned, double *ms, double *relres, int *outer, int *inner) -> int {
+        qcd_params q = *p;
+        q.learned = learned;
+        qcd_stats st;
+        for (int k = 0; k < 2; k++) {
+            QCD_CUDA(c, cudaMemsetAsync(xb, 0, bytes, c->stream));
+            std::memset(&st, 0, sizeof(st));
+            const int s = qcd_solve(c, (double *)xb, b, &q, nrhs, &st);
+            if (s != QCD_OK && s != QCD_ERR_NOCONV && s != QCD_ERR_BREAKDOWN) return s;
+            if (s != QCD_OK) st.true_rel_res = st.true_rel_res > 0 ? st.true_rel_res : 1.0;
+        }
+        *ms = st.ms_total;
+        *relres = st.true_rel_res;
+        *outer = st.outer_iters;
+        *inner = st.inner_iters;
+        return QCD_OK;
+    };
+    if ((rc = run(0, &v.plain_ms, &v.plain_relres, &v.plain_outer, &v.plain_inner))) return rc;
+    if ((rc = run(2, &v.learned_ms, &v.learned_relres, &v.learned_outer, &v.learned_inner))) return rc;
+    v.use_learned = (v.learned_relres <= p->tol && v.learned_ms < v.plain_ms) ? 1 : 0;
+    c->net.verdict = v.use_learned;
+    c->err.clear();
+    if (out) *out = v;
     return QCD_OK;
 }
 

@@ -6,11 +6,11 @@
 // T on colour and site, a layer is, per direction, a dense contraction over
 // (input channel, spin) for every (site, colour) row: a GEMM with M = 3V rows,
 // K = 9 x Cin x 4 complex, N = Cout x 4 complex.  It runs on the tensor cores
-// in BF16 with FP32 accumulation (mma.sync m16n8k16): a CTA gathers and
-// transports the inputs of 32 sites for one direction into shared memory (the
-// A tile), loads that direction's weights as a real 2x2-block matrix (the B
-// tile), multiplies, and moves to the next direction with the accumulators
-// in registers.  The data gradient is the same kernel with the adjoint
+// in BF16 with FP32 accumulation (mma.sync m16n8k16): per direction a CTA
+// stages the neighbour inputs and links of 64 sites in shared memory with
+// coalesced loads, transports them into the BF16 A tile, loads that
+// direction's weights as a real 2x2-block matrix (the B tile), multiplies,
+// and moves to the next direction with the accumulators in registers.  The data gradient is the same kernel with the adjoint
 // weights (T_d^dag = T_{opposite d} and W commutes with T); the weight
 // gradient is sum over rows of A^T G, computed the same way with the
 // reduction over rows.
@@ -25,10 +25,6 @@
 
 namespace qcd {
 namespace {
-
-constexpr int kTileSites = 32;             // sites per CTA tile
-constexpr int kTileRows = 3 * kTileSites;  // (site, colour) rows
-constexpr int kLayerThreads = 192;         // 6 warps, one 16-row MMA tile each
 
 // activation formats
 enum { PLANE32 = 0, SITE16 = 1, SITE32 = 2 };
@@ -69,97 +65,285 @@ __device__ __forceinline__ void mma_bf16(float c[4], uint32_t a0, uint32_t a1, u
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-// z = T_d x_ch (one site, 12 complex, FP32); returns false when n is outside the lattice
-template <int FMT>
-__device__ __forceinline__ void transport(const void *x, int ch, const float2 *__restrict__ U, const Geo &g, int d,
-                                          long n, float2 z[12]) {
+// Row (n, a) of the transported inputs of direction d: z[c'][beta] = sum_b W_d[a][b] x_{c'}(m)[beta][b]
+// with W = 1 (d = 0), U_mu(n) and m = n + mu (forward), U_mu(n - mu)^dag and m = n - mu (backward),
+// times the boundary sign; written as CIN x 4 complex into the BF16 row `dst` (2 values each).
+template <int CIN, int FMT>
+__device__ __forceinline__ void transport_row(const void *x, const float2 *__restrict__ U, const Geo &g, int d,
+                                              long n, int a, __nv_bfloat16 *dst) {
+    long m = n;
+    float2 w[3];
     if (d == 0) {
-#pragma unroll
-        for (int k = 0; k < 12; k++) z[k] = act_ld<FMT>(x, g.V, ch, n, k);
-        return;
-    }
-    const int mu = (d - 1) >> 1;
-    const bool fwd = ((d - 1) & 1) == 0;
-    int xc[4];
-    site_coords(g, n, xc);
-    long stride = 1;
-    for (int m = 0; m < mu; m++) stride *= g.L[m];
-    long m;
-    float sgn = 1.f;
-    if (fwd) {
-        m = (xc[mu] == g.L[mu] - 1) ? n - stride * (g.L[mu] - 1) : n + stride;
-        if (mu == 3 && xc[3] == g.L[3] - 1) sgn = (float)g.bc_t;
+        w[0] = w[1] = w[2] = make_float2(0.f, 0.f);
+        w[a] = make_float2(1.f, 0.f);
     } else {
-        m = (xc[mu] == 0) ? n + stride * (g.L[mu] - 1) : n - stride;
-        if (mu == 3 && xc[3] == 0) sgn = (float)g.bc_t;
+        const int mu = (d - 1) >> 1;
+        const bool fwd = ((d - 1) & 1) == 0;
+        int xc[4];
+        site_coords(g, n, xc);
+        long stride = 1;
+        for (int q = 0; q < mu; q++) stride *= g.L[q];
+        float sgn = 1.f;
+        if (fwd) {
+            m = (xc[mu] == g.L[mu] - 1) ? n - stride * (g.L[mu] - 1) : n + stride;
+            if (mu == 3 && xc[3] == g.L[3] - 1) sgn = (float)g.bc_t;
+        } else {
+            m = (xc[mu] == 0) ? n + stride * (g.L[mu] - 1) : n - stride;
+            if (mu == 3 && xc[3] == 0) sgn = (float)g.bc_t;
+        }
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            // forward: row a of U_mu(n); backward: row a of U_mu(m)^dag = conj(column a of U_mu(m))
+            float2 u = fwd ? __ldg(U + (long)(mu * 9 + a * 3 + b) * g.V + n) : __ldg(U + (long)(mu * 9 + b * 3 + a) * g.V + m);
+            if (!fwd) u.y = -u.y;
+            w[b] = cscale(u, sgn);
+        }
     }
-    const long ls = fwd ? n : m;
-    float2 u[9];
 #pragma unroll
-    for (int i = 0; i < 9; i++) u[i] = __ldg(U + (long)(mu * 9 + i) * g.V + ls);
-    float2 xm[12];
+    for (int ch = 0; ch < CIN; ch++) {
+        uint32_t packed[4];
 #pragma unroll
-    for (int k = 0; k < 12; k++) xm[k] = act_ld<FMT>(x, g.V, ch, m, k);
-#pragma unroll
-    for (int s = 0; s < 4; s++)
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
+        for (int be = 0; be < 4; be++) {
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int b = 0; b < 3; b++) acc = fwd ? cfma(u[a * 3 + b], xm[s * 3 + b], acc) : cfmac(u[b * 3 + a], xm[s * 3 + b], acc);
-            z[s * 3 + a] = cscale(acc, sgn);
+            for (int b = 0; b < 3; b++) acc = cfma(w[b], act_ld<FMT>(x, g.V, ch, m, be * 3 + b), acc);
+            packed[be] = pack_bf16(acc.x, acc.y);
         }
+        *reinterpret_cast<uint4 *>(dst + ch * 8) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+    }
 }
 
+constexpr int kLayerSites = 64;                 // sites per CTA tile of the layer kernel
+constexpr int kLayerRows = 3 * kLayerSites;     // 192 rows = 12 warps x 16 (MMA); threads < 192 gather one row each
+constexpr int kLayerWarps = kLayerRows / 16;
+static_assert(kLayerWarps * 32 >= kLayerRows, "one gathering thread per row");
+
+__device__ __forceinline__ void cp_async16z(void *smem, const void *gmem, bool valid) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    const int n = valid ? 16 : 0;  // src-size 0: zero fill, nothing read
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async8z(void *smem, const void *gmem, bool valid) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    const int n = valid ? 8 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void ldsm_x4(const void *p, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(sa));
+}
+__device__ __forceinline__ void ldsm_x2(const void *p, uint32_t &r0, uint32_t &r1) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(sa));
+}
+
+// Shared-memory plan of the layer kernel: two stages (directions d and d+1) of the neighbour
+// inputs X[site][ch][12] (site records padded by 16 bytes), the links L[site][9] and the weight
+// tile B[N][KDP+8]; the transported A tile [192][KDP+8]; the neighbour table and boundary signs
+// of all nine directions.  Row strides of KDP+8 BF16 keep ldmatrix free of bank conflicts.
+template <int CIN, int COUT, int FIN> struct LayerSmem {
+    static constexpr int KD = CIN * 8, KDP = KD < 16 ? 16 : KD, N = COUT * 8, AS = KDP + 8;
+    static constexpr int XC = FIN == SITE16 ? 4 : 8;  // bytes per staged complex input
+    static constexpr int XS = CIN * 12 * XC + 16;     // bytes per staged site
+    static constexpr size_t x_bytes = (size_t)kLayerSites * XS;
+    static constexpr size_t l_bytes = (size_t)kLayerSites * 9 * sizeof(float2);
+    static constexpr size_t b_bytes = (size_t)N * AS * sizeof(__nv_bfloat16);
+    static constexpr size_t stage = x_bytes + l_bytes + b_bytes;
+    static constexpr size_t a_bytes = (size_t)kLayerRows * AS * sizeof(__nv_bfloat16);
+    static constexpr size_t total = 2 * stage + a_bytes + (size_t)9 * kLayerSites * (sizeof(int) + sizeof(float));
+    static_assert(XS % 16 == 0 && x_bytes % 16 == 0 && l_bytes % 16 == 0 && b_bytes % 16 == 0 && a_bytes % 16 == 0,
+                  "16-byte staging");
+};
+
 // y = layer(x): CIN -> COUT channels.  Bt: [9][N][KDP] BF16, N = COUT*8, KDP = max(16, CIN*8).
+// A CTA owns 64 sites (192 rows, one 16-row MMA tile per warp).  Per direction: the neighbour
+// inputs (all channels), their links and the direction's weights are staged with cp.async one
+// direction ahead; one thread per (site, channel pair) applies the 3x3 colour transport to the
+// four spins and writes the BF16 A rows; the warps then accumulate A B into registers, with
+// fragments read by ldmatrix.
 template <int CIN, int COUT, int FIN, int FOUT>
-__global__ void __launch_bounds__(kLayerThreads) k_layer(void *y, const void *x, const float2 *__restrict__ U,
-                                                         const __nv_bfloat16 *__restrict__ Bt, Geo g) {
-    constexpr int KD = CIN * 8, KDP = KD < 16 ? 16 : KD, N = COUT * 8, NT = N / 8;
-    constexpr int AS = KDP + 8;  // padded row strides (bank spread)
-    __shared__ __align__(16) __nv_bfloat16 A[kTileRows][AS];
-    __shared__ __align__(16) __nv_bfloat16 B[N][AS];
+__global__ void __launch_bounds__(kLayerWarps * 32, FIN == SITE32 ? 1 : 2) k_layer(void *y, const void *x, const float2 *__restrict__ U,
+                                                               const __nv_bfloat16 *__restrict__ Bt, Geo g) {
+    using S = LayerSmem<CIN, COUT, FIN>;
+    constexpr int KDP = S::KDP, N = S::N, AS = S::AS, NT = N / 8, XS = S::XS;
+    constexpr int NTH = kLayerWarps * 32;
+    constexpr int CPI = CIN < 2 ? CIN : 2;             // channels per transport item
+    constexpr int ITEMS = kLayerSites * (CIN / CPI);  // transport items per direction
+    static_assert(CIN % CPI == 0 && ITEMS <= NTH, "one transport item per thread");
+    extern __shared__ __align__(16) unsigned char ly_smem[];
+    __nv_bfloat16 *A = reinterpret_cast<__nv_bfloat16 *>(ly_smem + 2 * S::stage);
+    int *nbt = reinterpret_cast<int *>(ly_smem + 2 * S::stage + S::a_bytes);  // [9][64] neighbour, -1 past the end
+    float *sgt = reinterpret_cast<float *>(nbt + 9 * kLayerSites);            // [9][64] boundary sign
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gq = lane >> 2, tq = lane & 3;
-    const long n0 = (long)blockIdx.x * kTileSites;
-    for (int i = tid; i < kTileRows * AS; i += kLayerThreads) (&A[0][0])[i] = __float2bfloat16(0.f);
+    const int V = (int)g.V;
+    const int n0 = blockIdx.x * kLayerSites;
+
+    // neighbour table of the tile for all nine directions
+    if (tid < kLayerSites) {
+        const int n = n0 + tid;
+        int xc0 = 0, xc1 = 0, xc2 = 0, xc3 = 0;
+        if (n < V) {
+            int r = n;
+            xc0 = r % g.L[0]; r /= g.L[0];
+            xc1 = r % g.L[1]; r /= g.L[1];
+            xc2 = r % g.L[2]; xc3 = r / g.L[2];
+        }
+        const int xc[4] = {xc0, xc1, xc2, xc3};
+        nbt[tid] = n < V ? n : -1;
+        sgt[tid] = 1.f;
+        int stride = 1;
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            const int Lm = g.L[mu];
+            const int f = xc[mu] == Lm - 1 ? n - stride * (Lm - 1) : n + stride;
+            const int bk = xc[mu] == 0 ? n + stride * (Lm - 1) : n - stride;
+            nbt[(1 + 2 * mu) * kLayerSites + tid] = n < V ? f : -1;
+            nbt[(2 + 2 * mu) * kLayerSites + tid] = n < V ? bk : -1;
+            sgt[(1 + 2 * mu) * kLayerSites + tid] = (mu == 3 && xc[3] == Lm - 1) ? (float)g.bc_t : 1.f;
+            sgt[(2 + 2 * mu) * kLayerSites + tid] = (mu == 3 && xc[3] == 0) ? (float)g.bc_t : 1.f;
+            stride *= Lm;
+        }
+    }
+    __syncthreads();
+
+    // stage direction d into buffer d & 1
+    auto issue = [&](int d) {
+        unsigned char *X = ly_smem + (d & 1) * S::stage;
+        float2 *L = reinterpret_cast<float2 *>(X + S::x_bytes);
+        __nv_bfloat16 *B = reinterpret_cast<__nv_bfloat16 *>(X + S::x_bytes + S::l_bytes);
+        const int *nb = nbt + d * kLayerSites;
+        if constexpr (FIN == PLANE32) {
+            static_assert(CIN == 1, "plane layout holds one channel");
+            for (int i = tid; i < kLayerSites * 6; i += NTH) {
+                const int st = i % kLayerSites, p = i / kLayerSites;
+                const int m = nb[st];
+                cp_async16z(X + st * XS + p * 16, static_cast<const float4 *>(x) + (long)p * V + (m < 0 ? 0 : m), m >= 0);
+            }
+        } else {
+            constexpr int CH16 = 12 * S::XC / 16;  // 16-byte chunks per site and channel
+            for (int i = tid; i < kLayerSites * CIN * CH16; i += NTH) {
+                const int k = i % CH16, rest = i / CH16, st = rest % kLayerSites, ch = rest / kLayerSites;
+                const int m = nb[st];
+                const unsigned char *src =
+                    static_cast<const unsigned char *>(x) + (((long)ch * V + (m < 0 ? 0 : m)) * 12) * S::XC + k * 16;
+                cp_async16z(X + st * XS + (ch * CH16 + k) * 16, src, m >= 0);
+            }
+        }
+        if (d > 0) {
+            const int mu = (d - 1) >> 1;
+            const bool fwd = ((d - 1) & 1) == 0;
+            for (int i = tid; i < kLayerSites * 9; i += NTH) {
+                const int st = i % kLayerSites, e = i / kLayerSites;
+                const int m = nb[st];
+                const int ls = fwd ? n0 + st : m;  // U_mu(n) forward, U_mu(n - mu) backward
+                cp_async8z(L + st * 9 + e, U + (long)(mu * 9 + e) * V + (m < 0 ? 0 : ls), m >= 0);
+            }
+        }
+        const uint4 *Bd = reinterpret_cast<const uint4 *>(Bt + (long)d * N * KDP);
+        for (int i = tid; i < N * KDP / 8; i += NTH) {
+            const int row = i / (KDP / 8), col = (i % (KDP / 8)) * 8;
+            cp_async16z(B + row * AS + col, Bd + i, true);
+        }
+        cp_commit();
+    };
+
+    // KDP > CIN*8 (one input channel): the upper K half of A stays zero
+    if constexpr (KDP > CIN * 8) {
+        for (int i = tid; i < kLayerRows; i += NTH)
+            *reinterpret_cast<uint4 *>(A + i * AS + CIN * 8) = make_uint4(0, 0, 0, 0);
+    }
     float acc[NT][4];
 #pragma unroll
     for (int j = 0; j < NT; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+
+    issue(0);
     for (int d = 0; d < 9; d++) {
-        __syncthreads();
-        // A tile: rows (site, colour), columns (input channel, spin, re/im)
-        for (int item = tid; item < kTileSites * CIN; item += kLayerThreads) {
-            const int s = item % kTileSites, ch = item / kTileSites;
-            const long n = n0 + s;
-            float2 z[12];
-            if (n < g.V) transport<FIN>(x, ch, U, g, d, n, z);
-            else
+        cp_wait<0>();
+        __syncthreads();  // stage d visible; every warp is done with the previous A and stage
+        if (d + 1 < 9) issue(d + 1);
+        const unsigned char *X = ly_smem + (d & 1) * S::stage;
+        const float2 *L = reinterpret_cast<const float2 *>(X + S::x_bytes);
+        const __nv_bfloat16 *B = reinterpret_cast<const __nv_bfloat16 *>(X + S::x_bytes + S::l_bytes);
+        // transport: A[3 st + a][8 ch + 2 be (+1)] = sum_b W[a][b] x_ch(m)[be][b], W = 1, U_mu(n) or
+        // U_mu(n - mu)^dag, times the boundary sign
+        if (tid < ITEMS) {
+            const int st = tid / (CIN / CPI), cg = (tid % (CIN / CPI)) * CPI;
+            const bool fwd = ((d - 1) & 1) == 0;
+            const float sg = sgt[d * kLayerSites + st];
 #pragma unroll
-                for (int k = 0; k < 12; k++) z[k] = make_float2(0.f, 0.f);
+            for (int cc = 0; cc < CPI; cc++) {
+                const int ch = cg + cc;
+                float2 v[12];
+                if constexpr (FIN == SITE16) {
+                    const uint4 *q = reinterpret_cast<const uint4 *>(X + st * XS + ch * 48);
 #pragma unroll
-            for (int be = 0; be < 4; be++)
+                    for (int t = 0; t < 3; t++) {
+                        const uint4 u4 = q[t];
+                        const uint32_t wds[4] = {u4.x, u4.y, u4.z, u4.w};
+#pragma unroll
+                        for (int e = 0; e < 4; e++)
+                            v[t * 4 + e] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&wds[e]));
+                    }
+                } else {
+                    const float4 *q = reinterpret_cast<const float4 *>(X + st * XS + ch * 96);
+#pragma unroll
+                    for (int t = 0; t < 6; t++) {
+                        const float4 f4 = q[t];
+                        v[2 * t] = make_float2(f4.x, f4.y);
+                        v[2 * t + 1] = make_float2(f4.z, f4.w);
+                    }
+                }
 #pragma unroll
                 for (int a = 0; a < 3; a++) {
-                    const int col = (ch * 4 + be) * 2;
-                    *reinterpret_cast<uint32_t *>(&A[s * 3 + a][col]) = pack_bf16(z[be * 3 + a].x, z[be * 3 + a].y);
+                    float2 w[3];  // row a of the transport matrix
+                    if (d > 0) {
+#pragma unroll
+                        for (int b = 0; b < 3; b++) {
+                            float2 u = fwd ? L[st * 9 + a * 3 + b] : L[st * 9 + b * 3 + a];
+                            if (!fwd) u.y = -u.y;
+                            w[b] = cscale(u, sg);
+                        }
+                    }
+                    uint32_t packed[4];
+#pragma unroll
+                    for (int be = 0; be < 4; be++) {
+                        float2 z;
+                        if (d == 0) {
+                            z = v[be * 3 + a];
+                        } else {
+                            z = cmul(w[0], v[be * 3]);
+                            z = cfma(w[1], v[be * 3 + 1], z);
+                            z = cfma(w[2], v[be * 3 + 2], z);
+                        }
+                        packed[be] = pack_bf16(z.x, z.y);
+                    }
+                    *reinterpret_cast<uint4 *>(A + (st * 3 + a) * AS + ch * 8) =
+                        make_uint4(packed[0], packed[1], packed[2], packed[3]);
                 }
+            }
         }
-        // B tile of direction d
-        const __nv_bfloat16 *Bd = Bt + (long)d * N * KDP;
-        for (int i = tid; i < N * KDP; i += kLayerThreads) B[i / KDP][i % KDP] = Bd[i];
         __syncthreads();
         const int r0 = warp * 16;
 #pragma unroll
         for (int k0 = 0; k0 < KDP; k0 += 16) {
-            const uint32_t a0 = *reinterpret_cast<const uint32_t *>(&A[r0 + gq][k0 + 2 * tq]);
-            const uint32_t a1 = *reinterpret_cast<const uint32_t *>(&A[r0 + gq + 8][k0 + 2 * tq]);
-            const uint32_t a2 = *reinterpret_cast<const uint32_t *>(&A[r0 + gq][k0 + 2 * tq + 8]);
-            const uint32_t a3 = *reinterpret_cast<const uint32_t *>(&A[r0 + gq + 8][k0 + 2 * tq + 8]);
+            uint32_t a0, a1, a2, a3;
+            ldsm_x4(A + (r0 + (lane & 15)) * AS + k0 + (lane >> 4) * 8, a0, a1, a2, a3);
 #pragma unroll
-            for (int j = 0; j < NT; j++) {
-                const uint32_t b0 = *reinterpret_cast<const uint32_t *>(&B[j * 8 + gq][k0 + 2 * tq]);
-                const uint32_t b1 = *reinterpret_cast<const uint32_t *>(&B[j * 8 + gq][k0 + 2 * tq + 8]);
+            for (int j = 0; j + 1 < NT; j += 2) {
+                uint32_t b0, b1, b2, b3;
+                ldsm_x4(B + (j * 8 + (lane >> 4) * 8 + (lane & 7)) * AS + k0 + ((lane >> 3) & 1) * 8, b0, b1, b2, b3);
                 mma_bf16(acc[j], a0, a1, a2, a3, b0, b1);
+                mma_bf16(acc[j + 1], a0, a1, a2, a3, b2, b3);
+            }
+            if constexpr (NT % 2 == 1) {
+                uint32_t b0, b1;
+                ldsm_x2(B + ((NT - 1) * 8 + (lane & 7)) * AS + k0 + ((lane >> 3) & 1) * 8, b0, b1);
+                mma_bf16(acc[NT - 1], a0, a1, a2, a3, b0, b1);
             }
         }
     }
@@ -171,7 +355,7 @@ __global__ void __launch_bounds__(kLayerThreads) k_layer(void *y, const void *x,
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             const int r = warp * 16 + gq + 8 * h;
-            const long n = n0 + r / 3;
+            const long n = (long)n0 + r / 3;
             if (n < g.V) act_st<FOUT>(y, g.V, c, n, al * 3 + r % 3, make_float2(acc[j][2 * h], acc[j][2 * h + 1]));
         }
     }
@@ -179,53 +363,54 @@ __global__ void __launch_bounds__(kLayerThreads) k_layer(void *y, const void *x,
 
 // P[d][k][j] += sum over rows of A_d[row][k] G[row][j]  (real; A from x, G from the output gradient)
 template <int CIN, int COUT, int FIN>
-__global__ void __launch_bounds__(128) k_wgrad(float *__restrict__ P, const void *x, const float2 *__restrict__ G,
-                                               const float2 *__restrict__ U, Geo g, int ntiles) {
+__global__ void __launch_bounds__(kLayerWarps * 32) k_wgrad(float *__restrict__ P, const void *x,
+                                                            const float2 *__restrict__ G,
+                                                            const float2 *__restrict__ U, Geo g, int ntiles) {
     constexpr int KD = CIN * 8, KDP = KD < 16 ? 16 : KD, N = COUT * 8, NM = KDP / 16, NT = N / 8;
-    constexpr int PAIRS = NM * NT, PW = (PAIRS + 3) / 4;  // (m-tile, n-tile) pairs per warp
-    constexpr int RS = kTileRows + 8;
-    __shared__ __align__(16) __nv_bfloat16 At[KDP][RS];
-    __shared__ __align__(16) __nv_bfloat16 Gt[N][RS];
+    constexpr int NW = kLayerWarps, PAIRS = NM * NT, PW = (PAIRS + NW - 1) / NW;  // (m-tile, n-tile) pairs per warp
+    constexpr int AS = KDP + 8, RS = kLayerRows + 8;
+    // dynamic shared memory: A [rows][AS] as built, At [KDP][RS] transposed for the MMA, Gt [N][RS]
+    extern __shared__ __align__(16) unsigned char wg_smem[];
+    auto A = reinterpret_cast<__nv_bfloat16(*)[AS]>(wg_smem);
+    auto At = reinterpret_cast<__nv_bfloat16(*)[RS]>(wg_smem + sizeof(__nv_bfloat16) * kLayerRows * AS);
+    auto Gt = reinterpret_cast<__nv_bfloat16(*)[RS]>(wg_smem + sizeof(__nv_bfloat16) * (kLayerRows * AS + KDP * RS));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gq = lane >> 2, tq = lane & 3;
-    for (int i = tid; i < KDP * RS; i += 128) (&At[0][0])[i] = __float2bfloat16(0.f);
+    for (int i = tid; i < kLayerRows * AS; i += NW * 32) (&A[0][0])[i] = __float2bfloat16(0.f);
     for (int d = 0; d < 9; d++) {
         float acc[PW][4];
 #pragma unroll
         for (int q = 0; q < PW; q++) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-            const long n0 = (long)tile * kTileSites;
+            const long n0 = (long)tile * kLayerSites;
             __syncthreads();
-            for (int item = tid; item < kTileSites * CIN; item += 128) {
-                const int s = item % kTileSites, ch = item / kTileSites;
-                const long n = n0 + s;
-                float2 z[12];
-                if (n < g.V) transport<FIN>(x, ch, U, g, d, n, z);
-                else
+            if (tid < kLayerRows) {
+                const int r = tid;
+                const long n = n0 + r / 3;
+                if (n < g.V) {
+                    transport_row<CIN, FIN>(x, U, g, d, n, r % 3, &A[r][0]);
+                } else {
+                    for (int k = 0; k < KD; k++) A[r][k] = __float2bfloat16(0.f);
+                }
+                // output gradient row (n, a): COUT x 4 complex
+                for (int c = 0; c < COUT; c++)
 #pragma unroll
-                    for (int k = 0; k < 12; k++) z[k] = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int be = 0; be < 4; be++)
-#pragma unroll
-                    for (int a = 0; a < 3; a++) {
-                        const int col = (ch * 4 + be) * 2;
-                        At[col][s * 3 + a] = __float2bfloat16(z[be * 3 + a].x);
-                        At[col + 1][s * 3 + a] = __float2bfloat16(z[be * 3 + a].y);
+                    for (int al = 0; al < 4; al++) {
+                        const float2 v = n < g.V ? G[((long)c * g.V + n) * 12 + al * 3 + r % 3] : make_float2(0.f, 0.f);
+                        Gt[(c * 4 + al) * 2][r] = __float2bfloat16(v.x);
+                        Gt[(c * 4 + al) * 2 + 1][r] = __float2bfloat16(v.y);
                     }
             }
-            for (int item = tid; item < kTileSites * COUT * 12; item += 128) {
-                const int s = item % kTileSites, rest = item / kTileSites, k = rest % 12, c = rest / 12;
-                const long n = n0 + s;
-                const float2 v = n < g.V ? G[((long)c * g.V + n) * 12 + k] : make_float2(0.f, 0.f);
-                const int al = k / 3, a = k % 3, col = (c * 4 + al) * 2;
-                Gt[col][s * 3 + a] = __float2bfloat16(v.x);
-                Gt[col + 1][s * 3 + a] = __float2bfloat16(v.y);
+            __syncthreads();
+            for (int i = tid; i < kLayerRows * KDP; i += NW * 32) {
+                const int r = i % kLayerRows, k = i / kLayerRows;
+                At[k][r] = A[r][k];
             }
             __syncthreads();
 #pragma unroll
-            for (int r0 = 0; r0 < kTileRows; r0 += 16) {
+            for (int r0 = 0; r0 < kLayerRows; r0 += 16) {
 #pragma unroll
                 for (int q = 0; q < PW; q++) {
-                    const int pr = warp + 4 * q;
+                    const int pr = warp + NW * q;
                     if (pr >= PAIRS) break;
                     const int m0 = (pr / NT) * 16, j0 = (pr % NT) * 8;
                     const uint32_t a0 = *reinterpret_cast<const uint32_t *>(&At[m0 + gq][r0 + 2 * tq]);
@@ -240,7 +425,7 @@ __global__ void __launch_bounds__(128) k_wgrad(float *__restrict__ P, const void
         }
 #pragma unroll
         for (int q = 0; q < PW; q++) {
-            const int pr = warp + 4 * q;
+            const int pr = warp + NW * q;
             if (pr >= PAIRS) break;
             const int m0 = (pr / NT) * 16, j0 = (pr % NT) * 8;
             float *Pd = P + (long)d * KDP * N;
@@ -387,20 +572,34 @@ Geo geo(const qcd_ctx *c) {
 
 template <int CIN, int COUT, int FIN, int FOUT>
 int launch_layer(qcd_ctx *c, void *y, const void *x, const __nv_bfloat16 *Bt) {
-    const long tiles = (c->lat.V + kTileSites - 1) / kTileSites;
+    constexpr size_t smem = LayerSmem<CIN, COUT, FIN>::total;
+    static bool attr = false;
+    if (!attr) {
+        QCD_CUDA(c, cudaFuncSetAttribute(k_layer<CIN, COUT, FIN, FOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+        attr = true;
+    }
+    const long tiles = (c->lat.V + kLayerSites - 1) / kLayerSites;
     cudaEvent_t ev;
     prof_begin(c, QCD_K_LEARNED, &ev);
-    k_layer<CIN, COUT, FIN, FOUT><<<(unsigned)tiles, kLayerThreads, 0, c->stream>>>(y, x, c->U32, Bt, geo(c));
+    k_layer<CIN, COUT, FIN, FOUT><<<(unsigned)tiles, kLayerWarps * 32, smem, c->stream>>>(y, x, c->U32, Bt, geo(c));
     return prof_end(c, QCD_K_LEARNED, ev);
 }
 
 template <int CIN, int COUT, int FIN>
 int launch_wgrad(qcd_ctx *c, float *P, const void *x, const float2 *G) {
-    const int tiles = (int)((c->lat.V + kTileSites - 1) / kTileSites);
-    const int grid = tiles < 608 ? tiles : 608;
+    constexpr int KD = CIN * 8, KDP = KD < 16 ? 16 : KD, N = COUT * 8;
+    constexpr size_t smem = sizeof(__nv_bfloat16) * ((size_t)kLayerRows * (KDP + 8) + (size_t)(KDP + N) * (kLayerRows + 8));
+    static bool attr = false;
+    if (!attr) {
+        QCD_CUDA(c, cudaFuncSetAttribute(k_wgrad<CIN, COUT, FIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    const int tiles = (int)((c->lat.V + kLayerSites - 1) / kLayerSites);
+    const int grid = tiles < 304 ? tiles : 304;
     cudaEvent_t ev;
     prof_begin(c, QCD_K_LEARNED, &ev);
-    k_wgrad<CIN, COUT, FIN><<<grid, 128, 0, c->stream>>>(P, x, G, c->U32, geo(c), tiles);
+    k_wgrad<CIN, COUT, FIN><<<grid, kLayerWarps * 32, smem, c->stream>>>(P, x, G, c->U32, geo(c), tiles);
     return prof_end(c, QCD_K_LEARNED, ev);
 }
 

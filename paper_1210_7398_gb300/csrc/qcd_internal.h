@@ -68,6 +68,7 @@ constexpr int kLearnedChans[kLearnedLayers + 1] = {1, 8, 8, 1};
 
 struct Learned {
     bool ready = false;
+    int verdict = -1;        // last qcd_learned_evaluate: -1 none, 0 plain SAP faster, 1 learned faster
     long step = 0;           // Adam steps taken
     float2 *W = nullptr;     // FP32 master weights (complex)
     float2 *grad = nullptr;  // accumulated gradient, real pairs 2 (Re, Im) of dL/dW*

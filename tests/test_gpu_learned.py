@@ -111,3 +111,37 @@ def test_training_reduces_loss_and_solver_converges():
     r = b.cpu().numpy()[0] - oracle.apply_D(dims, U, F, KAPPA, x.cpu().numpy()[0])
     assert np.linalg.norm(r) / np.linalg.norm(b.cpu().numpy()[0]) <= 1e-10, st
     s.close()
+
+
+def test_trained_correction_gain_and_fallback():
+    """What the trained network gains over plain SAP on a 12^3 x 24 field with small SAP blocks
+    (2^3 x 3, 2 sweeps, 2 cycles): fewer inner iterations at the same FP64 accuracy.  The
+    verdict picks the faster method, and learned = 1 follows it (the fallback)."""
+    dims = (12, 12, 12, 24)
+    s, U = setup(dims, seed=1001)
+    prm = q.make_params(KAPPA, CSW, (2, 2, 2, 3), (2, 2, 2, 3), nsweep=2, nsap=2, tol=1e-10)
+    q.qcd_learned_set_weights(s.ctx, q.learned_init_weights(4000))
+    src = qi.gaussian_spinor_torch(dims, 3000, 64, "cuda").to(torch.complex64).contiguous()
+    hist = q.qcd_learned_train(s.ctx, src, 64, prm, epochs=8, batch=8, lr=3e-3)
+    assert hist[-1] < 0.5 * hist[0], hist
+    b = torch.from_numpy(qi.gaussian_spinor(dims, seed=2001)).cuda()
+    v = q.qcd_learned_evaluate(s.ctx, b, 1, prm)
+    print("learned-correction verdict:", v)
+    assert v["plain_relres"] <= 1e-10 and v["learned_relres"] <= 1e-10, v
+    assert v["learned_inner"] < v["plain_inner"], v
+    assert v["use_learned"] == (1 if v["learned_ms"] < v["plain_ms"] else 0)
+    # learned = 1 uses the correction exactly when the verdict favours it
+    prm_l = q.make_params(KAPPA, CSW, (2, 2, 2, 3), (2, 2, 2, 3), nsweep=2, nsap=2, tol=1e-10)
+    prm_l.learned = 1
+    q.qcd_set_profiling(s.ctx, True)
+    q.qcd_kernel_stats(s.ctx, 6, reset=True)
+    x = torch.zeros_like(b)
+    st = s.solve(x, b, prm_l)
+    n_learned, _ = q.qcd_kernel_stats(s.ctx, 6, reset=True)
+    q.qcd_set_profiling(s.ctx, False)
+    assert (n_learned > 0) == bool(v["use_learned"]), (n_learned, v)
+    assert st["inner_iters"] == (v["learned_inner"] if v["use_learned"] else v["plain_inner"])
+    F = oracle.clover(dims, U, CSW, KAPPA)[1]
+    r = b.cpu().numpy()[0] - oracle.apply_D(dims, U, F, KAPPA, x.cpu().numpy()[0])
+    assert np.linalg.norm(r) / np.linalg.norm(b.cpu().numpy()[0]) <= 1e-10, st
+    s.close()
