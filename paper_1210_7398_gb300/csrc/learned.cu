@@ -160,6 +160,70 @@ template <int CIN, int COUT, int FIN> struct LayerSmem {
                   "16-byte staging");
 };
 
+// Transport of one (site, channel group) item of the layer kernel: the A rows of the site,
+// A[a][8 ch + 2 be (+1)] = sum_b W[a][b] x_ch[be][b] for the CPI channels from cg on.  KIND:
+// 0 identity, 1 forward W = U_mu(n), 2 backward W = U_mu(n - mu)^dag, 3 / 4 the same times the
+// time-boundary sign.  xs: the staged neighbour site, l: its nine link elements.
+template <int CIN, int CPI, int FIN, int KIND>
+__device__ __forceinline__ void transport_item(const unsigned char *xs, const float2 *l, float sg, __nv_bfloat16 *arow,
+                                               int cg, int as) {
+    constexpr bool FWD = KIND == 1 || KIND == 3, SIGN = KIND >= 3;
+#pragma unroll
+    for (int cc = 0; cc < CPI; cc++) {
+        const int ch = cg + cc;
+        float2 v[12];
+        if constexpr (FIN == SITE16) {
+            const uint4 *q = reinterpret_cast<const uint4 *>(xs + ch * 48);
+#pragma unroll
+            for (int t = 0; t < 3; t++) {
+                const uint4 u4 = q[t];
+                const uint32_t wds[4] = {u4.x, u4.y, u4.z, u4.w};
+#pragma unroll
+                for (int e = 0; e < 4; e++)
+                    v[t * 4 + e] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&wds[e]));
+            }
+        } else {
+            const float4 *q = reinterpret_cast<const float4 *>(xs + ch * 96);
+#pragma unroll
+            for (int t = 0; t < 6; t++) {
+                const float4 f4 = q[t];
+                v[2 * t] = make_float2(f4.x, f4.y);
+                v[2 * t + 1] = make_float2(f4.z, f4.w);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            float2 w[3];  // row a of the transport matrix
+            if constexpr (KIND > 0) {
+#pragma unroll
+                for (int b = 0; b < 3; b++) {
+                    float2 u = FWD ? l[a * 3 + b] : l[b * 3 + a];
+                    if (!FWD) u.y = -u.y;
+                    w[b] = SIGN ? cscale(u, sg) : u;
+                }
+            }
+            uint32_t packed[4];
+#pragma unroll
+            for (int be = 0; be < 4; be++) {
+                if constexpr (KIND == 0) {
+                    packed[be] = pack_bf16(v[be * 3 + a].x, v[be * 3 + a].y);
+                } else {
+                    // packed FP32 pairs: p = sum_b Re(w_b) x_b, q = sum_b Im(w_b) x_b; w x = (p.x - q.y, p.y + q.x)
+                    float2 pr = __fmul2_rn(make_float2(w[0].x, w[0].x), v[be * 3]);
+                    float2 pi = __fmul2_rn(make_float2(w[0].y, w[0].y), v[be * 3]);
+#pragma unroll
+                    for (int b = 1; b < 3; b++) {
+                        pr = __ffma2_rn(make_float2(w[b].x, w[b].x), v[be * 3 + b], pr);
+                        pi = __ffma2_rn(make_float2(w[b].y, w[b].y), v[be * 3 + b], pi);
+                    }
+                    packed[be] = pack_bf16(pr.x - pi.y, pr.y + pi.x);
+                }
+            }
+            *reinterpret_cast<uint4 *>(arow + a * as + ch * 8) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        }
+    }
+}
+
 // y = layer(x): CIN -> COUT channels.  Bt: [9][N][KDP] BF16, N = COUT*8, KDP = max(16, CIN*8).
 // A CTA owns 64 sites (192 rows, one 16-row MMA tile per warp).  Per direction: the neighbour
 // inputs (all channels), their links and the direction's weights are staged with cp.async one
@@ -172,9 +236,9 @@ __global__ void __launch_bounds__(kLayerWarps * 32, FIN == SITE32 ? 1 : 2) k_lay
     using S = LayerSmem<CIN, COUT, FIN>;
     constexpr int KDP = S::KDP, N = S::N, AS = S::AS, NT = N / 8, XS = S::XS;
     constexpr int NTH = kLayerWarps * 32;
-    constexpr int CPI = CIN < 2 ? CIN : 2;             // channels per transport item
+    constexpr int CPI = 1;                            // channels per transport item
     constexpr int ITEMS = kLayerSites * (CIN / CPI);  // transport items per direction
-    static_assert(CIN % CPI == 0 && ITEMS <= NTH, "one transport item per thread");
+    static_assert(CIN % CPI == 0, "whole channel groups");
     extern __shared__ __align__(16) unsigned char ly_smem[];
     __nv_bfloat16 *A = reinterpret_cast<__nv_bfloat16 *>(ly_smem + 2 * S::stage);
     int *nbt = reinterpret_cast<int *>(ly_smem + 2 * S::stage + S::a_bytes);  // [9][64] neighbour, -1 past the end
@@ -262,6 +326,7 @@ __global__ void __launch_bounds__(kLayerWarps * 32, FIN == SITE32 ? 1 : 2) k_lay
     for (int j = 0; j < NT; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
 
     issue(0);
+#pragma unroll 1
     for (int d = 0; d < 9; d++) {
         cp_wait<0>();
         __syncthreads();  // stage d visible; every warp is done with the previous A and stage
@@ -270,62 +335,15 @@ __global__ void __launch_bounds__(kLayerWarps * 32, FIN == SITE32 ? 1 : 2) k_lay
         const float2 *L = reinterpret_cast<const float2 *>(X + S::x_bytes);
         const __nv_bfloat16 *B = reinterpret_cast<const __nv_bfloat16 *>(X + S::x_bytes + S::l_bytes);
         // transport: A[3 st + a][8 ch + 2 be (+1)] = sum_b W[a][b] x_ch(m)[be][b], W = 1, U_mu(n) or
-        // U_mu(n - mu)^dag, times the boundary sign
-        if (tid < ITEMS) {
-            const int st = tid / (CIN / CPI), cg = (tid % (CIN / CPI)) * CPI;
-            const bool fwd = ((d - 1) & 1) == 0;
+        // U_mu(n - mu)^dag, times the boundary sign (time direction only)
+        for (int it = tid; it < ITEMS; it += NTH) {
+            const int st = it / (CIN / CPI), cg = (it % (CIN / CPI)) * CPI;
             const float sg = sgt[d * kLayerSites + st];
-#pragma unroll
-            for (int cc = 0; cc < CPI; cc++) {
-                const int ch = cg + cc;
-                float2 v[12];
-                if constexpr (FIN == SITE16) {
-                    const uint4 *q = reinterpret_cast<const uint4 *>(X + st * XS + ch * 48);
-#pragma unroll
-                    for (int t = 0; t < 3; t++) {
-                        const uint4 u4 = q[t];
-                        const uint32_t wds[4] = {u4.x, u4.y, u4.z, u4.w};
-#pragma unroll
-                        for (int e = 0; e < 4; e++)
-                            v[t * 4 + e] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&wds[e]));
-                    }
-                } else {
-                    const float4 *q = reinterpret_cast<const float4 *>(X + st * XS + ch * 96);
-#pragma unroll
-                    for (int t = 0; t < 6; t++) {
-                        const float4 f4 = q[t];
-                        v[2 * t] = make_float2(f4.x, f4.y);
-                        v[2 * t + 1] = make_float2(f4.z, f4.w);
-                    }
-                }
-#pragma unroll
-                for (int a = 0; a < 3; a++) {
-                    float2 w[3];  // row a of the transport matrix
-                    if (d > 0) {
-#pragma unroll
-                        for (int b = 0; b < 3; b++) {
-                            float2 u = fwd ? L[st * 9 + a * 3 + b] : L[st * 9 + b * 3 + a];
-                            if (!fwd) u.y = -u.y;
-                            w[b] = cscale(u, sg);
-                        }
-                    }
-                    uint32_t packed[4];
-#pragma unroll
-                    for (int be = 0; be < 4; be++) {
-                        float2 z;
-                        if (d == 0) {
-                            z = v[be * 3 + a];
-                        } else {
-                            z = cmul(w[0], v[be * 3]);
-                            z = cfma(w[1], v[be * 3 + 1], z);
-                            z = cfma(w[2], v[be * 3 + 2], z);
-                        }
-                        packed[be] = pack_bf16(z.x, z.y);
-                    }
-                    *reinterpret_cast<uint4 *>(A + (st * 3 + a) * AS + ch * 8) =
-                        make_uint4(packed[0], packed[1], packed[2], packed[3]);
-                }
-            }
+            if (d == 0) transport_item<CIN, CPI, FIN, 0>(X + st * XS, L + st * 9, sg, A + st * 3 * AS, cg, AS);
+            else if (d < 7 && (d & 1)) transport_item<CIN, CPI, FIN, 1>(X + st * XS, L + st * 9, sg, A + st * 3 * AS, cg, AS);
+            else if (d < 7) transport_item<CIN, CPI, FIN, 2>(X + st * XS, L + st * 9, sg, A + st * 3 * AS, cg, AS);
+            else if (d & 1) transport_item<CIN, CPI, FIN, 3>(X + st * XS, L + st * 9, sg, A + st * 3 * AS, cg, AS);
+            else transport_item<CIN, CPI, FIN, 4>(X + st * XS, L + st * 9, sg, A + st * 3 * AS, cg, AS);
         }
         __syncthreads();
         const int r0 = warp * 16;
