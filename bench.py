@@ -224,6 +224,117 @@ def learned_section(q, qi, torch, s, dims, prm, b, nrhs, npairs, epochs, lr=3e-3
             "fallback": "plain SAP" if not v["use_learned"] else None}
 
 
+def timed(torch, fn):
+    """Wall time of fn() on the device, synchronised on both sides (seconds)."""
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = fn()
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0, r
+
+
+def point_sources_torch(torch, dims, first, count):
+    """Spin-colour point sources first..first+count-1 at the origin, complex128 on the device."""
+    V = 1
+    for L in dims:
+        V *= L
+    b = torch.zeros((count, V, 4, 3), dtype=torch.complex128, device="cuda")
+    for j in range(count):
+        k = first + j
+        b[j, 0, k // 3, k % 3] = 1.0
+    return b
+
+
+def batched_section(q, qi, torch, csw, eps, tol, inner_tol, candidates):
+    """Uneven instances solved one after the other and then concurrently (qcd_solve_multi):
+    24^3x48 with 12 point sources and 8^3x16, 12^3x24, 16^3x32 with one Gaussian source each;
+    each instance's SAP set-up autotuned on its own source (FP16 storage among the candidates)."""
+    specs = [((24, 24, 24, 48), 0.120, 12), ((8, 8, 8, 16), 0.118, 1), ((12, 12, 12, 24), 0.120, 1),
+             ((16, 16, 16, 32), 0.122, 1)]
+    solvers, streams, bs, prms, nr, info = [], [], [], [], [], []
+    for i, (dims, kappa, nrhs) in enumerate(specs):
+        st = torch.cuda.Stream()
+        sv = q.Solver(dims, stream=st.cuda_stream)
+        Ug = qi.gauge_field(dims, eps, seed=1002 + i, device="cuda")
+        torch.cuda.synchronize()  # made on torch's stream, read on the context's
+        sv.load_gauge(Ug)
+        del Ug
+        sv.build_clover(kappa, csw)
+        b = point_sources_torch(torch, dims, 0, 12) if nrhs == 12 else \
+            qi.gaussian_spinor_torch(dims, 2002 + i, 1, "cuda").contiguous()
+        base = q.make_params(kappa, csw, tuple(L // 2 for L in dims), tuple(L // 2 for L in dims), tol=tol,
+                             inner_tol=inner_tol)
+        torch.cuda.synchronize()  # inputs made on torch's stream are complete before the context's stream reads them
+        best, ms = q.qcd_autotune(sv.ctx, b[:1].contiguous(), base, max_candidates=candidates)
+        solvers.append(sv)
+        streams.append(st)
+        bs.append(b)
+        prms.append(best)
+        nr.append(nrhs)
+        info.append({"lattice": "x".join(map(str, dims)), "kappa": kappa, "nrhs": nrhs, "params": q.params_dict(best)})
+    # warm both ways once, then time
+    xs = [torch.zeros_like(b) for b in bs]
+    q.qcd_solve_multi([sv.ctx for sv in solvers], xs, bs, prms, nr)
+    seq = []
+    for sv, x, b, p, n, inf in zip(solvers, xs, bs, prms, nr, info):
+        x.zero_()
+        t, st = timed(torch, lambda: sv.solve(x, b, p, nrhs=n))
+        seq.append(t)
+        inf.update({"seconds_alone": t, "outer_iters": st["outer_iters"], "inner_iters": st["inner_iters"],
+                    "true_rel_res": st["true_rel_res"]})
+    for x in xs:
+        x.zero_()
+    t_multi, (rc, sts) = timed(torch, lambda: q.qcd_solve_multi([sv.ctx for sv in solvers], xs, bs, prms, nr))
+    for inf, st in zip(info, sts):
+        inf["true_rel_res_multi"] = st["true_rel_res"]
+    for sv in solvers:
+        sv.close()
+    return {"instances": info, "seconds_sequential": sum(seq), "seconds_concurrent": t_multi,
+            "speedup_concurrent": sum(seq) / t_multi,
+            "note": "concurrent = qcd_solve_multi: one host thread and one stream per instance; "
+                    "each instance replays its captured inner iteration"}
+
+
+def headline_section(q, qi, torch, w, group, candidates):
+    """48^3 x 96, kappa 0.122, the 12 spin-colour point sources in right-hand-side groups of `group`:
+    plain FP32 SAP (the workload's literal set-up) against the autotuned set-up."""
+    dims = (48, 48, 48, 96)
+    st = torch.cuda.Stream()
+    sv = q.Solver(dims, stream=st.cuda_stream)
+    Ug = qi.gauge_field(dims, w["eps"], seed=1004, device="cuda")
+    torch.cuda.synchronize()  # made on torch's stream, read on the context's
+    sv.load_gauge(Ug)
+    del Ug
+    torch.cuda.empty_cache()
+    sv.build_clover(0.122, w["csw"])
+    plain = q.make_params(0.122, w["csw"], w["block"], w["subblock"], omega=w["omega"], nsweep=w["nsweep"],
+                          nsap=w["nsap"], tol=w["tol"], inner_tol=w["inner_tol"])
+    g = qi.gaussian_spinor_torch(dims, 2004, 1, "cuda").contiguous()
+    torch.cuda.synchronize()
+    t_tune, (best, _) = timed(torch, lambda: q.qcd_autotune(sv.ctx, g, plain, max_candidates=candidates))
+    del g
+    out = {"lattice": "48x48x48x96", "kappa": 0.122, "sources": 12, "rhs_group": group,
+           "tuning_seconds": t_tune, "chosen_params": q.params_dict(best)}
+    for name, p in (("plain", plain), ("chosen", best)):
+        total, iters, res = 0.0, [], 0.0
+        for k0 in range(0, 12, group):
+            b = point_sources_torch(torch, dims, k0, group)
+            x = torch.zeros_like(b)
+            torch.cuda.synchronize()
+            t, stt = timed(torch, lambda: sv.solve(x, b, p, nrhs=group))
+            total += t
+            iters.append((stt["outer_iters"], stt["inner_iters"]))
+            res = max(res, stt["true_rel_res"])
+            del b, x
+            torch.cuda.empty_cache()
+        out[name] = {"seconds": total, "seconds_per_source": total / 12, "iters_per_group": iters,
+                     "true_rel_res_max": res}
+    out["speedup_chosen_vs_plain"] = out["plain"]["seconds"] / out["chosen"]["seconds"]
+    sv.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -240,6 +351,14 @@ def run_gpu(args):
     import qcd_inputs as qi
 
     peaks = read_peaks()
+    # all work of this run on one non-default stream: the library replays its captured inner
+    # iteration only there, and torch's fills and copies stay ordered with the solves
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        return run_gpu_on_stream(args, q, qi, torch, np, peaks, rank, world, local)
+
+
+def run_gpu_on_stream(args, q, qi, torch, np, peaks, rank, world, local):
     w = WORKLOAD
     dims = w["dims"]
     V = qi.volume(dims)
@@ -360,6 +479,12 @@ def run_gpu(args):
             chosen["value"] = lr_sec["verdict"]["learned_ms"] / 1000.0
             chosen["params"]["learned"] = 1
             chosen["speedup_vs_plain"] = ms_step / lr_sec["verdict"]["learned_ms"]
+    batched = None
+    if args.batched_full:
+        batched = batched_section(q, qi, torch, w["csw"], w["eps"], w["tol"], w["inner_tol"], 16)
+    headline = None
+    if args.headline:
+        headline = headline_section(q, qi, torch, w, args.rhs_group, 12)
     learned_full = None
     if args.learned_full:
         # 24^3 x 48, kappa 0.122, 12 point sources, 256 training pairs, plain SAP with 4 sweeps
@@ -426,6 +551,10 @@ def run_gpu(args):
                "dslash": dsl, "chosen": chosen, "cpu_baseline": cpu}
         if learned_full is not None:
             out["learned_24x24x24x48"] = learned_full
+        if batched is not None:
+            out["batched_uneven"] = batched
+        if headline is not None:
+            out["headline_48x48x48x96"] = headline
         print(json.dumps(out))
     if world > 1:
         torch.distributed.barrier()
@@ -443,6 +572,11 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--skip-chosen", action="store_true", help="skip the autotuned (chosen) measurement")
     ap.add_argument("--tune-candidates", type=int, default=48, help="solves the autotuner may time")
+    ap.add_argument("--batched-full", action="store_true",
+                    help="also solve 24^3x48 (12 point sources) + 8^3x16, 12^3x24, 16^3x32 alone and concurrently")
+    ap.add_argument("--headline", action="store_true",
+                    help="also solve 48^3x96 with 12 point sources, plain and autotuned")
+    ap.add_argument("--rhs-group", type=int, default=4, help="right-hand sides per 48^3x96 solve")
     ap.add_argument("--learned-full", action="store_true",
                     help="also train and judge the learned correction on 24^3 x 48 with 12 point sources")
     args = ap.parse_args()

@@ -170,6 +170,18 @@ int qcd_sap_precondition_noalloc(qcd_ctx *ctx, float *out, const float *in, cons
 int qcd_solve(qcd_ctx *ctx, double *x, const double *b, const qcd_params *p, int nrhs,
               qcd_stats *st);
 
+/* Solves n independent problems at once: instance i is ctxs[i] (its own
+ * lattice, gauge field, clover field and kappa) with x[i], b[i], params[i],
+ * nrhs[i] as in qcd_solve.  The instances run concurrently on the GPU, each on
+ * its context's stream driven by its own host thread, so that small lattices
+ * fill the SMs a large one leaves idle.  Every context must have its own
+ * stream, other than the legacy default stream (QCD_ERR_ARG otherwise), and
+ * none may be used by another thread during the call.  stats (may be NULL):
+ * [n], one per instance.  Returns the first non-OK status in instance order,
+ * QCD_OK when all converged.  No counterpart in the paper. */
+int qcd_solve_multi(int n, qcd_ctx *const *ctxs, double *const *x, const double *const *b, const qcd_params *params,
+                    const int *nrhs, qcd_stats *stats);
+
 /* on != 0 (default): qcd_solve captures one inner BiCGStab iteration as a CUDA
  * graph and replays it, when the context stream is not the legacy default
  * stream and kernel profiling is off.  Results do not depend on it. */
@@ -177,10 +189,12 @@ int qcd_set_graphs(qcd_ctx *ctx, int on);
 
 /* Tuning knob of the SAP block kernel; results do not depend on it.  The
  * least number of CTAs (one thread-block cluster) that share one SAP block,
- * 1..8: the kernel splits each block along t over the smallest divisor of
- * block[3] that is >= min_ctas and whose slabs fit in shared memory.  More
- * CTAs per block spread a step's sites over more SMs at the price of more
- * cluster barriers.  Default 1. */
+ * 0..8: the kernel splits each block along t over a divisor C <= 8 of
+ * block[3] whose slabs fit in shared memory.  min_ctas >= 1: the smallest such
+ * C >= min_ctas.  0 (default): the largest such C for which the blocks of one
+ * colour, one cluster each, still fit the SM count (at least the smallest C
+ * that fits).  More CTAs per block spread a step's sites over more SMs at the
+ * price of more cluster barriers. */
 int qcd_set_sap_ctas(qcd_ctx *ctx, int min_ctas);
 
 /* Autotuner (no counterpart in the paper, which fixes 6^4 blocks with 3^4

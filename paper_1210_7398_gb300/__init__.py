@@ -28,7 +28,7 @@ EXPORTS = ("qcd_create", "qcd_destroy", "qcd_last_error", "qcd_set_boundary", "q
            "qcd_kernel_stats", "qcd_launch_count", "qcd_bench_dslash", "qcd_sap_precondition_noalloc",
            "qcd_set_sap_ctas", "qcd_set_graphs", "qcd_autotune", "qcd_learned_weight_count",
            "qcd_learned_set_weights", "qcd_learned_get_weights", "qcd_learned_apply", "qcd_learned_loss_grad",
-           "qcd_learned_train", "qcd_learned_evaluate")
+           "qcd_learned_train", "qcd_learned_evaluate", "qcd_solve_multi")
 
 
 class QcdError(RuntimeError):
@@ -100,6 +100,7 @@ def load_library(path: str = LIB_PATH):
         "qcd_learned_loss_grad": (I, [P, P, P, ctypes.POINTER(D), P]),
         "qcd_learned_train": (I, [P, P, I, ctypes.POINTER(qcd_params), I, I, ctypes.c_float, P]),
         "qcd_learned_evaluate": (I, [P, P, I, ctypes.POINTER(qcd_params), ctypes.POINTER(qcd_learned_verdict)]),
+        "qcd_solve_multi": (I, [I, P, P, P, P, P, P]),
         "qcd_autotune": (I, [P, P, I, ctypes.POINTER(qcd_params), ctypes.POINTER(qcd_params),
                              ctypes.POINTER(D), I]),
         "qcd_kernel_stats": (I, [P, I, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(D), I]),
@@ -191,6 +192,24 @@ def qcd_solve(ctx, x, b, params: qcd_params, nrhs: int = 1, check: bool = True):
     d = st.as_dict()
     d["rc"] = rc
     return d
+
+
+def qcd_solve_multi(ctxs, xs, bs, params, nrhs, check: bool = True):
+    """Solves the instances (contexts with distinct streams) concurrently; returns (rc, [stats dict])."""
+    n = len(ctxs)
+    C = ctypes.c_void_p * n
+    prm = (qcd_params * n)(*params)
+    nr = (ctypes.c_int * n)(*[int(v) for v in nrhs])
+    st = (qcd_stats * n)()
+    cv = ctypes.c_void_p
+    arrs = [C(*[cv(c) if not isinstance(c, cv) else c for c in ctxs]), C(*[_ptr(v) for v in xs]),
+            C(*[_ptr(v) for v in bs]), prm, nr, st]
+    rc = load_library().qcd_solve_multi(n, *[ctypes.cast(a, cv) for a in arrs])
+    out = [st[i].as_dict() for i in range(n)]
+    if check and rc != QCD_OK:
+        bad = next((i for i in range(n) if out[i]["status"] != QCD_OK), 0)
+        _check(ctxs[bad], rc)
+    return rc, out
 
 
 def qcd_set_sap_ctas(ctx, min_ctas: int):

@@ -6,6 +6,8 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <thread>
+#include <vector>
 
 #include "qcd_internal.h"
 
@@ -389,6 +391,35 @@ int qcd_solve(qcd_ctx *c, double *x, const double *b, const qcd_params *p, int n
     return status;
 }
 
+int qcd_solve_multi(int n, qcd_ctx *const *ctxs, double *const *x, const double *const *b, const qcd_params *params,
+                    const int *nrhs, qcd_stats *stats) {
+    if (n < 1 || !ctxs || !x || !b || !params || !nrhs) return QCD_ERR_ARG;
+    for (int i = 0; i < n; i++) {
+        if (!ctxs[i]) return QCD_ERR_ARG;
+        if (!ctxs[i]->stream) return fail(ctxs[i], QCD_ERR_ARG, "qcd_solve_multi: each context needs its own stream");
+        for (int j = 0; j < i; j++)
+            if (ctxs[j] == ctxs[i] || ctxs[j]->stream == ctxs[i]->stream)
+                return fail(ctxs[i], QCD_ERR_ARG, "qcd_solve_multi: contexts and streams must be distinct");
+    }
+    std::vector<int> rc(n, QCD_OK);
+    std::vector<qcd_stats> st(n);
+    auto one = [&](int i) {
+        cudaSetDevice(ctxs[i]->device);
+        std::memset(&st[i], 0, sizeof(qcd_stats));
+        rc[i] = qcd_solve(ctxs[i], x[i], b[i], &params[i], nrhs[i], &st[i]);
+    };
+    std::vector<std::thread> th;
+    th.reserve(n - 1);
+    for (int i = 1; i < n; i++) th.emplace_back(one, i);
+    one(0);
+    for (auto &t : th) t.join();
+    if (stats)
+        for (int i = 0; i < n; i++) stats[i] = st[i];
+    for (int i = 0; i < n; i++)
+        if (rc[i] != QCD_OK) return rc[i];
+    return QCD_OK;
+}
+
 int qcd_set_graphs(qcd_ctx *c, int on) {
     int rc = ready(c);
     if (rc) return rc;
@@ -399,7 +430,7 @@ int qcd_set_graphs(qcd_ctx *c, int on) {
 int qcd_set_sap_ctas(qcd_ctx *c, int min_ctas) {
     int rc = ready(c);
     if (rc) return rc;
-    if (min_ctas < 1 || min_ctas > 8) return fail(c, QCD_ERR_ARG, "min_ctas must lie in 1..8");
+    if (min_ctas < 0 || min_ctas > 8) return fail(c, QCD_ERR_ARG, "min_ctas must lie in 0..8");
     QCD_CUDA(c, c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
     if (c->sap_min_ctas != min_ctas) sap_invalidate(c);
     c->sap_min_ctas = min_ctas;

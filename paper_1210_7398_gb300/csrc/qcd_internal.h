@@ -120,7 +120,7 @@ struct qcd_ctx {
     // learned correction
     qcd::Learned net;
     long field_version = 0;  // bumped whenever the links or the clover field change
-    int sap_min_ctas = 1;    // lower bound on the CTAs (cluster size) per SAP block
+    int sap_min_ctas = 0;    // lower bound on the CTAs (cluster size) per SAP block; 0: fill the SMs
 
     // workspace, grown on demand
     std::vector<void *> allocations;

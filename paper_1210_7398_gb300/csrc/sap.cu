@@ -408,8 +408,9 @@ __global__ void __launch_bounds__(512) k_ssor_warp(SsorArgs a) {
         if (++k == 2 * nch) k = 0;
         if (++tring == kRing) tring = 0;
         if (t + 1 < T) {
-            if (a.C > 1 && a.flags[k]) cg::this_cluster().sync();
-            else __syncthreads();
+            const unsigned char f = a.flags[k];
+            if (f == 2) cg::this_cluster().sync();
+            else if (f == 1) __syncthreads();
         }
     }
     cp_async_wait<0>();
@@ -566,17 +567,19 @@ bool make_chunks(SapPlan &np, int C) {
     return true;
 }
 
-// Cluster barriers: a site reads its in-block neighbours in other slabs
-// through distributed shared memory.  Each such read must come after the
+// Barriers of the timeline.  A site reads its in-block neighbours (in other
+// slabs through distributed shared memory).  Each such read must come after the
 // neighbour's latest earlier write (barrier in (t_w, t]) and before its next
-// write (barrier in (t, t_n]).  The intervals are taken over three sweeps and
-// stabbed greedily; the chosen positions, folded modulo one sweep, give a
-// periodic pattern that stabs every interval of any number of sweeps (no
-// interval spans a whole sweep, because every site is written twice per sweep).
+// write (barrier in (t, t_n]), unless the same warp does both (the own value).
+// The intervals are taken over three sweeps and stabbed greedily, first those
+// of neighbours in other slabs with cluster barriers (flag 2), then the rest
+// with CTA barriers (flag 1) where no barrier stabs them yet; the positions,
+// folded modulo one sweep, give a periodic pattern that stabs every interval of
+// any number of sweeps (no interval spans a whole sweep, because every site is
+// written twice per sweep).  Position 0 is the barrier after the zero fill.
 void make_flags(SapPlan &np) {
     const int P = 2 * np.nchunks;
     np.h_flags.assign(P, 0);
-    if (np.C == 1) return;
     std::vector<int> chunk_of(np.vol, -1);
     for (int r = 0; r < np.C; r++)
         for (int ch = 0; ch < np.nchunks; ch++)
@@ -591,7 +594,7 @@ void make_flags(SapPlan &np) {
         }
         std::sort(w.begin(), w.end());
     };
-    std::vector<std::pair<int, int>> iv;  // (lo, hi]: need a barrier p with lo < p <= hi
+    std::vector<std::pair<int, int>> remote, local;  // (lo, hi]: need a barrier p with lo < p <= hi
     std::vector<int> wi, wj;
     const int plane = np.b[0] * np.b[1] * np.b[2];
     for (int yl = 0; yl < np.vol; yl++) {
@@ -603,7 +606,8 @@ void make_flags(SapPlan &np) {
                 const int ym = y[m] + dir;
                 if (ym < 0 || ym >= np.b[m]) continue;
                 const int nb = yl + dir * stride;
-                if ((yl / plane) / np.slab_t == (nb / plane) / np.slab_t) continue;
+                const bool other = (yl / plane) / np.slab_t != (nb / plane) / np.slab_t;
+                auto &iv = other ? remote : local;
                 writes(yl, wi);
                 writes(nb, wj);
                 for (int t : wi) {
@@ -619,15 +623,18 @@ void make_flags(SapPlan &np) {
             stride *= np.b[m];
         }
     }
-    std::sort(iv.begin(), iv.end(), [](const std::pair<int, int> &u, const std::pair<int, int> &v) {
-        return u.second < v.second;
-    });
-    int last = 0;  // the barrier after the zero fill, at p = 0
-    for (auto &v : iv) {
-        if (last > v.first) continue;  // already stabbed (last <= v.second by the sort order)
-        last = v.second;
-        if (last > 0) np.h_flags[last % P] = 1;  // p = 0 is the barrier after the zero fill
-    }
+    auto by_hi = [](const std::pair<int, int> &u, const std::pair<int, int> &v) { return u.second < v.second; };
+    auto stabbed = [&](const std::pair<int, int> &v) {
+        for (int p = v.first + 1; p <= v.second; p++)
+            if (p == 0 || np.h_flags[p % P]) return true;
+        return false;
+    };
+    std::sort(remote.begin(), remote.end(), by_hi);
+    for (auto &v : remote)
+        if (!stabbed(v) && v.second > 0) np.h_flags[v.second % P] = 2;
+    std::sort(local.begin(), local.end(), by_hi);
+    for (auto &v : local)
+        if (!stabbed(v) && v.second > 0) np.h_flags[v.second % P] = 1;
 }
 
 }  // namespace
@@ -657,29 +664,34 @@ int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &np,
         }
         order[lam * nsb + sig] = yl;
     }
-    // cut the order into steps of pairwise non-adjacent consecutive sites
-    std::vector<int> step_of(np.vol, -1);
-    np.h_step_ptr.push_back(0);
-    int cur = 0, cnt = 0;
+    // Level schedule of the ll order: a site's level is one more than the highest level of its
+    // in-block neighbours that come earlier in the order.  Neighbours never share a level, and
+    // every earlier neighbour of a site sits on a lower level and every later one on a higher
+    // level, so updating the levels one after the other (in any order within a level) reads
+    // exactly the values the sequential ll sweep reads: the same result, bit for bit, in as many
+    // dependent steps as the longest chain of the order (12 instead of 2592 for 6^3 x 12 blocks
+    // with 3^3 x 6 sub-blocks).  The backward sweep runs the levels in reverse.
+    std::vector<int> key_of(np.vol), level(np.vol, 0);
+    for (int k = 0; k < np.vol; k++) key_of[order[k]] = k;
+    int nlev = 0;
     for (int k = 0; k < np.vol; k++) {
         const int yl = order[k];
         int y[4], r = yl;
         for (int m = 0; m < 4; m++) { y[m] = r % b[m]; r /= b[m]; }
-        bool conflict = false;
-        int stride = 1;
+        int lv = 0, stride = 1;
         for (int m = 0; m < 4; m++) {
-            if (y[m] + 1 < b[m] && step_of[yl + stride] == cur && cnt > 0) conflict = true;
-            if (y[m] > 0 && step_of[yl - stride] == cur && cnt > 0) conflict = true;
+            if (y[m] + 1 < b[m] && key_of[yl + stride] < k) lv = std::max(lv, level[yl + stride] + 1);
+            if (y[m] > 0 && key_of[yl - stride] < k) lv = std::max(lv, level[yl - stride] + 1);
             stride *= b[m];
         }
-        if (conflict) {
-            np.h_step_ptr.push_back(k);
-            cur++;
-            cnt = 0;
-        }
-        step_of[yl] = cur;
-        np.h_step_site.push_back(yl);
-        cnt++;
+        level[yl] = lv;
+        nlev = std::max(nlev, lv + 1);
+    }
+    np.h_step_ptr.push_back(0);
+    for (int lv = 0; lv < nlev; lv++) {
+        for (int k = 0; k < np.vol; k++)
+            if (level[order[k]] == lv) np.h_step_site.push_back(order[k]);
+        if (lv + 1 < nlev) np.h_step_ptr.push_back((int)np.h_step_site.size());
     }
     np.h_step_ptr.push_back(np.vol);
     np.nsteps = (int)np.h_step_ptr.size() - 1;
@@ -705,13 +717,24 @@ int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &np,
         for (int m = 0; m < 4; m++) { y[m] = r % b[m]; r /= b[m]; }
         np.h_site_off[yl] = y[0] + c->lat.L[0] * (y[1] + c->lat.L[1] * (y[2] + c->lat.L[2] * y[3]));
     }
-    // slabs: the fewest CTAs per block whose shared memory fits
-    // slabs: the fewest CTAs per block (a divisor of b_t, at most 8, at least the requested
-    // minimum) whose shared memory fits
-    bool ok = false;
-    for (int C = std::max(1, min_ctas); C <= 8 && !ok; C++)
-        if (b[3] % C == 0) ok = make_chunks(np, C);
-    if (!ok) return QCD_ERR_ARG;
+    // slabs: a divisor C of b_t, at most 8, whose shared memory fits.  With min_ctas >= 1 the
+    // smallest such C >= min_ctas; with min_ctas = 0 the largest one that keeps the blocks of
+    // one colour (one CTA cluster each) within the SM count, and at least the smallest that fits
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        sms = 1;
+    }
+    const int nblk1 = np.nb[0] * np.nb[1] * np.nb[2] * np.nb[3] / 2;
+    int Cfit = 0;
+    for (int C = std::max(1, min_ctas); C <= 8 && !Cfit; C++)
+        if (b[3] % C == 0 && make_chunks(np, C)) Cfit = C;
+    if (!Cfit) return QCD_ERR_ARG;
+    int Cuse = Cfit;
+    if (min_ctas <= 0)
+        for (int C = Cfit + 1; C <= 8; C++)
+            if (b[3] % C == 0 && (long)nblk1 * C <= sms) Cuse = C;
+    if (!make_chunks(np, Cuse)) return QCD_ERR_ARG;
     make_flags(np);
     return QCD_OK;
 }

@@ -189,7 +189,7 @@ def test_sap_identical_for_every_cluster_width():
     prm = q.make_params(kappa, CSW, b, sb, omega=1.0, nsweep=2, nsap=2)
     vin = torch.from_numpy(v.astype(np.complex64)).cuda()
     outs = []
-    for ctas in (1, 2, 3, 4, 6):
+    for ctas in (0, 1, 2, 3, 4, 6):
         q.qcd_set_sap_ctas(s.ctx, ctas)
         out = torch.empty_like(vin)
         s.sap_precondition(out, vin, prm)
