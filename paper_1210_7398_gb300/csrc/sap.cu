@@ -74,7 +74,7 @@ __device__ __forceinline__ void masked_hops(const float4 *src, const float2 *__r
 namespace cg = cooperative_groups;
 
 constexpr int kRing = 3;           // staging depth (timeline steps in flight)
-constexpr int kMaxSlots = 16;      // sites per CTA per timeline step
+constexpr int kMaxSlots = 32;      // sites (one warp each) per CTA per timeline step
 constexpr size_t kSmemLimit = 200 * 1024;
 
 // Per-site record of the SSOR kernel, in 4-byte words.  W_d for d = 2 mu + (backward):
@@ -199,7 +199,7 @@ struct SsorArgs {
 
 // K3: y = A_BB f on every block of one colour; blockIdx.x / C enumerates blocks
 template <bool HALF>
-__global__ void __launch_bounds__(512) k_ssor_warp(SsorArgs a) {
+__global__ void __launch_bounds__(32 * kMaxSlots) k_ssor_warp(SsorArgs a) {
     using L = Rec<HALF>;
     extern __shared__ __align__(16) float sm[];
     // one right-hand side per blockIdx.y (the whole cluster shares it, so the early exit is uniform)
@@ -514,10 +514,10 @@ void free_plan(qcd_ctx *c) {
     p = SapPlan();
 }
 
-// Split the block into C slabs along t and every ll step into chunks of at
-// most kMaxSlots sites per slab.  Returns false if the shared memory of a CTA
-// (its slab of y plus the staging ring) would exceed kSmemLimit.
-bool make_chunks(SapPlan &np, int C) {
+// Split the block into C slabs along t and every step (level) into chunks of
+// at most maxslots sites per slab, of equal size.  Returns false if the shared
+// memory of a CTA (its slab of y plus the staging ring) would exceed kSmemLimit.
+bool make_chunks(SapPlan &np, int C, int maxslots) {
     if (np.b[3] % C) return false;
     np.C = C;
     np.slab_t = np.b[3] / C;
@@ -535,10 +535,11 @@ bool make_chunks(SapPlan &np, int C) {
         }
         size_t most = 1;
         for (auto &v : per) most = std::max(most, v.size());
-        const int nc = (int)((most + kMaxSlots - 1) / kMaxSlots);
+        const int nc = (int)((most + maxslots - 1) / maxslots);
         for (int j = 0; j < nc; j++) {
             for (int r = 0; r < C; r++) {
-                const int lo = j * kMaxSlots, hi = std::min((int)per[r].size(), lo + kMaxSlots);
+                const int sz = (int)per[r].size();
+                const int lo = (int)((long)j * sz / nc), hi = (int)((long)(j + 1) * sz / nc);
                 for (int q = lo; q < hi; q++) lists[r].push_back(per[r][q]);
                 nslot = std::max(nslot, hi - lo);
                 ptr[r].push_back((int)lists[r].size());
@@ -726,15 +727,17 @@ int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &np,
         sms = 1;
     }
     const int nblk1 = np.nb[0] * np.nb[1] * np.nb[2] * np.nb[3] / 2;
+    // up to 32 sites (warps) per step and CTA where the staging ring fits, else 16
+    auto fit = [&](int C) { return b[3] % C == 0 && (make_chunks(np, C, kMaxSlots) || make_chunks(np, C, 16)); };
     int Cfit = 0;
     for (int C = std::max(1, min_ctas); C <= 8 && !Cfit; C++)
-        if (b[3] % C == 0 && make_chunks(np, C)) Cfit = C;
+        if (fit(C)) Cfit = C;
     if (!Cfit) return QCD_ERR_ARG;
     int Cuse = Cfit;
     if (min_ctas <= 0)
         for (int C = Cfit + 1; C <= 8; C++)
             if (b[3] % C == 0 && (long)nblk1 * C <= sms) Cuse = C;
-    if (!make_chunks(np, Cuse)) return QCD_ERR_ARG;
+    if (!fit(Cuse)) return QCD_ERR_ARG;
     make_flags(np);
     return QCD_OK;
 }
