@@ -172,8 +172,9 @@ def kernel_model(cls, V, nrhs_steps, prm, peaks):
     return None
 
 
-def dslash_bandwidth(q, torch, dims, iters, peaks, seed=1002):
-    """GB/s of the FP32 operator D (K1) on internal-layout buffers, CUDA events on the context stream."""
+def dslash_bandwidth(q, torch, dims, iters, peaks, seed=1002, variants=(("f32", 1),)):
+    """GB/s of the operator D (K1) on internal-layout buffers, CUDA events on the context stream,
+    for each (precision, right-hand sides) variant."""
     import qcd_inputs as qi
     V = qi.volume(dims)
     U = qi.gauge_field(dims, 0.3, seed=seed, device="cuda")
@@ -182,27 +183,35 @@ def dslash_bandwidth(q, torch, dims, iters, peaks, seed=1002):
     del U
     s.build_clover(0.12, 1.6)
     stream = torch.cuda.current_stream()
-    q.qcd_bench_dslash(s.ctx, q.QCD_F32, 1, 3)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    times = []
-    for _ in range(iters):
-        flush.fill_(1.0)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        q.qcd_bench_dslash(s.ctx, q.QCD_F32, 1, 1)
-        b.record(stream)
-        torch.cuda.synchronize()
-        times.append(a.elapsed_time(b))
+    out = []
+    for prec, nrhs in variants:
+        pc = q.QCD_F32 if prec == "f32" else q.QCD_F64
+        q.qcd_bench_dslash(s.ctx, pc, nrhs, 3)
+        times = []
+        for _ in range(iters):
+            flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            q.qcd_bench_dslash(s.ctx, pc, nrhs, 1)
+            b.record(stream)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        ms = statistics.median(times)
+        # per right-hand side: both spinors; links and clover once per launch
+        spin = 192 if prec == "f32" else 384
+        field = D_BYTES_PER_SITE[prec] - spin
+        byts = V * (spin * nrhs + field)
+        gbs = byts / (ms * 1e-3) / 1e9
+        out.append({"lattice": "x".join(map(str, dims)), "V": V, "prec": prec, "nrhs": nrhs, "ms": ms, "GB_s": gbs,
+                    "GFLOP_s": V * nrhs * TABLE1_FLOP_PER_SITE / (ms * 1e-3) / 1e9,
+                    "frac_measured": gbs / peaks["hbm_gbs"], "frac_nominal_8TBs": gbs / 8000.0,
+                    "bytes_per_launch": byts, "timing": "median of %d launches, L2 flushed before each" % iters})
     s.close()
     del flush
     torch.cuda.empty_cache()
-    ms = statistics.median(times)
-    gbs = V * D_BYTES_PER_SITE["f32"] / (ms * 1e-3) / 1e9
-    return {"lattice": "x".join(map(str, dims)), "V": V, "prec": "f32", "ms": ms, "GB_s": gbs,
-            "GFLOP_s": V * TABLE1_FLOP_PER_SITE / (ms * 1e-3) / 1e9, "frac_measured": gbs / peaks["hbm_gbs"],
-            "frac_nominal_8TBs": gbs / 8000.0, "bytes_per_site": D_BYTES_PER_SITE["f32"],
-            "timing": "median of %d launches, L2 flushed before each" % iters}
+    return out
 
 
 def learned_section(q, qi, torch, s, dims, prm, b, nrhs, npairs, epochs, lr=3e-3, batch=8):
@@ -359,6 +368,9 @@ def run_gpu(args):
 
 
 def run_gpu_on_stream(args, q, qi, torch, np, peaks, rank, world, local):
+    if args.only_dslash:  # profiling aid: the FP32 D on 24^3 x 48 alone
+        print(json.dumps({"dslash": dslash_bandwidth(q, torch, (24, 24, 24, 48), 5, peaks)}))
+        return 0
     w = WORKLOAD
     dims = w["dims"]
     V = qi.volume(dims)
@@ -521,8 +533,9 @@ def run_gpu_on_stream(args, q, qi, torch, np, peaks, rank, world, local):
             v["share"] = v["ms"] / tot_k if tot_k else 0.0
         dsl = []
         if not args.skip_dslash:
-            for dd in ((24, 24, 24, 48), (48, 48, 48, 96)):
-                dsl.append(dslash_bandwidth(q, torch, dd, 20, peaks))
+            dsl += dslash_bandwidth(q, torch, (24, 24, 24, 48), 20, peaks,
+                                    variants=(("f32", 1), ("f32", 12), ("f64", 1)))
+            dsl += dslash_bandwidth(q, torch, (48, 48, 48, 96), 20, peaks)
         cpu = None
         if world == 1 and not args.skip_cpu:
             try:
@@ -577,6 +590,7 @@ def main():
     ap.add_argument("--headline", action="store_true",
                     help="also solve 48^3x96 with 12 point sources, plain and autotuned")
     ap.add_argument("--rhs-group", type=int, default=4, help="right-hand sides per 48^3x96 solve")
+    ap.add_argument("--only-dslash", action="store_true", help="profiling aid: time only the FP32 D on 24^3x48")
     ap.add_argument("--learned-full", action="store_true",
                     help="also train and judge the learned correction on 24^3 x 48 with 12 point sources")
     args = ap.parse_args()
