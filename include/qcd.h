@@ -128,8 +128,10 @@ int qcd_load_gauge(qcd_ctx *ctx, const double *U, int on_device);
 int qcd_build_clover(qcd_ctx *ctx, double kappa, double csw);
 
 /* out = D in for nrhs right-hand sides (Eq. (2)).  prec = QCD_F64: in/out are
- * complex128 [nrhs][V][4][3]; QCD_F32: complex64.  in and out must not
- * overlap.  Requires qcd_build_clover. */
+ * complex128 [nrhs][V][4][3]; QCD_F32: complex64; QCD_F16: complex64 in/out
+ * with the links and the clover field stored in FP16 (FP32 arithmetic; the
+ * FP16 copies are made on first use after each field change).  in and out
+ * must not overlap.  Requires qcd_build_clover. */
 int qcd_apply_D(qcd_ctx *ctx, void *out, const void *in, int prec, int nrhs);
 
 /* out = M_SAP in (Eq. (4), Alg. 1) in FP32 for nrhs right-hand sides:

@@ -1,5 +1,6 @@
-// K1: the operator D = 1 - kappa F H of Eq. (2) on the whole lattice, in FP64
-// and FP32, one thread per site and right-hand side.
+// K1: the operator D = 1 - kappa F H of Eq. (2) on the whole lattice, in FP64,
+// FP32, and FP32 with FP16 storage of links and clover; one thread per site and
+// one or two right-hand sides.
 //
 // Each thread gathers its 8 neighbour spinors, projects each to a half-spinor
 // (the rank-2 projector 1 -/+ gamma_mu), multiplies by the link, reconstructs
@@ -13,10 +14,32 @@
 
 namespace qcd {
 
+// FP16 storage of links and clover (FP32 arithmetic): links as half2, clover
+// planes as four halves (uint2).  |entries| <= about 1.5, far inside FP16 range.
+__device__ __forceinline__ void load_link(const __half2 *__restrict__ U, long V, long n, int mu, float2 u[9]) {
+    const unsigned *p = reinterpret_cast<const unsigned *>(U);
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        const unsigned w = __ldg(p + (mu * 9 + i) * V + n);
+        u[i] = __half22float2(*reinterpret_cast<const __half2 *>(&w));
+    }
+}
+__device__ __forceinline__ void load_clover(const uint2 *__restrict__ F, long V, long n, float f[72]) {
+#pragma unroll
+    for (int k = 0; k < 18; k++) {
+        const uint2 v = __ldg(F + k * V + n);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
+        f[4 * k] = a.x; f[4 * k + 1] = a.y; f[4 * k + 2] = b.x; f[4 * k + 3] = b.y;
+    }
+}
+
 // MINB: resident blocks per SM requested from the register allocator.  The FP32
 // kernel is bound by memory latency, so it trades registers for occupancy
 // (7 blocks of 128 threads); the FP64 kernel is bound by GB300's FP64 rate and
-// keeps its registers.
+// keeps its registers.  NR: right-hand sides per thread; each link and the
+// clover field are loaded once and applied to all of them, so the field bytes
+// per right-hand side drop from 576 to 576 / NR (FP32).
 template <int MINB, typename R, typename SP, typename LK, typename CL>
 __global__ void __launch_bounds__(128, MINB) dslash_kernel(SP *__restrict__ out, const SP *__restrict__ in,
                                                      const LK *__restrict__ U, const CL *__restrict__ F,
@@ -57,6 +80,79 @@ __global__ void __launch_bounds__(128, MINB) dslash_kernel(SP *__restrict__ out,
     store_spinor(out + (long)rhs * PLANES * g.V, g.V, n, psi);
 }
 
+// The same with NR right-hand sides per thread.
+template <int MINB, int NR, typename R, typename SP, typename LK, typename CL>
+__global__ void __launch_bounds__(128, MINB) dslash_kernel_nr(SP *__restrict__ out, const SP *__restrict__ in,
+                                                     const LK *__restrict__ U, const CL *__restrict__ F,
+                                                     R kappa, Geo g, int nrhs) {
+    using C = typename CT<R>::C;
+    const long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (n >= g.V) return;
+    const int r0 = blockIdx.y * NR;
+    const int nr = nrhs - r0 < NR ? nrhs - r0 : NR;
+    constexpr int PLANES = sizeof(C) * 12 / sizeof(SP);
+    const SP *src = in + (long)r0 * PLANES * g.V;
+    int x[4];
+    site_coords(g, n, x);
+    C acc[NR][12];
+#pragma unroll
+    for (int r = 0; r < NR; r++)
+#pragma unroll
+        for (int k = 0; k < 12; k++) acc[r][k] = cmk<C>(0, 0);
+    C psi[12], u[9];
+    const R tsgn_f = (x[3] == g.L[3] - 1) ? (R)g.bc_t : (R)1;
+    const R tsgn_b = (x[3] == 0) ? (R)g.bc_t : (R)1;
+#define QCD_HOP(MU, FWD, SGN)                                                   \
+    {                                                                                   \
+        const long m = FWD ? nbr_fwd<MU>(g, n, x) : nbr_bwd<MU>(g, n, x);               \
+        load_link(U, g.V, FWD ? n : m, MU, u);                                           \
+        _Pragma("unroll") for (int r = 0; r < NR; r++) if (NR == 1 || r < nr) {         \
+            load_spinor(src + (long)r * PLANES * g.V, g.V, m, psi);                      \
+            hop_term<MU, FWD>(psi, u, SGN, acc[r]);                                      \
+        }                                                                               \
+    }
+    QCD_HOP(0, true, (R)1)
+    QCD_HOP(0, false, (R)1)
+    QCD_HOP(1, true, (R)1)
+    QCD_HOP(1, false, (R)1)
+    QCD_HOP(2, true, (R)1)
+    QCD_HOP(2, false, (R)1)
+    QCD_HOP(3, true, tsgn_f)
+    QCD_HOP(3, false, tsgn_b)
+#undef QCD_HOP
+    R f[72];
+    load_clover(F, g.V, n, f);
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+        if (NR == 1 || r < nr) {
+            C fa[12];
+            clover_mul<R, C>(f, acc[r], fa);
+            load_spinor(src + (long)r * PLANES * g.V, g.V, n, psi);
+#pragma unroll
+            for (int k = 0; k < 12; k++) {
+                psi[k].x = fma(-kappa, fa[k].x, psi[k].x);
+                psi[k].y = fma(-kappa, fa[k].y, psi[k].y);
+            }
+            store_spinor(out + (long)(r0 + r) * PLANES * g.V, g.V, n, psi);
+        }
+    }
+}
+
+namespace {
+// FP16 copies of the FP32 links and clover field
+__global__ void k_fields_to_half(__half2 *__restrict__ U16, uint2 *__restrict__ F16, const float2 *__restrict__ U32,
+                                 const float4 *__restrict__ F32, long V) {
+    const long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (n >= V) return;
+    for (int k = 0; k < 36; k++) U16[k * V + n] = __float22half2_rn(U32[k * V + n]);
+    for (int k = 0; k < 18; k++) {
+        const float4 v = F32[k * V + n];
+        const __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+        F16[k * V + n] = make_uint2(*reinterpret_cast<const unsigned *>(&a), *reinterpret_cast<const unsigned *>(&b));
+    }
+}
+}  // namespace
+
 static Geo geo_of(const qcd_ctx *c) {
     Geo g;
     for (int m = 0; m < 4; m++) g.L[m] = c->lat.L[m];
@@ -71,17 +167,47 @@ int dslash64(qcd_ctx *c, double2 *out, const double2 *in, int nrhs) {
     cudaEvent_t ev;
     prof_begin(c, QCD_K_DSLASH64, &ev);
     dslash_kernel<3, double, double2, double2, double2><<<grid, 128, 0, c->stream>>>(out, in, c->U64, c->F64,
-                                                                                  c->kappa, g, nrhs);
+                                                                                     c->kappa, g, nrhs);
     return prof_end(c, QCD_K_DSLASH64, ev);
 }
 
 int dslash32(qcd_ctx *c, float4 *out, const float4 *in, int nrhs) {
     Geo g = geo_of(c);
-    dim3 grid((unsigned)((g.V + 127) / 128), nrhs);
     cudaEvent_t ev;
     prof_begin(c, QCD_K_DSLASH32, &ev);
-    dslash_kernel<7, float, float4, float2, float4><<<grid, 128, 0, c->stream>>>(out, in, c->U32, c->F32,
-                                                                              (float)c->kappa, g, nrhs);
+    if (nrhs == 1) {
+        dslash_kernel<7, float, float4, float2, float4><<<dim3((unsigned)((g.V + 127) / 128), 1), 128, 0, c->stream>>>(
+            out, in, c->U32, c->F32, (float)c->kappa, g, 1);
+    } else {
+        dim3 grid((unsigned)((g.V + 127) / 128), (nrhs + 1) / 2);
+        dslash_kernel_nr<4, 2, float, float4, float2, float4><<<grid, 128, 0, c->stream>>>(out, in, c->U32, c->F32,
+                                                                                     (float)c->kappa, g, nrhs);
+    }
+    return prof_end(c, QCD_K_DSLASH32, ev);
+}
+
+int dslash16(qcd_ctx *c, float4 *out, const float4 *in, int nrhs) {
+    Geo g = geo_of(c);
+    if (!c->U16) {
+        int rc = dev_alloc(c, (void **)&c->U16, sizeof(__half2) * 36 * g.V);
+        if (!rc) rc = dev_alloc(c, (void **)&c->F16, sizeof(uint2) * 18 * g.V);
+        if (rc) return rc;
+    }
+    if (c->half_version != c->field_version) {
+        k_fields_to_half<<<(unsigned)((g.V + 255) / 256), 256, 0, c->stream>>>(c->U16, c->F16, c->U32, c->F32, g.V);
+        QCD_CUDA(c, cudaGetLastError());
+        c->half_version = c->field_version;
+    }
+    cudaEvent_t ev;
+    prof_begin(c, QCD_K_DSLASH32, &ev);
+    if (nrhs == 1) {
+        dslash_kernel<7, float, float4, __half2, uint2><<<dim3((unsigned)((g.V + 127) / 128), 1), 128, 0, c->stream>>>(
+            out, in, c->U16, c->F16, (float)c->kappa, g, 1);
+    } else {
+        dim3 grid((unsigned)((g.V + 127) / 128), (nrhs + 1) / 2);
+        dslash_kernel_nr<4, 2, float, float4, __half2, uint2><<<grid, 128, 0, c->stream>>>(out, in, c->U16, c->F16,
+                                                                                     (float)c->kappa, g, nrhs);
+    }
     return prof_end(c, QCD_K_DSLASH32, ev);
 }
 

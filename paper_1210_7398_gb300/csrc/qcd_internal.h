@@ -13,6 +13,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -113,6 +114,9 @@ struct qcd_ctx {
     float2 *U32 = nullptr;
     double2 *F64 = nullptr;
     float4 *F32 = nullptr;
+    __half2 *U16 = nullptr;  // FP16 copies for the FP16-storage operator, made on first use
+    uint2 *F16 = nullptr;    // [18][V], four halves per plane
+    long half_version = -1;  // field_version the FP16 copies were made from
     int *d_status = nullptr;  // device status word (clover singularity)
 
     // SAP plan cache (one geometry at a time)
@@ -181,6 +185,7 @@ int build_clover(qcd_ctx *c, double kappa, double csw);
 // operator D (dslash.cu)
 int dslash64(qcd_ctx *c, double2 *out, const double2 *in, int nrhs);
 int dslash32(qcd_ctx *c, float4 *out, const float4 *in, int nrhs);
+int dslash16(qcd_ctx *c, float4 *out, const float4 *in, int nrhs);
 
 // SAP (sap.cu)
 // host part of a plan (tables in h_*; device pointers left null); QCD_ERR_ARG on bad geometry

@@ -61,6 +61,41 @@ def test_dslash_fp64_fp32_vs_oracle(dims, bc_t):
     s.close()
 
 
+# FP16 storage of links and clover (FP32 arithmetic and spinors): each stored
+# value carries a relative rounding of at most 2^-11 = 4.9e-4; the hop sum and
+# the clover product add a few of them, so 2e-3 relative in norm.
+D_F16_TOL = 2e-3
+
+
+@pytest.mark.parametrize("dims,bc_t", [((4, 4, 4, 4), 1), ((6, 4, 4, 6), -1), ((8, 8, 8, 16), 1)])
+def test_dslash_odd_rhs_counts_and_fp16_storage(dims, bc_t):
+    """Three right-hand sides take the two-per-thread kernel and a single tail;
+    the FP16-storage operator stays within its rounding bound."""
+    kappa = 0.12
+    s, U, F = make_solver(dims, kappa, seed=1000, bc_t=bc_t)
+    psi = qi.gaussian_spinor(dims, seed=2000, nrhs=3)
+    ref = np.stack([oracle.apply_D(dims, U, F, kappa, psi[k], bc_t=bc_t) for k in range(3)])
+    dev32 = torch.from_numpy(psi).cuda().to(torch.complex64)
+    out32 = torch.empty_like(dev32)
+    s.apply_D(out32, dev32, q.QCD_F32, nrhs=3)
+    torch.cuda.synchronize()
+    for k in range(3):
+        assert rel_norm(out32[k].cpu().numpy().astype(np.complex128), ref[k]) <= 2e-6
+    out16 = torch.empty_like(dev32)
+    s.apply_D(out16, dev32, q.QCD_F16, nrhs=3)
+    torch.cuda.synchronize()
+    for k in range(3):
+        assert rel_norm(out16[k].cpu().numpy().astype(np.complex128), ref[k]) <= D_F16_TOL
+    # the FP16 copies follow a change of the fields
+    s.build_clover(0.11, CSW)
+    _, F2 = oracle.clover(dims, U, CSW, 0.11)
+    s.apply_D(out16, dev32, q.QCD_F16, nrhs=3)
+    torch.cuda.synchronize()
+    ref2 = oracle.apply_D(dims, U, F2, 0.11, psi[0], bc_t=bc_t)
+    assert rel_norm(out16[0].cpu().numpy().astype(np.complex128), ref2) <= D_F16_TOL
+    s.close()
+
+
 def test_dslash_free_field_plane_wave():
     """U = 1: D e^{ipn} u = [1 - kappa sum(2cos p - 2i gamma sin p)] e^{ipn} u (closed form)."""
     dims, kappa = (8, 4, 4, 8), 0.11
