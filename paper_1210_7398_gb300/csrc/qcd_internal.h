@@ -46,6 +46,7 @@ struct SapPlan {
     std::vector<int> h_step_ptr, h_step_site, h_origin[2];
     int *d_origin[2] = {nullptr, nullptr};  // [nblk[c]][4] block origins per colour
     bool half = false;  // FP16 storage of the block spinor and the records (FP32 arithmetic)
+    bool thread = false;  // thread-per-site SSOR kernel (block fields in shared memory, no records)
     int C = 1, slab_t = 0, slab_vol = 0;
     int nchunks = 0, nslot = 0, nwarps = 0;
     size_t smem_bytes = 0;
@@ -190,7 +191,7 @@ int dslash16(qcd_ctx *c, float4 *out, const float4 *in, int nrhs);
 // SAP (sap.cu)
 // host part of a plan (tables in h_*; device pointers left null); QCD_ERR_ARG on bad geometry
 int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &plan, int min_ctas = 1,
-                  bool half = false);
+                  bool half = false, bool thread_ok = false);
 // builds and uploads the plan of this geometry into c->plan (allocates its tables)
 int sap_prepare(qcd_ctx *c, const int b[4], const int s[4], bool half);
 // drops the cached plan (it is rebuilt on next use)

@@ -3,6 +3,7 @@
 // dependent ll steps (block size) against SAP quality (outer/inner iteration
 // counts), so candidates are compared by measured time to solution.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -30,7 +31,7 @@ bool valid_block(const qcd_ctx *c, const int b[4], const int s[4]) {
 int time_solve(qcd_ctx *c, double2 *xi, const double2 *bi, int nrhs, const qcd_params *p, double *ms, bool *ok) {
     *ok = false;
     const int old_ctas = c->sap_min_ctas;
-    if (p->sap_ctas > 0 && p->sap_ctas != c->sap_min_ctas) {
+    if (p->sap_ctas != 0 && p->sap_ctas != c->sap_min_ctas) {
         sap_invalidate(c);
         c->sap_min_ctas = p->sap_ctas;
     }
@@ -123,6 +124,15 @@ extern "C" int qcd_autotune(qcd_ctx *c, const double *b, int nrhs, const qcd_par
                 cands.push_back(cd);
             }
         }
+    // blocks of about 256 sites first (a few levels of many sites each), so that a small
+    // candidate budget covers the promising region
+    std::stable_sort(cands.begin(), cands.end(), [](const Cand &u, const Cand &v) {
+        auto dist = [](const Cand &x) {
+            const double vol = (double)x.p.block[0] * x.p.block[1] * x.p.block[2] * x.p.block[3];
+            return std::fabs(std::log(vol / 256.0));
+        };
+        return dist(u) < dist(v);
+    });
     int tried = 0;
     auto run = [&](Cand &cd) -> int {
         if (tried >= max_candidates) return QCD_OK;
@@ -149,7 +159,7 @@ extern "C" int qcd_autotune(qcd_ctx *c, const double *b, int nrhs, const qcd_par
         for (size_t i = 0; i < cands.size() && i < 3; i++) {
             if (!cands[i].ok) continue;
             for (int storage : {QCD_F32, QCD_F16})
-                for (int ctas : {0, 2})
+                for (int ctas : {0, -1, 2})
                     for (int ns : {2, 4})
                         for (int np : {2, 4}) {
                             Cand cd = cands[i];
