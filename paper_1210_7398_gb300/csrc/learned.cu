@@ -160,6 +160,85 @@ template <int CIN, int COUT, int FIN> struct LayerSmem {
                   "16-byte staging");
 };
 
+// Neighbour table of a 64-site tile for all nine directions: nbt[d][st] the neighbour site
+// (-1 past the end of the lattice), sgt[d][st] the boundary sign of the hop.
+__device__ __forceinline__ void layer_neighbours(int *nbt, float *sgt, const Geo &g, int n0, int tid) {
+    if (tid >= kLayerSites) return;
+    const int V = (int)g.V;
+    const int n = n0 + tid;
+    int xc0 = 0, xc1 = 0, xc2 = 0, xc3 = 0;
+    if (n < V) {
+        int r = n;
+        xc0 = r % g.L[0]; r /= g.L[0];
+        xc1 = r % g.L[1]; r /= g.L[1];
+        xc2 = r % g.L[2]; xc3 = r / g.L[2];
+    }
+    const int xc[4] = {xc0, xc1, xc2, xc3};
+    nbt[tid] = n < V ? n : -1;
+    sgt[tid] = 1.f;
+    int stride = 1;
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        const int Lm = g.L[mu];
+        const int f = xc[mu] == Lm - 1 ? n - stride * (Lm - 1) : n + stride;
+        const int bk = xc[mu] == 0 ? n + stride * (Lm - 1) : n - stride;
+        nbt[(1 + 2 * mu) * kLayerSites + tid] = n < V ? f : -1;
+        nbt[(2 + 2 * mu) * kLayerSites + tid] = n < V ? bk : -1;
+        sgt[(1 + 2 * mu) * kLayerSites + tid] = (mu == 3 && xc[3] == Lm - 1) ? (float)g.bc_t : 1.f;
+        sgt[(2 + 2 * mu) * kLayerSites + tid] = (mu == 3 && xc[3] == 0) ? (float)g.bc_t : 1.f;
+        stride *= Lm;
+    }
+}
+
+// Stages direction d of a layer into buffer d & 1 with cp.async (one commit group): the
+// neighbour inputs of the tile (all channels), their links (forward U_mu(n), backward
+// U_mu(n - mu)) and the direction's weight tile.
+template <int CIN, int COUT, int FIN>
+__device__ __forceinline__ void layer_issue(unsigned char *smem, const int *nbt, const void *x,
+                                            const float2 *__restrict__ U, const __nv_bfloat16 *__restrict__ Bt,
+                                            const Geo &g, int n0, int d, int tid, int nth) {
+    using S = LayerSmem<CIN, COUT, FIN>;
+    constexpr int KDP = S::KDP, N = S::N, AS = S::AS, XS = S::XS;
+    const int V = (int)g.V;
+    unsigned char *X = smem + (d & 1) * S::stage;
+    float2 *L = reinterpret_cast<float2 *>(X + S::x_bytes);
+    __nv_bfloat16 *B = reinterpret_cast<__nv_bfloat16 *>(X + S::x_bytes + S::l_bytes);
+    const int *nb = nbt + d * kLayerSites;
+    if constexpr (FIN == PLANE32) {
+        static_assert(CIN == 1, "plane layout holds one channel");
+        for (int i = tid; i < kLayerSites * 6; i += nth) {
+            const int st = i % kLayerSites, p = i / kLayerSites;
+            const int m = nb[st];
+            cp_async16z(X + st * XS + p * 16, static_cast<const float4 *>(x) + (long)p * V + (m < 0 ? 0 : m), m >= 0);
+        }
+    } else {
+        constexpr int CH16 = 12 * S::XC / 16;  // 16-byte chunks per site and channel
+        for (int i = tid; i < kLayerSites * CIN * CH16; i += nth) {
+            const int k = i % CH16, rest = i / CH16, st = rest % kLayerSites, ch = rest / kLayerSites;
+            const int m = nb[st];
+            const unsigned char *src =
+                static_cast<const unsigned char *>(x) + (((long)ch * V + (m < 0 ? 0 : m)) * 12) * S::XC + k * 16;
+            cp_async16z(X + st * XS + (ch * CH16 + k) * 16, src, m >= 0);
+        }
+    }
+    if (d > 0) {
+        const int mu = (d - 1) >> 1;
+        const bool fwd = ((d - 1) & 1) == 0;
+        for (int i = tid; i < kLayerSites * 9; i += nth) {
+            const int st = i % kLayerSites, e = i / kLayerSites;
+            const int m = nb[st];
+            const int ls = fwd ? n0 + st : m;  // U_mu(n) forward, U_mu(n - mu) backward
+            cp_async8z(L + st * 9 + e, U + (long)(mu * 9 + e) * V + (m < 0 ? 0 : ls), m >= 0);
+        }
+    }
+    const uint4 *Bd = reinterpret_cast<const uint4 *>(Bt + (long)d * N * KDP);
+    for (int i = tid; i < N * KDP / 8; i += nth) {
+        const int row = i / (KDP / 8), col = (i % (KDP / 8)) * 8;
+        cp_async16z(B + row * AS + col, Bd + i, true);
+    }
+    cp_commit();
+}
+
 // Transport of one (site, channel group) item of the layer kernel: the A rows of the site,
 // A[a][8 ch + 2 be (+1)] = sum_b W[a][b] x_ch[be][b] for the CPI channels from cg on.  KIND:
 // 0 identity, 1 forward W = U_mu(n), 2 backward W = U_mu(n - mu)^dag, 3 / 4 the same times the
@@ -247,74 +326,9 @@ __global__ void __launch_bounds__(kLayerWarps * 32, FIN == SITE32 ? 1 : 2) k_lay
     const int V = (int)g.V;
     const int n0 = blockIdx.x * kLayerSites;
 
-    // neighbour table of the tile for all nine directions
-    if (tid < kLayerSites) {
-        const int n = n0 + tid;
-        int xc0 = 0, xc1 = 0, xc2 = 0, xc3 = 0;
-        if (n < V) {
-            int r = n;
-            xc0 = r % g.L[0]; r /= g.L[0];
-            xc1 = r % g.L[1]; r /= g.L[1];
-            xc2 = r % g.L[2]; xc3 = r / g.L[2];
-        }
-        const int xc[4] = {xc0, xc1, xc2, xc3};
-        nbt[tid] = n < V ? n : -1;
-        sgt[tid] = 1.f;
-        int stride = 1;
-#pragma unroll
-        for (int mu = 0; mu < 4; mu++) {
-            const int Lm = g.L[mu];
-            const int f = xc[mu] == Lm - 1 ? n - stride * (Lm - 1) : n + stride;
-            const int bk = xc[mu] == 0 ? n + stride * (Lm - 1) : n - stride;
-            nbt[(1 + 2 * mu) * kLayerSites + tid] = n < V ? f : -1;
-            nbt[(2 + 2 * mu) * kLayerSites + tid] = n < V ? bk : -1;
-            sgt[(1 + 2 * mu) * kLayerSites + tid] = (mu == 3 && xc[3] == Lm - 1) ? (float)g.bc_t : 1.f;
-            sgt[(2 + 2 * mu) * kLayerSites + tid] = (mu == 3 && xc[3] == 0) ? (float)g.bc_t : 1.f;
-            stride *= Lm;
-        }
-    }
+    layer_neighbours(nbt, sgt, g, n0, tid);
     __syncthreads();
-
-    // stage direction d into buffer d & 1
-    auto issue = [&](int d) {
-        unsigned char *X = ly_smem + (d & 1) * S::stage;
-        float2 *L = reinterpret_cast<float2 *>(X + S::x_bytes);
-        __nv_bfloat16 *B = reinterpret_cast<__nv_bfloat16 *>(X + S::x_bytes + S::l_bytes);
-        const int *nb = nbt + d * kLayerSites;
-        if constexpr (FIN == PLANE32) {
-            static_assert(CIN == 1, "plane layout holds one channel");
-            for (int i = tid; i < kLayerSites * 6; i += NTH) {
-                const int st = i % kLayerSites, p = i / kLayerSites;
-                const int m = nb[st];
-                cp_async16z(X + st * XS + p * 16, static_cast<const float4 *>(x) + (long)p * V + (m < 0 ? 0 : m), m >= 0);
-            }
-        } else {
-            constexpr int CH16 = 12 * S::XC / 16;  // 16-byte chunks per site and channel
-            for (int i = tid; i < kLayerSites * CIN * CH16; i += NTH) {
-                const int k = i % CH16, rest = i / CH16, st = rest % kLayerSites, ch = rest / kLayerSites;
-                const int m = nb[st];
-                const unsigned char *src =
-                    static_cast<const unsigned char *>(x) + (((long)ch * V + (m < 0 ? 0 : m)) * 12) * S::XC + k * 16;
-                cp_async16z(X + st * XS + (ch * CH16 + k) * 16, src, m >= 0);
-            }
-        }
-        if (d > 0) {
-            const int mu = (d - 1) >> 1;
-            const bool fwd = ((d - 1) & 1) == 0;
-            for (int i = tid; i < kLayerSites * 9; i += NTH) {
-                const int st = i % kLayerSites, e = i / kLayerSites;
-                const int m = nb[st];
-                const int ls = fwd ? n0 + st : m;  // U_mu(n) forward, U_mu(n - mu) backward
-                cp_async8z(L + st * 9 + e, U + (long)(mu * 9 + e) * V + (m < 0 ? 0 : ls), m >= 0);
-            }
-        }
-        const uint4 *Bd = reinterpret_cast<const uint4 *>(Bt + (long)d * N * KDP);
-        for (int i = tid; i < N * KDP / 8; i += NTH) {
-            const int row = i / (KDP / 8), col = (i % (KDP / 8)) * 8;
-            cp_async16z(B + row * AS + col, Bd + i, true);
-        }
-        cp_commit();
-    };
+    auto issue = [&](int d) { layer_issue<CIN, COUT, FIN>(ly_smem, nbt, x, U, Bt, g, n0, d, tid, NTH); };
 
     // KDP > CIN*8 (one input channel): the upper K half of A stays zero
     if constexpr (KDP > CIN * 8) {
@@ -376,6 +390,98 @@ __global__ void __launch_bounds__(kLayerWarps * 32, FIN == SITE32 ? 1 : 2) k_lay
             const long n = (long)n0 + r / 3;
             if (n < g.V) act_st<FOUT>(y, g.V, c, n, al * 3 + r % 3, make_float2(acc[j][2 * h], acc[j][2 * h + 1]));
         }
+    }
+}
+
+// A layer with one output channel (the last layer), weights first: since W_d acts on spin and
+// channel and T_d on colour and site, W_d T_d x = T_d W_d x.  Per direction the staged
+// neighbour inputs are only re-laid out as A rows (neighbour site, colour) - no arithmetic -,
+// the MMA gives P = W_d x at the neighbours (4 spins), and the 3x3 colour transport is applied
+// to P, one output channel instead of CIN input channels.  Output accumulated in registers
+// of the thread that owns (site, spin).
+template <int CIN, int FIN, int FOUT>
+__global__ void __launch_bounds__(kLayerWarps * 32, 2) k_layer_wfirst(void *y, const void *x,
+                                                                      const float2 *__restrict__ U,
+                                                                      const __nv_bfloat16 *__restrict__ Bt, Geo g) {
+    using S = LayerSmem<CIN, 1, FIN>;
+    constexpr int KDP = S::KDP, AS = S::AS, XS = S::XS;
+    constexpr int NTH = kLayerWarps * 32;
+    static_assert(FIN == SITE16 && CIN * 8 == KDP, "hidden BF16 input of whole 16-column groups");
+    extern __shared__ __align__(16) unsigned char ly_smem[];
+    __nv_bfloat16 *A = reinterpret_cast<__nv_bfloat16 *>(ly_smem + 2 * S::stage);
+    int *nbt = reinterpret_cast<int *>(ly_smem + 2 * S::stage + S::a_bytes);
+    float *sgt = reinterpret_cast<float *>(nbt + 9 * kLayerSites);
+    float2 *Ps = reinterpret_cast<float2 *>(sgt + 9 * kLayerSites);  // [192 rows][4 spins]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gq = lane >> 2, tq = lane & 3;
+    const int n0 = blockIdx.x * kLayerSites;
+    layer_neighbours(nbt, sgt, g, n0, tid);
+    __syncthreads();
+    // the output (site, spin) this thread accumulates: 3 colours
+    const int ost = tid >> 2, oal = tid & 3;
+    float2 yacc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    layer_issue<CIN, 1, FIN>(ly_smem, nbt, x, U, Bt, g, n0, 0, tid, NTH);
+#pragma unroll 1
+    for (int d = 0; d < 9; d++) {
+        cp_wait<0>();
+        __syncthreads();  // stage d visible; A and P of the previous direction consumed
+        if (d + 1 < 9) layer_issue<CIN, 1, FIN>(ly_smem, nbt, x, U, Bt, g, n0, d + 1, tid, NTH);
+        const unsigned char *X = ly_smem + (d & 1) * S::stage;
+        const float2 *L = reinterpret_cast<const float2 *>(X + S::x_bytes);
+        const __nv_bfloat16 *B = reinterpret_cast<const __nv_bfloat16 *>(X + S::x_bytes + S::l_bytes);
+        // A[3 st + b][8 ch + 2 be (+1)] = x_ch(m)[be][b]: a permutation of the staged BF16 words
+        for (int it = tid; it < kLayerSites * CIN; it += NTH) {
+            const int st = it / CIN, ch = it % CIN;
+            const uint4 *q = reinterpret_cast<const uint4 *>(X + st * XS + ch * 48);
+            const uint4 q0 = q[0], q1 = q[1], q2 = q[2];
+            const uint32_t w[12] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
+#pragma unroll
+            for (int b = 0; b < 3; b++)
+                *reinterpret_cast<uint4 *>(A + (st * 3 + b) * AS + ch * 8) = make_uint4(w[b], w[3 + b], w[6 + b], w[9 + b]);
+        }
+        __syncthreads();
+        // P = A B: 16 rows per warp, 8 columns (4 spins, re/im)
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        const int r0 = warp * 16;
+#pragma unroll
+        for (int k0 = 0; k0 < KDP; k0 += 16) {
+            uint32_t a0, a1, a2, a3, b0, b1;
+            ldsm_x4(A + (r0 + (lane & 15)) * AS + k0 + (lane >> 4) * 8, a0, a1, a2, a3);
+            ldsm_x2(B + (lane & 7) * AS + k0 + ((lane >> 3) & 1) * 8, b0, b1);
+            mma_bf16(acc, a0, a1, a2, a3, b0, b1);
+        }
+        Ps[(r0 + gq) * 4 + tq] = make_float2(acc[0], acc[1]);
+        Ps[(r0 + gq + 8) * 4 + tq] = make_float2(acc[2], acc[3]);
+        __syncthreads();
+        // y(st)[a][al] += sum_b W[a][b] P[(st, b)][al], W = 1, U_mu(n) or U_mu(n - mu)^dag, times the sign
+        if (tid < kLayerSites * 4) {
+            const float2 p0 = Ps[(ost * 3) * 4 + oal], p1 = Ps[(ost * 3 + 1) * 4 + oal], p2 = Ps[(ost * 3 + 2) * 4 + oal];
+            if (d == 0) {
+                yacc[0] = cadd(yacc[0], p0);
+                yacc[1] = cadd(yacc[1], p1);
+                yacc[2] = cadd(yacc[2], p2);
+            } else {
+                const bool fwd = ((d - 1) & 1) == 0;
+                const float sg = sgt[d * kLayerSites + ost];
+                const float2 pv[3] = {p0, p1, p2};
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    float2 z = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int b = 0; b < 3; b++) {
+                        float2 u = fwd ? L[ost * 9 + a * 3 + b] : L[ost * 9 + b * 3 + a];
+                        if (!fwd) u.y = -u.y;
+                        z = cfma(u, pv[b], z);
+                    }
+                    yacc[a] = cadd(yacc[a], cscale(z, sg));
+                }
+            }
+        }
+    }
+    if (tid < kLayerSites * 4) {
+        const long n = (long)n0 + ost;
+        if (n < g.V)
+#pragma unroll
+            for (int a = 0; a < 3; a++) act_st<FOUT>(y, g.V, 0, n, oal * 3 + a, yacc[a]);
     }
 }
 
@@ -604,6 +710,22 @@ int launch_layer(qcd_ctx *c, void *y, const void *x, const __nv_bfloat16 *Bt) {
     return prof_end(c, QCD_K_LEARNED, ev);
 }
 
+template <int CIN, int FIN, int FOUT>
+int launch_layer_wfirst(qcd_ctx *c, void *y, const void *x, const __nv_bfloat16 *Bt) {
+    constexpr size_t smem = LayerSmem<CIN, 1, FIN>::total + sizeof(float2) * kLayerRows * 4;
+    static bool attr = false;
+    if (!attr) {
+        QCD_CUDA(c, cudaFuncSetAttribute(k_layer_wfirst<CIN, FIN, FOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+        attr = true;
+    }
+    const long tiles = (c->lat.V + kLayerSites - 1) / kLayerSites;
+    cudaEvent_t ev;
+    prof_begin(c, QCD_K_LEARNED, &ev);
+    k_layer_wfirst<CIN, FIN, FOUT><<<(unsigned)tiles, kLayerWarps * 32, smem, c->stream>>>(y, x, c->U32, Bt, geo(c));
+    return prof_end(c, QCD_K_LEARNED, ev);
+}
+
 template <int CIN, int COUT, int FIN>
 int launch_wgrad(qcd_ctx *c, float *P, const void *x, const float2 *G) {
     constexpr int KD = CIN * 8, KDP = KD < 16 ? 16 : KD, N = COUT * 8;
@@ -730,7 +852,7 @@ int learned_forward(qcd_ctx *c, float4 *y, const float4 *x) {
     if (rc) return rc;
     if ((rc = launch_layer<1, 8, PLANE32, SITE16>(c, L.a1, x, L.B + layer_boff(0, false)))) return rc;
     if ((rc = launch_layer<8, 8, SITE16, SITE16>(c, L.a2, L.a1, L.B + layer_boff(1, false)))) return rc;
-    return launch_layer<8, 1, SITE16, PLANE32>(c, y, L.a2, L.B + layer_boff(2, false));
+    return launch_layer_wfirst<8, SITE16, PLANE32>(c, y, L.a2, L.B + layer_boff(2, false));
 }
 
 // loss of one pair (rho: plane layout FP32, eps: site layout FP32) and, with accumulate,
