@@ -201,9 +201,10 @@ struct SsorArgs {
     Geo g;                     // lattice
 };
 
-// K3: y = A_BB f on every block of one colour; blockIdx.x / C enumerates blocks
-template <bool HALF>
-__global__ void __launch_bounds__(32 * kMaxSlots) k_ssor_warp(SsorArgs a) {
+// K3: y = A_BB f on every block of one colour; blockIdx.x / C enumerates blocks.  MAXW: the
+// most warps per CTA the instance is launched with (32 leaves each thread 64 registers)
+template <bool HALF, int MAXW>
+__global__ void __launch_bounds__(32 * MAXW) k_ssor_warp(SsorArgs a) {
     using L = Rec<HALF>;
     extern __shared__ __align__(16) float sm[];
     // one right-hand side per blockIdx.y (the whole cluster shares it, so the early exit is uniform)
@@ -840,8 +841,13 @@ int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &np,
         sms = 1;
     }
     const int nblk1 = np.nb[0] * np.nb[1] * np.nb[2] * np.nb[3] / 2;
-    // up to 32 sites (warps) per step and CTA where the staging ring fits, else 16
-    auto fit = [&](int C) { return b[3] % C == 0 && (make_chunks(np, C, kMaxSlots) || make_chunks(np, C, 16)); };
+    // up to 32 sites (warps) per step and CTA where one colour's blocks leave SMs idle and the
+    // staging ring fits (fewer dependent steps), else 16 (more registers per thread; several
+    // blocks share an SM when many blocks fill the GPU)
+    const bool few = (long)nblk1 < sms;
+    auto fit = [&](int C) {
+        return b[3] % C == 0 && ((few && make_chunks(np, C, kMaxSlots)) || make_chunks(np, C, 16));
+    };
     int Cfit = 0;
     for (int C = std::max(1, min_ctas); C <= 8 && !Cfit; C++)
         if (fit(C)) Cfit = C;  // (min_ctas < 0 without a thread-per-site fit: as 0)
@@ -977,8 +983,10 @@ int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
     bg.vol = p.vol;
     static bool attr_done = false;
     if (!attr_done) {
-        QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_warp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
-        QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_warp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+        QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_warp<false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+        QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_warp<true, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+        QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_warp<false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+        QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_warp<true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
         QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_thread, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
         attr_done = true;
     }
@@ -1031,7 +1039,12 @@ int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
                 k_ssor_thread<<<dim3(p.nblk[col], nrhs), 32 * p.nwarps, p.smem_bytes, c->stream>>>(a);
                 e = cudaGetLastError();
             } else {
-                e = p.half ? cudaLaunchKernelEx(&cfg, k_ssor_warp<true>, a) : cudaLaunchKernelEx(&cfg, k_ssor_warp<false>, a);
+                if (p.nwarps > 16)
+                    e = p.half ? cudaLaunchKernelEx(&cfg, k_ssor_warp<true, 32>, a)
+                               : cudaLaunchKernelEx(&cfg, k_ssor_warp<false, 32>, a);
+                else
+                    e = p.half ? cudaLaunchKernelEx(&cfg, k_ssor_warp<true, 16>, a)
+                               : cudaLaunchKernelEx(&cfg, k_ssor_warp<false, 16>, a);
             }
             if (e != cudaSuccess) return cuda_fail(c, e, "launch of the SSOR block kernel");
             if ((rc = prof_end(c, QCD_K_SSOR, ev))) return rc;
