@@ -99,6 +99,17 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(value: float, world: int, device: str = "cuda") -> float:
+    """The largest of every rank's value (the slowest replica decides the step time)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle sample (cpu_baseline leg and --impl reference)
 # ---------------------------------------------------------------------------
@@ -371,6 +382,26 @@ def run_gpu_on_stream(args, q, qi, torch, np, peaks, rank, world, local):
     if args.only_dslash:  # profiling aid: the FP32 D on 24^3 x 48 alone
         print(json.dumps({"dslash": dslash_bandwidth(q, torch, (24, 24, 24, 48), 5, peaks)}))
         return 0
+    if args.only_learned:  # profiling aid: the learned correction's three layers on 24^3 x 48
+        dl = (24, 24, 24, 48)
+        sl = q.Solver(dl)
+        sl.load_gauge(qi.gauge_field(dl, 0.3, seed=1003, device="cuda"))
+        sl.build_clover(0.122, 1.6)
+        q.qcd_learned_set_weights(sl.ctx, q.learned_init_weights(4000, scale_last=1.0))
+        xin = qi.gaussian_spinor_torch(dl, 2003, 1, "cuda").to(torch.complex64).contiguous()
+        yout = torch.empty_like(xin)
+        for _ in range(3):
+            q.qcd_learned_apply(sl.ctx, yout, xin)
+        q.qcd_set_profiling(sl.ctx, True)
+        for k in range(len(q.KERNEL_CLASSES)):
+            q.qcd_kernel_stats(sl.ctx, k, reset=True)
+        for _ in range(5):
+            q.qcd_learned_apply(sl.ctx, yout, xin)
+        n, ms = q.qcd_kernel_stats(sl.ctx, q.KERNEL_CLASSES.index("learned"), reset=True)
+        q.qcd_set_profiling(sl.ctx, False)
+        sl.close()
+        print(json.dumps({"learned_layers_24x24x24x48": {"launches": n, "ms": ms, "ms_per_application": ms / 5}}))
+        return 0
     w = WORKLOAD
     dims = w["dims"]
     V = qi.volume(dims)
@@ -424,11 +455,7 @@ def run_gpu_on_stream(args, q, qi, torch, np, peaks, rank, world, local):
         n, ms = q.qcd_kernel_stats(s.ctx, k, reset=True)
         kstats[nm] = {"launches": n, "ms": ms}
     q.qcd_set_profiling(s.ctx, False)
-    ms_step = sum(step_ms) / len(step_ms)
-    if world > 1:
-        t = torch.tensor([ms_step], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(sum(step_ms) / len(step_ms), world)
 
     # true residual of the last solve, checked with the library's FP64 D
     xr = x.cpu().numpy()
@@ -591,6 +618,8 @@ def main():
                     help="also solve 48^3x96 with 12 point sources, plain and autotuned")
     ap.add_argument("--rhs-group", type=int, default=4, help="right-hand sides per 48^3x96 solve")
     ap.add_argument("--only-dslash", action="store_true", help="profiling aid: time only the FP32 D on 24^3x48")
+    ap.add_argument("--only-learned", action="store_true",
+                    help="profiling aid: time only the learned correction's layers on 24^3x48")
     ap.add_argument("--learned-full", action="store_true",
                     help="also train and judge the learned correction on 24^3 x 48 with 12 point sources")
     args = ap.parse_args()
