@@ -93,7 +93,7 @@ typedef struct {
                            qcd_learned_evaluate found it slower than plain SAP, in
                            which case plain SAP is used (the fallback).  2: always use
                            the learned correction                                     */
-    int sap_ctas;       /* SSOR kernel form, as qcd_set_sap_ctas (-1..8); 0 = context
+    int sap_ctas;       /* SSOR kernel form, as qcd_set_sap_ctas (-1..16); 0 = context
                            setting; results do not depend on it                       */
 } qcd_params;
 
@@ -191,7 +191,7 @@ int qcd_set_graphs(qcd_ctx *ctx, int on);
 
 /* Tuning knob of the SAP block kernel; results do not depend on it.  The
  * block solve has two forms: a warp per site update over a cluster of C CTAs
- * per block (C t-slabs, C a divisor of block[3], at most 8, whose slabs fit in
+ * per block (C t-slabs, C a divisor of block[3], at most 16, whose slabs fit in
  * shared memory), and a thread per site update with one CTA per block (FP32
  * storage, blocks of at most about 1,700 sites).  min_ctas >= 1: the warp form
  * with the smallest such C >= min_ctas.  0 (default): the warp form with the

@@ -75,6 +75,7 @@ namespace cg = cooperative_groups;
 
 constexpr int kRing = 3;           // staging depth (timeline steps in flight)
 constexpr int kMaxSlots = 32;      // sites (one warp each) per CTA per timeline step
+constexpr int kMaxCluster = 16;    // CTAs per SAP block (clusters above 8 need the non-portable size)
 constexpr size_t kSmemLimit = 200 * 1024;
 
 // Per-site record of the SSOR kernel, in 4-byte words.  W_d for d = 2 mu + (backward):
@@ -849,12 +850,12 @@ int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &np,
         return b[3] % C == 0 && ((few && make_chunks(np, C, kMaxSlots)) || make_chunks(np, C, 16));
     };
     int Cfit = 0;
-    for (int C = std::max(1, min_ctas); C <= 8 && !Cfit; C++)
+    for (int C = std::max(1, min_ctas); C <= kMaxCluster && !Cfit; C++)
         if (fit(C)) Cfit = C;  // (min_ctas < 0 without a thread-per-site fit: as 0)
     if (!Cfit) return QCD_ERR_ARG;
     int Cuse = Cfit;
     if (min_ctas <= 0)
-        for (int C = Cfit + 1; C <= 8; C++)
+        for (int C = Cfit + 1; C <= kMaxCluster; C++)
             if (b[3] % C == 0 && (long)nblk1 * C <= sms) Cuse = C;
     if (!fit(Cuse)) return QCD_ERR_ARG;
     make_flags(np);
@@ -944,7 +945,7 @@ int sap_prepare(qcd_ctx *c, const int b[4], const int s[4], bool half) {
         free_plan(c);
         SapPlan np;
         if (sap_plan_host(c, b, s, np, c->sap_min_ctas, half, true) != QCD_OK)
-            return fail(c, QCD_ERR_ARG, "SAP block too large for the shared memory of a cluster of 8 CTAs");
+            return fail(c, QCD_ERR_ARG, "SAP block too large for the shared memory of a cluster of 16 CTAs");
         void *region = nullptr;
         int rc = dev_alloc(c, &region, sap_table_bytes(np));
         if (rc) return rc;
@@ -987,6 +988,10 @@ int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
         QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_warp<true, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
         QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_warp<false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
         QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_warp<true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+        QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_warp<false, 16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_warp<true, 16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_warp<false, 32>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_warp<true, 32>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
         QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_thread, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
         attr_done = true;
     }

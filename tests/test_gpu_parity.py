@@ -221,7 +221,7 @@ def test_errors_are_reported_not_fatal():
 
 
 def test_sap_identical_for_every_cluster_width():
-    """The SSOR kernel may split a block over 1..8 CTAs (a thread-block cluster);
+    """The SSOR kernel may split a block over 1..16 CTAs (a thread-block cluster);
     the arithmetic and its order do not change, so the output is bitwise equal."""
     dims, b, sb = (12, 12, 12, 24), (6, 6, 6, 12), (3, 3, 3, 6)
     kappa = 0.12
@@ -230,7 +230,7 @@ def test_sap_identical_for_every_cluster_width():
     prm = q.make_params(kappa, CSW, b, sb, omega=1.0, nsweep=2, nsap=2)
     vin = torch.from_numpy(v.astype(np.complex64)).cuda()
     outs = []
-    for ctas in (0, 1, 2, 3, 4, 6):
+    for ctas in (0, 1, 2, 3, 4, 6, 12):
         q.qcd_set_sap_ctas(s.ctx, ctas)
         out = torch.empty_like(vin)
         s.sap_precondition(out, vin, prm)
