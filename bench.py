@@ -30,6 +30,9 @@ WORKLOAD = dict(name="12^3x24 plain nested BiCGStab + SAP(6^3x12 blocks, 3^3x6 l
 TABLE1_FLOP_PER_SITE = 1896  # flop per site of the clover hopping matrix without SU(3) reconstruction (Table 1)
 D_BYTES_PER_SITE = {"f32": 768, "f64": 1536, "f16": 480}  # in + out spinor, 4 links (each shared by 2 sites), clover
 L2_FLUSH_BYTES = 512 << 20
+# DRAM bytes (read + write) per launch of a kernel class on this workload, from one ncu capture
+# of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum); None where not captured
+NCU_TRAFFIC = {"ssor": 28917760 + 0}
 
 
 def read_peaks():
@@ -553,7 +556,7 @@ def run_gpu_on_stream(args, q, qi, torch, np, peaks, rank, world, local):
             avg_ms = kstats[dom]["ms"] / kstats[dom]["launches"]
             achieved = units / (avg_ms * 1e-3)
             roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                    "frac": achieved / peak, "traffic": None, "avg_launch_ms": avg_ms,
+                    "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(dom), "avg_launch_ms": avg_ms,
                     "peak_source": peaks["source"] if bound == "hbm" else "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
         tot_k = sum(v["ms"] for v in kstats.values())
         for v in kstats.values():

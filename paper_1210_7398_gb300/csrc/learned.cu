@@ -212,13 +212,18 @@ __device__ __forceinline__ void layer_issue(unsigned char *smem, const int *nbt,
             cp_async16z(X + st * XS + p * 16, static_cast<const float4 *>(x) + (long)p * V + (m < 0 ? 0 : m), m >= 0);
         }
     } else {
+        // thread -> (site, 16-byte chunk) fixed, channels strided: no index arithmetic in the loop
         constexpr int CH16 = 12 * S::XC / 16;  // 16-byte chunks per site and channel
-        for (int i = tid; i < kLayerSites * CIN * CH16; i += nth) {
-            const int k = i % CH16, rest = i / CH16, st = rest % kLayerSites, ch = rest / kLayerSites;
+        constexpr int PAIRS = kLayerSites * CH16;
+        static_assert(kLayerWarps * 32 % PAIRS == 0 || PAIRS % (kLayerWarps * 32) == 0, "even split");
+        for (int pr = tid; pr < PAIRS; pr += nth) {
+            const int st = pr / CH16, k = pr - st * CH16;
             const int m = nb[st];
-            const unsigned char *src =
-                static_cast<const unsigned char *>(x) + (((long)ch * V + (m < 0 ? 0 : m)) * 12) * S::XC + k * 16;
-            cp_async16z(X + st * XS + (ch * CH16 + k) * 16, src, m >= 0);
+            const unsigned char *src = static_cast<const unsigned char *>(x) + ((long)(m < 0 ? 0 : m) * 12) * S::XC + k * 16;
+            unsigned char *dst = X + st * XS + k * 16;
+            const long sstride = (long)V * 12 * S::XC;
+#pragma unroll
+            for (int ch = 0; ch < CIN; ch++) cp_async16z(dst + ch * CH16 * 16, src + ch * sstride, m >= 0);
         }
     }
     if (d > 0) {
