@@ -112,6 +112,29 @@ template <bool HALF> __device__ __forceinline__ float2 ld_c(const float *w) {
     if constexpr (HALF) return __half22float2(*reinterpret_cast<const __half2 *>(w));
     else return *reinterpret_cast<const float2 *>(w);
 }
+// distributed shared memory: a shared-window address mapped to CTA `rank` of the cluster, and
+// loads through it (valid for the executing CTA's own addresses too)
+__device__ __forceinline__ uint32_t mapa_u32(uint32_t a, int rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ float ld_cluster_f32(uint32_t a) {
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];\n" : "=f"(v) : "r"(a) : "memory");
+    return v;
+}
+template <bool HALF> __device__ __forceinline__ float2 ld_cl_c(uint32_t a) {
+    if constexpr (HALF) {
+        uint32_t w;
+        asm volatile("ld.shared::cluster.b32 %0, [%1];\n" : "=r"(w) : "r"(a) : "memory");
+        return __half22float2(*reinterpret_cast<const __half2 *>(&w));
+    } else {
+        float2 v;
+        asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+        return v;
+    }
+}
 template <bool HALF> __device__ __forceinline__ void st_c(float *w, float2 v) {
     if constexpr (HALF) *reinterpret_cast<__half2 *>(w) = __float22half2_rn(v);
     else *reinterpret_cast<float2 *>(w) = v;
@@ -204,7 +227,7 @@ struct SsorArgs {
 
 // K3: y = A_BB f on every block of one colour; blockIdx.x / C enumerates blocks.  MAXW: the
 // most warps per CTA the instance is launched with (32 leaves each thread 64 registers)
-template <bool HALF, int MAXW>
+template <bool HALF, int MAXW, bool CL>
 __global__ void __launch_bounds__(32 * MAXW) k_ssor_warp(SsorArgs a) {
     using L = Rec<HALF>;
     extern __shared__ __align__(16) float sm[];
@@ -212,7 +235,7 @@ __global__ void __launch_bounds__(32 * MAXW) k_ssor_warp(SsorArgs a) {
     if (a.gate && !a.gate[blockIdx.y].active) return;
     a.f += (size_t)blockIdx.y * 6 * a.V;
     a.y += (size_t)blockIdx.y * 6 * a.V;
-    const int rank = a.C > 1 ? (int)cg::this_cluster().block_rank() : 0;
+    const int rank = CL ? (int)cg::this_cluster().block_rank() : 0;
     const int nch = a.nchunks;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int *cptr_g = a.chunk_ptr + rank * (nch + 1);
@@ -225,6 +248,8 @@ __global__ void __launch_bounds__(32 * MAXW) k_ssor_warp(SsorArgs a) {
     float2 *scr0 = reinterpret_cast<float2 *>(csite + ((ntab + 1) & ~1));                 // [nw][12]
     float2 *scr = scr0 + warp * 12;
     float *yscale = reinterpret_cast<float *>(scr0 + nw * 12);                             // [4]
+    const uint32_t ys_u32 = (uint32_t)__cvta_generic_to_shared(ys);
+    const uint32_t scale_u32 = (uint32_t)__cvta_generic_to_shared(yscale);
     const int blk = blockIdx.x / a.C;
     const long n0 = a.origin_site[blk];
     const float4 *rec = a.rec + (size_t)blk * a.vol * L::chunks;
@@ -318,21 +343,25 @@ __global__ void __launch_bounds__(32 * MAXW) k_ssor_warp(SsorArgs a) {
         const int code = sdi[L::nbr + d];
         if (c < 3 && code >= 0) {
             const int sl = code >> 24;
-            const float *slab = ys;
             float sc = my_scale;
-            if (a.C > 1 && sl != rank) {
-                slab = cg::this_cluster().map_shared_rank(ys, sl);
-                if constexpr (HALF) sc = *cg::this_cluster().map_shared_rank(yscale, sl);
-            }
-            const float *pn = slab + (code & 0xffffff);
             const float *W = sd + L::W + (d * 9 + c * 3) * L::cw;
             float2 w0 = make_float2(0.f, 0.f), w1 = make_float2(0.f, 0.f);
+            // the neighbour spinor: a shared-window address (mapped to the owning CTA when it is
+            // remote), read with ld.shared::cluster; a CTA without a cluster reads its own shared memory
+            uint32_t ad = ys_u32 + 4u * (uint32_t)(code & 0xffffff);
+            if constexpr (CL) {
+                if (sl != rank) {
+                    ad = mapa_u32(ad, sl);
+                    if constexpr (HALF) sc = ld_cluster_f32(mapa_u32(scale_u32, sl));
+                }
+            }
+            auto nq = [&](int k) -> float2 {  // complex k of the neighbour spinor
+                if constexpr (CL) return ld_cl_c<HALF>(ad + 4u * (uint32_t)(k * L::cw));
+                else return ld_c<HALF>(ys + (code & 0xffffff) + k * L::cw);
+            };
 #pragma unroll
             for (int cc = 0; cc < 3; cc++) {
-                const float2 qa = ld_c<HALF>(pn + (pa * 3 + cc) * L::cw);
-                const float2 qb = ld_c<HALF>(pn + (pb * 3 + cc) * L::cw);
-                const float2 qc = ld_c<HALF>(pn + (pc * 3 + cc) * L::cw);
-                const float2 qd = ld_c<HALF>(pn + (pd * 3 + cc) * L::cw);
+                const float2 qa = nq(pa * 3 + cc), qb = nq(pb * 3 + cc), qc = nq(pc * 3 + cc), qd = nq(pd * 3 + cc);
                 const float2 u = ld_c<HALF>(W + cc * L::cw);
                 w0 = cfma(u, cfma(za, qb, qa), w0);
                 w1 = cfma(u, cfma(zc, qd, qc), w1);
@@ -400,7 +429,7 @@ __global__ void __launch_bounds__(32 * MAXW) k_ssor_warp(SsorArgs a) {
 
     issue(0);
     issue(1);
-    if (a.C > 1) cg::this_cluster().sync();
+    if (CL) cg::this_cluster().sync();
     else __syncthreads();
     int k = 0, tring = 0;  // sweep position and ring slot of the current step
     for (int t = 0; t < T; t++) {
@@ -415,13 +444,13 @@ __global__ void __launch_bounds__(32 * MAXW) k_ssor_warp(SsorArgs a) {
         if (++tring == kRing) tring = 0;
         if (t + 1 < T) {
             const unsigned char f = a.flags[k];
-            if (f == 2) cg::this_cluster().sync();
+            if (CL && f == 2) cg::this_cluster().sync();
             else if (f == 1) __syncthreads();
         }
     }
     cp_async_wait<0>();
     // no CTA may leave (or overwrite) its slab while a peer can still read it
-    if (a.C > 1) cg::this_cluster().sync();
+    if (CL) cg::this_cluster().sync();
     else __syncthreads();
     for (int i = threadIdx.x; i < a.slab_vol * 6; i += blockDim.x) {
         const int sl = i / 6, q = i - 6 * sl;
@@ -984,14 +1013,14 @@ int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
     bg.vol = p.vol;
     static bool attr_done = false;
     if (!attr_done) {
-        QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_warp<false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
-        QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_warp<true, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
-        QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_warp<false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
-        QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_warp<true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
-        QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_warp<false, 16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-        QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_warp<true, 16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-        QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_warp<false, 32>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-        QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_warp<true, 32>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        const void *ks[] = {(const void *)k_ssor_warp<false, 16, false>, (const void *)k_ssor_warp<true, 16, false>,
+                            (const void *)k_ssor_warp<false, 32, false>, (const void *)k_ssor_warp<true, 32, false>,
+                            (const void *)k_ssor_warp<false, 16, true>, (const void *)k_ssor_warp<true, 16, true>,
+                            (const void *)k_ssor_warp<false, 32, true>, (const void *)k_ssor_warp<true, 32, true>};
+        for (const void *k : ks) {
+            QCD_CUDA(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+            QCD_CUDA(c, cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        }
         QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_thread, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
         attr_done = true;
     }
@@ -1044,12 +1073,14 @@ int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
                 k_ssor_thread<<<dim3(p.nblk[col], nrhs), 32 * p.nwarps, p.smem_bytes, c->stream>>>(a);
                 e = cudaGetLastError();
             } else {
-                if (p.nwarps > 16)
-                    e = p.half ? cudaLaunchKernelEx(&cfg, k_ssor_warp<true, 32>, a)
-                               : cudaLaunchKernelEx(&cfg, k_ssor_warp<false, 32>, a);
+                void (*kern)(SsorArgs);
+                if (p.C > 1)
+                    kern = p.nwarps > 16 ? (p.half ? k_ssor_warp<true, 32, true> : k_ssor_warp<false, 32, true>)
+                                         : (p.half ? k_ssor_warp<true, 16, true> : k_ssor_warp<false, 16, true>);
                 else
-                    e = p.half ? cudaLaunchKernelEx(&cfg, k_ssor_warp<true, 16>, a)
-                               : cudaLaunchKernelEx(&cfg, k_ssor_warp<false, 16>, a);
+                    kern = p.nwarps > 16 ? (p.half ? k_ssor_warp<true, 32, false> : k_ssor_warp<false, 32, false>)
+                                         : (p.half ? k_ssor_warp<true, 16, false> : k_ssor_warp<false, 16, false>);
+                e = cudaLaunchKernelEx(&cfg, kern, a);
             }
             if (e != cudaSuccess) return cuda_fail(c, e, "launch of the SSOR block kernel");
             if ((rc = prof_end(c, QCD_K_SSOR, ev))) return rc;
