@@ -278,6 +278,27 @@ __global__ void __launch_bounds__(32 * MAXW) k_ssor_warp(SsorArgs a) {
                 al[2] = make_float2(1.f, 0.f); be[3] = make_float2(1.f, 0.f); break;
         default: pa = pb = 0; pc = pd = 1; za = zc = make_float2(1.f, 0.f); break;
     }
+    // the four spin contributions a lane forms, in the order the reduce-scatter consumes them:
+    // e0 = spin 2 b4 + b3 (kept), e1 = its pair-mate, f0 / f1 = the spins of the other pair sent
+    // to lane ^ 16; each is (al w0 or be w1) for one non-zero factor in {+-1, +-i}, or zero
+    float2 rm[4];
+    bool rw1[4];
+    {
+        const int hb4 = (lane >> 4) & 1, hb3 = (lane >> 3) & 1;
+        const int sp[4] = {2 * hb4 + hb3, 2 * hb4 + 1 - hb3, 2 * (1 - hb4) + hb3, 2 * (1 - hb4) + 1 - hb3};
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            float2 av = al[0], bv = be[0];
+#pragma unroll
+            for (int t = 1; t < 4; t++)
+                if (sp[j] == t) {
+                    av = al[t];
+                    bv = be[t];
+                }
+            rw1[j] = bv.x != 0.f || bv.y != 0.f;
+            rm[j] = rw1[j] ? bv : av;
+        }
+    }
     // ---- lane constants of the clover phase: lane (s, c), s = lane >> 3, holds spin s ----
     const int so = lane >> 3;
     const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0;
@@ -337,9 +358,9 @@ __global__ void __launch_bounds__(32 * MAXW) k_ssor_warp(SsorArgs a) {
     // one SSOR site update by the whole warp
     auto update = [&](const float *sd) {
         const int *sdi = reinterpret_cast<const int *>(sd);
-        float2 acc[4];
+        float2 e[4];  // e0, e1, f0, f1 (see the lane constants)
 #pragma unroll
-        for (int s = 0; s < 4; s++) acc[s] = make_float2(0.f, 0.f);
+        for (int j = 0; j < 4; j++) e[j] = make_float2(0.f, 0.f);
         const int code = sdi[L::nbr + d];
         if (c < 3 && code >= 0) {
             const int sl = code >> 24;
@@ -368,25 +389,17 @@ __global__ void __launch_bounds__(32 * MAXW) k_ssor_warp(SsorArgs a) {
             }
             if constexpr (HALF) { w0 = cscale(w0, sc); w1 = cscale(w1, sc); }
 #pragma unroll
-            for (int s = 0; s < 4; s++) acc[s] = cfma(be[s], w1, cmul(al[s], w0));
+            for (int j = 0; j < 4; j++) e[j] = cmul(rm[j], rw1[j] ? w1 : w0);
         }
-        // reduce-scatter over the 8 directions: lane bit 4 picks spins {0,1} / {2,3}, bit 3 one of them
-        float2 k0, k1;
-        {
-            const float2 s0 = b4 ? acc[0] : acc[2], s1 = b4 ? acc[1] : acc[3];
-            k0 = b4 ? acc[2] : acc[0];
-            k1 = b4 ? acc[3] : acc[1];
-            k0.x += __shfl_xor_sync(0xffffffffu, s0.x, 16);
-            k0.y += __shfl_xor_sync(0xffffffffu, s0.y, 16);
-            k1.x += __shfl_xor_sync(0xffffffffu, s1.x, 16);
-            k1.y += __shfl_xor_sync(0xffffffffu, s1.y, 16);
-        }
-        float2 A = b3 ? k1 : k0;
-        {
-            const float2 sn = b3 ? k0 : k1;
-            A.x += __shfl_xor_sync(0xffffffffu, sn.x, 8);
-            A.y += __shfl_xor_sync(0xffffffffu, sn.y, 8);
-        }
+        // reduce-scatter over the 8 directions (lane bits 4, 3, 2): the pair of the other b4 goes to
+        // lane ^ 16, the pair-mate to lane ^ 8, then the two halves of the direction sum meet
+        e[0].x += __shfl_xor_sync(0xffffffffu, e[2].x, 16);
+        e[0].y += __shfl_xor_sync(0xffffffffu, e[2].y, 16);
+        e[1].x += __shfl_xor_sync(0xffffffffu, e[3].x, 16);
+        e[1].y += __shfl_xor_sync(0xffffffffu, e[3].y, 16);
+        float2 A = e[0];
+        A.x += __shfl_xor_sync(0xffffffffu, e[1].x, 8);
+        A.y += __shfl_xor_sync(0xffffffffu, e[1].y, 8);
         A.x += __shfl_xor_sync(0xffffffffu, A.x, 4);
         A.y += __shfl_xor_sync(0xffffffffu, A.y, 4);
         // lane (s, c) holds spin s, colour c of the hop sum; its chiral component (chirality s >> 1)
