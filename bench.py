@@ -230,7 +230,7 @@ def dslash_bandwidth(q, torch, dims, iters, peaks, seed=1002, variants=(("f32", 
 
 def learned_section(q, qi, torch, s, dims, prm, b, nrhs, npairs, epochs, lr=3e-3, batch=8):
     """Trains the learned correction on npairs (residual, error) pairs of the plain SAP set-up prm
-    (sources seed 3000, weights seed 4000), then lets qcd_learned_evaluate judge it on b."""
+    (sources seed 3000, weights seed 4000), then lets qcd_learned_evaluate assess it on b."""
     t0 = time.perf_counter()
     q.qcd_learned_set_weights(s.ctx, q.learned_init_weights(4000))
     src = qi.gaussian_spinor_torch(dims, 3000, npairs, "cuda").to(torch.complex64).contiguous()
@@ -316,6 +316,76 @@ def batched_section(q, qi, torch, csw, eps, tol, inner_tol, candidates):
             "speedup_concurrent": sum(seq) / t_multi,
             "note": "concurrent = qcd_solve_multi: one host thread and one stream per instance; "
                     "each instance replays its captured inner iteration"}
+
+
+def ll_levels(b, s):
+    """Dependent steps per SSOR pass of the ll order on a b block with s sub-blocks: the longest
+    chain of in-block neighbours in increasing ll key (the level schedule the kernel runs)."""
+    nq = [b[m] // s[m] for m in range(4)]
+    nsb = nq[0] * nq[1] * nq[2] * nq[3]
+    vol = b[0] * b[1] * b[2] * b[3]
+
+    def coords(yl):
+        y = []
+        for m in range(4):
+            y.append(yl % b[m])
+            yl //= b[m]
+        return y
+
+    key = [0] * vol
+    for yl in range(vol):
+        y = coords(yl)
+        lam = sig = 0
+        for m in (3, 2, 1, 0):
+            lam = lam * s[m] + y[m] % s[m]
+            sig = sig * nq[m] + y[m] // s[m]
+        key[yl] = lam * nsb + sig
+    level = [0] * vol
+    for yl in sorted(range(vol), key=lambda v: key[v]):
+        y = coords(yl)
+        lv, stride = 0, 1
+        for m in range(4):
+            for dd in (-1, 1):
+                if 0 <= y[m] + dd < b[m]:
+                    nb = yl + dd * stride
+                    if key[nb] < key[yl]:
+                        lv = max(lv, level[nb] + 1)
+            stride *= b[m]
+        level[yl] = lv
+    return max(level) + 1
+
+
+def geometry_section(q, qi, torch, s, w, b):
+    """SAP block and sub-block geometries on the plain 12^3 x 24 solve (FP32 storage, the
+    workload's omega, sweeps and cycles): time to solution, iterations, SSOR launch time."""
+    geoms = [((6, 6, 6, 12), (3, 3, 3, 6)), ((6, 6, 6, 6), (3, 3, 3, 3)), ((6, 6, 6, 12), (2, 2, 2, 4)),
+             ((6, 6, 6, 12), (6, 6, 6, 12)), ((6, 6, 6, 6), (2, 2, 2, 2)), ((6, 6, 6, 6), (6, 6, 6, 6)),
+             ((3, 3, 3, 6), (3, 3, 3, 6)), ((3, 3, 3, 6), (1, 1, 1, 2)), ((3, 3, 3, 3), (1, 1, 1, 1)),
+             ((2, 2, 2, 2), (1, 1, 1, 1))]
+    out = []
+    x = torch.zeros_like(b)
+    stream = torch.cuda.current_stream()
+    for blk, sub in geoms:
+        p = q.make_params(w["kappa"], w["csw"], blk, sub, omega=w["omega"], nsweep=w["nsweep"], nsap=w["nsap"],
+                          tol=w["tol"], inner_tol=w["inner_tol"])
+        x.zero_()
+        s.solve(x, b, p)
+        x.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        st = s.solve(x, b, p)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        q.qcd_set_profiling(s.ctx, True)
+        q.qcd_kernel_stats(s.ctx, q.KERNEL_CLASSES.index("ssor"), reset=True)
+        x.zero_()
+        s.solve(x, b, p)
+        n, ms = q.qcd_kernel_stats(s.ctx, q.KERNEL_CLASSES.index("ssor"), reset=True)
+        q.qcd_set_profiling(s.ctx, False)
+        out.append({"block": list(blk), "subblock": list(sub), "levels_per_pass": ll_levels(blk, sub),
+                    "ms": ev[0].elapsed_time(ev[1]), "outer_iters": st["outer_iters"], "inner_iters": st["inner_iters"],
+                    "ssor_ms_per_launch": ms / max(1, n), "true_rel_res": st["true_rel_res"]})
+    return out
 
 
 def headline_section(q, qi, torch, w, group, candidates):
@@ -521,6 +591,9 @@ def run_gpu_on_stream(args, q, qi, torch, np, peaks, rank, world, local):
             chosen["value"] = lr_sec["verdict"]["learned_ms"] / 1000.0
             chosen["params"]["learned"] = 1
             chosen["speedup_vs_plain"] = ms_step / lr_sec["verdict"]["learned_ms"]
+    geometry = None
+    if args.geometry_sweep:
+        geometry = geometry_section(q, qi, torch, s, w, bd)
     batched = None
     if args.batched_full:
         batched = batched_section(q, qi, torch, w["csw"], w["eps"], w["tol"], w["inner_tol"], 16)
@@ -596,6 +669,8 @@ def run_gpu_on_stream(args, q, qi, torch, np, peaks, rank, world, local):
             out["learned_24x24x24x48"] = learned_full
         if batched is not None:
             out["batched_uneven"] = batched
+        if geometry is not None:
+            out["geometry_sweep"] = geometry
         if headline is not None:
             out["headline_48x48x48x96"] = headline
         print(json.dumps(out))
@@ -617,6 +692,8 @@ def main():
     ap.add_argument("--tune-candidates", type=int, default=48, help="solves the autotuner may time")
     ap.add_argument("--batched-full", action="store_true",
                     help="also solve 24^3x48 (12 point sources) + 8^3x16, 12^3x24, 16^3x32 alone and concurrently")
+    ap.add_argument("--geometry-sweep", action="store_true",
+                    help="also time the plain 12^3x24 solve over SAP block / sub-block geometries")
     ap.add_argument("--headline", action="store_true",
                     help="also solve 48^3x96 with 12 point sources, plain and autotuned")
     ap.add_argument("--rhs-group", type=int, default=4, help="right-hand sides per 48^3x96 solve")
@@ -624,7 +701,7 @@ def main():
     ap.add_argument("--only-learned", action="store_true",
                     help="profiling aid: time only the learned correction's layers on 24^3x48")
     ap.add_argument("--learned-full", action="store_true",
-                    help="also train and judge the learned correction on 24^3 x 48 with 12 point sources")
+                    help="also train and assess the learned correction on 24^3 x 48 with 12 point sources")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -257,7 +257,7 @@ typedef struct {
     int pad;
 } qcd_learned_verdict;
 
-/* Judges the trained correction on b (complex128 [nrhs][V][4][3], host or
+/* Assesses the trained correction on b (complex128 [nrhs][V][4][3], host or
  * device) with the solver settings *p (p->learned ignored): solves with plain
  * SAP and with the correction, compares time to solution, and records the
  * verdict in the context; qcd_learned_set_weights and qcd_learned_train clear
