@@ -28,7 +28,7 @@ WORKLOAD = dict(name="12^3x24 plain nested BiCGStab + SAP(6^3x12 blocks, 3^3x6 l
                 block=(6, 6, 6, 12), subblock=(3, 3, 3, 6), omega=1.0, nsweep=4, nsap=4, tol=1e-10,
                 inner_tol=1e-5)
 TABLE1_FLOP_PER_SITE = 1896  # flop per site of the clover hopping matrix without SU(3) reconstruction (Table 1)
-D_BYTES_PER_SITE = {"f32": 768, "f64": 1536, "f16": 480}  # in + out spinor, 4 links (each shared by 2 sites), clover
+D_BYTES_PER_SITE = {"f32": 768, "f64": 1536, "f16": 480, "su3": 672}  # in + out spinor, 4 links (each shared by 2 sites), clover
 L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) per launch of a kernel class on this workload, from one ncu capture
 # of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum); None where not captured
@@ -200,7 +200,7 @@ def dslash_bandwidth(q, torch, dims, iters, peaks, seed=1002, variants=(("f32", 
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     out = []
     for prec, nrhs in variants:
-        pc = {"f32": q.QCD_F32, "f64": q.QCD_F64, "f16": q.QCD_F16}[prec]
+        pc = {"f32": q.QCD_F32, "f64": q.QCD_F64, "f16": q.QCD_F16, "su3": q.QCD_F32_SU3}[prec]
         q.qcd_bench_dslash(s.ctx, pc, nrhs, 3)
         times = []
         for _ in range(iters):
@@ -637,7 +637,8 @@ def run_gpu_on_stream(args, q, qi, torch, np, peaks, rank, world, local):
         dsl = []
         if not args.skip_dslash:
             dsl += dslash_bandwidth(q, torch, (24, 24, 24, 48), 20, peaks,
-                                    variants=(("f32", 1), ("f32", 12), ("f16", 1), ("f16", 12), ("f64", 1)))
+                                    variants=(("f32", 1), ("f32", 12), ("f16", 1), ("f16", 12), ("su3", 1), ("su3", 12),
+                                              ("f64", 1)))
             dsl += dslash_bandwidth(q, torch, (48, 48, 48, 96), 20, peaks)
         cpu = None
         if world == 1 and not args.skip_cpu:

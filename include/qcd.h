@@ -73,7 +73,7 @@ enum {
     QCD_ERR_STATE = -8      /* wrong call order, or context poisoned by a CUDA error  */
 };
 
-enum { QCD_F64 = 0, QCD_F32 = 1, QCD_F16 = 2, QCD_BF16 = 3 };
+enum { QCD_F64 = 0, QCD_F32 = 1, QCD_F16 = 2, QCD_BF16 = 3, QCD_F32_SU3 = 4 };
 
 /* Solver and SAP parameters (Sec. 2, Sec. 3, Eq. (4)). */
 typedef struct {
@@ -130,8 +130,11 @@ int qcd_build_clover(qcd_ctx *ctx, double kappa, double csw);
 /* out = D in for nrhs right-hand sides (Eq. (2)).  prec = QCD_F64: in/out are
  * complex128 [nrhs][V][4][3]; QCD_F32: complex64; QCD_F16: complex64 in/out
  * with the links and the clover field stored in FP16 (FP32 arithmetic; the
- * FP16 copies are made on first use after each field change).  in and out
- * must not overlap.  Requires qcd_build_clover. */
+ * FP16 copies are made on first use after each field change); QCD_F32_SU3:
+ * complex64 in/out with each link stored as its first two rows and the third
+ * rebuilt as the conjugate cross product (SU(3) 12-real form, Table 1: 672
+ * instead of 768 bytes per site).  in and out must not overlap.  Requires
+ * qcd_build_clover. */
 int qcd_apply_D(qcd_ctx *ctx, void *out, const void *in, int prec, int nrhs);
 
 /* out = M_SAP in (Eq. (4), Alg. 1) in FP32 for nrhs right-hand sides:
@@ -289,7 +292,7 @@ long qcd_launch_count(const qcd_ctx *ctx);
 
 /* D on internal-layout buffers only, repeated `iters` times (no layout
  * conversion): the kernel the memory-bandwidth roofline is measured on.
- * prec = QCD_F64 or QCD_F32; nrhs >= 1.  Work buffers are allocated on first
+ * prec = QCD_F64, QCD_F32, QCD_F16 or QCD_F32_SU3; nrhs >= 1.  Work buffers are allocated on first
  * use and kept. */
 int qcd_bench_dslash(qcd_ctx *ctx, int prec, int nrhs, int iters);
 

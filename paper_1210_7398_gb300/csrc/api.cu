@@ -201,7 +201,7 @@ void qcd_destroy(qcd_ctx *c) {
     else cudaDeviceSynchronize();
     void *bufs[] = {c->net.W, c->net.grad, c->net.m, c->net.v, c->net.B, c->net.P, c->net.scal, c->net.act,
                     c->net.pairs,
-                    c->U64, c->U32, c->F64, c->F32, c->U16, c->F16, c->d_status, c->d_red, c->d_scalars, c->d_bicg, c->d_mask,
+                    c->U64, c->U32, c->F64, c->F32, c->U16, c->F16, c->U12, c->d_status, c->d_red, c->d_scalars, c->d_bicg, c->d_mask,
                     c->ws64, c->ws32,
                     c->d_io, c->bench_in, c->bench_out, c->plan.d_origin[0] /* the plan's table region */,
                     c->plan.d_rec};
@@ -271,7 +271,7 @@ int qcd_apply_D(qcd_ctx *c, void *out, const void *in, int prec, int nrhs) {
     int rc = ready(c);
     if (rc) return rc;
     if ((rc = need_clover(c))) return rc;
-    if (!out || !in || nrhs < 1 || (prec != QCD_F64 && prec != QCD_F32 && prec != QCD_F16))
+    if (!out || !in || nrhs < 1 || (prec != QCD_F64 && prec != QCD_F32 && prec != QCD_F16 && prec != QCD_F32_SU3))
         return fail(c, QCD_ERR_ARG, "qcd_apply_D: bad pointer, nrhs or precision");
     const long V = c->lat.V;
     const size_t elem = (prec == QCD_F64) ? 16 : 8;
@@ -295,7 +295,7 @@ int qcd_apply_D(qcd_ctx *c, void *out, const void *in, int prec, int nrhs) {
     } else {
         float4 *a = (float4 *)io, *b = (float4 *)(io + bytes);
         if ((rc = spinor32_to_internal(c, a, (const float2 *)din, nrhs))) return rc;
-        if ((rc = (prec == QCD_F16 ? dslash16 : dslash32)(c, b, a, nrhs))) return rc;
+        if ((rc = (prec == QCD_F16 ? dslash16 : prec == QCD_F32_SU3 ? dslash12 : dslash32)(c, b, a, nrhs))) return rc;
         if ((rc = spinor32_from_internal(c, (float2 *)dout, b, nrhs))) return rc;
     }
     if (!dev_out) QCD_CUDA(c, cudaMemcpyAsync(out, dout, bytes, cudaMemcpyDeviceToHost, c->stream));
@@ -680,7 +680,7 @@ int qcd_bench_dslash(qcd_ctx *c, int prec, int nrhs, int iters) {
     int rc = ready(c);
     if (rc) return rc;
     if ((rc = need_clover(c))) return rc;
-    if ((prec != QCD_F64 && prec != QCD_F32 && prec != QCD_F16) || nrhs < 1 || iters < 1)
+    if ((prec != QCD_F64 && prec != QCD_F32 && prec != QCD_F16 && prec != QCD_F32_SU3) || nrhs < 1 || iters < 1)
         return fail(c, QCD_ERR_ARG, "qcd_bench_dslash: bad precision, nrhs or iters");
     const size_t bytes = (prec == QCD_F64 ? 16 : 8) * 12 * c->lat.V * (size_t)nrhs;
     if (c->bench_bytes < bytes) {
@@ -697,6 +697,7 @@ int qcd_bench_dslash(qcd_ctx *c, int prec, int nrhs, int iters) {
     for (int i = 0; i < iters; i++) {
         if (prec == QCD_F64) rc = dslash64(c, (double2 *)c->bench_out, (const double2 *)c->bench_in, nrhs);
         else if (prec == QCD_F16) rc = dslash16(c, (float4 *)c->bench_out, (const float4 *)c->bench_in, nrhs);
+        else if (prec == QCD_F32_SU3) rc = dslash12(c, (float4 *)c->bench_out, (const float4 *)c->bench_in, nrhs);
         else rc = dslash32(c, (float4 *)c->bench_out, (const float4 *)c->bench_in, nrhs);
         if (rc) return rc;
     }

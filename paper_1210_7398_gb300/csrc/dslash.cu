@@ -34,6 +34,25 @@ __device__ __forceinline__ void load_clover(const uint2 *__restrict__ F, long V,
     }
 }
 
+// SU(3) 12-real storage (Table 1's compressed links): the first two rows, 3 float4 per link
+// ([4][3][V]); the third row of a special unitary matrix is the complex conjugate of the cross
+// product of the first two.
+__device__ __forceinline__ void load_link(const float4 *__restrict__ U, long V, long n, int mu, float2 u[9]) {
+#pragma unroll
+    for (int p = 0; p < 3; p++) {
+        const float4 v = __ldg(U + (mu * 3 + p) * V + n);
+        u[2 * p] = make_float2(v.x, v.y);
+        u[2 * p + 1] = make_float2(v.z, v.w);
+    }
+    auto cross = [](float2 a, float2 b, float2 c, float2 d) {  // conj(a b - c d)
+        const float2 v = csub(cmul(a, b), cmul(c, d));
+        return make_float2(v.x, -v.y);
+    };
+    u[6] = cross(u[1], u[5], u[2], u[4]);
+    u[7] = cross(u[2], u[3], u[0], u[5]);
+    u[8] = cross(u[0], u[4], u[1], u[3]);
+}
+
 // MINB: resident blocks per SM requested from the register allocator.  The FP32
 // kernel is bound by memory latency, so it trades registers for occupancy
 // (7 blocks of 128 threads); the FP64 kernel is bound by GB300's FP64 rate and
@@ -139,6 +158,16 @@ __global__ void __launch_bounds__(128, MINB) dslash_kernel_nr(SP *__restrict__ o
 }
 
 namespace {
+// first two rows of every FP32 link
+__global__ void k_links_to_rows(float4 *__restrict__ U12, const float2 *__restrict__ U32, long V) {
+    const long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (n >= V) return;
+    for (int mu = 0; mu < 4; mu++)
+        for (int p = 0; p < 3; p++) {
+            const float2 a = U32[(mu * 9 + 2 * p) * V + n], b = U32[(mu * 9 + 2 * p + 1) * V + n];
+            U12[(mu * 3 + p) * V + n] = make_float4(a.x, a.y, b.x, b.y);
+        }
+}
 // FP16 copies of the FP32 links and clover field
 __global__ void k_fields_to_half(__half2 *__restrict__ U16, uint2 *__restrict__ F16, const float2 *__restrict__ U32,
                                  const float4 *__restrict__ F32, long V) {
@@ -206,6 +235,30 @@ int dslash16(qcd_ctx *c, float4 *out, const float4 *in, int nrhs) {
     } else {
         dim3 grid((unsigned)((g.V + 127) / 128), (nrhs + 1) / 2);
         dslash_kernel_nr<4, 2, float, float4, __half2, uint2><<<grid, 128, 0, c->stream>>>(out, in, c->U16, c->F16,
+                                                                                     (float)c->kappa, g, nrhs);
+    }
+    return prof_end(c, QCD_K_DSLASH32, ev);
+}
+
+int dslash12(qcd_ctx *c, float4 *out, const float4 *in, int nrhs) {
+    Geo g = geo_of(c);
+    if (!c->U12) {
+        int rc = dev_alloc(c, (void **)&c->U12, sizeof(float4) * 12 * g.V);
+        if (rc) return rc;
+    }
+    if (c->u12_version != c->field_version) {
+        k_links_to_rows<<<(unsigned)((g.V + 255) / 256), 256, 0, c->stream>>>(c->U12, c->U32, g.V);
+        QCD_CUDA(c, cudaGetLastError());
+        c->u12_version = c->field_version;
+    }
+    cudaEvent_t ev;
+    prof_begin(c, QCD_K_DSLASH32, &ev);
+    if (nrhs == 1) {
+        dslash_kernel<7, float, float4, float4, float4><<<dim3((unsigned)((g.V + 127) / 128), 1), 128, 0, c->stream>>>(
+            out, in, c->U12, c->F32, (float)c->kappa, g, 1);
+    } else {
+        dim3 grid((unsigned)((g.V + 127) / 128), (nrhs + 1) / 2);
+        dslash_kernel_nr<4, 2, float, float4, float4, float4><<<grid, 128, 0, c->stream>>>(out, in, c->U12, c->F32,
                                                                                      (float)c->kappa, g, nrhs);
     }
     return prof_end(c, QCD_K_DSLASH32, ev);

@@ -118,6 +118,8 @@ struct qcd_ctx {
     __half2 *U16 = nullptr;  // FP16 copies for the FP16-storage operator, made on first use
     uint2 *F16 = nullptr;    // [18][V], four halves per plane
     long half_version = -1;  // field_version the FP16 copies were made from
+    float4 *U12 = nullptr;   // links as their first two rows [4][3][V] (SU(3) 12-real form), made on first use
+    long u12_version = -1;
     int *d_status = nullptr;  // device status word (clover singularity)
 
     // SAP plan cache (one geometry at a time)
@@ -187,6 +189,7 @@ int build_clover(qcd_ctx *c, double kappa, double csw);
 int dslash64(qcd_ctx *c, double2 *out, const double2 *in, int nrhs);
 int dslash32(qcd_ctx *c, float4 *out, const float4 *in, int nrhs);
 int dslash16(qcd_ctx *c, float4 *out, const float4 *in, int nrhs);
+int dslash12(qcd_ctx *c, float4 *out, const float4 *in, int nrhs);
 
 // SAP (sap.cu)
 // host part of a plan (tables in h_*; device pointers left null); QCD_ERR_ARG on bad geometry

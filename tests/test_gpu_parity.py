@@ -70,7 +70,8 @@ D_F16_TOL = 2e-3
 @pytest.mark.parametrize("dims,bc_t", [((4, 4, 4, 4), 1), ((6, 4, 4, 6), -1), ((8, 8, 8, 16), 1)])
 def test_dslash_odd_rhs_counts_and_fp16_storage(dims, bc_t):
     """Three right-hand sides take the two-per-thread kernel and a single tail;
-    the FP16-storage operator stays within its rounding bound."""
+    the FP16-storage operator stays within its rounding bound; the SU(3)
+    12-real link form keeps FP32 accuracy."""
     kappa = 0.12
     s, U, F = make_solver(dims, kappa, seed=1000, bc_t=bc_t)
     psi = qi.gaussian_spinor(dims, seed=2000, nrhs=3)
@@ -86,6 +87,12 @@ def test_dslash_odd_rhs_counts_and_fp16_storage(dims, bc_t):
     torch.cuda.synchronize()
     for k in range(3):
         assert rel_norm(out16[k].cpu().numpy().astype(np.complex128), ref[k]) <= D_F16_TOL
+    # SU(3) 12-real links (two rows stored, the third rebuilt): FP32 accuracy
+    out12 = torch.empty_like(dev32)
+    s.apply_D(out12, dev32, q.QCD_F32_SU3, nrhs=3)
+    torch.cuda.synchronize()
+    for k in range(3):
+        assert rel_norm(out12[k].cpu().numpy().astype(np.complex128), ref[k]) <= 2e-6
     # the FP16 copies follow a change of the fields
     s.build_clover(0.11, CSW)
     _, F2 = oracle.clover(dims, U, CSW, 0.11)
