@@ -194,12 +194,13 @@ int qcd_set_graphs(qcd_ctx *ctx, int on);
 
 /* Tuning knob of the SAP block kernel; results do not depend on it.  The
  * block solve has two forms: a warp per site update over a cluster of C CTAs
- * per block (C t-slabs, C a divisor of block[3], at most 16, whose slabs fit in
- * shared memory), and a thread per site update with one CTA per block (FP32
+ * per block (C <= 16, each CTA owning an equal share of every dependency
+ * level of the sweep, its sites' spinors in its shared memory, which must
+ * fit), and a thread per site update with one CTA per block (FP32
  * storage, blocks of at most about 1,700 sites).  min_ctas >= 1: the warp form
  * with the smallest such C >= min_ctas.  0 (default): the warp form with the
- * largest C for which one colour's clusters still fit the SM count (at least
- * the smallest C that fits).  -1: the thread form where it fits, else as 0.
+ * largest C in {1, 2, 4, 8} for which one colour's clusters still fit the SM
+ * count (at least the smallest C that fits).  -1: the thread form where it fits, else as 0.
  * More CTAs per block spread a step's sites over more SMs at the price of more
  * cluster barriers. */
 int qcd_set_sap_ctas(qcd_ctx *ctx, int min_ctas);

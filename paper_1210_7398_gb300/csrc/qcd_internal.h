@@ -47,18 +47,22 @@ struct SapPlan {
     int *d_origin[2] = {nullptr, nullptr};  // [nblk[c]][4] block origins per colour
     bool half = false;  // FP16 storage of the block spinor and the records (FP32 arithmetic)
     bool thread = false;  // thread-per-site SSOR kernel (block fields in shared memory, no records)
-    int C = 1, slab_t = 0, slab_vol = 0;
+    int C = 1, slab_vol = 0;  // CTAs per block (cluster), most sites one CTA owns
     int nchunks = 0, nslot = 0, nwarps = 0;
     size_t smem_bytes = 0;
     std::vector<int> h_chunk_ptr;   // [C][nchunks + 1], offsets into h_chunk_site
     std::vector<int> h_chunk_site;  // block-local site indices, CTA-major
     std::vector<unsigned char> h_flags;  // [2 * nchunks]
     std::vector<int> h_site_off;    // [vol] global index offset of a block-local site from its block origin
+    std::vector<int> h_own;         // [vol] (owning CTA << 24) | index in that CTA's slab of y
+    std::vector<int> h_own_off;     // [C][slab_vol] global offset of each owned site, -1 past the last
     std::vector<int> h_origin_site[2];  // [nblk[c]] global index of each block origin
     int *d_chunk_ptr = nullptr;
     int2 *d_chunk_site = nullptr;   // (block-local site, global offset from the block origin)
     unsigned char *d_flags = nullptr;
     int *d_site_off = nullptr;
+    int *d_own = nullptr;
+    int *d_own_off = nullptr;
     int *d_origin_site[2] = {nullptr, nullptr};
     float *d_rec = nullptr;         // per-site records (links, clover, neighbour codes), V x 912 bytes
     long rec_version = -1;          // field version the records were built from

@@ -143,7 +143,7 @@ template <bool HALF> __device__ __forceinline__ void st_c(float *w, float2 v) {
 // Builds the per-site records of every block (blocks of colour 0 first).
 template <bool HALF>
 __global__ void k_sap_records(float *__restrict__ rec, const float2 *__restrict__ U, const float4 *__restrict__ F,
-                              Geo g, BlockGeo bg, int slab_t, int slab_vol, const int *__restrict__ org0,
+                              Geo g, BlockGeo bg, const int *__restrict__ own, const int *__restrict__ org0,
                               const int *__restrict__ org1, int nblk0, long total) {
     using L = Rec<HALF>;
     const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
@@ -181,8 +181,7 @@ __global__ void k_sap_records(float *__restrict__ rec, const float2 *__restrict_
                 st_c<HALF>(W + (a * 3 + bb) * L::cw, u);
             }
         const int nb = yl + (fwd ? bs[mu] : -bs[mu]);
-        const int sl = (mu == 3 ? ym : y[3]) / slab_t;
-        Ri[L::nbr + d] = (sl << 24) | ((nb - sl * slab_vol) * L::ywords);
+        Ri[L::nbr + d] = (own[nb] & ~0xffffff) | ((own[nb] & 0xffffff) * L::ywords);
     }
     float fp[72];
     for (int k = 0; k < 18; k++) {
@@ -199,9 +198,8 @@ __global__ void k_sap_records(float *__restrict__ rec, const float2 *__restrict_
                 else { const int q = 36 * ch + 6 + 2 * (j * (j - 1) / 2 + ii); e = make_float2(fp[q], -fp[q + 1]); }
                 st_c<HALF>(R + L::F + (36 * ch + 6 * ii + j) * L::cw, e);
             }
-    const int sl = y[3] / slab_t;
     Ri[L::site] = (int)n;
-    Ri[L::yoff] = (yl - sl * slab_vol) * L::ywords;
+    Ri[L::yoff] = (own[yl] & 0xffffff) * L::ywords;
     for (int k = L::nbr + 8; k < L::words; k++) Ri[k] = 0;
 }
 
@@ -216,6 +214,7 @@ struct SsorArgs {
     const int *chunk_ptr;      // [C][nchunks + 1]
     const int2 *chunk_site;    // (block-local site, global offset from the block origin)
     const int *site_off;       // [vol] global offset of a block-local site from the block origin
+    const int *own_off;        // [C][slab_vol] global offset of each site a CTA owns, -1 past the last
     const unsigned char *flags;  // [2 * nchunks] cluster barrier before a timeline step
     const int *origin_site;    // [blocks of this colour] global index of the block origin
     const BicgScalars *gate;   // blockIdx.y = right-hand side; skipped when inactive (null: all)
@@ -240,14 +239,15 @@ __global__ void __launch_bounds__(32 * MAXW) k_ssor_warp(SsorArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int *cptr_g = a.chunk_ptr + rank * (nch + 1);
     const int tab0 = cptr_g[0], ntab = cptr_g[nch] - tab0;
-    // shared memory: [y slab | staging ring | chunk pointers | chunk sites | per-warp scratch | scale]
+    // shared memory: [y slab | scale | staging ring | chunk pointers | chunk sites | per-warp scratch];
+    // the slab and the scale sit at the same offsets in every CTA of the cluster (peers read them)
     float *ys = sm;                                                    // [slab_vol][ywords]
-    float *ring = ys + (size_t)a.slab_vol * L::ywords;                 // [kRing][nslot][stage]
+    float *yscale = ys + (size_t)a.slab_vol * L::ywords;               // [4]
+    float *ring = yscale + 4;                                          // [kRing][nslot][stage]
     int *cptr = reinterpret_cast<int *>(ring + (size_t)kRing * a.nslot * L::stage);      // [nch + 1]
     int2 *csite = reinterpret_cast<int2 *>(cptr + ((nch + 1 + 3) & ~3));                  // [ntab]
     float2 *scr0 = reinterpret_cast<float2 *>(csite + ((ntab + 1) & ~1));                 // [nw][12]
     float2 *scr = scr0 + warp * 12;
-    float *yscale = reinterpret_cast<float *>(scr0 + nw * 12);                             // [4]
     const uint32_t ys_u32 = (uint32_t)__cvta_generic_to_shared(ys);
     const uint32_t scale_u32 = (uint32_t)__cvta_generic_to_shared(yscale);
     const int blk = blockIdx.x / a.C;
@@ -317,7 +317,9 @@ __global__ void __launch_bounds__(32 * MAXW) k_ssor_warp(SsorArgs a) {
         float m = 0.f;
         for (int i = threadIdx.x; i < a.slab_vol * 6; i += blockDim.x) {
             const int sl = i / 6, q = i - 6 * sl;
-            const float4 v = a.f[(long)q * a.V + n0 + a.site_off[rank * a.slab_vol + sl]];
+            const int off = a.own_off[rank * a.slab_vol + sl];
+            if (off < 0) continue;
+            const float4 v = a.f[(long)q * a.V + n0 + off];
             m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
         }
         for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
@@ -467,7 +469,9 @@ __global__ void __launch_bounds__(32 * MAXW) k_ssor_warp(SsorArgs a) {
     else __syncthreads();
     for (int i = threadIdx.x; i < a.slab_vol * 6; i += blockDim.x) {
         const int sl = i / 6, q = i - 6 * sl;
-        const long n = n0 + a.site_off[rank * a.slab_vol + sl];
+        const int off = a.own_off[rank * a.slab_vol + sl];
+        if (off < 0) continue;
+        const long n = n0 + off;
         float4 v;
         if constexpr (HALF) {
             const float2 lo = cscale(ld_c<true>(ys + sl * 12 + 2 * q), my_scale);
@@ -659,11 +663,34 @@ void free_plan(qcd_ctx *c) {
 // Split the block into C slabs along t and every step (level) into chunks of
 // at most maxslots sites per slab, of equal size.  Returns false if the shared
 // memory of a CTA (its slab of y plus the staging ring) would exceed kSmemLimit.
+// Which CTA of the cluster owns (updates and stores) each site of the block.  C = 1: all.
+// C > 1: the sites of every level are dealt round-robin over the C CTAs in ll order, so each
+// CTA gets an equal share of every level (a t-slab split would give each CTA a band of levels
+// and leave most CTAs idle at the ends of the chain); neighbours then mostly sit in other
+// CTAs and are read through distributed shared memory.
+void assign_owners(SapPlan &np, int C) {
+    np.h_own.assign(np.vol, 0);
+    std::vector<int> cnt(C, 0);
+    if (C == 1) {  // one CTA: the block spinor in natural site order
+        for (int yl = 0; yl < np.vol; yl++) np.h_own[yl] = yl;
+        cnt[0] = np.vol;
+    } else {
+        for (int st = 0; st < np.nsteps; st++)
+            for (int k = np.h_step_ptr[st]; k < np.h_step_ptr[st + 1]; k++) {
+                const int r = (k - np.h_step_ptr[st]) % C;
+                np.h_own[np.h_step_site[k]] = (r << 24) | cnt[r]++;
+            }
+    }
+    np.slab_vol = *std::max_element(cnt.begin(), cnt.end());
+    np.h_own_off.assign((size_t)C * np.slab_vol, -1);
+    for (int yl = 0; yl < np.vol; yl++)
+        np.h_own_off[(size_t)(np.h_own[yl] >> 24) * np.slab_vol + (np.h_own[yl] & 0xffffff)] = np.h_site_off[yl];
+}
+
 bool make_chunks(SapPlan &np, int C, int maxslots, bool check_smem = true) {
-    if (np.b[3] % C) return false;
+    if (C > np.vol) return false;
     np.C = C;
-    np.slab_t = np.b[3] / C;
-    np.slab_vol = np.vol / C;
+    assign_owners(np, C);
     std::vector<std::vector<int>> per(C);
     std::vector<std::vector<int>> lists(C);  // chunk lists per CTA
     std::vector<std::vector<int>> ptr(C, std::vector<int>(1, 0));
@@ -672,8 +699,7 @@ bool make_chunks(SapPlan &np, int C, int maxslots, bool check_smem = true) {
         for (auto &v : per) v.clear();
         for (int k = np.h_step_ptr[st]; k < np.h_step_ptr[st + 1]; k++) {
             const int yl = np.h_step_site[k];
-            const int yt = yl / (np.b[0] * np.b[1] * np.b[2]);
-            per[yt / np.slab_t].push_back(yl);
+            per[np.h_own[yl] >> 24].push_back(yl);
         }
         size_t most = 1;
         for (auto &v : per) most = std::max(most, v.size());
@@ -739,7 +765,6 @@ void make_flags(SapPlan &np) {
     };
     std::vector<std::pair<int, int>> remote, local;  // (lo, hi]: need a barrier p with lo < p <= hi
     std::vector<int> wi, wj;
-    const int plane = np.b[0] * np.b[1] * np.b[2];
     for (int yl = 0; yl < np.vol; yl++) {
         int y[4], r = yl;
         for (int m = 0; m < 4; m++) { y[m] = r % np.b[m]; r /= np.b[m]; }
@@ -749,7 +774,7 @@ void make_flags(SapPlan &np) {
                 const int ym = y[m] + dir;
                 if (ym < 0 || ym >= np.b[m]) continue;
                 const int nb = yl + dir * stride;
-                const bool other = (yl / plane) / np.slab_t != (nb / plane) / np.slab_t;
+                const bool other = (np.h_own[yl] >> 24) != (np.h_own[nb] >> 24);
                 auto &iv = other ? remote : local;
                 writes(yl, wi);
                 writes(nb, wj);
@@ -875,9 +900,9 @@ int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &np,
         make_flags(np);
         return QCD_OK;
     }
-    // slabs: a divisor C of b_t, at most 8, whose shared memory fits.  With min_ctas >= 1 the
-    // smallest such C >= min_ctas; with min_ctas = 0 the largest one that keeps the blocks of
-    // one colour (one CTA cluster each) within the SM count, and at least the smallest that fits
+    // CTAs per block: C <= 16 whose shared memory fits.  With min_ctas >= 1 the smallest such
+    // C >= min_ctas; with min_ctas = 0 the largest one that keeps the blocks of one colour (one
+    // CTA cluster each) within the SM count, and at least the smallest that fits
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms < 1) {
         cudaGetLastError();
@@ -888,17 +913,18 @@ int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &np,
     // staging ring fits (fewer dependent steps), else 16 (more registers per thread; several
     // blocks share an SM when many blocks fill the GPU)
     const bool few = (long)nblk1 < sms;
-    auto fit = [&](int C) {
-        return b[3] % C == 0 && ((few && make_chunks(np, C, kMaxSlots)) || make_chunks(np, C, 16));
-    };
+    auto fit = [&](int C) { return (few && make_chunks(np, C, kMaxSlots)) || make_chunks(np, C, 16); };
     int Cfit = 0;
     for (int C = std::max(1, min_ctas); C <= kMaxCluster && !Cfit; C++)
         if (fit(C)) Cfit = C;  // (min_ctas < 0 without a thread-per-site fit: as 0)
     if (!Cfit) return QCD_ERR_ARG;
+    // automatic width: the largest power of two up to 8 (the portable cluster size; measured
+    // faster than 12 or 16 on GB300, with every level split evenly over the CTAs) that keeps
+    // one colour's clusters within the SM count
     int Cuse = Cfit;
     if (min_ctas <= 0)
-        for (int C = Cfit + 1; C <= kMaxCluster; C++)
-            if (b[3] % C == 0 && (long)nblk1 * C <= sms) Cuse = C;
+        for (int C = 2; C <= 8; C *= 2)
+            if (C > Cuse && (long)nblk1 * C <= sms) Cuse = C;
     if (!fit(Cuse)) return QCD_ERR_ARG;
     make_flags(np);
     return QCD_OK;
@@ -909,7 +935,8 @@ size_t sap_table_bytes(const SapPlan &p) {
     return up16(sizeof(int) * p.h_origin[0].size()) + up16(sizeof(int) * p.h_origin[1].size()) +
            up16(sizeof(int) * p.h_origin_site[0].size()) + up16(sizeof(int) * p.h_origin_site[1].size()) +
            up16(sizeof(int) * p.h_chunk_ptr.size()) + up16(sizeof(int2) * p.h_chunk_site.size()) +
-           up16(sizeof(int) * p.h_site_off.size()) + up16(p.h_flags.size());
+           up16(sizeof(int) * p.h_site_off.size()) + up16(p.h_flags.size()) + up16(sizeof(int) * p.h_own.size()) +
+           up16(sizeof(int) * p.h_own_off.size());
 }
 
 // Copies every table of the plan into one device region (sap_table_bytes long) on the
@@ -936,8 +963,10 @@ int sap_upload_tables(qcd_ctx *c, SapPlan &p, void *region) {
     p.d_chunk_site = (int2 *)put(cs.data(), sizeof(int2) * cs.size());
     p.d_site_off = (int *)put(p.h_site_off.data(), sizeof(int) * p.h_site_off.size());
     p.d_flags = (unsigned char *)put(p.h_flags.data(), p.h_flags.size());
+    p.d_own = (int *)put(p.h_own.data(), sizeof(int) * p.h_own.size());
+    p.d_own_off = (int *)put(p.h_own_off.data(), sizeof(int) * p.h_own_off.size());
     if (!p.d_origin[0] || !p.d_origin[1] || !p.d_origin_site[0] || !p.d_origin_site[1] || !p.d_chunk_ptr ||
-        !p.d_chunk_site || !p.d_site_off || !p.d_flags)
+        !p.d_chunk_site || !p.d_site_off || !p.d_flags || !p.d_own || !p.d_own_off)
         return cuda_fail(c, cudaGetLastError(), "cudaMemcpyAsync(SAP tables)");
     // the host vectors may be released only once the copies have consumed them
     QCD_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -966,10 +995,10 @@ int sap_build_records(qcd_ctx *c, SapPlan &p, float *rec) {
     prof_begin(c, QCD_K_OTHER, &ev);
     if (p.half)
         k_sap_records<true><<<(unsigned)((total + 127) / 128), 128, 0, c->stream>>>(
-            rec, c->U32, c->F32, g, bg, p.slab_t, p.slab_vol, p.d_origin[0], p.d_origin[1], p.nblk[0], total);
+            rec, c->U32, c->F32, g, bg, p.d_own, p.d_origin[0], p.d_origin[1], p.nblk[0], total);
     else
         k_sap_records<false><<<(unsigned)((total + 127) / 128), 128, 0, c->stream>>>(
-            rec, c->U32, c->F32, g, bg, p.slab_t, p.slab_vol, p.d_origin[0], p.d_origin[1], p.nblk[0], total);
+            rec, c->U32, c->F32, g, bg, p.d_own, p.d_origin[0], p.d_origin[1], p.nblk[0], total);
     int rc = prof_end(c, QCD_K_OTHER, ev);
     if (rc) return rc;
     p.d_rec = rec;
@@ -1052,6 +1081,7 @@ int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
     a.chunk_ptr = p.d_chunk_ptr;
     a.chunk_site = p.d_chunk_site;
     a.site_off = p.d_site_off;
+    a.own_off = p.d_own_off;
     a.flags = p.d_flags;
     a.gate = gate;
     a.U = c->U32;

@@ -237,7 +237,7 @@ def test_sap_identical_for_every_cluster_width():
     prm = q.make_params(kappa, CSW, b, sb, omega=1.0, nsweep=2, nsap=2)
     vin = torch.from_numpy(v.astype(np.complex64)).cuda()
     outs = []
-    for ctas in (0, 1, 2, 3, 4, 6, 12):
+    for ctas in (0, 1, 2, 3, 4, 5, 6, 8, 12, 16):
         q.qcd_set_sap_ctas(s.ctx, ctas)
         out = torch.empty_like(vin)
         s.sap_precondition(out, vin, prm)
@@ -247,6 +247,15 @@ def test_sap_identical_for_every_cluster_width():
         assert torch.equal(o, outs[0])
     ref = oracle.sap(dims, U, F, kappa, b, sb, 1.0, 2, 2, v)
     assert rel_norm(outs[0].cpu().numpy().astype(np.complex128), ref) <= 1e-5
+    # FP16 storage: one scale per CTA, so not bitwise across widths, but each within its bound;
+    # widths that do not divide the level sizes leave the CTAs unequal shares
+    prm16 = q.make_params(kappa, CSW, b, sb, omega=1.0, nsweep=2, nsap=2, sap_storage=q.QCD_F16)
+    for ctas in (1, 3, 5, 12, 16):
+        q.qcd_set_sap_ctas(s.ctx, ctas)
+        out = torch.empty_like(vin)
+        s.sap_precondition(out, vin, prm16)
+        torch.cuda.synchronize()
+        assert rel_norm(out.cpu().numpy().astype(np.complex128), ref) <= SAP_F16_TOL, ctas
     s.close()
 
 
