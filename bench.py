@@ -32,7 +32,7 @@ D_BYTES_PER_SITE = {"f32": 768, "f64": 1536, "f16": 480, "su3": 672}  # in + out
 L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) per launch of a kernel class on this workload, from one ncu capture
 # of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum); None where not captured
-NCU_TRAFFIC = {"ssor": 28917760 + 0}
+NCU_TRAFFIC = {"ssor": 28918016 + 0}
 
 
 def read_peaks():
