@@ -7,19 +7,22 @@
 //   r_c' -= D_c'c y_c              (K4, hops that leave the block)
 // which equals Alg. 1 (y = K r, w = D y, x += y, r -= w) term by term.
 //
-// K3 runs one CTA per SAP block, or a cluster of C CTAs that split the block
-// into slabs along t when its spinor does not fit one CTA's shared memory.
-// The ll order (key = lambda * N_sb + sigma, lambda the lexicographic local
-// position inside a sub-block, sigma the lexicographic sub-block index) is cut
-// into steps of consecutive sites that are pairwise non-adjacent; the sites of
-// one step are updated in parallel, which gives exactly the sequential result,
-// and steps are separated by barriers (the paper's OpenMP barriers between
+// K3 runs a cluster of C CTAs per SAP block (C = 1 when the block fits one
+// CTA and the GPU is full of blocks).  The ll order (key = lambda * N_sb +
+// sigma, lambda the lexicographic local position inside a sub-block, sigma the
+// lexicographic sub-block index) is run as a wavefront of dependency levels:
+// a site's level is one more than the highest level of its earlier in-block
+// neighbours, so the sites of one level are pairwise non-adjacent and updating
+// level after level gives exactly the sequential result.  Each CTA owns an
+// equal share of every level (dealt round-robin); barriers (CTA or cluster)
+// are placed only where data flows (the paper's OpenMP barriers between
 // dependent sites).  Each site update is done by one warp: lane (d, c) takes
 // hop direction d = 2 mu + (backward) and colour row c, the 8 directions are
-// summed with butterfly shuffles, and 12 lanes apply the chiral clover blocks.
-// The block's spinor y lives in shared memory (remote slabs are read through
-// distributed shared memory); links, clover and source of the sites of the
-// next two steps are staged with cp.async while the current step computes.
+// summed with butterfly shuffles, and 24 lanes apply the chiral clover rows.
+// Each CTA keeps its sites' spinors in shared memory (neighbours owned by peer
+// CTAs are read through distributed shared memory); records and source of the
+// sites of the next two chunks are staged with cp.async while the current one
+// computes.
 #include <cooperative_groups.h>
 #include <cuda_fp16.h>
 
@@ -81,10 +84,11 @@ constexpr size_t kSmemLimit = 200 * 1024;
 // Per-site record of the SSOR kernel, in 4-byte words.  W_d for d = 2 mu + (backward):
 // U_mu(n) forward, U_mu(n - mu)^dag backward, 3x3 row-major complex (zero when the hop leaves
 // the block); then the two chiral blocks of F/2 as full 6x6 complex rows; then ints: global
-// site, offset (words) of the site's spinor in its slab, and per direction the neighbour code
-// (slab << 24) | offset (words) of the neighbour's spinor in that slab, or -1 when the hop
-// leaves the block.  FP32 storage keeps complex numbers as float2 (2 words), FP16 storage as
-// half2 (1 word) with the block spinor scaled by one FP32 factor per slab.
+// site, offset (words) of the site's spinor in its owner CTA's slab of y, and per direction
+// the neighbour code (owner CTA << 24) | offset (words) of the neighbour's spinor in that
+// CTA's slab, or -1 when the hop leaves the block.  FP32 storage keeps complex numbers as
+// float2 (2 words), FP16 storage as half2 (1 word) with the spinors a CTA owns scaled by one
+// FP32 factor per CTA.
 template <bool HALF> struct Rec {
     static constexpr int cw = HALF ? 1 : 2;        // words per complex
     static constexpr int W = 0, F = 72 * cw;       // colour matrices, clover rows
@@ -660,9 +664,6 @@ void free_plan(qcd_ctx *c) {
     p = SapPlan();
 }
 
-// Split the block into C slabs along t and every step (level) into chunks of
-// at most maxslots sites per slab, of equal size.  Returns false if the shared
-// memory of a CTA (its slab of y plus the staging ring) would exceed kSmemLimit.
 // Which CTA of the cluster owns (updates and stores) each site of the block.  C = 1: all.
 // C > 1: the sites of every level are dealt round-robin over the C CTAs in ll order, so each
 // CTA gets an equal share of every level (a t-slab split would give each CTA a band of levels
@@ -687,6 +688,9 @@ void assign_owners(SapPlan &np, int C) {
         np.h_own_off[(size_t)(np.h_own[yl] >> 24) * np.slab_vol + (np.h_own[yl] & 0xffffff)] = np.h_site_off[yl];
 }
 
+// Deals the block over C CTAs (assign_owners) and cuts every step (level) of each CTA into
+// chunks of at most maxslots sites, of equal size.  Returns false if the shared memory of a
+// CTA (its slab of y plus the staging ring) would exceed kSmemLimit.
 bool make_chunks(SapPlan &np, int C, int maxslots, bool check_smem = true) {
     if (C > np.vol) return false;
     np.C = C;
@@ -736,12 +740,12 @@ bool make_chunks(SapPlan &np, int C, int maxslots, bool check_smem = true) {
     return true;
 }
 
-// Barriers of the timeline.  A site reads its in-block neighbours (in other
-// slabs through distributed shared memory).  Each such read must come after the
+// Barriers of the timeline.  A site reads its in-block neighbours (those owned
+// by other CTAs through distributed shared memory).  Each such read must come after the
 // neighbour's latest earlier write (barrier in (t_w, t]) and before its next
 // write (barrier in (t, t_n]), unless the same warp does both (the own value).
 // The intervals are taken over three sweeps and stabbed greedily, first those
-// of neighbours in other slabs with cluster barriers (flag 2), then the rest
+// of neighbours owned by other CTAs with cluster barriers (flag 2), then the rest
 // with CTA barriers (flag 1) where no barrier stabs them yet; the positions,
 // folded modulo one sweep, give a periodic pattern that stabs every interval of
 // any number of sweeps (no interval spans a whole sweep, because every site is
