@@ -30,12 +30,13 @@ struct Lattice {
 };
 
 // SAP geometry: block decomposition (Eq. (3)) plus the ll-order schedule of
-// the SSOR passes, grouped into steps whose sites are pairwise non-adjacent.
-// For the SSOR kernel each block is split along t into C slabs (one CTA each,
-// a thread-block cluster when C > 1) and each step into chunks of at most
-// nslot sites per CTA; the chunks form the kernel's timeline (forward pass,
-// then the reversed backward pass).  flags[p] (p < 2*nchunks) asks for a
-// cluster barrier before timeline step p of every sweep.
+// the SSOR passes, grouped into dependency levels (steps) whose sites are
+// pairwise non-adjacent.  For the SSOR kernel each block is dealt over C CTAs
+// (a thread-block cluster when C > 1), each CTA owning an equal share of every
+// level, and each level into chunks of at most nslot sites per CTA; the chunks
+// form the kernel's timeline (forward pass, then the reversed backward pass).
+// flags[p] (p < 2*nchunks) asks for a CTA (1) or cluster (2) barrier before
+// timeline step p of every sweep.
 struct SapPlan {
     int b[4] = {0, 0, 0, 0}, s[4] = {0, 0, 0, 0};
     int nb[4] = {0, 0, 0, 0};
@@ -46,7 +47,6 @@ struct SapPlan {
     std::vector<int> h_step_ptr, h_step_site, h_origin[2];
     int *d_origin[2] = {nullptr, nullptr};  // [nblk[c]][4] block origins per colour
     bool half = false;  // FP16 storage of the block spinor and the records (FP32 arithmetic)
-    bool thread = false;  // thread-per-site SSOR kernel (block fields in shared memory, no records)
     int C = 1, slab_vol = 0;  // CTAs per block (cluster), most sites one CTA owns
     int nchunks = 0, nslot = 0, nwarps = 0;
     size_t smem_bytes = 0;
@@ -198,7 +198,7 @@ int dslash12(qcd_ctx *c, float4 *out, const float4 *in, int nrhs);
 // SAP (sap.cu)
 // host part of a plan (tables in h_*; device pointers left null); QCD_ERR_ARG on bad geometry
 int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &plan, int min_ctas = 1,
-                  bool half = false, bool thread_ok = false);
+                  bool half = false);
 // builds and uploads the plan of this geometry into c->plan (allocates its tables)
 int sap_prepare(qcd_ctx *c, const int b[4], const int s[4], bool half);
 // drops the cached plan (it is rebuilt on next use)

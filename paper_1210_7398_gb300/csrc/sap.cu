@@ -222,10 +222,6 @@ struct SsorArgs {
     const unsigned char *flags;  // [2 * nchunks] cluster barrier before a timeline step
     const int *origin_site;    // [blocks of this colour] global index of the block origin
     const BicgScalars *gate;   // blockIdx.y = right-hand side; skipped when inactive (null: all)
-    const float2 *U;           // links, FP32 [4][9][V] (thread-per-site kernel)
-    const float4 *F;           // clover, FP32 [18][V] (thread-per-site kernel)
-    int b[4];                  // block extents
-    Geo g;                     // lattice
 };
 
 // K3: y = A_BB f on every block of one colour; blockIdx.x / C enumerates blocks.  MAXW: the
@@ -488,100 +484,6 @@ __global__ void __launch_bounds__(32 * MAXW) k_ssor_warp(SsorArgs a) {
     }
 }
 
-// K3, thread-per-site form for the throughput regime (many blocks, large
-// levels): the block spinor y lives in shared memory as in the warp kernel;
-// every site update of a level is done by one thread (the whole 8-direction
-// hop with links and clover read from the FP32 fields, the clover product and
-// the relaxation, as in K1), with a CTA barrier between levels.  The level
-// order is the warp kernel's, so the same values are read; a site update costs
-// about 1,200 thread instructions instead of the warp kernel's ~500 warp
-// instructions, and a CTA needs only 112 bytes of shared memory per site, so
-// several blocks share an SM; but each warp-wide link or clover load touches
-// 32 scattered sites.
-constexpr int kTsY = 28;  // padded words of one site's spinor (bank spread for 16-byte loads)
-constexpr int kThreadSiteBytes = 4 * kTsY;
-constexpr int kThreadMaxThreads = 256;
-
-__global__ void __launch_bounds__(kThreadMaxThreads) k_ssor_thread(SsorArgs a) {
-    extern __shared__ __align__(16) float sm[];
-    if (a.gate && !a.gate[blockIdx.y].active) return;
-    a.f += (size_t)blockIdx.y * 6 * a.V;
-    a.y += (size_t)blockIdx.y * 6 * a.V;
-    const int vol = a.vol, nch = a.nchunks;
-    float *ys = sm;  // [vol][kTsY]
-    int *cptr = reinterpret_cast<int *>(ys + (size_t)vol * kTsY);  // [nch + 1]
-    int2 *csite = reinterpret_cast<int2 *>(cptr + ((nch + 1 + 3) & ~3));
-    const long n0 = a.origin_site[blockIdx.x];
-    const int ntab = a.chunk_ptr[nch] - a.chunk_ptr[0];
-    for (int i = threadIdx.x; i <= nch; i += blockDim.x) cptr[i] = a.chunk_ptr[i] - a.chunk_ptr[0];
-    for (int i = threadIdx.x; i < ntab; i += blockDim.x) csite[i] = a.chunk_site[a.chunk_ptr[0] + i];
-    for (int i = threadIdx.x; i < vol * kTsY / 4; i += blockDim.x)
-        reinterpret_cast<float4 *>(ys)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    __syncthreads();
-    const int b0 = a.b[0], b1 = a.b[1], b2 = a.b[2], b3 = a.b[3];
-    const int st1 = b0, st2 = b0 * b1, st3 = b0 * b1 * b2;
-    const long gs1 = a.g.L[0], gs2 = gs1 * a.g.L[1], gs3 = gs2 * a.g.L[2];  // global strides
-    auto ld_y = [&](int yl, float2 psi[12]) {
-        const float4 *p = reinterpret_cast<const float4 *>(ys + yl * kTsY);
-#pragma unroll
-        for (int q = 0; q < 6; q++) {
-            const float4 v = p[q];
-            psi[2 * q] = make_float2(v.x, v.y);
-            psi[2 * q + 1] = make_float2(v.z, v.w);
-        }
-    };
-    for (int sw = 0; sw < a.nsweep; sw++)
-        for (int k = 0; k < 2 * nch; k++) {
-            const int ch = k < nch ? k : 2 * nch - 1 - k;
-            for (int i = cptr[ch] + threadIdx.x; i < cptr[ch + 1]; i += blockDim.x) {
-                const int2 e = csite[i];
-                const int yl = e.x;
-                const long n = n0 + e.y;
-                int r = yl;
-                const int y0 = r % b0; r /= b0;
-                const int y1 = r % b1; r /= b1;
-                const int y2 = r % b2;
-                const int y3 = r / b2;
-                float2 acc[12], psi[12], u[9];
-#pragma unroll
-                for (int q = 0; q < 12; q++) acc[q] = make_float2(0.f, 0.f);
-                // in-block hops only (D_BB); a block never wraps around the lattice, so no boundary sign
-                if (y0 + 1 < b0) { ld_y(yl + 1, psi); load_link(a.U, a.V, n, 0, u); hop_term<0, true>(psi, u, 1.f, acc); }
-                if (y0 > 0) { ld_y(yl - 1, psi); load_link(a.U, a.V, n - 1, 0, u); hop_term<0, false>(psi, u, 1.f, acc); }
-                if (y1 + 1 < b1) { ld_y(yl + st1, psi); load_link(a.U, a.V, n, 1, u); hop_term<1, true>(psi, u, 1.f, acc); }
-                if (y1 > 0) { ld_y(yl - st1, psi); load_link(a.U, a.V, n - gs1, 1, u); hop_term<1, false>(psi, u, 1.f, acc); }
-                if (y2 + 1 < b2) { ld_y(yl + st2, psi); load_link(a.U, a.V, n, 2, u); hop_term<2, true>(psi, u, 1.f, acc); }
-                if (y2 > 0) { ld_y(yl - st2, psi); load_link(a.U, a.V, n - gs2, 2, u); hop_term<2, false>(psi, u, 1.f, acc); }
-                if (y3 + 1 < b3) { ld_y(yl + st3, psi); load_link(a.U, a.V, n, 3, u); hop_term<3, true>(psi, u, 1.f, acc); }
-                if (y3 > 0) { ld_y(yl - st3, psi); load_link(a.U, a.V, n - gs3, 3, u); hop_term<3, false>(psi, u, 1.f, acc); }
-                float fc[72];
-                load_clover(a.F, a.V, n, fc);
-                float2 fa[12];
-                clover_mul<float, float2>(fc, acc, fa);
-                float2 fv[12], yo[12];
-                load_spinor(a.f, a.V, n, fv);
-                ld_y(yl, yo);
-                float4 *yp = reinterpret_cast<float4 *>(ys + yl * kTsY);
-#pragma unroll
-                for (int q = 0; q < 6; q++) {
-                    float2 o[2];
-#pragma unroll
-                    for (int h = 0; h < 2; h++) {
-                        const int c = 2 * q + h;
-                        const float tx = fmaf(a.kappa, fa[c].x, fv[c].x), ty = fmaf(a.kappa, fa[c].y, fv[c].y);
-                        o[h] = make_float2(fmaf(a.omega, tx - yo[c].x, yo[c].x), fmaf(a.omega, ty - yo[c].y, yo[c].y));
-                    }
-                    yp[q] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
-                }
-            }
-            __syncthreads();
-        }
-    for (int i = threadIdx.x; i < vol * 6; i += blockDim.x) {
-        const int yl = i / 6, q = i - 6 * yl;
-        a.y[(long)q * a.V + n0 + a.site_off[yl]] = reinterpret_cast<const float4 *>(ys + yl * kTsY)[q];
-    }
-}
-
 // K4: after the block solve of colour c (y on colour-c sites):
 //   colour-c sites:  x += y;  r -= D_cc y          (if upd_in)
 //   other sites:     r += kappa F H_{c'c} y        (if upd_cross)
@@ -811,8 +713,7 @@ void make_flags(SapPlan &np) {
 
 }  // namespace
 
-int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &np, int min_ctas, bool half,
-                  bool thread_ok) {
+int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &np, int min_ctas, bool half) {
     if (!geometry_ok(c, b, s)) return QCD_ERR_ARG;
     np = SapPlan();
     np.half = half;
@@ -890,20 +791,6 @@ int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &np,
         for (int m = 0; m < 4; m++) { y[m] = r % b[m]; r /= b[m]; }
         np.h_site_off[yl] = y[0] + c->lat.L[0] * (y[1] + c->lat.L[1] * (y[2] + c->lat.L[2] * y[3]));
     }
-    // blocks whose fields fit one CTA: the thread-per-site kernel, one chunk per level
-    // the thread-per-site kernel on request (min_ctas = -1): measured on GB300 it does not beat
-    // the warp kernel (its scattered link and clover loads waste most of each L2 sector), so the
-    // automatic choice is the warp kernel and the autotuner may pick this one
-    if (thread_ok && !half && min_ctas < 0 &&
-        (size_t)np.vol * kThreadSiteBytes + 16 * (size_t)np.vol + 4096 <= kSmemLimit) {
-        make_chunks(np, 1, 1 << 20, false);
-        np.thread = true;
-        np.nwarps = std::min(kThreadMaxThreads / 32, (np.nslot + 31) / 32);
-        np.smem_bytes = (size_t)np.vol * kThreadSiteBytes + sizeof(int) * ((np.nchunks + 1 + 3) & ~3) +
-                        sizeof(int2) * ((np.vol + 1) & ~1);
-        make_flags(np);
-        return QCD_OK;
-    }
     // CTAs per block: C <= 16 whose shared memory fits.  With min_ctas >= 1 the smallest such
     // C >= min_ctas; with min_ctas = 0 the largest one that keeps the blocks of one colour (one
     // CTA cluster each) within the SM count, and at least the smallest that fits
@@ -920,7 +807,7 @@ int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &np,
     auto fit = [&](int C) { return (few && make_chunks(np, C, kMaxSlots)) || make_chunks(np, C, 16); };
     int Cfit = 0;
     for (int C = std::max(1, min_ctas); C <= kMaxCluster && !Cfit; C++)
-        if (fit(C)) Cfit = C;  // (min_ctas < 0 without a thread-per-site fit: as 0)
+        if (fit(C)) Cfit = C;
     if (!Cfit) return QCD_ERR_ARG;
     // automatic width: the largest power of two up to 8 (the portable cluster size; measured
     // faster than 12 or 16 on GB300, with every level split evenly over the CTAs) that keeps
@@ -978,15 +865,10 @@ int sap_upload_tables(qcd_ctx *c, SapPlan &p, void *region) {
 }
 
 size_t sap_record_bytes(const SapPlan &p) {
-    if (p.thread) return 0;
     return (size_t)(p.nblk[0] + p.nblk[1]) * p.vol * (p.half ? Rec<true>::words : Rec<false>::words) * sizeof(float);
 }
 
 int sap_build_records(qcd_ctx *c, SapPlan &p, float *rec) {
-    if (p.thread) {  // the thread-per-site kernel reads the fields directly
-        p.rec_version = c->field_version;
-        return QCD_OK;
-    }
     Geo g;
     for (int m = 0; m < 4; m++) g.L[m] = c->lat.L[m];
     g.V = c->lat.V;
@@ -1019,7 +901,7 @@ int sap_prepare(qcd_ctx *c, const int b[4], const int s[4], bool half) {
     if (!(p.vol && std::equal(b, b + 4, p.b) && std::equal(s, s + 4, p.s) && p.half == half)) {
         free_plan(c);
         SapPlan np;
-        if (sap_plan_host(c, b, s, np, c->sap_min_ctas, half, true) != QCD_OK)
+        if (sap_plan_host(c, b, s, np, c->sap_min_ctas, half) != QCD_OK)
             return fail(c, QCD_ERR_ARG, "SAP block too large for the shared memory of a cluster of 16 CTAs");
         void *region = nullptr;
         int rc = dev_alloc(c, &region, sap_table_bytes(np));
@@ -1067,7 +949,6 @@ int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
             QCD_CUDA(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
             QCD_CUDA(c, cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
         }
-        QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_thread, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
         attr_done = true;
     }
     SsorArgs a;
@@ -1088,10 +969,6 @@ int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
     a.own_off = p.d_own_off;
     a.flags = p.d_flags;
     a.gate = gate;
-    a.U = c->U32;
-    a.F = c->F32;
-    a.g = g;
-    for (int m = 0; m < 4; m++) a.b[m] = p.b[m];
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1116,10 +993,7 @@ int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
             cfg.gridDim = dim3(p.nblk[col] * p.C, nrhs);
             prof_begin(c, QCD_K_SSOR, &ev);
             cudaError_t e;
-            if (p.thread) {
-                k_ssor_thread<<<dim3(p.nblk[col], nrhs), 32 * p.nwarps, p.smem_bytes, c->stream>>>(a);
-                e = cudaGetLastError();
-            } else {
+            {
                 void (*kern)(SsorArgs);
                 if (p.C > 1)
                     kern = p.nwarps > 16 ? (p.half ? k_ssor_warp<true, 32, true> : k_ssor_warp<false, 32, true>)
