@@ -230,15 +230,17 @@ __global__ void __launch_bounds__(64) k_clover(double2 *__restrict__ F64, float4
 }  // namespace
 
 int build_clover(qcd_ctx *c, double kappa, double csw) {
-    static bool tables_done = false;
-    if (!tables_done) {
+    static std::atomic<unsigned long long> tables_done{0};
+    static std::mutex tables_mu;
+    int trc = once_per_device(tables_done, tables_mu, c->device, [&]() -> int {
         double2 tab[6][2][2][2];
         bool ok = false;
         host_sigma_tables(tab, &ok);
         if (!ok) return fail(c, QCD_ERR_STATE, "internal: sigma_{mu nu} is not block diagonal in the chiral basis");
         QCD_CUDA(c, cudaMemcpyToSymbol(c_sigma_chiral, tab, sizeof(tab)));
-        tables_done = true;
-    }
+        return QCD_OK;
+    });
+    if (trc) return trc;
     Geo g;
     for (int m = 0; m < 4; m++) g.L[m] = c->lat.L[m];
     g.V = c->lat.V;

@@ -702,12 +702,14 @@ Geo geo(const qcd_ctx *c) {
 template <int CIN, int COUT, int FIN, int FOUT>
 int launch_layer(qcd_ctx *c, void *y, const void *x, const __nv_bfloat16 *Bt) {
     constexpr size_t smem = LayerSmem<CIN, COUT, FIN>::total;
-    static bool attr = false;
-    if (!attr) {
-        QCD_CUDA(c, cudaFuncSetAttribute(k_layer<CIN, COUT, FIN, FOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    static std::mutex attr_mu;
+    if (int arc = once_per_device(attr, attr_mu, c->device, [&]() -> int {
+            QCD_CUDA(c, cudaFuncSetAttribute(k_layer<CIN, COUT, FIN, FOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem));
+            return QCD_OK;
+        }))
+        return arc;
     const long tiles = (c->lat.V + kLayerSites - 1) / kLayerSites;
     cudaEvent_t ev;
     prof_begin(c, QCD_K_LEARNED, &ev);
@@ -718,12 +720,14 @@ int launch_layer(qcd_ctx *c, void *y, const void *x, const __nv_bfloat16 *Bt) {
 template <int CIN, int FIN, int FOUT>
 int launch_layer_wfirst(qcd_ctx *c, void *y, const void *x, const __nv_bfloat16 *Bt) {
     constexpr size_t smem = LayerSmem<CIN, 1, FIN>::total + sizeof(float2) * kLayerRows * 4;
-    static bool attr = false;
-    if (!attr) {
-        QCD_CUDA(c, cudaFuncSetAttribute(k_layer_wfirst<CIN, FIN, FOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    static std::mutex attr_mu;
+    if (int arc = once_per_device(attr, attr_mu, c->device, [&]() -> int {
+            QCD_CUDA(c, cudaFuncSetAttribute(k_layer_wfirst<CIN, FIN, FOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem));
+            return QCD_OK;
+        }))
+        return arc;
     const long tiles = (c->lat.V + kLayerSites - 1) / kLayerSites;
     cudaEvent_t ev;
     prof_begin(c, QCD_K_LEARNED, &ev);
@@ -735,11 +739,13 @@ template <int CIN, int COUT, int FIN>
 int launch_wgrad(qcd_ctx *c, float *P, const void *x, const float2 *G) {
     constexpr int KD = CIN * 8, KDP = KD < 16 ? 16 : KD, N = COUT * 8;
     constexpr size_t smem = sizeof(__nv_bfloat16) * ((size_t)kLayerRows * (KDP + 8) + (size_t)(KDP + N) * (kLayerRows + 8));
-    static bool attr = false;
-    if (!attr) {
-        QCD_CUDA(c, cudaFuncSetAttribute(k_wgrad<CIN, COUT, FIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    static std::mutex attr_mu;
+    if (int arc = once_per_device(attr, attr_mu, c->device, [&]() -> int {
+            QCD_CUDA(c, cudaFuncSetAttribute(k_wgrad<CIN, COUT, FIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            return QCD_OK;
+        }))
+        return arc;
     const int tiles = (int)((c->lat.V + kLayerSites - 1) / kLayerSites);
     const int grid = tiles < 304 ? tiles : 304;
     cudaEvent_t ev;

@@ -16,7 +16,9 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -173,6 +175,18 @@ int prof_end(qcd_ctx *c, int kclass, cudaEvent_t a);
 int check_launch(qcd_ctx *c, const char *what);
 
 // ---- memory ------------------------------------------------------------------
+// Runs fn() once per call site and device (kernel attributes, constant tables); thread-safe,
+// since several host threads may drive contexts at once.  Returns fn's status; a failed
+// fn() is tried again on the next call.
+template <typename Fn> int once_per_device(std::atomic<unsigned long long> &done, std::mutex &mu, int device, Fn fn) {
+    const unsigned long long bit = 1ull << (device & 63);
+    if (done.load(std::memory_order_acquire) & bit) return 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.load(std::memory_order_relaxed) & bit) return 0;
+    const int rc = fn();
+    if (rc == 0) done.fetch_or(bit, std::memory_order_release);
+    return rc;
+}
 int dev_alloc(qcd_ctx *c, void **p, size_t bytes);
 void dev_free(qcd_ctx *c, void *p);
 

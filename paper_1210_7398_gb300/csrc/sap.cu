@@ -939,18 +939,20 @@ int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
     BlockGeo bg;
     for (int m = 0; m < 4; m++) bg.b[m] = p.b[m];
     bg.vol = p.vol;
-    static bool attr_done = false;
-    if (!attr_done) {
-        const void *ks[] = {(const void *)k_ssor_warp<false, 16, false>, (const void *)k_ssor_warp<true, 16, false>,
-                            (const void *)k_ssor_warp<false, 32, false>, (const void *)k_ssor_warp<true, 32, false>,
-                            (const void *)k_ssor_warp<false, 16, true>, (const void *)k_ssor_warp<true, 16, true>,
-                            (const void *)k_ssor_warp<false, 32, true>, (const void *)k_ssor_warp<true, 32, true>};
-        for (const void *k : ks) {
-            QCD_CUDA(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
-            QCD_CUDA(c, cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-        }
-        attr_done = true;
-    }
+    static std::atomic<unsigned long long> attr_done{0};
+    static std::mutex attr_mu;
+    if (int arc = once_per_device(attr_done, attr_mu, c->device, [&]() -> int {
+            const void *ks[] = {(const void *)k_ssor_warp<false, 16, false>, (const void *)k_ssor_warp<true, 16, false>,
+                                (const void *)k_ssor_warp<false, 32, false>, (const void *)k_ssor_warp<true, 32, false>,
+                                (const void *)k_ssor_warp<false, 16, true>, (const void *)k_ssor_warp<true, 16, true>,
+                                (const void *)k_ssor_warp<false, 32, true>, (const void *)k_ssor_warp<true, 32, true>};
+            for (const void *k : ks) {
+                QCD_CUDA(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+                QCD_CUDA(c, cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+            }
+            return QCD_OK;
+        }))
+        return arc;
     SsorArgs a;
     a.y = y;
     a.f = r;
