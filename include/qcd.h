@@ -93,7 +93,7 @@ typedef struct {
                            qcd_learned_evaluate found it slower than plain SAP, in
                            which case plain SAP is used (the fallback).  2: always use
                            the learned correction                                     */
-    int sap_ctas;       /* CTAs per SAP block, as qcd_set_sap_ctas (0..16); 0 = context
+    int sap_ctas;       /* SSOR kernel form, as qcd_set_sap_ctas (-1..16); 0 = context
                            setting; results do not depend on it                       */
 } qcd_params;
 
@@ -193,13 +193,17 @@ int qcd_solve_multi(int n, qcd_ctx *const *ctxs, double *const *x, const double 
 int qcd_set_graphs(qcd_ctx *ctx, int on);
 
 /* Tuning knob of the SAP block kernel; results do not depend on it.  The
- * block solve runs one warp per site update over a cluster of C CTAs per
- * block (C <= 16, each CTA owning an equal share of every dependency level of
- * the sweep and keeping its sites' spinors in its shared memory, which must
- * fit).  min_ctas >= 1: the smallest such C >= min_ctas.  0 (default): the
- * largest C in {1, 2, 4, 8} for which one colour's clusters still fit the SM
- * count (at least the smallest C that fits).  More CTAs per block spread a
- * level's sites over more SMs at the price of more cluster barriers. */
+ * block solve has two forms.  The warp form runs one warp per site update over
+ * a cluster of C CTAs per block (C <= 16, each CTA owning an equal share of
+ * every dependency level of the sweep and keeping its sites' spinors in its
+ * shared memory, which must fit).  The thread form (FP32 storage, blocks whose
+ * spinor fits one CTA) runs one thread per site update with the block's links
+ * and clover field stored per block in level order.  min_ctas >= 1: the warp
+ * form with the smallest such C >= min_ctas.  0 (default): the warp form with
+ * the largest C in {1, 2, 4, 8} for which one colour's clusters still fit the
+ * SM count (at least the smallest C that fits).  -1: the thread form where it
+ * fits, else as 0.  More CTAs per block spread a level's sites over more SMs
+ * at the price of more cluster barriers. */
 int qcd_set_sap_ctas(qcd_ctx *ctx, int min_ctas);
 
 /* Autotuner (no counterpart in the paper, which fixes 6^4 blocks with 3^4
@@ -209,8 +213,8 @@ int qcd_set_sap_ctas(qcd_ctx *ctx, int min_ctas);
  * sap_ctas, nsweep, nsap; omega from base) and its time in *best_ms.  Stage 1
  * tries block splits (L_mu / block_mu in {2, 4, 6, 8}, spatial directions
  * alike) with sub-blocks block/2, block/3 or block, blocks of about 256 sites
- * first; stage 2 refines the three fastest over FP16 storage, 2 CTAs per
- * block and (nsweep, nsap) in {2, 4} x {2, 4}.  At most
+ * first; stage 2 refines the three fastest over FP16 storage, the kernel
+ * form (sap_ctas 0, -1, 2) and (nsweep, nsap) in {2, 4} x {2, 4}.  At most
  * max_candidates solves are timed (<= 0: 64).
  * b: complex128 [nrhs][V][4][3], host or device.  Synchronises. */
 int qcd_autotune(qcd_ctx *ctx, const double *b, int nrhs, const qcd_params *base, qcd_params *best,

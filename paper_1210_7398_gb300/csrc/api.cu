@@ -149,7 +149,7 @@ int check_params(qcd_ctx *c, const qcd_params *p) {
     if (p->bc_t != c->bc_t) return fail(c, QCD_ERR_ARG, "params.bc_t differs from the context boundary condition");
     if (p->kappa != c->kappa || p->csw != c->csw)
         return fail(c, QCD_ERR_ARG, "params.kappa/csw differ from the clover field built");
-    if (p->sap_ctas < 0 || p->sap_ctas > 16) return fail(c, QCD_ERR_ARG, "sap_ctas must lie in 0..16");
+    if (p->sap_ctas < -1 || p->sap_ctas > 16) return fail(c, QCD_ERR_ARG, "sap_ctas must lie in -1..16");
     if (p->sap_ctas != 0 && p->sap_ctas != c->sap_min_ctas) {
         sap_invalidate(c);
         c->sap_min_ctas = p->sap_ctas;
@@ -430,7 +430,7 @@ int qcd_set_graphs(qcd_ctx *c, int on) {
 int qcd_set_sap_ctas(qcd_ctx *c, int min_ctas) {
     int rc = ready(c);
     if (rc) return rc;
-    if (min_ctas < 0 || min_ctas > 16) return fail(c, QCD_ERR_ARG, "min_ctas must lie in 0..16");
+    if (min_ctas < -1 || min_ctas > 16) return fail(c, QCD_ERR_ARG, "min_ctas must lie in -1..16");
     QCD_CUDA(c, c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
     if (c->sap_min_ctas != min_ctas) sap_invalidate(c);
     c->sap_min_ctas = min_ctas;

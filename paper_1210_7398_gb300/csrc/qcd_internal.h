@@ -49,6 +49,7 @@ struct SapPlan {
     std::vector<int> h_step_ptr, h_step_site, h_origin[2];
     int *d_origin[2] = {nullptr, nullptr};  // [nblk[c]][4] block origins per colour
     bool half = false;  // FP16 storage of the block spinor and the records (FP32 arithmetic)
+    bool thread = false;  // thread form of the SSOR kernel (SoA per-block fields instead of records)
     int C = 1, slab_vol = 0;  // CTAs per block (cluster), most sites one CTA owns
     int nchunks = 0, nslot = 0, nwarps = 0;
     size_t smem_bytes = 0;
@@ -58,6 +59,7 @@ struct SapPlan {
     std::vector<int> h_site_off;    // [vol] global index offset of a block-local site from its block origin
     std::vector<int> h_own;         // [vol] (owning CTA << 24) | index in that CTA's slab of y
     std::vector<int> h_own_off;     // [C][slab_vol] global offset of each owned site, -1 past the last
+    std::vector<int> h_pos;         // thread form: [vol] level position of each block-local site
     std::vector<int> h_origin_site[2];  // [nblk[c]] global index of each block origin
     int *d_chunk_ptr = nullptr;
     int2 *d_chunk_site = nullptr;   // (block-local site, global offset from the block origin)
@@ -65,6 +67,7 @@ struct SapPlan {
     int *d_site_off = nullptr;
     int *d_own = nullptr;
     int *d_own_off = nullptr;
+    int *d_pos = nullptr;
     int *d_origin_site[2] = {nullptr, nullptr};
     float *d_rec = nullptr;         // per-site records (links, clover, neighbour codes), V x 912 bytes
     long rec_version = -1;          // field version the records were built from

@@ -222,6 +222,8 @@ struct SsorArgs {
     const unsigned char *flags;  // [2 * nchunks] cluster barrier before a timeline step
     const int *origin_site;    // [blocks of this colour] global index of the block origin
     const BicgScalars *gate;   // blockIdx.y = right-hand side; skipped when inactive (null: all)
+    int gb0;                   // thread form: index of this colour's first block in the SoA records
+    int b[4];                  // thread form: block extents
 };
 
 // K3: y = A_BB f on every block of one colour; blockIdx.x / C enumerates blocks.  MAXW: the
@@ -482,6 +484,138 @@ __global__ void __launch_bounds__(32 * MAXW) k_ssor_warp(SsorArgs a) {
         }
         a.y[(long)q * a.V + n] = v;
     }
+}
+
+// K3, thread form for the throughput regime (blocks that fit one CTA, many blocks per colour):
+// one CTA per block with the block spinor y in shared memory, and every site update of a level
+// done by one thread (the 8-direction projected hop, the clover product and the relaxation, as
+// in K1), with a CTA barrier between levels.  The links and clover of each block are stored per
+// block in level order and structure-of-arrays form ([block][element][level position]), so the
+// threads of a level read consecutive addresses: the loads are coalesced and every byte is
+// used.  A site update costs about 1,200 thread instructions against the warp form's ~400
+// warp instructions.  The level order is the warp form's, so the same values are read.
+constexpr int kTsY = 28;  // padded words of one site's spinor in shared memory
+constexpr int kTsMaxThreads = 256;
+constexpr int kSoaLinks = 72;   // float2 per site: 8 hop links (U_mu(n) forward, U_mu(n - mu) backward)
+constexpr int kSoaClover = 18;  // float4 per site: the packed clover field
+constexpr size_t kSoaBytesPerSite = kSoaLinks * sizeof(float2) + kSoaClover * sizeof(float4);
+
+__global__ void __launch_bounds__(kTsMaxThreads) k_ssor_soa(SsorArgs a) {
+    extern __shared__ __align__(16) float sm[];
+    if (a.gate && !a.gate[blockIdx.y].active) return;
+    a.f += (size_t)blockIdx.y * 6 * a.V;
+    a.y += (size_t)blockIdx.y * 6 * a.V;
+    const int vol = a.vol, nch = a.nchunks;
+    float *ys = sm;                                                // [vol][kTsY]
+    int *cptr = reinterpret_cast<int *>(ys + (size_t)vol * kTsY);  // [nch + 1]
+    int2 *csite = reinterpret_cast<int2 *>(cptr + ((nch + 1 + 3) & ~3));
+    const long n0 = a.origin_site[blockIdx.x];
+    const size_t gb = (size_t)a.gb0 + blockIdx.x;
+    const float2 *lk = reinterpret_cast<const float2 *>(a.rec) + gb * kSoaLinks * vol;
+    const float4 *cl = reinterpret_cast<const float4 *>(reinterpret_cast<const float2 *>(a.rec) +
+                                                        (size_t)a.V * kSoaLinks) + gb * kSoaClover * vol;
+    for (int i = threadIdx.x; i <= nch; i += blockDim.x) cptr[i] = a.chunk_ptr[i];
+    for (int i = threadIdx.x; i < vol; i += blockDim.x) csite[i] = a.chunk_site[i];
+    for (int i = threadIdx.x; i < vol * kTsY / 4; i += blockDim.x)
+        reinterpret_cast<float4 *>(ys)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    const int b0 = a.b[0], b1 = a.b[1], b2 = a.b[2], b3 = a.b[3];
+    const int st1 = b0, st2 = b0 * b1, st3 = b0 * b1 * b2;
+    auto ld_y = [&](int yl, float2 psi[12]) {
+        const float4 *p = reinterpret_cast<const float4 *>(ys + yl * kTsY);
+#pragma unroll
+        for (int q = 0; q < 6; q++) {
+            const float4 v = p[q];
+            psi[2 * q] = make_float2(v.x, v.y);
+            psi[2 * q + 1] = make_float2(v.z, v.w);
+        }
+    };
+    for (int sw = 0; sw < a.nsweep; sw++)
+        for (int k = 0; k < 2 * nch; k++) {
+            const int ch = k < nch ? k : 2 * nch - 1 - k;
+            for (int pos = cptr[ch] + threadIdx.x; pos < cptr[ch + 1]; pos += blockDim.x) {
+                const int2 e = csite[pos];
+                const int yl = e.x;
+                int r = yl;
+                const int y0 = r % b0; r /= b0;
+                const int y1 = r % b1; r /= b1;
+                const int y2 = r % b2;
+                const int y3 = r / b2;
+                float2 acc[12], psi[12], u[9];
+#pragma unroll
+                for (int q = 0; q < 12; q++) acc[q] = make_float2(0.f, 0.f);
+                auto ld_u = [&](int d) {
+#pragma unroll
+                    for (int c = 0; c < 9; c++) u[c] = __ldg(lk + (size_t)(d * 9 + c) * vol + pos);
+                };
+                // in-block hops only (D_BB); a block never wraps around the lattice, so no boundary sign
+                if (y0 + 1 < b0) { ld_y(yl + 1, psi); ld_u(0); hop_term<0, true>(psi, u, 1.f, acc); }
+                if (y0 > 0) { ld_y(yl - 1, psi); ld_u(1); hop_term<0, false>(psi, u, 1.f, acc); }
+                if (y1 + 1 < b1) { ld_y(yl + st1, psi); ld_u(2); hop_term<1, true>(psi, u, 1.f, acc); }
+                if (y1 > 0) { ld_y(yl - st1, psi); ld_u(3); hop_term<1, false>(psi, u, 1.f, acc); }
+                if (y2 + 1 < b2) { ld_y(yl + st2, psi); ld_u(4); hop_term<2, true>(psi, u, 1.f, acc); }
+                if (y2 > 0) { ld_y(yl - st2, psi); ld_u(5); hop_term<2, false>(psi, u, 1.f, acc); }
+                if (y3 + 1 < b3) { ld_y(yl + st3, psi); ld_u(6); hop_term<3, true>(psi, u, 1.f, acc); }
+                if (y3 > 0) { ld_y(yl - st3, psi); ld_u(7); hop_term<3, false>(psi, u, 1.f, acc); }
+                float fc[72];
+#pragma unroll
+                for (int q = 0; q < 18; q++) {
+                    const float4 v = __ldg(cl + (size_t)q * vol + pos);
+                    fc[4 * q] = v.x; fc[4 * q + 1] = v.y; fc[4 * q + 2] = v.z; fc[4 * q + 3] = v.w;
+                }
+                float2 fa[12];
+                clover_mul<float, float2>(fc, acc, fa);
+                float2 fv[12], yo[12];
+                load_spinor(a.f, a.V, n0 + e.y, fv);
+                ld_y(yl, yo);
+                float4 *yp = reinterpret_cast<float4 *>(ys + yl * kTsY);
+#pragma unroll
+                for (int q = 0; q < 6; q++) {
+                    float2 o[2];
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        const int c = 2 * q + h;
+                        const float tx = fmaf(a.kappa, fa[c].x, fv[c].x), ty = fmaf(a.kappa, fa[c].y, fv[c].y);
+                        o[h] = make_float2(fmaf(a.omega, tx - yo[c].x, yo[c].x), fmaf(a.omega, ty - yo[c].y, yo[c].y));
+                    }
+                    yp[q] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < vol * 6; i += blockDim.x) {
+        const int yl = i / 6, q = i - 6 * yl;
+        a.y[(long)q * a.V + n0 + a.site_off[yl]] = reinterpret_cast<const float4 *>(ys + yl * kTsY)[q];
+    }
+}
+
+// SoA per-block fields of the thread form: links [gb][72][pos] (float2) for all blocks, then the
+// clover planes [gb][18][pos] (float4); pos the level position of the site in its block
+__global__ void k_sap_soa(float2 *__restrict__ lk, float4 *__restrict__ cl, const float2 *__restrict__ U,
+                          const float4 *__restrict__ F, Geo g, BlockGeo bg, const int *__restrict__ pos_of,
+                          const int *__restrict__ org0, const int *__restrict__ org1, int nblk0, long total) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int gb = (int)(i / bg.vol), yl = (int)(i % bg.vol);
+    const int *o = gb < nblk0 ? org0 + 4 * gb : org1 + 4 * (gb - nblk0);
+    int y[4], r = yl;
+    for (int m = 0; m < 4; m++) { y[m] = r % bg.b[m]; r /= bg.b[m]; }
+    const long gs[4] = {1, g.L[0], (long)g.L[0] * g.L[1], (long)g.L[0] * g.L[1] * g.L[2]};
+    long n = 0;
+    for (int m = 0; m < 4; m++) n += gs[m] * (o[m] + y[m]);
+    const int pos = pos_of[yl];
+    const size_t vol = bg.vol;
+    for (int d = 0; d < 8; d++) {
+        const int mu = d >> 1;
+        const bool fwd = (d & 1) == 0;
+        const int ym = y[mu] + (fwd ? 1 : -1);
+        const bool in = ym >= 0 && ym < bg.b[mu];
+        const long src = fwd ? n : n - gs[mu];
+        for (int c = 0; c < 9; c++)
+            lk[((size_t)gb * kSoaLinks + d * 9 + c) * vol + pos] =
+                in ? U[(long)(mu * 9 + c) * g.V + src] : make_float2(0.f, 0.f);
+    }
+    for (int q = 0; q < kSoaClover; q++) cl[((size_t)gb * kSoaClover + q) * vol + pos] = F[(long)q * g.V + n];
 }
 
 // K4: after the block solve of colour c (y on colour-c sites):
@@ -791,6 +925,21 @@ int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &np,
         for (int m = 0; m < 4; m++) { y[m] = r % b[m]; r /= b[m]; }
         np.h_site_off[yl] = y[0] + c->lat.L[0] * (y[1] + c->lat.L[1] * (y[2] + c->lat.L[2] * y[3]));
     }
+    // the thread form on request (min_ctas < 0), FP32 storage, the block spinor in one CTA
+    if (min_ctas < 0 && !half) {
+        make_chunks(np, 1, 1 << 20, false);  // one chunk per level, in level order
+        const size_t smem = (size_t)np.vol * kTsY * 4 + sizeof(int) * ((np.nchunks + 1 + 3) & ~3) +
+                            sizeof(int2) * ((np.vol + 1) & ~1);
+        if (smem <= kSmemLimit) {
+            np.thread = true;
+            np.nwarps = std::min(kTsMaxThreads / 32, (np.nslot + 31) / 32);
+            np.smem_bytes = smem;
+            np.h_pos.assign(np.vol, 0);
+            for (int k = 0; k < np.vol; k++) np.h_pos[np.h_chunk_site[k]] = k;
+            make_flags(np);
+            return QCD_OK;
+        }
+    }
     // CTAs per block: C <= 16 whose shared memory fits.  With min_ctas >= 1 the smallest such
     // C >= min_ctas; with min_ctas = 0 the largest one that keeps the blocks of one colour (one
     // CTA cluster each) within the SM count, and at least the smallest that fits
@@ -827,7 +976,7 @@ size_t sap_table_bytes(const SapPlan &p) {
            up16(sizeof(int) * p.h_origin_site[0].size()) + up16(sizeof(int) * p.h_origin_site[1].size()) +
            up16(sizeof(int) * p.h_chunk_ptr.size()) + up16(sizeof(int2) * p.h_chunk_site.size()) +
            up16(sizeof(int) * p.h_site_off.size()) + up16(p.h_flags.size()) + up16(sizeof(int) * p.h_own.size()) +
-           up16(sizeof(int) * p.h_own_off.size());
+           up16(sizeof(int) * p.h_own_off.size()) + up16(sizeof(int) * p.h_pos.size());
 }
 
 // Copies every table of the plan into one device region (sap_table_bytes long) on the
@@ -856,8 +1005,9 @@ int sap_upload_tables(qcd_ctx *c, SapPlan &p, void *region) {
     p.d_flags = (unsigned char *)put(p.h_flags.data(), p.h_flags.size());
     p.d_own = (int *)put(p.h_own.data(), sizeof(int) * p.h_own.size());
     p.d_own_off = (int *)put(p.h_own_off.data(), sizeof(int) * p.h_own_off.size());
+    p.d_pos = p.h_pos.empty() ? nullptr : (int *)put(p.h_pos.data(), sizeof(int) * p.h_pos.size());
     if (!p.d_origin[0] || !p.d_origin[1] || !p.d_origin_site[0] || !p.d_origin_site[1] || !p.d_chunk_ptr ||
-        !p.d_chunk_site || !p.d_site_off || !p.d_flags || !p.d_own || !p.d_own_off)
+        !p.d_chunk_site || !p.d_site_off || !p.d_flags || !p.d_own || !p.d_own_off || (p.thread && !p.d_pos))
         return cuda_fail(c, cudaGetLastError(), "cudaMemcpyAsync(SAP tables)");
     // the host vectors may be released only once the copies have consumed them
     QCD_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -865,6 +1015,7 @@ int sap_upload_tables(qcd_ctx *c, SapPlan &p, void *region) {
 }
 
 size_t sap_record_bytes(const SapPlan &p) {
+    if (p.thread) return (size_t)(p.nblk[0] + p.nblk[1]) * p.vol * kSoaBytesPerSite;
     return (size_t)(p.nblk[0] + p.nblk[1]) * p.vol * (p.half ? Rec<true>::words : Rec<false>::words) * sizeof(float);
 }
 
@@ -879,7 +1030,12 @@ int sap_build_records(qcd_ctx *c, SapPlan &p, float *rec) {
     const long total = (long)(p.nblk[0] + p.nblk[1]) * p.vol;
     cudaEvent_t ev;
     prof_begin(c, QCD_K_OTHER, &ev);
-    if (p.half)
+    if (p.thread) {
+        float2 *lk = reinterpret_cast<float2 *>(rec);
+        float4 *cl = reinterpret_cast<float4 *>(lk + (size_t)total * kSoaLinks);
+        k_sap_soa<<<(unsigned)((total + 127) / 128), 128, 0, c->stream>>>(lk, cl, c->U32, c->F32, g, bg, p.d_pos,
+                                                                           p.d_origin[0], p.d_origin[1], p.nblk[0], total);
+    } else if (p.half)
         k_sap_records<true><<<(unsigned)((total + 127) / 128), 128, 0, c->stream>>>(
             rec, c->U32, c->F32, g, bg, p.d_own, p.d_origin[0], p.d_origin[1], p.nblk[0], total);
     else
@@ -950,6 +1106,7 @@ int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
                 QCD_CUDA(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
                 QCD_CUDA(c, cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
             }
+            QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_soa, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
             return QCD_OK;
         }))
         return arc;
@@ -995,7 +1152,14 @@ int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
             cfg.gridDim = dim3(p.nblk[col] * p.C, nrhs);
             prof_begin(c, QCD_K_SSOR, &ev);
             cudaError_t e;
-            {
+            if (p.thread) {
+                SsorArgs at = a;
+                at.rec = reinterpret_cast<const float4 *>(p.d_rec);
+                at.gb0 = col ? p.nblk[0] : 0;
+                for (int m = 0; m < 4; m++) at.b[m] = p.b[m];
+                k_ssor_soa<<<dim3(p.nblk[col], nrhs), 32 * p.nwarps, p.smem_bytes, c->stream>>>(at);
+                e = cudaGetLastError();
+            } else {
                 void (*kern)(SsorArgs);
                 if (p.C > 1)
                     kern = p.nwarps > 16 ? (p.half ? k_ssor_warp<true, 32, true> : k_ssor_warp<false, 32, true>)

@@ -159,7 +159,7 @@ extern "C" int qcd_autotune(qcd_ctx *c, const double *b, int nrhs, const qcd_par
         for (size_t i = 0; i < cands.size() && i < 3; i++) {
             if (!cands[i].ok) continue;
             for (int storage : {QCD_F32, QCD_F16})
-                for (int ctas : {0, 2})
+                for (int ctas : {0, -1, 2})
                     for (int ns : {2, 4})
                         for (int np : {2, 4}) {
                             Cand cd = cands[i];

@@ -146,6 +146,12 @@ def test_sap_vs_oracle(case):
     s.sap_precondition(out, vin, prm)
     torch.cuda.synchronize()
     assert rel_norm(out.cpu().numpy().astype(np.complex128), ref) <= 1e-5
+    # the thread form of the block solve (one thread per site update), where the block fits a CTA
+    q.qcd_set_sap_ctas(s.ctx, -1)
+    out_t = torch.empty_like(vin)
+    s.sap_precondition(out_t, vin, prm)
+    torch.cuda.synchronize()
+    assert rel_norm(out_t.cpu().numpy().astype(np.complex128), ref) <= 1e-5
     s.close()
 
 
