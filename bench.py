@@ -599,7 +599,7 @@ def run_gpu_on_stream(args, q, qi, torch, np, peaks, rank, world, local):
         batched = batched_section(q, qi, torch, w["csw"], w["eps"], w["tol"], w["inner_tol"], 16)
     headline = None
     if args.headline:
-        headline = headline_section(q, qi, torch, w, args.rhs_group, 12)
+        headline = headline_section(q, qi, torch, w, args.rhs_group, 20)
     learned_full = None
     if args.learned_full:
         # 24^3 x 48, kappa 0.122, 12 point sources, 256 training pairs, plain SAP with 4 sweeps
