@@ -219,6 +219,21 @@ def test_errors_are_reported_not_fatal():
     with pytest.raises(q.QcdError) as e:
         s.apply_D(flat[1:], flat[:-1], q.QCD_F32)
     assert e.value.code == q.QCD_ERR_ARG
+    # out-of-range settings and arguments are rejected with QCD_ERR_ARG
+    with pytest.raises(q.QcdError) as e:
+        q.qcd_set_sap_ctas(s.ctx, 17)
+    assert e.value.code == q.QCD_ERR_ARG
+    with pytest.raises(q.QcdError) as e:
+        s.apply_D(torch.empty_like(psi), psi, 7)  # no such precision
+    assert e.value.code == q.QCD_ERR_ARG
+    wrong_kappa = q.make_params(0.11, CSW, (2, 2, 2, 2), (1, 1, 1, 1))  # differs from the clover built
+    with pytest.raises(q.QcdError) as e:
+        s.solve(torch.zeros_like(psi), psi, wrong_kappa)
+    assert e.value.code == q.QCD_ERR_ARG
+    bad_omega = q.make_params(0.12, CSW, (2, 2, 2, 2), (1, 1, 1, 1), omega=2.0)
+    with pytest.raises(q.QcdError) as e:
+        s.solve(torch.zeros_like(psi), psi, bad_omega)
+    assert e.value.code == q.QCD_ERR_ARG
     # the context is still usable
     out = torch.empty_like(psi)
     s.apply_D(out, psi, q.QCD_F64)
