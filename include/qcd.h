@@ -139,7 +139,10 @@ int qcd_apply_D(qcd_ctx *ctx, void *out, const void *in, int prec, int nrhs);
 
 /* out = M_SAP in (Eq. (4), Alg. 1) in FP32 for nrhs right-hand sides:
  * complex64 [nrhs][V][4][3].  Uses p->block, p->subblock, p->omega,
- * p->nsweep, p->nsap, p->sap_storage. */
+ * p->nsweep, p->nsap, p->sap_storage.  All right-hand sides go through one
+ * batched application (one grid row of block solves per right-hand side);
+ * each result equals, bit for bit, the call with that one alone.  Device
+ * scratch grows to 4 nrhs + 1 complex64 fields. */
 int qcd_sap_precondition(qcd_ctx *ctx, float *out, const float *in, const qcd_params *p, int nrhs);
 
 /* The paper has no counterpart to this entry point; it serves callers that

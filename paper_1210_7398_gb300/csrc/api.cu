@@ -315,23 +315,27 @@ int qcd_sap_precondition(qcd_ctx *c, float *out, const float *in, const qcd_para
     const bool dev_in = is_device_ptr(in), dev_out = is_device_ptr(out);
     if ((dev_in && !aligned16(in)) || (dev_out && !aligned16(out)))
         return fail(c, QCD_ERR_ARG, "device spinors must be 16-byte aligned");
-    // io: v (internal), x (internal), work (2), staging (1)
-    if ((rc = ensure_io(c, 5 * bytes))) return rc;
+    // io: v, x (internal, nrhs each), work (2 nrhs), staging (1); all right-hand sides go
+    // through one batched SAP application
+    if ((rc = ensure_io(c, (4 * (size_t)nrhs + 1) * bytes))) return rc;
     char *io = (char *)c->d_io;
-    float4 *v = (float4 *)io, *x = (float4 *)(io + bytes), *work = (float4 *)(io + 2 * bytes);
-    char *stage = io + 4 * bytes;
-    for (int k = 0; k < nrhs; k++) {
-        const char *src = (const char *)in + k * bytes;
-        char *dst = (char *)out + k * bytes;
-        if (!dev_in) {
-            QCD_CUDA(c, cudaMemcpyAsync(stage, src, bytes, cudaMemcpyHostToDevice, c->stream));
-            src = stage;
+    float4 *v = (float4 *)io, *x = (float4 *)(io + nrhs * bytes), *work = (float4 *)(io + 2 * nrhs * bytes);
+    char *stage = io + 4 * nrhs * bytes;
+    if (dev_in) {
+        if ((rc = spinor32_to_internal(c, v, (const float2 *)in, nrhs))) return rc;
+    } else {
+        for (int k = 0; k < nrhs; k++) {
+            QCD_CUDA(c, cudaMemcpyAsync(stage, (const char *)in + k * bytes, bytes, cudaMemcpyHostToDevice, c->stream));
+            if ((rc = spinor32_to_internal(c, v + k * 6 * V, (const float2 *)stage, 1))) return rc;
         }
-        if ((rc = spinor32_to_internal(c, v, (const float2 *)src, 1))) return rc;
-        if ((rc = sap_apply(c, x, v, work, p->omega, p->nsweep, p->nsap))) return rc;
-        if ((rc = spinor32_from_internal(c, (float2 *)(dev_out ? dst : stage), x, 1))) return rc;
-        if (!dev_out) {
-            QCD_CUDA(c, cudaMemcpyAsync(dst, stage, bytes, cudaMemcpyDeviceToHost, c->stream));
+    }
+    if ((rc = sap_apply(c, x, v, work, p->omega, p->nsweep, p->nsap, nrhs))) return rc;
+    if (dev_out) {
+        if ((rc = spinor32_from_internal(c, (float2 *)out, x, nrhs))) return rc;
+    } else {
+        for (int k = 0; k < nrhs; k++) {
+            if ((rc = spinor32_from_internal(c, (float2 *)stage, x + k * 6 * V, 1))) return rc;
+            QCD_CUDA(c, cudaMemcpyAsync((char *)out + k * bytes, stage, bytes, cudaMemcpyDeviceToHost, c->stream));
             QCD_CUDA(c, cudaStreamSynchronize(c->stream));
         }
     }

@@ -299,6 +299,33 @@ def test_sap_fp16_storage_vs_oracle(case):
     s.close()
 
 
+@pytest.mark.parametrize("storage", [q.QCD_F32, q.QCD_F16], ids=["f32", "f16"])
+@pytest.mark.parametrize("geo", [((8, 8, 8, 8), (4, 4, 4, 4), (2, 2, 2, 2)),
+                                 ((12, 12, 12, 24), (6, 6, 6, 12), (3, 3, 3, 6))], ids=["8^4", "12^3x24"])
+def test_sap_batched_equals_single_per_rhs(geo, storage):
+    """Three right-hand sides through one batched SAP call equal, bitwise, three single
+    calls, for the automatic cluster width and for 1, 2 and 4 CTAs per block."""
+    dims, b, sb = geo
+    kappa = 0.12
+    s, U, F = make_solver(dims, kappa, seed=1007)
+    v = qi.gaussian_spinor(dims, seed=2007, nrhs=3)
+    prm = q.make_params(kappa, CSW, b, sb, omega=1.1, nsweep=3, nsap=2, sap_storage=storage)
+    vin = torch.from_numpy(v.astype(np.complex64)).cuda()
+    for ctas in (0, 1, 2, 4):
+        q.qcd_set_sap_ctas(s.ctx, ctas)
+        out = torch.empty_like(vin)
+        s.sap_precondition(out, vin, prm, nrhs=3)
+        for k in range(3):
+            one = torch.empty_like(vin[k:k + 1])
+            s.sap_precondition(one, vin[k:k + 1].contiguous(), prm)
+            torch.cuda.synchronize()
+            assert torch.equal(one[0], out[k]), (ctas, k)
+    ref = oracle.sap(dims, U, F, kappa, b, sb, 1.1, 3, 2, v[2])
+    tol = 1e-5 if storage == q.QCD_F32 else SAP_F16_TOL
+    assert rel_norm(out[2].cpu().numpy().astype(np.complex128), ref) <= tol
+    s.close()
+
+
 def test_solve_with_fp16_sap_reaches_fp64_tolerance():
     dims, block, sub = (12, 12, 12, 24), (6, 6, 6, 12), (3, 3, 3, 6)
     kappa = 0.12
