@@ -209,6 +209,16 @@ int qcd_set_graphs(qcd_ctx *ctx, int on);
  * at the price of more cluster barriers. */
 int qcd_set_sap_ctas(qcd_ctx *ctx, int min_ctas);
 
+/* Second tuning knob of the warp form above: lanes per site update.  form = 1:
+ * 32 lanes (lane = hop direction and colour row, one update per warp); 2: 8
+ * lanes (lane = hop direction, four updates per warp: a quarter of the issued
+ * instructions, but a quarter of the warps to hide latency); 0 (default):
+ * per launch, the 8-lane form where the grid keeps at least 16 of its warps
+ * resident per SM (many small blocks, several right-hand sides), else 32.
+ * Both perform the same rounding steps in the same order: results are
+ * identical bit for bit.  QCD_ERR_ARG outside 0..2. */
+int qcd_set_sap_form(qcd_ctx *ctx, int form);
+
 /* Autotuner (no counterpart in the paper, which fixes 6^4 blocks with 3^4
  * sub-blocks).  Starting from *base (kappa, csw, tol, inner_tol, bc_t, limits),
  * times complete solves of D x = b from x0 = 0 for candidate SAP set-ups and

@@ -26,7 +26,7 @@ KERNEL_CLASSES = ("dslash32", "dslash64", "ssor", "saphop", "blas", "other", "le
 EXPORTS = ("qcd_create", "qcd_destroy", "qcd_last_error", "qcd_set_boundary", "qcd_load_gauge",
            "qcd_build_clover", "qcd_apply_D", "qcd_sap_precondition", "qcd_solve", "qcd_set_profiling",
            "qcd_kernel_stats", "qcd_launch_count", "qcd_bench_dslash", "qcd_sap_precondition_noalloc",
-           "qcd_set_sap_ctas", "qcd_set_graphs", "qcd_autotune", "qcd_learned_weight_count",
+           "qcd_set_sap_ctas", "qcd_set_sap_form", "qcd_set_graphs", "qcd_autotune", "qcd_learned_weight_count",
            "qcd_learned_set_weights", "qcd_learned_get_weights", "qcd_learned_apply", "qcd_learned_loss_grad",
            "qcd_learned_train", "qcd_learned_evaluate", "qcd_solve_multi")
 
@@ -92,6 +92,7 @@ def load_library(path: str = LIB_PATH):
         "qcd_solve": (I, [P, P, P, ctypes.POINTER(qcd_params), I, ctypes.POINTER(qcd_stats)]),
         "qcd_set_profiling": (I, [P, I]),
         "qcd_set_sap_ctas": (I, [P, I]),
+        "qcd_set_sap_form": (I, [P, I]),
         "qcd_set_graphs": (I, [P, I]),
         "qcd_learned_weight_count": (ctypes.c_long, []),
         "qcd_learned_set_weights": (I, [P, P, ctypes.c_long]),
@@ -214,6 +215,11 @@ def qcd_solve_multi(ctxs, xs, bs, params, nrhs, check: bool = True):
 
 def qcd_set_sap_ctas(ctx, min_ctas: int):
     return _check(ctx, load_library().qcd_set_sap_ctas(ctx, int(min_ctas)))
+
+
+def qcd_set_sap_form(ctx, form: int):
+    """0: lanes per SSOR site update chosen per launch; 1: 32; 2: 8 (identical results)."""
+    return _check(ctx, load_library().qcd_set_sap_form(ctx, int(form)))
 
 
 def qcd_autotune(ctx, b, base: qcd_params, nrhs: int = 1, max_candidates: int = 0):

@@ -441,6 +441,14 @@ int qcd_set_sap_ctas(qcd_ctx *c, int min_ctas) {
     return QCD_OK;
 }
 
+int qcd_set_sap_form(qcd_ctx *c, int form) {
+    int rc = ready(c);
+    if (rc) return rc;
+    if (form < 0 || form > 2) return fail(c, QCD_ERR_ARG, "form must lie in 0..2");
+    c->sap_form = form;
+    return QCD_OK;
+}
+
 int qcd_set_profiling(qcd_ctx *c, int on) {
     int rc = ready(c);
     if (rc) return rc;

@@ -52,6 +52,7 @@ struct SapPlan {
     bool thread = false;  // thread form of the SSOR kernel (SoA per-block fields instead of records)
     int C = 1, slab_vol = 0;  // CTAs per block (cluster), most sites one CTA owns
     int nchunks = 0, nslot = 0, nwarps = 0;
+    int sms = 1;        // SM count of the device the plan was made for
     size_t smem_bytes = 0;
     std::vector<int> h_chunk_ptr;   // [C][nchunks + 1], offsets into h_chunk_site
     std::vector<int> h_chunk_site;  // block-local site indices, CTA-major
@@ -137,6 +138,7 @@ struct qcd_ctx {
     qcd::Learned net;
     long field_version = 0;  // bumped whenever the links or the clover field change
     int sap_min_ctas = 0;    // lower bound on the CTAs (cluster size) per SAP block; 0: fill the SMs
+    int sap_form = 0;        // SSOR lanes per site update: 0 by occupancy, 1 warp form (32), 2 octet form (8)
 
     // workspace, grown on demand
     std::vector<void *> allocations;

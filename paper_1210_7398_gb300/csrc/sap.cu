@@ -80,6 +80,7 @@ constexpr int kRing = 3;           // staging depth (timeline steps in flight)
 constexpr int kMaxSlots = 32;      // sites (one warp each) per CTA per timeline step
 constexpr int kMaxCluster = 16;    // CTAs per SAP block (clusters above 8 need the non-portable size)
 constexpr size_t kSmemLimit = 200 * 1024;
+constexpr size_t kSmemPerSm = 228 * 1024;  // shared memory of one SM (GB300)
 
 // Per-site record of the SSOR kernel, in 4-byte words.  W_d for d = 2 mu + (backward):
 // U_mu(n) forward, U_mu(n - mu)^dag backward, 3x3 row-major complex (zero when the hop leaves
@@ -485,6 +486,294 @@ __global__ void __launch_bounds__(32 * MAXW) k_ssor_warp(SsorArgs a) {
         a.y[(long)q * a.V + n] = v;
     }
 }
+
+// K3, octet form: the same ll wavefront, chunks, staging and barriers as k_ssor_warp, but one
+// site update per 8 lanes (lane = hop direction d = 2 mu + (backward)) and four sites per warp.
+// A lane forms its direction's whole projected hop (3 colours, 4 spins), the 8 directions meet
+// in a three-step reduce-scatter,
+// every lane gathers the sum, and each chirality's 4 lanes apply 1 or 2 rows of its 6x6 block.
+// The arithmetic per site is the warp form's, rounding step by rounding step, spread over 8
+// lanes instead of 32: a quarter of the issued instructions per update, but a quarter of the
+// warps to hide each lane's longer dependency chains.
+template <bool HALF, bool CL>
+__global__ void __launch_bounds__(256) k_ssor_oct(SsorArgs a) {
+    using L = Rec<HALF>;
+    extern __shared__ __align__(16) float sm[];
+    if (a.gate && !a.gate[blockIdx.y].active) return;  // uniform over the cluster
+    a.f += (size_t)blockIdx.y * 6 * a.V;
+    a.y += (size_t)blockIdx.y * 6 * a.V;
+    const int rank = CL ? (int)cg::this_cluster().block_rank() : 0;
+    const int nch = a.nchunks;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int grp = lane >> 3, d = lane & 7;             // site slot in the warp, direction
+    const unsigned gm = 0xffu << (lane & 24);            // the 8 lanes of this site
+    const int *cptr_g = a.chunk_ptr + rank * (nch + 1);
+    const int tab0 = cptr_g[0], ntab = cptr_g[nch] - tab0;
+    // shared memory as in k_ssor_warp: [y slab | scale | staging ring | chunk pointers | chunk sites]
+    float *ys = sm;
+    float *yscale = ys + (size_t)a.slab_vol * L::ywords;
+    float *ring = yscale + 4;
+    int *cptr = reinterpret_cast<int *>(ring + (size_t)kRing * a.nslot * L::stage);
+    int2 *csite = reinterpret_cast<int2 *>(cptr + ((nch + 1 + 3) & ~3));
+    const uint32_t ys_u32 = (uint32_t)__cvta_generic_to_shared(ys);
+    const uint32_t scale_u32 = (uint32_t)__cvta_generic_to_shared(yscale);
+    const int blk = blockIdx.x / a.C;
+    const long n0 = a.origin_site[blk];
+    const float4 *rec = a.rec + (size_t)blk * a.vol * L::chunks;
+
+    // ---- direction constants: half-spinors h0 = psi[pa] + za psi[pb], h1 = psi[pc] + zc psi[pd],
+    // w = W_d h, and spin s of the hop gets fs[s] (w1 if u1[s], else w0), (1 -+ gamma_mu) in the
+    // Dirac representation ----
+    int pa = 0, pb = 3, pc = 1, pd = 2;
+    float2 za = make_float2(0.f, 1.f), zc = make_float2(0.f, 1.f);
+    float2 al[4] = {make_float2(1.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    float2 be[4] = {make_float2(0.f, 0.f), make_float2(1.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    switch (d) {
+        case 0: al[3] = make_float2(0.f, -1.f); be[2] = make_float2(0.f, -1.f); break;
+        case 1: za = zc = make_float2(0.f, -1.f); al[3] = make_float2(0.f, 1.f); be[2] = make_float2(0.f, 1.f); break;
+        case 2: za = make_float2(1.f, 0.f); zc = make_float2(-1.f, 0.f); al[3] = make_float2(1.f, 0.f);
+                be[2] = make_float2(-1.f, 0.f); break;
+        case 3: za = make_float2(-1.f, 0.f); zc = make_float2(1.f, 0.f); al[3] = make_float2(-1.f, 0.f);
+                be[2] = make_float2(1.f, 0.f); break;
+        case 4: pb = 2; pd = 3; za = make_float2(0.f, 1.f); zc = make_float2(0.f, -1.f);
+                al[2] = make_float2(0.f, -1.f); be[3] = make_float2(0.f, 1.f); break;
+        case 5: pb = 2; pd = 3; za = make_float2(0.f, -1.f); zc = make_float2(0.f, 1.f);
+                al[2] = make_float2(0.f, 1.f); be[3] = make_float2(0.f, -1.f); break;
+        case 6: pa = pb = 2; pc = pd = 3; za = zc = make_float2(1.f, 0.f);
+                al[0] = make_float2(0.f, 0.f); be[1] = make_float2(0.f, 0.f);
+                al[2] = make_float2(1.f, 0.f); be[3] = make_float2(1.f, 0.f); break;
+        default: pa = pb = 0; pc = pd = 1; za = zc = make_float2(1.f, 0.f); break;
+    }
+    float2 fs[4];
+    bool u1[4];
+#pragma unroll
+    for (int s = 0; s < 4; s++) {
+        u1[s] = be[s].x != 0.f || be[s].y != 0.f;
+        fs[s] = u1[s] ? be[s] : al[s];
+    }
+    const bool b2 = (d & 4) != 0, b1 = (d & 2) != 0, b0 = (d & 1) != 0;
+    const int chir = d >> 2, jj = d & 3;  // clover phase: chirality, first row
+
+    // ---- set-up (as k_ssor_warp): zero this CTA's slab of y, copy its chunk tables, FP16: scale ----
+    float4 *ys4 = reinterpret_cast<float4 *>(ys);
+    for (int i = threadIdx.x; i < a.slab_vol * L::ywords / 4; i += blockDim.x) ys4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = threadIdx.x; i <= nch; i += blockDim.x) cptr[i] = cptr_g[i] - tab0;
+    for (int i = threadIdx.x; i < ntab; i += blockDim.x) csite[i] = a.chunk_site[tab0 + i];
+    float inv_scale = 1.f, my_scale = 1.f;
+    if constexpr (HALF) {
+        float m = 0.f;
+        for (int i = threadIdx.x; i < a.slab_vol * 6; i += blockDim.x) {
+            const int sl = i / 6, q = i - 6 * sl;
+            const int off = a.own_off[rank * a.slab_vol + sl];
+            if (off < 0) continue;
+            const float4 v = a.f[(long)q * a.V + n0 + off];
+            m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+        }
+        for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+        if (threadIdx.x == 0) yscale[0] = 0.f;
+        __syncthreads();
+        if (lane == 0) atomicMax(reinterpret_cast<int *>(yscale), __float_as_int(m));  // m >= 0
+        __syncthreads();
+        my_scale = yscale[0] > 0.f ? yscale[0] : 1.f;
+        inv_scale = 1.f / my_scale;
+        __syncthreads();
+        if (threadIdx.x == 0) yscale[0] = my_scale;
+    }
+    __syncthreads();
+    const int T = a.nsweep * 2 * nch;
+    int kiss = 0, tiss = 0;  // sweep position and ring slot of the next staging
+    // stage the records and sources of this warp's (up to 4) sites of the next timeline step
+    auto issue = [&](int t) {
+        if (t < T) {
+            const int ch = kiss < nch ? kiss : 2 * nch - 1 - kiss;
+            const int base = cptr[ch], cnt = cptr[ch + 1] - base;
+            float *stage = ring + (size_t)tiss * a.nslot * L::stage;
+            for (int s4 = warp * 4; s4 < cnt; s4 += nw * 4) {
+                const int ns = cnt - s4 < 4 ? cnt - s4 : 4;
+                for (int q = lane; q < ns * L::stage_chunks; q += 32) {
+                    const int i = q / L::stage_chunks, p = q - i * L::stage_chunks;
+                    const int2 e = csite[base + s4 + i];
+                    float *dst = stage + (s4 + i) * L::stage;
+                    if (p < L::chunks) cp_async16(dst + 4 * p, rec + (size_t)e.x * L::chunks + p);
+                    else cp_async16(dst + 4 * p, a.f + (long)(p - L::chunks) * a.V + n0 + e.y);
+                }
+            }
+            if (++kiss == 2 * nch) kiss = 0;
+            if (++tiss == kRing) tiss = 0;
+        }
+        cp_async_commit();
+    };
+    // one SSOR site update by the 8 lanes of this group.  Every rounding step is the warp form's:
+    // the same per-direction products, the same butterfly tree over the directions (pairs
+    // differing in direction bit 2, then bit 1, then bit 0), the chiral components formed after
+    // the sum, the same clover row order; the two forms give identical bits.
+    auto update = [&](const float *sd) {
+        const int *sdi = reinterpret_cast<const int *>(sd);
+        // v: this direction's hop, [spin * 3 + colour][re, im]
+        float v[24];
+#pragma unroll
+        for (int i = 0; i < 24; i++) v[i] = 0.f;
+        const int code = sdi[L::nbr + d];
+        if (code >= 0) {
+            const int sl = code >> 24;
+            float sc = my_scale;
+            uint32_t ad = ys_u32 + 4u * (uint32_t)(code & 0xffffff);
+            if constexpr (CL) {
+                if (sl != rank) {
+                    ad = mapa_u32(ad, sl);
+                    if constexpr (HALF) sc = ld_cluster_f32(mapa_u32(scale_u32, sl));
+                }
+            }
+            auto nq = [&](int k) -> float2 {  // complex k = spin * 3 + colour of the neighbour spinor
+                if constexpr (CL) return ld_cl_c<HALF>(ad + 4u * (uint32_t)(k * L::cw));
+                else return ld_c<HALF>(ys + (code & 0xffffff) + k * L::cw);
+            };
+            float2 h0[3], h1[3];
+#pragma unroll
+            for (int cc = 0; cc < 3; cc++) {
+                h0[cc] = cfma(za, nq(pb * 3 + cc), nq(pa * 3 + cc));
+                h1[cc] = cfma(zc, nq(pd * 3 + cc), nq(pc * 3 + cc));
+            }
+            const float *W = sd + L::W + d * 9 * L::cw;
+#pragma unroll
+            for (int r = 0; r < 3; r++) {
+                float2 w0 = make_float2(0.f, 0.f), w1 = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int cc = 0; cc < 3; cc++) {
+                    const float2 u = ld_c<HALF>(W + (r * 3 + cc) * L::cw);
+                    w0 = cfma(u, h0[cc], w0);
+                    w1 = cfma(u, h1[cc], w1);
+                }
+                if constexpr (HALF) { w0 = cscale(w0, sc); w1 = cscale(w1, sc); }
+#pragma unroll
+                for (int s = 0; s < 4; s++) {
+                    const float2 e = cmul(fs[s], u1[s] ? w1 : w0);  // exact: fs[s] is 0, +-1 or +-i
+                    v[2 * (s * 3 + r)] = e.x;
+                    v[2 * (s * 3 + r) + 1] = e.y;
+                }
+            }
+        }
+        // reduce-scatter over the 8 directions: lane d ends with reals 3d .. 3d + 2 of the sum
+        float r12[12], r6[6], r3[3];
+#pragma unroll
+        for (int j = 0; j < 12; j++) {
+            const float send = b2 ? v[j] : v[12 + j], keep = b2 ? v[12 + j] : v[j];
+            r12[j] = keep + __shfl_xor_sync(gm, send, 4);
+        }
+#pragma unroll
+        for (int j = 0; j < 6; j++) {
+            const float send = b1 ? r12[j] : r12[6 + j], keep = b1 ? r12[6 + j] : r12[j];
+            r6[j] = keep + __shfl_xor_sync(gm, send, 2);
+        }
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const float send = b0 ? r6[j] : r6[3 + j], keep = b0 ? r6[3 + j] : r6[j];
+            r3[j] = keep + __shfl_xor_sync(gm, send, 1);
+        }
+        // all-gather: every lane gets the whole hop sum S
+        float g6[6], g12[12], S[24];
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const float o = __shfl_xor_sync(gm, r3[j], 1);
+            g6[j] = b0 ? o : r3[j];
+            g6[3 + j] = b0 ? r3[j] : o;
+        }
+#pragma unroll
+        for (int j = 0; j < 6; j++) {
+            const float o = __shfl_xor_sync(gm, g6[j], 2);
+            g12[j] = b1 ? o : g6[j];
+            g12[6 + j] = b1 ? g6[j] : o;
+        }
+#pragma unroll
+        for (int j = 0; j < 12; j++) {
+            const float o = __shfl_xor_sync(gm, g12[j], 4);
+            S[j] = b2 ? o : g12[j];
+            S[12 + j] = b2 ? g12[j] : o;
+        }
+        // chiral components of chirality chir: k = s * 3 + c (s = 0, 1), S_s -+ S_(s+2)
+        float x[12];
+#pragma unroll
+        for (int j = 0; j < 12; j++) x[j] = chir ? S[j] + S[12 + j] : S[j] - S[12 + j];
+        // rows jj and jj + 4 (the latter for jj < 2) of the chiral clover block chir
+        float2 eta[2];
+#pragma unroll
+        for (int t = 0; t < 2; t++) {
+            const int k = (t == 0 || jj < 2) ? jj + 4 * t : jj;
+            const float *row = sd + L::F + (36 * chir + 6 * k) * L::cw;
+            float2 e = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int m = 0; m < 6; m++) e = cfma(ld_c<HALF>(row + m * L::cw), make_float2(x[2 * m], x[2 * m + 1]), e);
+            eta[t] = e;
+        }
+        // the other chirality's rows (lane ^ 4); upper spins: eta0 + eta1, lower: eta1 - eta0
+#pragma unroll
+        for (int t = 0; t < 2; t++) {
+            float2 Q;
+            Q.x = __shfl_xor_sync(gm, eta[t].x, 4);
+            Q.y = __shfl_xor_sync(gm, eta[t].y, 4);
+            if (t == 0 || jj < 2) {
+                const int k = jj + 4 * t;
+                const float2 out = chir == 0 ? cadd(eta[t], Q) : csub(eta[t], Q);
+                const int idx = chir * 6 + k;  // spin * 3 + colour of the output
+                float *yp = ys + sdi[L::yoff] + idx * L::cw;
+                const float2 fv = *reinterpret_cast<const float2 *>(sd + L::words + idx * 2);
+                float2 yo = ld_c<HALF>(yp);
+                if constexpr (HALF) yo = cscale(yo, my_scale);
+                float2 tt;
+                tt.x = fmaf(a.kappa, out.x, fv.x);
+                tt.y = fmaf(a.kappa, out.y, fv.y);
+                float2 yn;
+                yn.x = fmaf(a.omega, tt.x - yo.x, yo.x);
+                yn.y = fmaf(a.omega, tt.y - yo.y, yo.y);
+                if constexpr (HALF) yn = cscale(yn, inv_scale);
+                st_c<HALF>(yp, yn);
+            }
+        }
+    };
+
+    issue(0);
+    issue(1);
+    if (CL) cg::this_cluster().sync();
+    else __syncthreads();
+    int k = 0, tring = 0;  // sweep position and ring slot of the current step
+    for (int t = 0; t < T; t++) {
+        issue(t + 2);
+        cp_async_wait<2>();
+        __syncwarp();
+        const int ch = k < nch ? k : 2 * nch - 1 - k;
+        const int base = cptr[ch], cnt = cptr[ch + 1] - base;
+        const float *stage = ring + (size_t)tring * a.nslot * L::stage;
+        for (int s4 = warp * 4; s4 < cnt; s4 += nw * 4)
+            if (s4 + grp < cnt) update(stage + (s4 + grp) * L::stage);
+        __syncwarp();  // this warp's ring slots may be restaged by the next issue
+        if (++k == 2 * nch) k = 0;
+        if (++tring == kRing) tring = 0;
+        if (t + 1 < T) {
+            const unsigned char f = a.flags[k];
+            if (CL && f == 2) cg::this_cluster().sync();
+            else if (f == 1) __syncthreads();
+        }
+    }
+    cp_async_wait<0>();
+    if (CL) cg::this_cluster().sync();
+    else __syncthreads();
+    for (int i = threadIdx.x; i < a.slab_vol * 6; i += blockDim.x) {
+        const int sl = i / 6, q = i - 6 * sl;
+        const int off = a.own_off[rank * a.slab_vol + sl];
+        if (off < 0) continue;
+        const long n = n0 + off;
+        float4 v;
+        if constexpr (HALF) {
+            const float2 lo = cscale(ld_c<true>(ys + sl * 12 + 2 * q), my_scale);
+            const float2 hi = cscale(ld_c<true>(ys + sl * 12 + 2 * q + 1), my_scale);
+            v = make_float4(lo.x, lo.y, hi.x, hi.y);
+        } else {
+            v = ys4[i];
+        }
+        a.y[(long)q * a.V + n] = v;
+    }
+}
+
 
 // K3, thread form for the throughput regime (blocks that fit one CTA, many blocks per colour):
 // one CTA per block with the block spinor y in shared memory, and every site update of a level
@@ -948,6 +1237,7 @@ int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &np,
         cudaGetLastError();
         sms = 1;
     }
+    np.sms = sms;
     const int nblk1 = np.nb[0] * np.nb[1] * np.nb[2] * np.nb[3] / 2;
     // up to 32 sites (warps) per step and CTA where one colour's blocks leave SMs idle and the
     // staging ring fits (fewer dependent steps), else 16 (more registers per thread; several
@@ -1106,6 +1396,12 @@ int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
                 QCD_CUDA(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
                 QCD_CUDA(c, cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
             }
+            const void *ko[] = {(const void *)k_ssor_oct<false, false>, (const void *)k_ssor_oct<true, false>,
+                                (const void *)k_ssor_oct<false, true>, (const void *)k_ssor_oct<true, true>};
+            for (const void *k : ko) {
+                QCD_CUDA(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+                QCD_CUDA(c, cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+            }
             QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_soa, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
             return QCD_OK;
         }))
@@ -1134,8 +1430,19 @@ int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
     attr[0].val.clusterDim.x = p.C;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(32 * p.nwarps);
     cfg.dynamicSmemBytes = p.smem_bytes;
+    // form of the block solve for this launch (the warp and octet forms give identical bits):
+    // the octet form issues a quarter of the instructions per site update with a quarter of the
+    // warps, so it is taken where the grid keeps at least 16 of its warps resident per SM (the
+    // warp form then has 64 and is bound by instruction issue; measured on GB300)
+    const int w_oct = (p.nslot + 3) / 4;
+    auto octet = [&](int col) {
+        if (c->sap_form) return c->sap_form == 2;
+        const long ctas = (long)p.nblk[col] * p.C * nrhs;
+        long per_sm = std::min<long>((long)(kSmemPerSm / (p.smem_bytes + 1024)), 64 / w_oct);
+        per_sm = std::min<long>(std::min<long>(per_sm, 32), (ctas + p.sms - 1) / p.sms);
+        return per_sm * w_oct >= 16;
+    };
     cfg.stream = c->stream;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
@@ -1150,6 +1457,8 @@ int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
                             : nullptr;
             a.origin_site = p.d_origin_site[col];
             cfg.gridDim = dim3(p.nblk[col] * p.C, nrhs);
+            const bool oct = !p.thread && octet(col);
+            cfg.blockDim = dim3(32 * (oct ? w_oct : p.nwarps));
             prof_begin(c, QCD_K_SSOR, &ev);
             cudaError_t e;
             if (p.thread) {
@@ -1161,7 +1470,10 @@ int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
                 e = cudaGetLastError();
             } else {
                 void (*kern)(SsorArgs);
-                if (p.C > 1)
+                if (oct)
+                    kern = p.C > 1 ? (p.half ? k_ssor_oct<true, true> : k_ssor_oct<false, true>)
+                                   : (p.half ? k_ssor_oct<true, false> : k_ssor_oct<false, false>);
+                else if (p.C > 1)
                     kern = p.nwarps > 16 ? (p.half ? k_ssor_warp<true, 32, true> : k_ssor_warp<false, 32, true>)
                                          : (p.half ? k_ssor_warp<true, 16, true> : k_ssor_warp<false, 16, true>);
                 else

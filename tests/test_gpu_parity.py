@@ -224,6 +224,9 @@ def test_errors_are_reported_not_fatal():
         q.qcd_set_sap_ctas(s.ctx, 17)
     assert e.value.code == q.QCD_ERR_ARG
     with pytest.raises(q.QcdError) as e:
+        q.qcd_set_sap_form(s.ctx, 3)
+    assert e.value.code == q.QCD_ERR_ARG
+    with pytest.raises(q.QcdError) as e:
         s.apply_D(torch.empty_like(psi), psi, 7)  # no such precision
     assert e.value.code == q.QCD_ERR_ARG
     wrong_kappa = q.make_params(0.11, CSW, (2, 2, 2, 2), (1, 1, 1, 1))  # differs from the clover built
@@ -323,6 +326,45 @@ def test_sap_batched_equals_single_per_rhs(geo, storage):
     ref = oracle.sap(dims, U, F, kappa, b, sb, 1.1, 3, 2, v[2])
     tol = 1e-5 if storage == q.QCD_F32 else SAP_F16_TOL
     assert rel_norm(out[2].cpu().numpy().astype(np.complex128), ref) <= tol
+    s.close()
+
+
+FORM_CASES = [
+    # dims, block, subblock, storage, cluster width (0: automatic), right-hand sides
+    ((8, 8, 8, 8), (4, 4, 4, 4), (2, 2, 2, 2), q.QCD_F32, 0, 1),
+    ((8, 8, 8, 8), (4, 4, 4, 4), (2, 2, 2, 2), q.QCD_F16, 2, 3),
+    ((12, 12, 12, 24), (6, 6, 6, 12), (3, 3, 3, 6), q.QCD_F32, 0, 1),
+    ((12, 12, 12, 24), (6, 6, 6, 12), (3, 3, 3, 6), q.QCD_F16, 5, 1),
+    ((12, 12, 12, 24), (3, 3, 3, 6), (1, 1, 1, 2), q.QCD_F16, 0, 12),
+    ((12, 12, 12, 24), (3, 3, 3, 6), (1, 1, 1, 2), q.QCD_F32, 1, 4),
+]
+
+
+@pytest.mark.parametrize("case", FORM_CASES, ids=lambda c: "%s-%s-c%d-n%d" % (
+    "x".join(map(str, c[1])), "f16" if c[3] == q.QCD_F16 else "f32", c[4], c[5]))
+def test_sap_lane_forms_identical(case):
+    """The 32-lane and the 8-lane site updates of the SSOR kernel perform the same
+    rounding steps in the same order: their SAP outputs are equal bit for bit (and the
+    automatic choice, per launch, equals both)."""
+    dims, b, sb, storage, ctas, nrhs = case
+    kappa = 0.12
+    s, U, F = make_solver(dims, kappa, seed=1008)
+    v = qi.gaussian_spinor(dims, seed=2008, nrhs=nrhs)
+    prm = q.make_params(kappa, CSW, b, sb, omega=1.1, nsweep=2, nsap=2, sap_storage=storage)
+    q.qcd_set_sap_ctas(s.ctx, ctas)
+    vin = torch.from_numpy(v.astype(np.complex64)).cuda()
+    outs = []
+    for form in (1, 2, 0):
+        q.qcd_set_sap_form(s.ctx, form)
+        out = torch.empty_like(vin)
+        s.sap_precondition(out, vin, prm, nrhs=nrhs)
+        torch.cuda.synchronize()
+        outs.append(out)
+    assert torch.equal(outs[0], outs[1])
+    assert torch.equal(outs[0], outs[2])
+    ref = oracle.sap(dims, U, F, kappa, b, sb, 1.1, 2, 2, v[0])
+    tol = 1e-5 if storage == q.QCD_F32 else SAP_F16_TOL
+    assert rel_norm(outs[1][0].cpu().numpy().astype(np.complex128), ref) <= tol
     s.close()
 
 
