@@ -196,7 +196,8 @@ int qcd_solve_multi(int n, qcd_ctx *const *ctxs, double *const *x, const double 
 int qcd_set_graphs(qcd_ctx *ctx, int on);
 
 /* Tuning knob of the SAP block kernel; results do not depend on it.  The
- * block solve has two forms.  The warp form runs one warp per site update over
+ * block solve has two forms.  The warp form runs 32 lanes (or 8, see
+ * qcd_set_sap_form) per site update over
  * a cluster of C CTAs per block (C <= 16, each CTA owning an equal share of
  * every dependency level of the sweep and keeping its sites' spinors in its
  * shared memory, which must fit).  The thread form (FP32 storage, blocks whose

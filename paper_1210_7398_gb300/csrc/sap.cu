@@ -18,7 +18,10 @@
 // are placed only where data flows (the paper's OpenMP barriers between
 // dependent sites).  Each site update is done by one warp: lane (d, c) takes
 // hop direction d = 2 mu + (backward) and colour row c, the 8 directions are
-// summed with butterfly shuffles, and 24 lanes apply the chiral clover rows.
+// summed with butterfly shuffles, and 24 lanes apply the chiral clover rows
+// (k_ssor_warp); or by 8 lanes, one per direction, four sites per warp
+// (k_ssor_oct: the same rounding steps, chosen per launch where many CTAs fill
+// the SMs).
 // Each CTA keeps its sites' spinors in shared memory (neighbours owned by peer
 // CTAs are read through distributed shared memory); records and source of the
 // sites of the next two chunks are staged with cp.async while the current one
