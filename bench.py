@@ -388,6 +388,55 @@ def geometry_section(q, qi, torch, s, w, b):
     return out
 
 
+def block_solver_section(q, qi, torch, s, w, b):
+    """The two block inverses of SAP at equal cost: ll-SSOR with nsweep sweeps against the even-odd
+    minimal-residual solver with 2 nsweep - 1 steps (and twice that).  Cost in block-restricted D
+    applications per block inverse: an SSOR sweep is 2 (forward and backward pass over every
+    site), an MR step 1 (two half-lattice hops), plus 1 for the even-odd set-up and the odd sites.
+    Workloads: the plain 12^3 x 24 solve, and 24^3 x 48 at kappa 0.122 with 4^4 blocks (2^4
+    sub-blocks), 4 sweeps, N_SAP 4 (many more iterations)."""
+    def compare(sv, bb, kappa, block, sub, nsweep, nsap):
+        rows = []
+        x = torch.zeros_like(bb)
+        stream = torch.cuda.current_stream()
+        for solver, steps in ((0, nsweep), (1, 2 * nsweep - 1), (1, 4 * nsweep - 1)):
+            p = q.make_params(kappa, w["csw"], block, sub, omega=w["omega"], nsweep=steps, nsap=nsap, tol=w["tol"],
+                              inner_tol=w["inner_tol"], block_solver=solver)
+            x.zero_()
+            sv.solve(x, bb, p)
+            x.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            st = sv.solve(x, bb, p)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            q.qcd_set_profiling(sv.ctx, True)
+            q.qcd_kernel_stats(sv.ctx, q.KERNEL_CLASSES.index("ssor"), reset=True)
+            x.zero_()
+            sv.solve(x, bb, p)
+            n, ms = q.qcd_kernel_stats(sv.ctx, q.KERNEL_CLASSES.index("ssor"), reset=True)
+            q.qcd_set_profiling(sv.ctx, False)
+            rows.append({"block_solver": "ll-ssor" if solver == 0 else "even-odd mr", "steps": steps,
+                         "cost_D_per_block_inverse": 2 * steps if solver == 0 else steps + 1,
+                         "ms": ev[0].elapsed_time(ev[1]), "outer_iters": st["outer_iters"],
+                         "inner_iters": st["inner_iters"], "block_kernel_ms_per_launch": ms / max(1, n),
+                         "true_rel_res": st["true_rel_res"]})
+        return rows
+
+    out = {"12x12x12x24": compare(s, b, w["kappa"], w["block"], w["subblock"], w["nsweep"], w["nsap"])}
+    dl = (24, 24, 24, 48)
+    sl = q.Solver(dl)
+    sl.load_gauge(qi.gauge_field(dl, w["eps"], seed=1003, device="cuda"))
+    sl.build_clover(0.122, w["csw"])
+    bl = qi.gaussian_spinor_torch(dl, 2003, 1, "cuda").contiguous()
+    torch.cuda.synchronize()
+    out["24x24x24x48_kappa0.122_4x4x4x4"] = compare(sl, bl, 0.122, (4, 4, 4, 4), (2, 2, 2, 2), 4, 4)
+    sl.close()
+    del bl
+    torch.cuda.empty_cache()
+    return out
+
+
 def headline_section(q, qi, torch, w, group, candidates):
     """48^3 x 96, kappa 0.122, the 12 spin-colour point sources in right-hand-side groups of `group`:
     plain FP32 SAP (the workload's literal set-up) against the autotuned set-up."""
@@ -589,20 +638,23 @@ def run_gpu_on_stream(args, q, qi, torch, np, peaks, rank, world, local):
                   "true_rel_res": ch_st["true_rel_res"], "speedup_vs_plain": ms_step / (sum(ch_ms) / len(ch_ms)),
                   "tuning": "qcd_autotune over block/sub-block splits, then FP16 storage, 2 CTAs per block "
                             "and (nsweep, nsap) in {2,4}^2 for the 3 fastest; best of timed full solves"}
-        # 12 spin-colour point sources solved together with the chosen set-up
+        # 12 spin-colour point sources solved together, with the set-up tuned for that batch
         pts = torch.from_numpy(qi.point_sources(dims)).cuda()
+        torch.cuda.synchronize()
+        best12, _ = q.qcd_autotune(s.ctx, pts, prm, nrhs=12, max_candidates=args.tune_candidates)
         xp = torch.zeros_like(pts)
-        s.solve(xp, pts, best, nrhs=12)
+        s.solve(xp, pts, best12, nrhs=12)
         torch.cuda.synchronize()
         xp.zero_()
         ev_a = torch.cuda.Event(enable_timing=True)
         ev_b = torch.cuda.Event(enable_timing=True)
         ev_a.record(stream)
-        bst = s.solve(xp, pts, best, nrhs=12)
+        bst = s.solve(xp, pts, best12, nrhs=12)
         ev_b.record(stream)
         torch.cuda.synchronize()
         tb = ev_a.elapsed_time(ev_b) / 1000.0
         chosen["batched_12_point_sources"] = {"seconds": tb, "seconds_per_source": tb / 12,
+                                              "params": q.params_dict(best12),
                                               "outer_iters": bst["outer_iters"], "inner_iters": bst["inner_iters"],
                                               "true_rel_res_max": bst["true_rel_res"]}
         # the learned correction on top of the chosen set-up; kept only when it is faster
@@ -612,6 +664,9 @@ def run_gpu_on_stream(args, q, qi, torch, np, peaks, rank, world, local):
             chosen["value"] = lr_sec["verdict"]["learned_ms"] / 1000.0
             chosen["params"]["learned"] = 1
             chosen["speedup_vs_plain"] = ms_step / lr_sec["verdict"]["learned_ms"]
+    block_solvers = None
+    if not args.skip_chosen:
+        block_solvers = block_solver_section(q, qi, torch, s, w, bd)
     geometry = None
     if args.geometry_sweep:
         geometry = geometry_section(q, qi, torch, s, w, bd)
@@ -693,6 +748,8 @@ def run_gpu_on_stream(args, q, qi, torch, np, peaks, rank, world, local):
             out["batched_uneven"] = batched
         if geometry is not None:
             out["geometry_sweep"] = geometry
+        if block_solvers is not None:
+            out["block_solvers"] = block_solvers
         if headline is not None:
             out["headline_48x48x48x96"] = headline
         print(json.dumps(out))

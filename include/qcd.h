@@ -81,7 +81,8 @@ typedef struct {
     int block[4];       /* SAP block extents (x, y, z, t)                              */
     int subblock[4];    /* ll-ordering sub-block extents; subblock | block             */
     double omega;       /* SSOR relaxation, 0 < omega < 2                              */
-    int nsweep;         /* SSOR sweeps (forward + backward pass) per block inverse     */
+    int nsweep;         /* SSOR sweeps (forward + backward pass) per block inverse, or
+                           minimal-residual steps when block_solver = 1                */
     int nsap;           /* SAP cycles N_SAP                                            */
     double tol;         /* outer: stop at ||b - D x|| <= tol ||b|| (true FP64 residual) */
     double inner_tol;   /* inner: stop at ||r|| <= inner_tol ||q||                     */
@@ -95,6 +96,13 @@ typedef struct {
                            the learned correction                                     */
     int sap_ctas;       /* SSOR kernel form, as qcd_set_sap_ctas (-1..16); 0 = context
                            setting; results do not depend on it                       */
+    int block_solver;   /* SAP block inverse A_BB.  0: ll-ordered SSOR (Sec. 3; uses
+                           subblock, omega, nsweep).  1: the even-odd alternative
+                           Sec. 3 compares it with: nsweep minimal-residual steps on
+                           the Schur complement 1 - kappa^2 F_e H_eo F_o H_oe of each
+                           block's even sites from 0, then the odd sites
+                           (sap_storage QCD_F32 and learned 0 only; subblock must
+                           still divide block; omega unused)                         */
 } qcd_params;
 
 typedef struct {
@@ -142,7 +150,8 @@ int qcd_apply_D(qcd_ctx *ctx, void *out, const void *in, int prec, int nrhs);
  * p->nsweep, p->nsap, p->sap_storage.  All right-hand sides go through one
  * batched application (one grid row of block solves per right-hand side);
  * each result equals, bit for bit, the call with that one alone.  Device
- * scratch grows to 4 nrhs + 1 complex64 fields. */
+ * scratch grows to 4 nrhs + 1 complex64 fields (7 nrhs + 1 with
+ * p->block_solver = 1). */
 int qcd_sap_precondition(qcd_ctx *ctx, float *out, const float *in, const qcd_params *p, int nrhs);
 
 /* The paper has no counterpart to this entry point; it serves callers that

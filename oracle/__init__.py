@@ -60,6 +60,10 @@ def lib():
             L.orc_ssor.restype = i
             L.orc_sap.argtypes = [P, i, P, P, d, P, P, d, i, i, P, P]
             L.orc_sap.restype = i
+            L.orc_sap_bs.argtypes = [P, i, P, P, d, P, P, d, i, i, i, P, P]
+            L.orc_sap_bs.restype = i
+            L.orc_eo_mr.argtypes = [P, i, P, P, d, P, i, i, P, P]
+            L.orc_eo_mr.restype = i
             L.orc_inner_bicgstab.argtypes = [P, i, P, P, d, P, P, d, i, i, d, i, P, P]
             L.orc_inner_bicgstab.restype = i
             L.orc_solve.argtypes = [P, i, P, P, d, P, P, d, i, i, d, d, i, i, P, P, P]
@@ -198,8 +202,24 @@ def ssor(dims, U, F, kappa, block, sub, omega, nsweep, colour, f, x=None, bc_t: 
     return x
 
 
-def sap(dims, U, F, kappa, block, sub, omega, nsweep, nsap, v, bc_t: int = 1):
-    """M_SAP v (Eq. (4)) with ll-ordered SSOR block inverses."""
+def eo_mr(dims, U, F, kappa, block, nmr, colour, f, x=None, bc_t: int = 1):
+    """x = the even-odd block inverse of f (nmr minimal-residual steps on the Schur complement
+    of D_BB on the even sites, then the odd sites) on every block of ``colour``."""
+    Lk, Lp = _ivec(dims)
+    bk, bp = _ivec(block)
+    U, Up = _c(U)
+    F, Fp = _c(F)
+    f, fp = _c(f)
+    x = np.zeros_like(f) if x is None else np.ascontiguousarray(x, dtype=np.complex128).copy()
+    st = lib().orc_eo_mr(Lp, bc_t, Up, Fp, kappa, bp, nmr, colour, fp, x.ctypes.data_as(ctypes.c_void_p))
+    if st != 0:
+        raise ValueError("bad SAP geometry or nmr")
+    return x
+
+
+def sap(dims, U, F, kappa, block, sub, omega, nsweep, nsap, v, bc_t: int = 1, block_solver: int = 0):
+    """M_SAP v (Eq. (4)).  block_solver 0: ll-ordered SSOR block inverses (nsweep sweeps);
+    1: even-odd minimal-residual block inverses (nsweep steps, omega and sub unused)."""
     Lk, Lp = _ivec(dims)
     bk, bp = _ivec(block)
     sk, sp = _ivec(sub)
@@ -207,8 +227,8 @@ def sap(dims, U, F, kappa, block, sub, omega, nsweep, nsap, v, bc_t: int = 1):
     F, Fp = _c(F)
     v, vp = _c(v)
     out = np.empty_like(v)
-    st = lib().orc_sap(Lp, bc_t, Up, Fp, kappa, bp, sp, omega, nsweep, nsap, vp,
-                       out.ctypes.data_as(ctypes.c_void_p))
+    st = lib().orc_sap_bs(Lp, bc_t, Up, Fp, kappa, bp, sp, omega, nsweep, nsap, block_solver, vp,
+                          out.ctypes.data_as(ctypes.c_void_p))
     if st != 0:
         raise ValueError("bad SAP geometry")
     return out

@@ -537,6 +537,126 @@ int orc_ssor(const int *L, int bc_t, const double *Ud, const double *Fd, double 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Even-odd alternative to the SSOR block inverse.  Sec. 3 names the even-   */
+/* odd site preconditioning of Luescher's SAP as the block solver that the   */
+/* ll-SSOR outperforms at equal cost, without formulas; this is the standard */
+/* construction.  Site parity p(n) = (n_0 + n_1 + n_2 + n_3) mod 2.  H_BB    */
+/* only links sites of opposite parity, so D_BB x = f reads                  */
+/*   x_e - kappa F_e H_eo x_o = f_e,   x_o - kappa F_o H_oe x_e = f_o,       */
+/* and eliminating x_o leaves the Schur complement on the even sites         */
+/*   Dhat x_e = fhat,  Dhat = 1 - kappa^2 F_e H_eo F_o H_oe,                 */
+/*   fhat = f_e + kappa F_e H_eo f_o.                                        */
+/* nmr minimal-residual steps from x_e = 0: r = fhat; per step p = Dhat r,   */
+/* alpha = <p, r> / <p, p>, x_e += alpha r, r -= alpha p; then               */
+/* x_o = f_o + kappa F_o H_oe x_e.  Applied to every block of colour c;      */
+/* sites of the other colour in x are left untouched.                        */
+/* ------------------------------------------------------------------------ */
+
+/* out = F(n) sum over the in-block neighbours j of n of h_nj src_j */
+static void block_FH(const int *L, int bc_t, const int *b, const cplx *U, const cplx *F, const cplx *src,
+                     long n, cplx out[12])
+{
+    int xn[4];
+    coords(L, n, xn);
+    cplx acc[12] = {0};
+    for (int mu = 0; mu < 4; mu++) {
+        int ymu = xn[mu] % b[mu];
+        if (ymu + 1 < b[mu]) add_hop_term(acc, L, bc_t, U, n, mu, +1, src);
+        if (ymu - 1 >= 0) add_hop_term(acc, L, bc_t, U, n, mu, -1, src);
+    }
+    for (int i = 0; i < 12; i++) {
+        cplx s = 0;
+        for (int j = 0; j < 12; j++) s += F[n * 144 + i * 12 + j] * acc[j];
+        out[i] = s;
+    }
+}
+
+int orc_eo_mr(const int *L, int bc_t, const double *Ud, const double *Fd, double kappa, const int *b,
+              int nmr, int colour, const double *fd, double *xd)
+{
+    init_tables();
+    if (orc_check_geometry(L, b, NULL) != 0 || nmr < 1) return -1;
+    const cplx *U = (const cplx *)Ud;
+    const cplx *F = (const cplx *)Fd;
+    const cplx *f = (const cplx *)fd;
+    cplx *x = (cplx *)xd;
+    long V = volume(L);
+    /* lattice-sized scratch; every block reads and writes only its own sites */
+    cplx *res = calloc(12 * V, sizeof(cplx)), *tod = calloc(12 * V, sizeof(cplx)), *pev = calloc(12 * V, sizeof(cplx));
+    int vol = b[0] * b[1] * b[2] * b[3];
+    int nb[4];
+    for (int mu = 0; mu < 4; mu++) nb[mu] = L[mu] / b[mu];
+    long nblocks = (long)nb[0] * nb[1] * nb[2] * nb[3];
+#pragma omp parallel for schedule(dynamic)
+    for (long B = 0; B < nblocks; B++) {
+        int Bc[4];
+        long rr = B;
+        for (int mu = 0; mu < 4; mu++) { Bc[mu] = (int)(rr % nb[mu]); rr /= nb[mu]; }
+        if (((Bc[0] + Bc[1] + Bc[2] + Bc[3]) & 1) != colour) continue;
+        long *ev = malloc(sizeof(long) * vol), *od = malloc(sizeof(long) * vol);
+        int ne = 0, no = 0;
+        for (int yl = 0; yl < vol; yl++) {
+            int y[4], xg[4], q = yl;
+            for (int mu = 0; mu < 4; mu++) { y[mu] = q % b[mu]; q /= b[mu]; }
+            for (int mu = 0; mu < 4; mu++) xg[mu] = Bc[mu] * b[mu] + y[mu];
+            long n = index_of(L, xg);
+            if ((xg[0] + xg[1] + xg[2] + xg[3]) & 1) od[no++] = n;
+            else ev[ne++] = n;
+        }
+        cplx h[12];
+        /* r = fhat on the even sites, x_e = 0 */
+        for (int k = 0; k < ne; k++) {
+            long n = ev[k];
+            block_FH(L, bc_t, b, U, F, f, n, h);
+            for (int i = 0; i < 12; i++) {
+                res[n * 12 + i] = f[n * 12 + i] + kappa * h[i];
+                x[n * 12 + i] = 0;
+            }
+        }
+        for (int it = 0; it < nmr; it++) {
+            /* p = Dhat r through t_o = F_o H_oe r */
+            for (int k = 0; k < no; k++) {
+                long m = od[k];
+                block_FH(L, bc_t, b, U, F, res, m, h);
+                for (int i = 0; i < 12; i++) tod[m * 12 + i] = h[i];
+            }
+            cplx pr = 0;
+            double pp = 0;
+            for (int k = 0; k < ne; k++) {
+                long n = ev[k];
+                block_FH(L, bc_t, b, U, F, tod, n, h);
+                for (int i = 0; i < 12; i++) {
+                    cplx pv = res[n * 12 + i] - kappa * kappa * h[i];
+                    pev[n * 12 + i] = pv;
+                    pr += conj(pv) * res[n * 12 + i];
+                    pp += creal(conj(pv) * pv);
+                }
+            }
+            cplx alpha = pp > 0 ? pr / pp : 0;
+            for (int k = 0; k < ne; k++) {
+                long n = ev[k];
+                for (int i = 0; i < 12; i++) {
+                    x[n * 12 + i] += alpha * res[n * 12 + i];
+                    res[n * 12 + i] -= alpha * pev[n * 12 + i];
+                }
+            }
+        }
+        /* x_o = f_o + kappa F_o H_oe x_e */
+        for (int k = 0; k < no; k++) {
+            long m = od[k];
+            block_FH(L, bc_t, b, U, F, x, m, h);
+            for (int i = 0; i < 12; i++) x[m * 12 + i] = f[m * 12 + i] + kappa * h[i];
+        }
+        free(ev);
+        free(od);
+    }
+    free(res);
+    free(tod);
+    free(pev);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* SAP (Eq. (4), Alg. 1).  One application of K together with w = D K v:    */
 /*   x_E = A_EE v_E;  w_O = D_OE x_E;  w_E = D_EE x_E;  f_O = v_O - w_O;     */
 /*   x_O = A_OO f_O;  f_E = D_EO x_O;  f_O = D_OO x_O;  w_O += f_O;          */
@@ -549,7 +669,14 @@ typedef struct {
     const int *L; int bc_t;
     const double *U, *F; double kappa;
     const int *b, *s; double omega; int nsweep; int nsap;
+    int solver; /* block inverse: 0 ll-SSOR (nsweep sweeps), 1 even-odd MR (nsweep steps) */
 } sap_cfg;
+
+static void block_inverse(const sap_cfg *c, int colour, const double *f, double *x)
+{
+    if (c->solver == 1) orc_eo_mr(c->L, c->bc_t, c->U, c->F, c->kappa, c->b, c->nsweep, colour, f, x);
+    else orc_ssor(c->L, c->bc_t, c->U, c->F, c->kappa, c->b, c->s, c->omega, c->nsweep, colour, f, x);
+}
 
 /* y = K v and w = D K v following Alg. 1 */
 static void sap_DK(const sap_cfg *c, const double *v, double *y, double *w)
@@ -562,7 +689,7 @@ static void sap_DK(const sap_cfg *c, const double *v, double *y, double *w)
     int *col = malloc(sizeof(int) * V);
     orc_colours(c->L, c->b, col);
     /* x_E = A_EE v_E */
-    orc_ssor(c->L, c->bc_t, c->U, c->F, c->kappa, c->b, c->s, c->omega, c->nsweep, 0, v, xE);
+    block_inverse(c, 0, v, xE);
     /* w_O = D_OE x_E ; w_E = D_EE x_E */
     orc_apply_D_colour(c->L, c->bc_t, c->b, c->U, c->F, c->kappa, 1, 0, xE, wO);
     orc_apply_D_colour(c->L, c->bc_t, c->b, c->U, c->F, c->kappa, 0, 0, xE, wE);
@@ -570,7 +697,7 @@ static void sap_DK(const sap_cfg *c, const double *v, double *y, double *w)
     for (long n = 0; n < V; n++)
         for (int k = 0; k < 24; k++) fO[n * 24 + k] = (col[n] == 1) ? v[n * 24 + k] - wO[n * 24 + k] : 0.0;
     /* x_O = A_OO f_O */
-    orc_ssor(c->L, c->bc_t, c->U, c->F, c->kappa, c->b, c->s, c->omega, c->nsweep, 1, fO, xO);
+    block_inverse(c, 1, fO, xO);
     /* f_E = D_EO x_O ; f_O = D_OO x_O */
     orc_apply_D_colour(c->L, c->bc_t, c->b, c->U, c->F, c->kappa, 0, 1, xO, fE);
     orc_apply_D_colour(c->L, c->bc_t, c->b, c->U, c->F, c->kappa, 1, 1, xO, fO);
@@ -588,12 +715,12 @@ static void sap_DK(const sap_cfg *c, const double *v, double *y, double *w)
     free(xE); free(xO); free(wO); free(wE); free(fO); free(fE); free(col);
 }
 
-/* out = M_SAP v */
-int orc_sap(const int *L, int bc_t, const double *U, const double *F, double kappa, const int *b,
-            const int *s, double omega, int nsweep, int nsap, const double *v, double *out)
+/* out = M_SAP v with the block inverse `solver` (0 ll-SSOR, 1 even-odd MR) */
+int orc_sap_bs(const int *L, int bc_t, const double *U, const double *F, double kappa, const int *b,
+               const int *s, double omega, int nsweep, int nsap, int solver, const double *v, double *out)
 {
-    if (orc_check_geometry(L, b, s) != 0 || nsweep < 1 || nsap < 1) return -1;
-    sap_cfg c = {L, bc_t, U, F, kappa, b, s, omega, nsweep, nsap};
+    if (orc_check_geometry(L, b, s) != 0 || nsweep < 1 || nsap < 1 || solver < 0 || solver > 1) return -1;
+    sap_cfg c = {L, bc_t, U, F, kappa, b, s, omega, nsweep, nsap, solver};
     long N = 24 * volume(L);
     double *r = malloc(sizeof(double) * N), *y = malloc(sizeof(double) * N), *w = malloc(sizeof(double) * N);
     memcpy(r, v, sizeof(double) * N);
@@ -607,6 +734,13 @@ int orc_sap(const int *L, int bc_t, const double *U, const double *F, double kap
     }
     free(r); free(y); free(w);
     return 0;
+}
+
+/* out = M_SAP v (ll-SSOR block inverses) */
+int orc_sap(const int *L, int bc_t, const double *U, const double *F, double kappa, const int *b,
+            const int *s, double omega, int nsweep, int nsap, const double *v, double *out)
+{
+    return orc_sap_bs(L, bc_t, U, F, kappa, b, s, omega, nsweep, nsap, 0, v, out);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -44,7 +44,7 @@ class qcd_params(ctypes.Structure):
                 ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
                 ("max_outer", ctypes.c_int), ("max_inner", ctypes.c_int),
                 ("bc_t", ctypes.c_int), ("sap_storage", ctypes.c_int),
-                ("learned", ctypes.c_int), ("sap_ctas", ctypes.c_int)]
+                ("learned", ctypes.c_int), ("sap_ctas", ctypes.c_int), ("block_solver", ctypes.c_int)]
 
 
 class qcd_learned_verdict(ctypes.Structure):
@@ -234,7 +234,8 @@ def qcd_autotune(ctx, b, base: qcd_params, nrhs: int = 1, max_candidates: int = 
 def params_dict(p: qcd_params) -> dict:
     return {"block": list(p.block), "subblock": list(p.subblock), "omega": p.omega, "nsweep": p.nsweep,
             "nsap": p.nsap, "sap_storage": {QCD_F32: "f32", QCD_F16: "f16"}.get(p.sap_storage, p.sap_storage),
-            "sap_ctas": p.sap_ctas, "learned": p.learned}
+            "sap_ctas": p.sap_ctas, "learned": p.learned,
+            "block_solver": {0: "ll-ssor", 1: "even-odd mr"}.get(p.block_solver, p.block_solver)}
 
 
 LEARNED_CHANS = (1, 8, 8, 1)
@@ -324,7 +325,8 @@ def qcd_bench_dslash(ctx, prec: int, nrhs: int, iters: int):
 
 
 def make_params(kappa, csw, block, subblock, omega=1.0, nsweep=4, nsap=4, tol=1e-10, inner_tol=1e-5,
-                max_outer=100, max_inner=500, bc_t=1, sap_storage=QCD_F32, sap_ctas=0) -> qcd_params:
+                max_outer=100, max_inner=500, bc_t=1, sap_storage=QCD_F32, sap_ctas=0,
+                block_solver=0) -> qcd_params:
     p = qcd_params()
     p.kappa, p.csw = float(kappa), float(csw)
     p.block = (ctypes.c_int * 4)(*block)
@@ -333,6 +335,7 @@ def make_params(kappa, csw, block, subblock, omega=1.0, nsweep=4, nsap=4, tol=1e
     p.tol, p.inner_tol = float(tol), float(inner_tol)
     p.max_outer, p.max_inner = int(max_outer), int(max_inner)
     p.bc_t, p.sap_storage, p.learned, p.sap_ctas = int(bc_t), int(sap_storage), 0, int(sap_ctas)
+    p.block_solver = int(block_solver)
     return p
 
 

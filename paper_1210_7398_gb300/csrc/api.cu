@@ -150,6 +150,9 @@ int check_params(qcd_ctx *c, const qcd_params *p) {
     if (p->kappa != c->kappa || p->csw != c->csw)
         return fail(c, QCD_ERR_ARG, "params.kappa/csw differ from the clover field built");
     if (p->sap_ctas < -1 || p->sap_ctas > 16) return fail(c, QCD_ERR_ARG, "sap_ctas must lie in -1..16");
+    if (p->block_solver < 0 || p->block_solver > 1) return fail(c, QCD_ERR_ARG, "block_solver must be 0 or 1");
+    if (p->block_solver == 1 && (p->sap_storage != QCD_F32 || p->learned != 0))
+        return fail(c, QCD_ERR_ARG, "block_solver 1 needs sap_storage QCD_F32 and learned 0");
     if (p->sap_ctas != 0 && p->sap_ctas != c->sap_min_ctas) {
         sap_invalidate(c);
         c->sap_min_ctas = p->sap_ctas;
@@ -315,12 +318,13 @@ int qcd_sap_precondition(qcd_ctx *c, float *out, const float *in, const qcd_para
     const bool dev_in = is_device_ptr(in), dev_out = is_device_ptr(out);
     if ((dev_in && !aligned16(in)) || (dev_out && !aligned16(out)))
         return fail(c, QCD_ERR_ARG, "device spinors must be 16-byte aligned");
-    // io: v, x (internal, nrhs each), work (2 nrhs), staging (1); all right-hand sides go
+    // io: v, x (internal, nrhs each), work (2 or 5 nrhs), staging (1); all right-hand sides go
     // through one batched SAP application
-    if ((rc = ensure_io(c, (4 * (size_t)nrhs + 1) * bytes))) return rc;
+    const int nw = sap_work_fields(p->block_solver);
+    if ((rc = ensure_io(c, ((2 + nw) * (size_t)nrhs + 1) * bytes))) return rc;
     char *io = (char *)c->d_io;
     float4 *v = (float4 *)io, *x = (float4 *)(io + nrhs * bytes), *work = (float4 *)(io + 2 * nrhs * bytes);
-    char *stage = io + 4 * nrhs * bytes;
+    char *stage = io + (2 + nw) * nrhs * bytes;
     if (dev_in) {
         if ((rc = spinor32_to_internal(c, v, (const float2 *)in, nrhs))) return rc;
     } else {
@@ -329,7 +333,7 @@ int qcd_sap_precondition(qcd_ctx *c, float *out, const float *in, const qcd_para
             if ((rc = spinor32_to_internal(c, v + k * 6 * V, (const float2 *)stage, 1))) return rc;
         }
     }
-    if ((rc = sap_apply(c, x, v, work, p->omega, p->nsweep, p->nsap, nrhs))) return rc;
+    if ((rc = sap_apply(c, x, v, work, p->omega, p->nsweep, p->nsap, nrhs, nullptr, p->block_solver))) return rc;
     if (dev_out) {
         if ((rc = spinor32_from_internal(c, (float2 *)out, x, nrhs))) return rc;
     } else {
@@ -558,6 +562,7 @@ int qcd_learned_train(qcd_ctx *c, const float *sources, int npairs, const qcd_pa
     pp.learned = 0;  // the pairs measure the error of plain SAP
     c->net.verdict = -1;
     if ((rc = check_params(c, &pp))) return rc;
+    if (pp.block_solver != 0) return fail(c, QCD_ERR_ARG, "training pairs come from the SSOR block solver (block_solver 0)");
     if ((rc = sap_prepare(c, pp.block, pp.subblock, pp.sap_storage == QCD_F16))) return rc;
     const long V = c->lat.V;
     const size_t f32 = 96 * (size_t)V, f64 = 192 * (size_t)V;

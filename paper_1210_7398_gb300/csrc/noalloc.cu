@@ -74,8 +74,9 @@ extern "C" int qcd_sap_precondition_noalloc(qcd_ctx *c, float *out, const float 
     if (!out || !in || !p) return fail(c, QCD_ERR_ARG, "qcd_sap_precondition_noalloc: NULL argument");
     if (!(p->omega > 0 && p->omega < 2) || p->nsweep < 1 || p->nsap < 1)
         return fail(c, QCD_ERR_ARG, "omega must lie in (0, 2); nsweep and nsap must be >= 1");
-    if (p->sap_storage != QCD_F32 || p->learned != 0)
-        return fail(c, QCD_ERR_ARG, "qcd_sap_precondition_noalloc supports sap_storage = QCD_F32, learned = 0");
+    if (p->sap_storage != QCD_F32 || p->learned != 0 || p->block_solver != 0)
+        return fail(c, QCD_ERR_ARG,
+                    "qcd_sap_precondition_noalloc supports sap_storage = QCD_F32, learned = 0, block_solver = 0");
     if (p->bc_t != c->bc_t || p->kappa != c->kappa || p->csw != c->csw)
         return fail(c, QCD_ERR_ARG, "params.bc_t/kappa/csw differ from the context");
     if (c->lat.V > kNoAllocMaxSites)

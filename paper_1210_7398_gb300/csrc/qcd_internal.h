@@ -222,11 +222,17 @@ int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &pla
 int sap_prepare(qcd_ctx *c, const int b[4], const int s[4], bool half);
 // drops the cached plan (it is rebuilt on next use)
 void sap_invalidate(qcd_ctx *c);
-// x = M_SAP v (FP32 internal layout, nrhs right-hand sides); work = 2 nrhs spinors; right-hand
-// sides inactive in gate (may be null) are skipped
+// x = M_SAP v (FP32 internal layout, nrhs right-hand sides); right-hand sides inactive in gate
+// (may be null) are skipped.  block_solver 0: ll-SSOR block inverses (nsweep sweeps), work = 2 nrhs
+// spinors; 1: even-odd minimal-residual block inverses (nsweep steps), work = 5 nrhs spinors
 struct BicgScalars;
 int sap_apply(qcd_ctx *c, float4 *x, const float4 *v, float4 *work, double omega, int nsweep, int nsap,
-              int nrhs = 1, const BicgScalars *gate = nullptr);
+              int nrhs = 1, const BicgScalars *gate = nullptr, int block_solver = 0);
+// the even-odd variant with an explicit plan (its block origins)
+int sap_apply_eo(qcd_ctx *c, const SapPlan &plan, float4 *x, const float4 *v, float4 *work, int nmr, int nsap,
+                 int nrhs, const BicgScalars *gate);
+// spinor fields of nrhs right-hand sides the work area of sap_apply needs
+inline int sap_work_fields(int block_solver) { return block_solver == 1 ? 5 : 2; }
 // the same with an explicit plan whose device tables and records are already in place
 int sap_apply_plan(qcd_ctx *c, const SapPlan &plan, float4 *x, const float4 *v, float4 *work, double omega,
                    int nsweep, int nsap, int nrhs = 1, const BicgScalars *gate = nullptr);

@@ -976,6 +976,170 @@ __global__ void __launch_bounds__(128) k_sap_hop(float4 *__restrict__ r, float4 
     }
 }
 
+// K3, even-odd alternative (block_solver = 1).  Sec. 3 names the even-odd site preconditioning
+// of Luescher's SAP as the block solver that the ll-SSOR outperforms at equal cost.  Site parity
+// p(n) = (n_0 + n_1 + n_2 + n_3) mod 2; H_BB links opposite parities, so D_BB x = f reduces to
+// the Schur complement on the block's even sites,
+//   Dhat = 1 - kappa^2 F_e H_eo F_o H_oe,  fhat = f_e + kappa F_e H_eo f_o,
+// solved by nmr minimal-residual steps from x_e = 0 (r = fhat; p = Dhat r;
+// alpha = <p, r> / <p, p>; x_e += alpha r; r -= alpha p), then x_o = f_o + kappa F_o H_oe x_e.
+// One CTA per block (blockIdx.x) and right-hand side (blockIdx.y).  r, p (even sites) and
+// t = F_o H_oe r (odd sites) live in lattice-sized scratch that only the block's CTA touches, so
+// __syncthreads orders the phases (and L2 holds the block's vectors); values written in this
+// launch are read back through coherent loads.
+constexpr int kEoThreads = 256;
+
+// out = F(n) sum of the in-block hops of src at site n
+template <bool COHERENT>
+__device__ __forceinline__ void block_FH(const float4 *src, const float2 *__restrict__ U,
+                                         const float4 *__restrict__ F, const Geo &g, long n, const int xc[4],
+                                         const int yl[4], const BlockGeo &bg, float2 out[12]) {
+    float2 acc[12];
+#pragma unroll
+    for (int q = 0; q < 12; q++) acc[q] = make_float2(0.f, 0.f);
+    masked_hops<true, COHERENT>(src, U, g, n, xc, yl, bg, acc);
+    float fc[72];
+    load_clover(F, g.V, n, fc);
+    clover_mul<float, float2>(fc, acc, out);
+}
+
+__global__ void __launch_bounds__(kEoThreads) k_block_eo_mr(float4 *y, const float4 *__restrict__ f, float4 *R,
+                                                            float4 *P, float4 *T, const float2 *__restrict__ U,
+                                                            const float4 *__restrict__ F, float kappa, Geo g,
+                                                            BlockGeo bg, const int *__restrict__ origin, int nmr,
+                                                            const BicgScalars *__restrict__ gate) {
+    if (gate && !gate[blockIdx.y].active) return;
+    const size_t off = (size_t)blockIdx.y * 6 * g.V;
+    y += off;
+    f += off;
+    R += off;
+    P += off;
+    T += off;
+    const int *o = origin + 4 * blockIdx.x;
+    const int par0 = (o[0] + o[1] + o[2] + o[3]) & 1;
+    __shared__ double red[3][kEoThreads / 32];
+    __shared__ float2 alpha_s;
+    // block-local site i (lexicographic): global and block-local coordinates, global index, parity
+    auto site = [&](int i, int xc[4], int yl[4]) -> long {
+        int r = i;
+        for (int m = 0; m < 4; m++) {
+            yl[m] = r % bg.b[m];
+            r /= bg.b[m];
+            xc[m] = o[m] + yl[m];
+        }
+        return xc[0] + (long)g.L[0] * (xc[1] + (long)g.L[1] * (xc[2] + (long)g.L[2] * xc[3]));
+    };
+    auto odd = [&](const int yl[4]) { return ((par0 + yl[0] + yl[1] + yl[2] + yl[3]) & 1) != 0; };
+    const float2 zero = make_float2(0.f, 0.f);
+    // r = fhat and x_e = 0 on the even sites
+    for (int i = threadIdx.x; i < bg.vol; i += blockDim.x) {
+        int xc[4], yl[4];
+        const long n = site(i, xc, yl);
+        if (odd(yl)) continue;
+        float2 h[12], v[12];
+        block_FH<false>(f, U, F, g, n, xc, yl, bg, h);
+        load_spinor(f, g.V, n, v);
+#pragma unroll
+        for (int q = 0; q < 12; q++) {
+            v[q].x = fmaf(kappa, h[q].x, v[q].x);
+            v[q].y = fmaf(kappa, h[q].y, v[q].y);
+            h[q] = zero;
+        }
+        store_spinor(R, g.V, n, v);
+        store_spinor(y, g.V, n, h);
+    }
+    __syncthreads();
+    const float k2 = kappa * kappa;
+    for (int it = 0; it < nmr; it++) {
+        // t = F_o H_oe r on the odd sites
+        for (int i = threadIdx.x; i < bg.vol; i += blockDim.x) {
+            int xc[4], yl[4];
+            const long n = site(i, xc, yl);
+            if (!odd(yl)) continue;
+            float2 h[12];
+            block_FH<true>(R, U, F, g, n, xc, yl, bg, h);
+            store_spinor(T, g.V, n, h);
+        }
+        __syncthreads();
+        // p = r - kappa^2 F_e H_eo t on the even sites, with <p, r> and <p, p>
+        float pr_re = 0.f, pr_im = 0.f, pp = 0.f;
+        for (int i = threadIdx.x; i < bg.vol; i += blockDim.x) {
+            int xc[4], yl[4];
+            const long n = site(i, xc, yl);
+            if (odd(yl)) continue;
+            float2 h[12], rv[12];
+            block_FH<true>(T, U, F, g, n, xc, yl, bg, h);
+            load_spinor_rw(R, g.V, n, rv);
+#pragma unroll
+            for (int q = 0; q < 12; q++) {
+                const float2 pv = make_float2(fmaf(-k2, h[q].x, rv[q].x), fmaf(-k2, h[q].y, rv[q].y));
+                pr_re = fmaf(pv.x, rv[q].x, fmaf(pv.y, rv[q].y, pr_re));
+                pr_im = fmaf(pv.x, rv[q].y, fmaf(-pv.y, rv[q].x, pr_im));
+                pp = fmaf(pv.x, pv.x, fmaf(pv.y, pv.y, pp));
+                h[q] = pv;
+            }
+            store_spinor(P, g.V, n, h);
+        }
+        double a0 = pr_re, a1 = pr_im, a2 = pp;
+        for (int sft = 16; sft > 0; sft >>= 1) {
+            a0 += __shfl_xor_sync(0xffffffffu, a0, sft);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, sft);
+            a2 += __shfl_xor_sync(0xffffffffu, a2, sft);
+        }
+        const int warp = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) == 0) {
+            red[0][warp] = a0;
+            red[1][warp] = a1;
+            red[2][warp] = a2;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s0 = 0, s1 = 0, s2 = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+                s0 += red[0][w];
+                s1 += red[1][w];
+                s2 += red[2][w];
+            }
+            alpha_s = s2 > 0 ? make_float2((float)(s0 / s2), (float)(s1 / s2)) : zero;
+        }
+        __syncthreads();
+        const float2 al = alpha_s;
+        // x_e += alpha r, r -= alpha p
+        for (int i = threadIdx.x; i < bg.vol; i += blockDim.x) {
+            int xc[4], yl[4];
+            const long n = site(i, xc, yl);
+            if (odd(yl)) continue;
+            float2 xv[12], rv[12], pv[12];
+            load_spinor_rw(y, g.V, n, xv);
+            load_spinor_rw(R, g.V, n, rv);
+            load_spinor_rw(P, g.V, n, pv);
+#pragma unroll
+            for (int q = 0; q < 12; q++) {
+                xv[q] = cfma(al, rv[q], xv[q]);
+                rv[q] = cfma(make_float2(-al.x, -al.y), pv[q], rv[q]);
+            }
+            store_spinor(y, g.V, n, xv);
+            store_spinor(R, g.V, n, rv);
+        }
+        __syncthreads();
+    }
+    // x_o = f_o + kappa F_o H_oe x_e
+    for (int i = threadIdx.x; i < bg.vol; i += blockDim.x) {
+        int xc[4], yl[4];
+        const long n = site(i, xc, yl);
+        if (!odd(yl)) continue;
+        float2 h[12], v[12];
+        block_FH<true>(y, U, F, g, n, xc, yl, bg, h);
+        load_spinor(f, g.V, n, v);
+#pragma unroll
+        for (int q = 0; q < 12; q++) {
+            v[q].x = fmaf(kappa, h[q].x, v[q].x);
+            v[q].y = fmaf(kappa, h[q].y, v[q].y);
+        }
+        store_spinor(y, g.V, n, v);
+    }
+}
+
 bool geometry_ok(const qcd_ctx *c, const int b[4], const int s[4]) {
     for (int m = 0; m < 4; m++) {
         if (b[m] < 1 || s[m] < 1 || c->lat.L[m] % b[m] != 0 || b[m] % s[m] != 0) return false;
@@ -1373,8 +1537,43 @@ int sap_prepare(qcd_ctx *c, const int b[4], const int s[4], bool half) {
 }
 
 int sap_apply(qcd_ctx *c, float4 *x, const float4 *v, float4 *work, double omega, int nsweep, int nsap, int nrhs,
-              const BicgScalars *gate) {
+              const BicgScalars *gate, int block_solver) {
+    if (block_solver == 1) return sap_apply_eo(c, c->plan, x, v, work, nsweep, nsap, nrhs, gate);
     return sap_apply_plan(c, c->plan, x, v, work, omega, nsweep, nsap, nrhs, gate);
+}
+
+int sap_apply_eo(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, float4 *work, int nmr, int nsap, int nrhs,
+                 const BicgScalars *gate) {
+    const long V = c->lat.V;
+    const size_t vec = 6 * (size_t)V * nrhs;  // float4 per spinor field of nrhs right-hand sides
+    float4 *r = work, *y = work + vec, *R = work + 2 * vec, *P = work + 3 * vec, *T = work + 4 * vec;
+    Geo g;
+    for (int m = 0; m < 4; m++) g.L[m] = c->lat.L[m];
+    g.V = V;
+    g.bc_t = c->bc_t;
+    BlockGeo bg;
+    for (int m = 0; m < 4; m++) bg.b[m] = p.b[m];
+    bg.vol = p.vol;
+    int rc;
+    if ((rc = blas_copy(c, r, v, sizeof(float4) * vec))) return rc;
+    if ((rc = blas_zero(c, x, sizeof(float4) * vec))) return rc;
+    for (int j = 0; j < nsap; j++) {
+        for (int col = 0; col < 2; col++) {
+            cudaEvent_t ev;
+            prof_begin(c, QCD_K_SSOR, &ev);
+            k_block_eo_mr<<<dim3(p.nblk[col], nrhs), kEoThreads, 0, c->stream>>>(
+                y, r, R, P, T, c->U32, c->F32, (float)c->kappa, g, bg, p.d_origin[col], nmr, gate);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_fail(c, e, "launch of the even-odd block kernel");
+            if ((rc = prof_end(c, QCD_K_SSOR, ev))) return rc;
+            const int last = (j == nsap - 1);
+            prof_begin(c, QCD_K_SAPHOP, &ev);
+            k_sap_hop<<<dim3((unsigned)((V + 127) / 128), nrhs), 128, 0, c->stream>>>(
+                r, x, y, c->U32, c->F32, (float)c->kappa, g, bg, col, !last, !(last && col == 1), gate);
+            if ((rc = prof_end(c, QCD_K_SAPHOP, ev))) return rc;
+        }
+    }
+    return QCD_OK;
 }
 
 int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, float4 *work, double omega, int nsweep,

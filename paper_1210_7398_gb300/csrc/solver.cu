@@ -48,13 +48,13 @@ int inner_iteration(qcd_ctx *c, const Ws &w, const qcd_params *p) {
     const int R = w.nrhs;
     TRY(scalars(c, SC_BETA, w.Si, w.red, R, p->inner_tol, nullptr));
     TRY(blas_p_update32(c, f2(w.ip), f2(w.ir), f2(w.iv), w.Si, n, R));
-    TRY(sap_apply(c, w.ipt, w.ip, w.sapw, p->omega, p->nsweep, p->nsap, R, w.Si));
+    TRY(sap_apply(c, w.ipt, w.ip, w.sapw, p->omega, p->nsweep, p->nsap, R, w.Si, p->block_solver));
     if (p->learned) TRY(learned_correct(c, w.ipt, w.ip, w.iv, reinterpret_cast<float4 *>(c->net.tmp), R));
     TRY(dslash32(c, w.iv, w.ipt, R));
     TRY(reduce32(c, RED_DOT_NORM, f2(w.irh), f2(w.iv), n, R, w.red, w.Si));
     TRY(scalars(c, SC_ALPHA, w.Si, w.red, R, p->inner_tol, nullptr));
     TRY(blas_s_update32(c, f2(w.is), f2(w.ir), f2(w.iv), w.Si, n, R));
-    TRY(sap_apply(c, w.ist, w.is, w.sapw, p->omega, p->nsweep, p->nsap, R, w.Si));
+    TRY(sap_apply(c, w.ist, w.is, w.sapw, p->omega, p->nsweep, p->nsap, R, w.Si, p->block_solver));
     if (p->learned) TRY(learned_correct(c, w.ist, w.is, w.it, reinterpret_cast<float4 *>(c->net.tmp), R));
     TRY(dslash32(c, w.it, w.ist, R));
     TRY(reduce32(c, RED_DOT_NORMA, f2(w.it), f2(w.is), n, R, w.red, w.Si));
@@ -152,11 +152,11 @@ int ensure(qcd_ctx *c, void **ptr, size_t *have, size_t need) {
     return QCD_OK;
 }
 
-int workspace(qcd_ctx *c, int nrhs, Ws *w) {
+int workspace(qcd_ctx *c, int nrhs, int block_solver, Ws *w) {
     const long V = c->lat.V;
     const size_t b64 = sizeof(double2) * 12 * V * nrhs, b32 = sizeof(float4) * 6 * V * nrhs;
     TRY(ensure(c, &c->ws64, &c->ws64_bytes, 11 * b64));
-    TRY(ensure(c, &c->ws32, &c->ws32_bytes, 12 * b32));
+    TRY(ensure(c, &c->ws32, &c->ws32_bytes, (10 + sap_work_fields(block_solver)) * b32));
     if (c->red_rhs < nrhs) {
         dev_free(c, c->d_red);
         dev_free(c, c->d_scalars);
@@ -186,7 +186,7 @@ int workspace(qcd_ctx *c, int nrhs, Ws *w) {
     for (int k = 0; k < 11; k++) *v64[k] = base + (size_t)k * 12 * V * nrhs;
     float4 *b32p = (float4 *)c->ws32;
     float4 **v32[] = {&w->q, &w->y, &w->ir, &w->irh, &w->ip, &w->iv, &w->is, &w->it, &w->ipt, &w->ist, &w->sapw};
-    for (int k = 0; k < 11; k++) *v32[k] = b32p + (size_t)k * 6 * V * nrhs;  // sapw spans two: r, y
+    for (int k = 0; k < 11; k++) *v32[k] = b32p + (size_t)k * 6 * V * nrhs;  // sapw spans the SAP work fields
     w->So = (BicgScalars *)c->d_bicg;
     w->Si = w->So + nrhs;
     w->hSo = (BicgScalars *)c->h_bicg;
@@ -201,7 +201,7 @@ int workspace(qcd_ctx *c, int nrhs, Ws *w) {
 
 int solve(qcd_ctx *c, double2 *x, const double2 *b, const qcd_params *p, int nrhs, qcd_stats *st) {
     Ws w;
-    TRY(workspace(c, nrhs, &w));
+    TRY(workspace(c, nrhs, p->block_solver, &w));
     const long n = 12 * w.V;
     const size_t b64 = sizeof(double2) * n * nrhs;
     const int R = nrhs;

@@ -121,6 +121,7 @@ extern "C" int qcd_autotune(qcd_ctx *c, const double *b, int nrhs, const qcd_par
                 std::memcpy(cd.p.subblock, sub, sizeof(sub));
                 cd.p.sap_storage = QCD_F32;
                 cd.p.sap_ctas = 0;
+                cd.p.block_solver = 0;  // the tuner explores the ll-SSOR set-ups
                 cands.push_back(cd);
             }
         }

@@ -368,6 +368,57 @@ def test_sap_lane_forms_identical(case):
     s.close()
 
 
+EO_CASES = [
+    # dims, block, MR steps, N_SAP
+    ((4, 4, 4, 4), (2, 2, 2, 2), 3, 2),
+    ((8, 8, 8, 8), (4, 4, 4, 4), 5, 2),
+    ((12, 12, 12, 24), (6, 6, 6, 12), 7, 2),
+    ((12, 12, 12, 24), (3, 3, 3, 6), 4, 3),  # blocks with unequal even and odd site counts
+]
+
+
+@pytest.mark.parametrize("case", EO_CASES, ids=lambda c: "x".join(map(str, c[0])) + "-" + "x".join(map(str, c[1])))
+def test_sap_even_odd_block_solver_vs_oracle(case):
+    """The even-odd minimal-residual block inverse (block_solver = 1) against the oracle's,
+    and two right-hand sides in one call equal to single calls bit for bit."""
+    dims, b, nmr, nsap = case
+    kappa = 0.12
+    s, U, F = make_solver(dims, kappa, seed=1009)
+    v = qi.gaussian_spinor(dims, seed=2009, nrhs=2)
+    ref = oracle.sap(dims, U, F, kappa, b, (1, 1, 1, 1), 1.0, nmr, nsap, v[0], block_solver=1)
+    prm = q.make_params(kappa, CSW, b, (1, 1, 1, 1), nsweep=nmr, nsap=nsap, block_solver=1)
+    vin = torch.from_numpy(v.astype(np.complex64)).cuda()
+    out = torch.empty_like(vin)
+    s.sap_precondition(out, vin, prm, nrhs=2)
+    one = torch.empty_like(vin[:1])
+    s.sap_precondition(one, vin[1:].contiguous(), prm)
+    torch.cuda.synchronize()
+    assert rel_norm(out[0].cpu().numpy().astype(np.complex128), ref) <= 1e-5
+    assert torch.equal(one[0], out[1])
+    # it is a different block inverse from the SSOR one
+    ssor = oracle.sap(dims, U, F, kappa, b, (1, 1, 1, 1), 1.0, nmr, nsap, v[0])
+    assert rel_norm(ssor, ref) > 1e-3
+    s.close()
+
+
+def test_solve_with_even_odd_block_solver():
+    dims, block = (12, 12, 12, 24), (6, 6, 6, 12)
+    kappa = 0.12
+    s, U, F = make_solver(dims, kappa, seed=1001)
+    b = qi.gaussian_spinor(dims, seed=2001)
+    prm = q.make_params(kappa, CSW, block, (3, 3, 3, 6), nsweep=7, nsap=4, tol=1e-10, block_solver=1)
+    x = torch.zeros(b.shape, dtype=torch.complex128, device="cuda")
+    st = s.solve(x, torch.from_numpy(b).cuda(), prm)
+    r = b[0] - oracle.apply_D(dims, U, F, kappa, x.cpu().numpy()[0])
+    assert np.linalg.norm(r) / np.linalg.norm(b[0]) <= 1e-10, st
+    for bad in (q.make_params(kappa, CSW, block, (3, 3, 3, 6), block_solver=2),
+                q.make_params(kappa, CSW, block, (3, 3, 3, 6), block_solver=1, sap_storage=q.QCD_F16)):
+        with pytest.raises(q.QcdError) as e:
+            s.solve(x, torch.from_numpy(b).cuda(), bad)
+        assert e.value.code == q.QCD_ERR_ARG
+    s.close()
+
+
 def test_solve_with_fp16_sap_reaches_fp64_tolerance():
     dims, block, sub = (12, 12, 12, 24), (6, 6, 6, 12), (3, 3, 3, 6)
     kappa = 0.12

@@ -277,3 +277,108 @@ def test_nested_bicgstab_matches_dense_lu(field44, case):
     r = src.reshape(-1) - Dm @ x.reshape(-1)
     assert np.linalg.norm(r) / np.linalg.norm(src) <= 1e-10
     assert np.linalg.norm(x.reshape(-1) - exact) / np.linalg.norm(exact) <= 1e-9
+
+
+# ---------------------------------------------------------------------------
+# even-odd minimal-residual block inverse (the alternative block solver that
+# Sec. 3 compares ll-SSOR with): pinned to the dense D of the 4^4 lattice
+# ---------------------------------------------------------------------------
+
+def parity_dof(dims):
+    return np.repeat(site_coords(dims).sum(axis=1) % 2, 12)
+
+
+def colour1_blocks(dims, b):
+    nb = [dims[m] // b[m] for m in range(4)]
+    return [B for B in itertools.product(*[range(n) for n in nb]) if sum(B) % 2 == 1]
+
+
+def test_eo_mr_odd_rows_exact_and_residual_monotone(field44):
+    """The odd sites are solved exactly after any number of steps (x_o is rebuilt from
+    x_e), and the block residual, which then lives on the even sites, never grows."""
+    dims, U, F, Dm = field44
+    b = (2, 2, 2, 2)
+    f = qi.gaussian_spinor(dims, seed=11)[0]
+    fl = f.reshape(-1)
+    col = np.repeat(oracle.colours(dims, b), 12)
+    par = parity_dof(dims)
+    prev = np.inf
+    for nmr in (1, 2, 3, 5, 8, 13):
+        x = oracle.eo_mr(dims, U, F, KAPPA, b, nmr, 1, f).reshape(-1)
+        assert np.all(x[col == 0] == 0)  # other colour untouched
+        res = fl - Dm @ np.where(col == 1, x, 0)  # blocks of one colour are not neighbours
+        assert np.abs(res[(col == 1) & (par == 1)]).max() < 1e-12 * np.abs(fl).max()
+        e = np.linalg.norm(res[col == 1])
+        assert e <= prev * (1 + 1e-12)
+        prev = e
+    assert prev < 0.5 * np.linalg.norm(fl[col == 1])
+
+
+def test_eo_mr_one_step_is_the_least_squares_step(field44):
+    """One step: x_e = alpha fhat with alpha minimising |fhat - alpha S fhat| for the
+    Schur complement S = 1 - D_eo D_oe of each dense block (D_ee = D_oo = 1)."""
+    dims, U, F, Dm = field44
+    b = (2, 2, 2, 2)
+    f = qi.gaussian_spinor(dims, seed=12)[0]
+    fl = f.reshape(-1)
+    x = oracle.eo_mr(dims, U, F, KAPPA, b, 1, 1, f).reshape(-1)
+    par = parity_dof(dims)
+    for B in colour1_blocks(dims, b):
+        idx = dof(block_sites_ll(dims, b, B, (1, 1, 1, 1)))
+        ev, od = idx[par[idx] == 0], idx[par[idx] == 1]
+        assert np.abs(Dm[np.ix_(ev, ev)] - np.eye(len(ev))).max() < 1e-15
+        Deo, Doe = Dm[np.ix_(ev, od)], Dm[np.ix_(od, ev)]
+        S = np.eye(len(ev)) - Deo @ Doe
+        fhat = fl[ev] - Deo @ fl[od]
+        alpha = np.linalg.lstsq((S @ fhat)[:, None], fhat, rcond=None)[0][0]
+        xe = alpha * fhat
+        assert np.abs(x[ev] - xe).max() < 1e-12 * np.abs(xe).max()
+        xo = fl[od] - Doe @ xe
+        assert np.abs(x[od] - xo).max() < 1e-12 * np.abs(xo).max()
+
+
+def test_eo_mr_converges_to_block_inverse(field44):
+    dims, U, F, Dm = field44
+    b = (2, 2, 2, 2)
+    f = qi.gaussian_spinor(dims, seed=13)[0]
+    fl = f.reshape(-1)
+    x = oracle.eo_mr(dims, U, F, KAPPA, b, 80, 1, f).reshape(-1)
+    for B in colour1_blocks(dims, b):
+        idx = dof(block_sites_ll(dims, b, B, (1, 1, 1, 1)))
+        exact = np.linalg.solve(Dm[np.ix_(idx, idx)], fl[idx])
+        assert np.abs(x[idx] - exact).max() < 1e-10 * np.abs(exact).max()
+
+
+def test_sap_with_eo_blocks_limit_equals_ssor_limit(field44):
+    """With many steps both block solvers give the exact block inverse, so the two SAP
+    variants agree; with few steps they differ."""
+    dims, U, F, Dm = field44
+    b, s = (2, 2, 2, 2), (1, 1, 1, 1)
+    v = qi.gaussian_spinor(dims, seed=14)[0]
+    a = oracle.sap(dims, U, F, KAPPA, b, s, 1.0, 80, 2, v, block_solver=1)
+    c = oracle.sap(dims, U, F, KAPPA, b, s, 1.0, 60, 2, v, block_solver=0)
+    assert np.abs(a - c).max() < 1e-10 * np.abs(c).max()
+    a2 = oracle.sap(dims, U, F, KAPPA, b, s, 1.0, 2, 2, v, block_solver=1)
+    assert np.abs(a2 - c).max() > 1e-4 * np.abs(c).max()
+
+
+def test_eo_mr_larger_blocks_matrix_free():
+    """4^4 blocks of an 8^4 lattice (and 3^3 x 6 blocks of 6^3 x 12, where a block holds
+    unequal numbers of even and odd sites): odd rows exact, residual non-increasing,
+    checked with the block-restricted operator."""
+    for dims, b in (((8, 8, 8, 8), (4, 4, 4, 4)), ((6, 6, 6, 12), (3, 3, 3, 6))):
+        U = qi.gauge_field(dims, 0.3, seed=1002)
+        _, F = oracle.clover(dims, U, CSW, KAPPA)
+        f = qi.gaussian_spinor(dims, seed=15)[0]
+        col = np.repeat(oracle.colours(dims, b), 12)
+        par = parity_dof(dims)
+        prev = np.inf
+        for nmr in (1, 3, 9, 27):
+            x = oracle.eo_mr(dims, U, F, KAPPA, b, nmr, 0, f)
+            Dx = oracle.apply_D_colour(dims, U, F, KAPPA, b, 0, 0, x).reshape(-1)
+            res = (f.reshape(-1) - Dx)[col == 0]
+            assert np.abs(res[par[col == 0] == 1]).max() < 1e-12 * np.abs(f).max()
+            e = np.linalg.norm(res)
+            assert e <= prev * (1 + 1e-12)
+            prev = e
+        assert prev < 0.1 * np.linalg.norm(f.reshape(-1)[col == 0])
