@@ -660,7 +660,7 @@ def run_gpu_on_stream(args, q, qi, torch, np, peaks, rank, world, local):
         # the learned correction on top of the chosen set-up; kept only when it is faster
         lr_sec = learned_section(q, qi, torch, s, dims, best, bd, 1, 64, 8)
         chosen["learned"] = lr_sec
-        if lr_sec["verdict"]["use_learned"]:
+        if lr_sec["verdict"]["use_learned"] and lr_sec["verdict"]["learned_ms"] < chosen["value"] * 1000.0:
             chosen["value"] = lr_sec["verdict"]["learned_ms"] / 1000.0
             chosen["params"]["learned"] = 1
             chosen["speedup_vs_plain"] = ms_step / lr_sec["verdict"]["learned_ms"]

@@ -138,6 +138,18 @@ int ensure_io(qcd_ctx *c, size_t bytes) {
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
+}  // namespace
+
+void qcd::use_sap_ctas(qcd_ctx *c, int sap_ctas) {
+    const int eff = sap_ctas != 0 ? sap_ctas : c->sap_ctas_user;
+    if (eff != c->sap_min_ctas) {
+        sap_invalidate(c);
+        c->sap_min_ctas = eff;
+    }
+}
+
+namespace {
+
 int check_params(qcd_ctx *c, const qcd_params *p) {
     if (!p) return fail(c, QCD_ERR_ARG, "params is NULL");
     if (!(p->omega > 0 && p->omega < 2)) return fail(c, QCD_ERR_ARG, "omega must lie in (0, 2)");
@@ -153,10 +165,7 @@ int check_params(qcd_ctx *c, const qcd_params *p) {
     if (p->block_solver < 0 || p->block_solver > 1) return fail(c, QCD_ERR_ARG, "block_solver must be 0 or 1");
     if (p->block_solver == 1 && (p->sap_storage != QCD_F32 || p->learned != 0))
         return fail(c, QCD_ERR_ARG, "block_solver 1 needs sap_storage QCD_F32 and learned 0");
-    if (p->sap_ctas != 0 && p->sap_ctas != c->sap_min_ctas) {
-        sap_invalidate(c);
-        c->sap_min_ctas = p->sap_ctas;
-    }
+    use_sap_ctas(c, p->sap_ctas);
     return QCD_OK;
 }
 
@@ -440,8 +449,8 @@ int qcd_set_sap_ctas(qcd_ctx *c, int min_ctas) {
     if (rc) return rc;
     if (min_ctas < -1 || min_ctas > 16) return fail(c, QCD_ERR_ARG, "min_ctas must lie in -1..16");
     QCD_CUDA(c, c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
-    if (c->sap_min_ctas != min_ctas) sap_invalidate(c);
-    c->sap_min_ctas = min_ctas;
+    c->sap_ctas_user = min_ctas;
+    use_sap_ctas(c, 0);
     return QCD_OK;
 }
 

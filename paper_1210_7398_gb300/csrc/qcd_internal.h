@@ -138,6 +138,7 @@ struct qcd_ctx {
     qcd::Learned net;
     long field_version = 0;  // bumped whenever the links or the clover field change
     int sap_min_ctas = 0;    // lower bound on the CTAs (cluster size) per SAP block; 0: fill the SMs
+    int sap_ctas_user = 0;   // the qcd_set_sap_ctas setting, which params with sap_ctas = 0 use
     int sap_form = 0;        // SSOR lanes per site update: 0 by occupancy, 1 warp form (32), 2 octet form (8)
 
     // workspace, grown on demand
@@ -213,6 +214,10 @@ int dslash64(qcd_ctx *c, double2 *out, const double2 *in, int nrhs);
 int dslash32(qcd_ctx *c, float4 *out, const float4 *in, int nrhs);
 int dslash16(qcd_ctx *c, float4 *out, const float4 *in, int nrhs);
 int dslash12(qcd_ctx *c, float4 *out, const float4 *in, int nrhs);
+
+// SSOR form for a call whose params carry sap_ctas (0: the context's qcd_set_sap_ctas setting);
+// rebuilds the SAP plan when it changes (api.cu)
+void use_sap_ctas(qcd_ctx *c, int sap_ctas);
 
 // SAP (sap.cu)
 // host part of a plan (tables in h_*; device pointers left null); QCD_ERR_ARG on bad geometry

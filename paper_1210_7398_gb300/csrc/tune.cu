@@ -30,15 +30,10 @@ bool valid_block(const qcd_ctx *c, const int b[4], const int s[4]) {
 // time one complete solve (x0 = 0) of the internal-layout right-hand sides bi
 int time_solve(qcd_ctx *c, double2 *xi, const double2 *bi, int nrhs, const qcd_params *p, double *ms, bool *ok) {
     *ok = false;
-    const int old_ctas = c->sap_min_ctas;
-    if (p->sap_ctas != 0 && p->sap_ctas != c->sap_min_ctas) {
-        sap_invalidate(c);
-        c->sap_min_ctas = p->sap_ctas;
-    }
+    use_sap_ctas(c, p->sap_ctas);  // sap_ctas 0: the context's setting, not the last candidate's
     int rc = sap_prepare(c, p->block, p->subblock, p->sap_storage == QCD_F16);
     if (rc == QCD_ERR_ARG) {  // geometry does not fit: not a candidate
         c->err.clear();
-        c->sap_min_ctas = old_ctas;
         return QCD_OK;
     }
     if (rc) return rc;
@@ -95,7 +90,6 @@ extern "C" int qcd_autotune(qcd_ctx *c, const double *b, int nrhs, const qcd_par
     cudaGetLastError();
     QCD_CUDA(c, cudaMemcpyAsync(stage, b, bytes, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     if ((rc = spinor64_to_internal(c, bi, stage, nrhs))) return rc;
-    const int old_ctas = c->sap_min_ctas;
     const bool old_prof = c->prof.on;
     c->prof.on = false;
 
@@ -179,10 +173,7 @@ extern "C" int qcd_autotune(qcd_ctx *c, const double *b, int nrhs, const qcd_par
         cands.insert(cands.end(), more.begin(), more.end());
     }
     c->prof.on = old_prof;
-    if (c->sap_min_ctas != old_ctas) {
-        sap_invalidate(c);
-        c->sap_min_ctas = old_ctas;
-    }
+    use_sap_ctas(c, 0);
     if (rc) return rc;
     const Cand *win = nullptr;
     for (auto &cd : cands)
