@@ -328,7 +328,6 @@ __global__ void __launch_bounds__(kLayerWarps * 32, FIN == SITE32 ? 1 : 2) k_lay
     int *nbt = reinterpret_cast<int *>(ly_smem + 2 * S::stage + S::a_bytes);  // [9][64] neighbour, -1 past the end
     float *sgt = reinterpret_cast<float *>(nbt + 9 * kLayerSites);            // [9][64] boundary sign
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gq = lane >> 2, tq = lane & 3;
-    const int V = (int)g.V;
     const int n0 = blockIdx.x * kLayerSites;
 
     layer_neighbours(nbt, sgt, g, n0, tid);
@@ -611,8 +610,9 @@ __global__ void k_wgrad_finish(float2 *__restrict__ grad, const float *__restric
     grad[i].y += 2.f * (ri - ir);
 }
 
-// r = a - b (plane layout FP32, 6 float4 per site)
-__global__ void k_sub_plane(float4 *__restrict__ r, const float4 *__restrict__ a, const float4 *__restrict__ b, long n) {
+// r = a - b (plane layout FP32, 6 float4 per site); r may be b (each element is read and
+// written by one thread)
+__global__ void k_sub_plane(float4 *r, const float4 *a, const float4 *b, long n) {
     const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float4 x = a[i], y = b[i];

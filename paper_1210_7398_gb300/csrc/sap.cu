@@ -307,7 +307,6 @@ __global__ void __launch_bounds__(32 * MAXW) k_ssor_warp(SsorArgs a) {
     }
     // ---- lane constants of the clover phase: lane (s, c), s = lane >> 3, holds spin s ----
     const int so = lane >> 3;
-    const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0;
     const int fch = so >> 1, fk = (so & 1) * 3 + (c < 3 ? c : 0);
     const int frow = L::F + (36 * fch + 6 * fk) * L::cw;  // this lane's row of the chiral block
     const bool owner = c < 3 && (lane & 4) == 0;         // one lane per (spin, colour) stores

@@ -48,3 +48,21 @@ def test_null_context_is_rejected(lib):
     q.load_library()
     assert q.load_library().qcd_set_boundary(None, 1) == q.QCD_ERR_ARG
     assert q.load_library().qcd_launch_count(None) == 0
+
+
+def test_plain_c_client(lib, tmp_path):
+    """include/qcd.h compiles as C99 with warnings as errors; a C program linked against the
+    library sees the struct layouts the binding mirrors and gets argument errors, not crashes."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    libdir = os.path.dirname(qbuild.LIB)
+    exe = str(tmp_path / "abi_check")
+    subprocess.check_call([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                           os.path.join(ROOT, "tests", "c", "abi_check.c"), "-L", libdir, "-lqcd",
+                           "-Wl,-rpath," + libdir, "-o", exe])
+    res = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert res.returncode == 0, res.stderr
+    assert res.stdout.strip() == "ok"

@@ -453,6 +453,31 @@ def test_batched_point_sources_equal_single_solves():
     s.close()
 
 
+def test_non_finite_rhs_is_reported_and_isolated():
+    """A right-hand side holding a NaN (a fault made on the host) never enters the iteration:
+    the call reports QCD_ERR_NOCONV, the other right-hand sides of the batch still reach 1e-10
+    under the oracle's D, and the context stays usable."""
+    dims, kappa = (8, 8, 8, 8), 0.12
+    s, U, F = make_solver(dims, kappa, seed=1010)
+    b = qi.gaussian_spinor(dims, seed=2010, nrhs=3)
+    b[1, 5, 2, 1] = np.nan
+    prm = q.make_params(kappa, CSW, (4, 4, 4, 4), (2, 2, 2, 2), tol=1e-10)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    st = s.solve(x, bd, prm, nrhs=3, check=False)
+    assert st["status"] == q.QCD_ERR_NOCONV, st
+    xs = x.cpu().numpy()
+    for k in (0, 2):
+        assert np.all(np.isfinite(xs[k]))
+        r = b[k] - oracle.apply_D(dims, U, F, kappa, xs[k])
+        assert np.linalg.norm(r) / np.linalg.norm(b[k]) <= 1e-10
+    x1 = torch.zeros_like(bd[:1])
+    st1 = s.solve(x1, bd[2:].contiguous(), prm)
+    assert st1["status"] == q.QCD_OK
+    assert torch.equal(x1[0], x[2])  # batched = single, also next to a failed right-hand side
+    s.close()
+
+
 def test_graph_replay_equals_direct_launches():
     """The inner iteration replayed as a CUDA graph (non-default stream) gives the
     same solution, bitwise, as direct launches."""
