@@ -67,7 +67,9 @@ enum {
     QCD_ERR_CUDA = -2,      /* a CUDA runtime call failed; the context is poisoned    */
     QCD_ERR_OOM = -3,       /* device allocation failed                               */
     QCD_ERR_SINGULAR = -4,  /* a chiral 6x6 block of the clover term is not invertible */
-    QCD_ERR_NOCONV = -5,    /* max_outer reached; x holds the last iterate            */
+    QCD_ERR_NOCONV = -5,    /* max_outer reached (x holds the last iterate), or a
+                               right-hand side holds a non-finite value (that one is
+                               not iterated; the others are solved as usual)        */
     QCD_ERR_BREAKDOWN = -6, /* BiCGStab breakdown not cured by 5 restarts             */
     QCD_ERR_TIMEOUT = -7,   /* a bounded device-side wait gave up                     */
     QCD_ERR_STATE = -8      /* wrong call order, or context poisoned by a CUDA error  */

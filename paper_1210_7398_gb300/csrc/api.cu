@@ -402,7 +402,7 @@ int qcd_solve(qcd_ctx *c, double *x, const double *b, const qcd_params *p, int n
     local.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (st) *st = local;
     if (status != QCD_OK) {
-        if (status == QCD_ERR_NOCONV) c->err = "not converged within max_outer";
+        if (status == QCD_ERR_NOCONV) c->err = "not converged within max_outer (or a right-hand side is not finite)";
         else if (status == QCD_ERR_BREAKDOWN) c->err = "BiCGStab breakdown not cured by restarts";
     }
     return status;

@@ -258,10 +258,12 @@ int solve(qcd_ctx *c, double2 *x, const double2 *b, const qcd_params *p, int nrh
         QCD_CUDA(c, cudaMemcpyAsync(h.data(), w.red, sizeof(double) * 3 * R, cudaMemcpyDeviceToHost, c->stream));
         QCD_CUDA(c, cudaStreamSynchronize(c->stream));
         for (int k = 0; k < R; k++)
-            if (hmask[k]) relres[k] = bn2[k] > 0 ? std::sqrt(h[3 * k + 2] / bn2[k]) : 0.0;
+            if (hmask[k])
+                relres[k] = !std::isfinite(bn2[k]) ? INFINITY : bn2[k] > 0 ? std::sqrt(h[3 * k + 2] / bn2[k]) : 0.0;
         return QCD_OK;
     };
-    // rhs with b = 0 are solved by x = 0; rhs whose initial residual is small enough are done
+    // rhs with b = 0 are solved by x = 0; rhs whose initial residual is small enough are done;
+    // rhs holding a non-finite value are settled (not converged) at once
     {
         bool any = false;
         TRY(any_active(c, w, w.So, w.hSo, &any, nullptr));
@@ -269,7 +271,7 @@ int solve(qcd_ctx *c, double2 *x, const double2 *b, const qcd_params *p, int nrh
             w.hmask[k] = 0;
             if (bn2[k] == 0) {
                 status[k] = QCD_OK;
-            } else if (!w.hSo[k].active || w.hSo[k].rn2 <= p->tol * p->tol * bn2[k]) {
+            } else if (!std::isfinite(bn2[k]) || !w.hSo[k].active || w.hSo[k].rn2 <= p->tol * p->tol * bn2[k]) {
                 w.hmask[k] = 1;
             }
         }
@@ -284,7 +286,10 @@ int solve(qcd_ctx *c, double2 *x, const double2 *b, const qcd_params *p, int nrh
             std::vector<int> restart(R, 0);
             for (int k = 0; k < R; k++) {
                 if (!w.hmask[k]) continue;
-                if (relres[k] <= p->tol) {
+                if (!std::isfinite(bn2[k])) {  // never iterated, never reported converged
+                    status[k] = QCD_ERR_NOCONV;
+                    h_active[k] = 0;
+                } else if (relres[k] <= p->tol) {
                     status[k] = QCD_OK;
                     h_active[k] = 0;
                 } else if (++restarts[k] > 5 || outer >= p->max_outer) {
