@@ -166,7 +166,9 @@ int qcd_sap_precondition(qcd_ctx *ctx, float *out, const float *in, const qcd_pa
  * this instead of qcd_sap_precondition.
  *
  * out = M_SAP in, exactly as qcd_sap_precondition with nrhs = 1, for device
- * pointers only (16-byte aligned complex64 [V][4][3]).  It calls no
+ * pointers only (16-byte aligned complex64 [V][4][3]), with
+ * p->sap_storage = QCD_F32, p->learned = 0 and p->block_solver = 0 (others
+ * are rejected with QCD_ERR_ARG).  It calls no
  * cudaMalloc, cudaFree or allocating library routine: its scratch (four FP32
  * spinor fields, the per-site SSOR records and the ll-schedule tables) is one
  * fixed __device__ array of about 68.3 MB that every GPU loading the library
