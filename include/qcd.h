@@ -233,6 +233,29 @@ int qcd_set_sap_ctas(qcd_ctx *ctx, int min_ctas);
  * identical bit for bit.  QCD_ERR_ARG outside 0..2. */
 int qcd_set_sap_form(qcd_ctx *ctx, int form);
 
+/* Diagnostic, host only (needs no GPU and no context): the schedule of the
+ * SSOR block kernel that a context with these lattice extents would run for
+ * SAP blocks `block` with ll sub-blocks `subblock` (Sec. 3), sap_ctas as in
+ * qcd_set_sap_ctas, half = 1 for FP16 storage, planned for an SM count `sms`
+ * (the automatic cluster width depends on it; GB300: 152).  Every site of a
+ * block has a dependency level (a site's level is one more than the highest
+ * level of its in-block neighbours earlier in the ll order); each CTA of the
+ * block's cluster owns some sites of every level; each level is cut into
+ * chunks (timeline steps of the forward pass; the backward pass runs them in
+ * reverse, step 2 nchunks - 1 - c for chunk c), and a barrier flag before a
+ * step orders the steps that exchange data (1: CTA barrier, 2: cluster
+ * barrier).  meta[8] receives: sites per block, levels, CTAs per block (C),
+ * chunks, most sites of one CTA in one chunk, most sites one CTA owns,
+ * thread form (0/1), shared memory bytes per CTA.  The arrays, each NULL or
+ * sized as stated, receive per block-local site (lexicographic, x fastest;
+ * meta[0] entries): its level, its owning CTA, its offset in that CTA's slab
+ * of the block spinor, its chunk; and flags[2 * meta[3]] per timeline step.
+ * Call with NULL arrays first to learn the sizes.  QCD_ERR_ARG for a
+ * geometry the library rejects. */
+int qcd_sap_plan_tables(const int dims[4], const int block[4], const int subblock[4], int sap_ctas, int half,
+                        int sms, int meta[8], int *level, int *owner, int *slot, int *chunk,
+                        unsigned char *flags);
+
 /* Autotuner (no counterpart in the paper, which fixes 6^4 blocks with 3^4
  * sub-blocks).  Starting from *base (kappa, csw, tol, inner_tol, bc_t, limits),
  * times complete solves of D x = b from x0 = 0 for candidate SAP set-ups and

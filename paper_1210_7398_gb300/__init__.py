@@ -26,7 +26,7 @@ KERNEL_CLASSES = ("dslash32", "dslash64", "ssor", "saphop", "blas", "other", "le
 EXPORTS = ("qcd_create", "qcd_destroy", "qcd_last_error", "qcd_set_boundary", "qcd_load_gauge",
            "qcd_build_clover", "qcd_apply_D", "qcd_sap_precondition", "qcd_solve", "qcd_set_profiling",
            "qcd_kernel_stats", "qcd_launch_count", "qcd_bench_dslash", "qcd_sap_precondition_noalloc",
-           "qcd_set_sap_ctas", "qcd_set_sap_form", "qcd_set_graphs", "qcd_autotune", "qcd_learned_weight_count",
+           "qcd_set_sap_ctas", "qcd_set_sap_form", "qcd_sap_plan_tables", "qcd_set_graphs", "qcd_autotune", "qcd_learned_weight_count",
            "qcd_learned_set_weights", "qcd_learned_get_weights", "qcd_learned_apply", "qcd_learned_loss_grad",
            "qcd_learned_train", "qcd_learned_evaluate", "qcd_solve_multi")
 
@@ -93,6 +93,7 @@ def load_library(path: str = LIB_PATH):
         "qcd_set_profiling": (I, [P, I]),
         "qcd_set_sap_ctas": (I, [P, I]),
         "qcd_set_sap_form": (I, [P, I]),
+        "qcd_sap_plan_tables": (I, [P, P, P, I, I, I, P, P, P, P, P, P]),
         "qcd_set_graphs": (I, [P, I]),
         "qcd_learned_weight_count": (ctypes.c_long, []),
         "qcd_learned_set_weights": (I, [P, P, ctypes.c_long]),
@@ -215,6 +216,31 @@ def qcd_solve_multi(ctxs, xs, bs, params, nrhs, check: bool = True):
 
 def qcd_set_sap_ctas(ctx, min_ctas: int):
     return _check(ctx, load_library().qcd_set_sap_ctas(ctx, int(min_ctas)))
+
+
+def qcd_sap_plan_tables(dims, block, subblock, sap_ctas: int = 0, half: bool = False, sms: int = 152) -> dict:
+    """The SSOR schedule for a geometry (host only, no GPU): meta counts and per-site arrays
+    (level, owner, slot, chunk; block-local lexicographic order) and the per-step barrier flags."""
+    import numpy as np
+    L = load_library()
+    iv = lambda v: (ctypes.c_int * 4)(*[int(x) for x in v])
+    meta = (ctypes.c_int * 8)()
+    rc = L.qcd_sap_plan_tables(iv(dims), iv(block), iv(subblock), int(sap_ctas), int(bool(half)), int(sms), meta,
+                               None, None, None, None, None)
+    if rc != QCD_OK:
+        raise QcdError(rc, "qcd_sap_plan_tables: geometry rejected")
+    vol, nch = meta[0], meta[3]
+    arrs = [np.empty(vol, dtype=np.int32) for _ in range(4)]
+    flags = np.empty(2 * nch, dtype=np.uint8)
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    rc = L.qcd_sap_plan_tables(iv(dims), iv(block), iv(subblock), int(sap_ctas), int(bool(half)), int(sms), meta,
+                               *[ptr(a) for a in arrs], ptr(flags))
+    if rc != QCD_OK:
+        raise QcdError(rc, "qcd_sap_plan_tables: geometry rejected")
+    names = ("vol", "levels", "ctas", "chunks", "nslot", "slab_vol", "thread", "smem_bytes")
+    out = {k: int(meta[i]) for i, k in enumerate(names)}
+    out.update(level=arrs[0], owner=arrs[1], slot=arrs[2], chunk=arrs[3], flags=flags)
+    return out
 
 
 def qcd_set_sap_form(ctx, form: int):

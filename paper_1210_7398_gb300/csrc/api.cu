@@ -462,6 +462,38 @@ int qcd_set_sap_form(qcd_ctx *c, int form) {
     return QCD_OK;
 }
 
+int qcd_sap_plan_tables(const int dims[4], const int block[4], const int subblock[4], int sap_ctas, int half, int sms,
+                        int meta[8], int *level, int *owner, int *slot, int *chunk, unsigned char *flags) {
+    if (!dims || !block || !subblock || !meta || sap_ctas < -1 || sap_ctas > 16 || sms < 1) return QCD_ERR_ARG;
+    qcd_ctx c;  // host-side planning only: no device, stream or allocation is touched
+    c.lat.V = 1;
+    for (int m = 0; m < 4; m++) {
+        if (dims[m] < 2) return QCD_ERR_ARG;
+        c.lat.L[m] = dims[m];
+        c.lat.V *= dims[m];
+    }
+    c.sms_override = sms;
+    SapPlan p;
+    if (sap_plan_host(&c, block, subblock, p, sap_ctas, half != 0) != QCD_OK) return QCD_ERR_ARG;
+    const int vals[8] = {p.vol, p.nsteps, p.C, p.nchunks, p.nslot, p.slab_vol, p.thread ? 1 : 0, (int)p.smem_bytes};
+    for (int k = 0; k < 8; k++) meta[k] = vals[k];
+    for (int st = 0; st < p.nsteps; st++)
+        for (int k = p.h_step_ptr[st]; k < p.h_step_ptr[st + 1]; k++)
+            if (level) level[p.h_step_site[k]] = st;
+    for (int yl = 0; yl < p.vol; yl++) {
+        if (owner) owner[yl] = p.thread ? 0 : p.h_own[yl] >> 24;
+        if (slot) slot[yl] = p.thread ? yl : p.h_own[yl] & 0xffffff;
+    }
+    const int nct = p.thread ? 1 : p.C;
+    for (int r = 0; r < nct; r++)
+        for (int ch = 0; ch < p.nchunks; ch++)
+            for (int k = p.h_chunk_ptr[r * (p.nchunks + 1) + ch]; k < p.h_chunk_ptr[r * (p.nchunks + 1) + ch + 1]; k++)
+                if (chunk) chunk[p.h_chunk_site[k]] = ch;
+    if (flags)
+        for (int k = 0; k < 2 * p.nchunks; k++) flags[k] = p.h_flags[k];
+    return QCD_OK;
+}
+
 int qcd_set_profiling(qcd_ctx *c, int on) {
     int rc = ready(c);
     if (rc) return rc;

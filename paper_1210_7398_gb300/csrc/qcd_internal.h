@@ -139,6 +139,7 @@ struct qcd_ctx {
     long field_version = 0;  // bumped whenever the links or the clover field change
     int sap_min_ctas = 0;    // lower bound on the CTAs (cluster size) per SAP block; 0: fill the SMs
     int sap_ctas_user = 0;   // the qcd_set_sap_ctas setting, which params with sap_ctas = 0 use
+    int sms_override = 0;    // SM count the SAP plan is made for (0: ask the device); diagnostics
     int sap_form = 0;        // SSOR lanes per site update: 0 by occupancy, 1 warp form (32), 2 octet form (8)
 
     // workspace, grown on demand

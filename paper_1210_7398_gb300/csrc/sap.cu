@@ -1398,8 +1398,9 @@ int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &np,
     // CTAs per block: C <= 16 whose shared memory fits.  With min_ctas >= 1 the smallest such
     // C >= min_ctas; with min_ctas = 0 the largest one that keeps the blocks of one colour (one
     // CTA cluster each) within the SM count, and at least the smallest that fits
-    int sms = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms < 1) {
+    int sms = c->sms_override;
+    if (sms < 1 &&
+        (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms < 1)) {
         cudaGetLastError();
         sms = 1;
     }
