@@ -225,8 +225,8 @@ int qcd_set_sap_ctas(qcd_ctx *ctx, int min_ctas);
 
 /* Second tuning knob of the warp form above: lanes per site update.  form = 1:
  * 32 lanes (lane = hop direction and colour row, one update per warp); 2: 8
- * lanes (lane = hop direction, four updates per warp: a quarter of the issued
- * instructions, but a quarter of the warps to hide latency); 0 (default):
+ * lanes (lane = hop direction, four updates per warp: about two thirds of the
+ * issued instructions, but a quarter of the warps to hide latency); 0 (default):
  * per launch, the 8-lane form where the grid keeps at least 16 of its warps
  * resident per SM (many small blocks, several right-hand sides), else 32.
  * Both perform the same rounding steps in the same order: results are

@@ -492,11 +492,11 @@ __global__ void __launch_bounds__(32 * MAXW) k_ssor_warp(SsorArgs a) {
 // K3, octet form: the same ll wavefront, chunks, staging and barriers as k_ssor_warp, but one
 // site update per 8 lanes (lane = hop direction d = 2 mu + (backward)) and four sites per warp.
 // A lane forms its direction's whole projected hop (3 colours, 4 spins), the 8 directions meet
-// in a three-step reduce-scatter,
-// every lane gathers the sum, and each chirality's 4 lanes apply 1 or 2 rows of its 6x6 block.
-// The arithmetic per site is the warp form's, rounding step by rounding step, spread over 8
-// lanes instead of 32: a quarter of the issued instructions per update, but a quarter of the
-// warps to hide each lane's longer dependency chains.
+// in a three-step reduce-scatter, every lane gathers the sum, and each chirality's 4 lanes apply
+// 1 or 2 rows of its 6x6 block.  The arithmetic per site is the warp form's, rounding step by
+// rounding step, spread over 8 lanes instead of 32: about two thirds of the issued instructions
+// per update (no idle colour lanes, fewer shuffles per site), but a quarter of the warps to hide
+// each lane's longer dependency chains.
 template <bool HALF, bool CL>
 __global__ void __launch_bounds__(256) k_ssor_oct(SsorArgs a) {
     using L = Rec<HALF>;
@@ -1634,9 +1634,9 @@ int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
     attr[0].val.clusterDim.z = 1;
     cfg.dynamicSmemBytes = p.smem_bytes;
     // form of the block solve for this launch (the warp and octet forms give identical bits):
-    // the octet form issues a quarter of the instructions per site update with a quarter of the
-    // warps, so it is taken where the grid keeps at least 16 of its warps resident per SM (the
-    // warp form then has 64 and is bound by instruction issue; measured on GB300)
+    // the octet form issues about two thirds of the instructions per site update with a quarter
+    // of the warps, so it is taken where the grid keeps at least 16 of its warps resident per SM
+    // (the warp form then has 64 and is bound by instruction issue; measured on GB300)
     const int w_oct = (p.nslot + 3) / 4;
     auto octet = [&](int col) {
         if (c->sap_form) return c->sap_form == 2;
