@@ -33,6 +33,21 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) per launch of a kernel class on this workload, from one ncu capture
 # of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum); None where not captured
 NCU_TRAFFIC = {"ssor": 28918016 + 0}
+# warp instructions per launch and SMs the launch occupies, from the ncu capture of the plain
+# workload's SSOR kernel (profiles/ssor_level_12x12x12x24_c8.md): 64 CTAs, one per SM
+NCU_ISSUE = {"ssor": (66.6e6, 64)}
+
+
+def issue_model(cls, avg_ms, sm_mhz):
+    """The instruction-issue floor of a kernel class: its warp instructions per launch issued at
+    4 per cycle (one per SM sub-partition) on the SMs it occupies, against the measured launch
+    time.  None when the class has no instruction count."""
+    if cls not in NCU_ISSUE or not avg_ms or not sm_mhz:
+        return None
+    instr, sms = NCU_ISSUE[cls]
+    floor_ms = instr / (sms * 4.0 * sm_mhz * 1e6) * 1e3
+    return {"warp_instructions_per_launch": instr, "sms": sms, "issue_per_cycle_per_sm": 4,
+            "floor_ms": floor_ms, "avg_launch_ms": avg_ms, "frac": floor_ms / avg_ms}
 
 
 def read_peaks():
@@ -707,6 +722,10 @@ def run_gpu_on_stream(args, q, qi, torch, np, peaks, rank, world, local):
             roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                     "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(dom), "avg_launch_ms": avg_ms,
                     "peak_source": peaks["source"] if bound == "hbm" else "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+            sm_mhz = clk.get("sm_mhz") if isinstance(clk, dict) else None
+            iss = issue_model(dom, avg_ms, sm_mhz or peaks["sm_max_mhz"])
+            if iss is not None:
+                roof["issue"] = iss
         tot_k = sum(v["ms"] for v in kstats.values())
         for v in kstats.values():
             v["share"] = v["ms"] / tot_k if tot_k else 0.0
