@@ -10,6 +10,10 @@
   dense matrices; with exact block inverses the odd part of (1-DK)v vanishes;
   M_SAP v approaches D^{-1} v as N_SAP grows.
 * Nested BiCGStab (Sec. 2): the solution equals a dense LU solve.
+* Colour blocks (Eq. 3): they sum to D and are the dense D restricted to one block (diagonal
+  blocks) or to neighbouring blocks (off-diagonal blocks).
+* Even-odd block inverse: odd rows exact, monotone residual, the one-step least-squares
+  optimum, the dense block inverse in the limit.
 """
 import itertools
 
@@ -382,3 +386,29 @@ def test_eo_mr_larger_blocks_matrix_free():
             assert e <= prev * (1 + 1e-12)
             prev = e
         assert prev < 0.1 * np.linalg.norm(f.reshape(-1)[col == 0])
+
+
+def test_colour_blocks_of_D(field44):
+    """Eq. 3: the four colour blocks P_r D P_c sum to D; D_EE and D_OO are D restricted to
+    pairs of sites in one block (blocks of one colour are never neighbours), D_OE and D_EO
+    to pairs in neighbouring blocks of opposite colour."""
+    dims, U, F, Dm = field44
+    b = (2, 2, 2, 2)
+    psi = qi.gaussian_spinor(dims, seed=16)[0]
+    parts = {(r, c): oracle.apply_D_colour(dims, U, F, KAPPA, b, r, c, psi).reshape(-1)
+             for r in (0, 1) for c in (0, 1)}
+    full = oracle.apply_D(dims, U, F, KAPPA, psi).reshape(-1)
+    assert np.abs(sum(parts.values()) - full).max() < 1e-13 * np.abs(full).max()
+    x = site_coords(dims)
+    blk = np.ravel_multi_index(tuple((x // np.array(b)).T), [dims[m] // b[m] for m in range(4)], order="F")
+    col = oracle.colours(dims, b)
+    same_block = np.repeat(np.repeat(blk[:, None] == blk[None, :], 12, axis=0), 12, axis=1)
+    cd = np.repeat(col, 12)
+    v = psi.reshape(-1)
+    for c in (0, 1):
+        rows = cd == c
+        expect = (Dm * same_block)[rows] @ np.where(cd == c, v, 0)
+        assert np.abs(parts[(c, c)][rows] - expect).max() < 1e-13 * np.abs(expect).max()
+        assert np.all(parts[(c, c)][~rows] == 0)
+    cross = (Dm * ~same_block)[cd == 1] @ np.where(cd == 0, v, 0)
+    assert np.abs(parts[(1, 0)][cd == 1] - cross).max() < 1e-13 * np.abs(cross).max()
