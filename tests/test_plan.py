@@ -154,3 +154,29 @@ def test_rejected_geometry():
         q.qcd_sap_plan_tables((12, 12, 12, 24), (4, 4, 4, 4), (2, 2, 2, 2))  # 3 blocks along x
     with pytest.raises(q.QcdError):
         q.qcd_sap_plan_tables((12, 12, 12, 24), (6, 6, 6, 12), (4, 3, 3, 6))  # sub-block does not divide
+
+
+def random_geometries(n, seed=7):
+    """Seeded sample of block / sub-block shapes (extents 1..6, sub-blocks dividing them) on
+    lattices of two blocks per direction."""
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < n:
+        b = [int(rng.integers(1, 7)) for _ in range(4)]
+        if np.prod(b) < 2 or np.prod(b) > 1296:
+            continue
+        s = [int(rng.choice([d for d in range(1, bm + 1) if bm % d == 0])) for bm in b]
+        out.append((tuple(2 * bm for bm in b), tuple(b), tuple(s)))
+    return out
+
+
+@pytest.mark.parametrize("geom", random_geometries(24), ids=lambda g: "x".join(map(str, g[1])) + "/" + "x".join(map(str, g[2])))
+@pytest.mark.parametrize("ctas,half", [(0, False), (3, False), (0, True), (-1, False)])
+def test_ssor_schedule_random_shapes(geom, ctas, half):
+    dims, b, s = geom
+    try:
+        t = q.qcd_sap_plan_tables(dims, b, s, sap_ctas=ctas, half=half, sms=152)
+    except q.QcdError:
+        assert ctas not in (0, -1)
+        return
+    check_schedule(b, s, t)
