@@ -180,3 +180,21 @@ def test_ssor_schedule_random_shapes(geom, ctas, half):
         assert ctas not in (0, -1)
         return
     check_schedule(b, s, t)
+
+
+@pytest.mark.parametrize("C", [2, 4, 8, 16])
+def test_dealing_keeps_sub_blocks_on_one_cta(C):
+    """The sites of a level come in ll order (local position, then sub-block), so dealing them
+    round-robin over C CTAs, C dividing the sub-block count, gives sub-block sigma to CTA
+    sigma mod C: most neighbour reads stay in the CTA's own shared memory."""
+    b, s = (6, 6, 6, 12), (3, 3, 3, 6)
+    t = q.qcd_sap_plan_tables((12, 12, 12, 24), b, s, sap_ctas=C, sms=152)
+    assert t["ctas"] == C
+    vol = int(np.prod(b))
+    y = np.array(np.unravel_index(np.arange(vol), b, order="F")).T
+    nq = [b[m] // s[m] for m in range(4)]
+    sigma = np.ravel_multi_index(tuple((y // np.array(s)).T), nq, order="F")
+    assert np.array_equal(t["owner"], sigma % C)
+    pairs = neighbour_pairs(b)
+    remote = np.mean(t["owner"][pairs[:, 0]] != t["owner"][pairs[:, 1]])
+    assert remote < 0.2
