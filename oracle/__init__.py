@@ -8,8 +8,8 @@ Every array is complex128 in the canonical layout (links [V,4,3,3],
 spinors [V,4,3], dense site matrices [V,12,12] with index spin*3+colour).
 Parity of the Krylov iteration counts and timings is not pinned by the paper
 (it prints none); the operator, the clover term, the ll ordering, SSOR, the
-even-odd block inverse, SAP and the final solution are pinned by the tests in
-``tests/test_oracle_*.py``.
+even-odd block inverse, SAP, the inner BiCGStab on its own and the final
+solution are pinned by the tests in ``tests/test_oracle_*.py``.
 """
 from __future__ import annotations
 

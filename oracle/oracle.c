@@ -13,8 +13,8 @@
  * applications) or across SAP blocks of one colour, where the result does not
  * depend on the order.
  *
- * Conventions (the paper fixes only some of them; the readings are listed in
- * the design notes):
+ * Conventions (the paper fixes only some of them; where it is silent the
+ * reading taken is stated here or at the function that depends on it):
  *   site n = x + Lx*(y + Ly*(z + Lz*t)); mu = 0..3 is x,y,z,t (paper mu=1..4)
  *   links  U[n][mu][a][b]   spinor psi[n][spin][colour]   (complex, re/im)
  *   Dirac representation, gamma_4 diagonal (Sec. 3, "Dirac representation"):
