@@ -161,7 +161,7 @@ int check_params(qcd_ctx *c, const qcd_params *p) {
     if (p->bc_t != c->bc_t) return fail(c, QCD_ERR_ARG, "params.bc_t differs from the context boundary condition");
     if (p->kappa != c->kappa || p->csw != c->csw)
         return fail(c, QCD_ERR_ARG, "params.kappa/csw differ from the clover field built");
-    if (p->sap_ctas < -1 || p->sap_ctas > 16) return fail(c, QCD_ERR_ARG, "sap_ctas must lie in -1..16");
+    if (p->sap_ctas < -2 || p->sap_ctas > 16) return fail(c, QCD_ERR_ARG, "sap_ctas must lie in -2..16");
     if (p->block_solver < 0 || p->block_solver > 1) return fail(c, QCD_ERR_ARG, "block_solver must be 0 or 1");
     if (p->block_solver == 1 && (p->sap_storage != QCD_F32 || p->learned != 0))
         return fail(c, QCD_ERR_ARG, "block_solver 1 needs sap_storage QCD_F32 and learned 0");
@@ -447,7 +447,7 @@ int qcd_set_graphs(qcd_ctx *c, int on) {
 int qcd_set_sap_ctas(qcd_ctx *c, int min_ctas) {
     int rc = ready(c);
     if (rc) return rc;
-    if (min_ctas < -1 || min_ctas > 16) return fail(c, QCD_ERR_ARG, "min_ctas must lie in -1..16");
+    if (min_ctas < -2 || min_ctas > 16) return fail(c, QCD_ERR_ARG, "min_ctas must lie in -2..16");
     QCD_CUDA(c, c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
     c->sap_ctas_user = min_ctas;
     use_sap_ctas(c, 0);
@@ -464,7 +464,7 @@ int qcd_set_sap_form(qcd_ctx *c, int form) {
 
 int qcd_sap_plan_tables(const int dims[4], const int block[4], const int subblock[4], int sap_ctas, int half, int sms,
                         int meta[8], int *level, int *owner, int *slot, int *chunk, unsigned char *flags) {
-    if (!dims || !block || !subblock || !meta || sap_ctas < -1 || sap_ctas > 16 || sms < 1) return QCD_ERR_ARG;
+    if (!dims || !block || !subblock || !meta || sap_ctas < -2 || sap_ctas > 16 || sms < 1) return QCD_ERR_ARG;
     qcd_ctx c;  // host-side planning only: no device, stream or allocation is touched
     c.lat.V = 1;
     for (int m = 0; m < 4; m++) {
@@ -475,16 +475,17 @@ int qcd_sap_plan_tables(const int dims[4], const int block[4], const int subbloc
     c.sms_override = sms;
     SapPlan p;
     if (sap_plan_host(&c, block, subblock, p, sap_ctas, half != 0) != QCD_OK) return QCD_ERR_ARG;
-    const int vals[8] = {p.vol, p.nsteps, p.C, p.nchunks, p.nslot, p.slab_vol, p.thread ? 1 : 0, (int)p.smem_bytes};
+    const int vals[8] = {p.vol, p.nsteps, p.C, p.nchunks, p.nslot, p.slab_vol, p.tile ? 2 : p.thread ? 1 : 0,
+                         (int)p.smem_bytes};
     for (int k = 0; k < 8; k++) meta[k] = vals[k];
     for (int st = 0; st < p.nsteps; st++)
         for (int k = p.h_step_ptr[st]; k < p.h_step_ptr[st + 1]; k++)
             if (level) level[p.h_step_site[k]] = st;
     for (int yl = 0; yl < p.vol; yl++) {
-        if (owner) owner[yl] = p.thread ? 0 : p.h_own[yl] >> 24;
-        if (slot) slot[yl] = p.thread ? yl : p.h_own[yl] & 0xffffff;
+        if (owner) owner[yl] = (p.thread || p.tile) ? 0 : p.h_own[yl] >> 24;
+        if (slot) slot[yl] = (p.thread || p.tile) ? yl : p.h_own[yl] & 0xffffff;
     }
-    const int nct = p.thread ? 1 : p.C;
+    const int nct = (p.thread || p.tile) ? 1 : p.C;
     for (int r = 0; r < nct; r++)
         for (int ch = 0; ch < p.nchunks; ch++)
             for (int k = p.h_chunk_ptr[r * (p.nchunks + 1) + ch]; k < p.h_chunk_ptr[r * (p.nchunks + 1) + ch + 1]; k++)

@@ -146,9 +146,10 @@ __device__ __forceinline__ void clover_mul(const R f[72], const C v[12], C out[1
 // diag(1,1,-1,-1)); the projector has rank 2, so the colour multiply acts on
 // the two-component half-spinor h only.  sgn is the boundary sign of a hop
 // across the t edge (only MU = 3 can carry one).
+
+// the half-spinor h[spin row * 3 + colour] of (1 -/+ gamma_mu) psi
 template <int MU, bool FWD, typename C>
-__device__ __forceinline__ void hop_term(const C psi[12], const C u[9], decltype(C::x) sgn, C acc[12]) {
-    C h[6];
+__device__ __forceinline__ void hop_project(const C psi[12], decltype(C::x) sgn, C h[6]) {
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         const C p0 = psi[c], p1 = psi[3 + c], p2 = psi[6 + c], p3 = psi[9 + c];
@@ -169,25 +170,12 @@ __device__ __forceinline__ void hop_term(const C psi[12], const C u[9], decltype
         h[c] = h0;
         h[3 + c] = h1;
     }
-    // colour multiply: U h (forward) or U^dag h (backward)
-    C w[6];
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        C w0 = cmk<C>(0, 0), w1 = cmk<C>(0, 0);
-#pragma unroll
-        for (int b = 0; b < 3; b++) {
-            if (FWD) {
-                w0 = cfma(u[a * 3 + b], h[b], w0);
-                w1 = cfma(u[a * 3 + b], h[3 + b], w1);
-            } else {
-                w0 = cfmac(u[b * 3 + a], h[b], w0);
-                w1 = cfmac(u[b * 3 + a], h[3 + b], w1);
-            }
-        }
-        w[a] = w0;
-        w[3 + a] = w1;
-    }
-    // reconstruct the lower (or, for mu = t backward, upper) spin components
+}
+
+// adds the transported half-spinor w (both spin rows) to acc, reconstructing the other two
+// spin components of (1 -/+ gamma_mu)
+template <int MU, bool FWD, typename C>
+__device__ __forceinline__ void hop_reconstruct(const C w[6], C acc[12]) {
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         const C w0 = w[a], w1 = w[3 + a];
@@ -208,6 +196,63 @@ __device__ __forceinline__ void hop_term(const C psi[12], const C u[9], decltype
             if (FWD) { acc[6 + a] = cadd(acc[6 + a], cmulmi(w0)); acc[9 + a] = cadd(acc[9 + a], cmuli(w1)); }
             else     { acc[6 + a] = cadd(acc[6 + a], cmuli(w0));  acc[9 + a] = cadd(acc[9 + a], cmulmi(w1)); }
         }
+    }
+}
+
+template <int MU, bool FWD, typename C>
+__device__ __forceinline__ void hop_term(const C psi[12], const C u[9], decltype(C::x) sgn, C acc[12]) {
+    C h[6];
+    hop_project<MU, FWD>(psi, sgn, h);
+    // colour multiply: U h (forward) or U^dag h (backward)
+    C w[6];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        C w0 = cmk<C>(0, 0), w1 = cmk<C>(0, 0);
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            if (FWD) {
+                w0 = cfma(u[a * 3 + b], h[b], w0);
+                w1 = cfma(u[a * 3 + b], h[3 + b], w1);
+            } else {
+                w0 = cfmac(u[b * 3 + a], h[b], w0);
+                w1 = cfmac(u[b * 3 + a], h[3 + b], w1);
+            }
+        }
+        w[a] = w0;
+        w[3 + a] = w1;
+    }
+    hop_reconstruct<MU, FWD>(w, acc);
+}
+
+// The same hop with the transport matrix given as it acts: W = U_mu(n) forward and
+// W = U_mu(n-mu)^dag backward, both as W h (row-major W[a][b]).
+template <int MU, bool FWD, typename C>
+__device__ __forceinline__ void hop_term_w(const C psi[12], const C W[9], C acc[12]) {
+    C h[6];
+    hop_project<MU, FWD>(psi, (decltype(C::x))1, h);
+    C w[6];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        C w0 = cmk<C>(0, 0), w1 = cmk<C>(0, 0);
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            w0 = cfma(W[a * 3 + b], h[b], w0);
+            w1 = cfma(W[a * 3 + b], h[3 + b], w1);
+        }
+        w[a] = w0;
+        w[3 + a] = w1;
+    }
+    hop_reconstruct<MU, FWD>(w, acc);
+}
+
+// third row of a special unitary 3x3 matrix from its first two: row2 = conj(row0 x row1)
+// (Table 1's reconstruction of a link from 12 reals)
+template <typename C> __device__ __forceinline__ void su3_third_row(C W[9]) {
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        const int k = (j + 1) % 3, l = (j + 2) % 3;
+        const C a = csub(cmul(W[k], W[3 + l]), cmul(W[l], W[3 + k]));
+        W[6 + j] = cmk<C>(a.x, -a.y);
     }
 }
 

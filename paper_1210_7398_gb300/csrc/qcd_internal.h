@@ -50,6 +50,7 @@ struct SapPlan {
     int *d_origin[2] = {nullptr, nullptr};  // [nblk[c]][4] block origins per colour
     bool half = false;  // FP16 storage of the block spinor and the records (FP32 arithmetic)
     bool thread = false;  // thread form of the SSOR kernel (SoA per-block fields instead of records)
+    bool tile = false;    // right-hand-side tiled thread form (ssor_tile.cu): per-block records in level order
     int C = 1, slab_vol = 0;  // CTAs per block (cluster), most sites one CTA owns
     int nchunks = 0, nslot = 0, nwarps = 0;
     int sms = 1;        // SM count of the device the plan was made for
@@ -70,6 +71,9 @@ struct SapPlan {
     int *d_own_off = nullptr;
     int *d_pos = nullptr;
     int *d_origin_site[2] = {nullptr, nullptr};
+    std::vector<int4> h_tile_pos;   // tile form: [vol][2] per level position (offset, site, neighbours)
+    int4 *d_tile_pos = nullptr;
+    int *d_lev_ptr = nullptr;       // tile form: [nsteps + 1] level boundaries (h_step_ptr)
     float *d_rec = nullptr;         // per-site records (links, clover, neighbour codes), V x 912 bytes
     long rec_version = -1;          // field version the records were built from
 };
@@ -250,6 +254,22 @@ int sap_upload_tables(qcd_ctx *c, SapPlan &plan, void *region);
 constexpr size_t kSapRecordBytesPerSite = 1200;
 size_t sap_record_bytes(const SapPlan &plan);
 int sap_build_records(qcd_ctx *c, SapPlan &plan, float *rec);
+
+// RHS-tiled thread form of the SSOR block solve (ssor_tile.cu): one CTA per (block, tile of up
+// to kTileMaxRhs right-hand sides), one thread per site update, the block spinors of the tile
+// in shared memory; per-site records of kTileRecordBytes (FP32) / kTileRecordBytesHalf (FP16)
+constexpr int kTileMaxThreads = 256;
+constexpr int kTileMaxRhs = 8;
+constexpr size_t kTileSmemLimit = 200 * 1024;
+constexpr int kTileRecordBytes = 672;
+constexpr int kTileRecordBytesHalf = 336;
+size_t tile_smem_bytes(int vol, bool half, int R);
+int tile_build_records(qcd_ctx *c, const SapPlan &p, void *rec);
+int tile_set_attributes(qcd_ctx *c);
+// right-hand sides per CTA, threads per CTA and shared memory of a tile launch for nrhs right-hand sides
+int tile_choose(const SapPlan &p, int nrhs, int *R, int *threads, size_t *smem);
+int tile_launch(qcd_ctx *c, const SapPlan &p, int col, float4 *y, const float4 *f, int nsweep, double omega,
+                int nrhs, const BicgScalars *gate);
 
 // BLAS (blas.cu), batched: vectors [nrhs][n] complex (double2 or float2), scalars per
 // right-hand side in device memory.  A right-hand side whose scalars say inactive is skipped.

@@ -1380,8 +1380,33 @@ int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &np,
         for (int m = 0; m < 4; m++) { y[m] = r % b[m]; r /= b[m]; }
         np.h_site_off[yl] = y[0] + c->lat.L[0] * (y[1] + c->lat.L[1] * (y[2] + c->lat.L[2] * y[3]));
     }
-    // the thread form on request (min_ctas < 0), FP32 storage, the block spinor in one CTA
-    if (min_ctas < 0 && !half) {
+    // the right-hand-side tiled thread form on request (min_ctas == -2), the block spinor of
+    // one right-hand side in one CTA
+    if (min_ctas == -2 && tile_smem_bytes(np.vol, half, 1) <= kTileSmemLimit) {
+        make_chunks(np, 1, 1 << 20, false);  // one chunk per level, in level order (diagnostics)
+        np.tile = true;
+        np.nwarps = 0;
+        np.smem_bytes = tile_smem_bytes(np.vol, half, 1);
+        make_flags(np);
+        // per level position: global offset, block-local site and its 8 in-block neighbours
+        // (d = 2 mu + backward; the site itself where the hop leaves the block)
+        np.h_tile_pos.assign(2 * (size_t)np.vol, make_int4(0, 0, 0, 0));
+        for (int k = 0; k < np.vol; k++) {
+            const int yl = np.h_step_site[k];
+            int y[4], r = yl, nbk[8], stride = 1;
+            for (int m = 0; m < 4; m++) { y[m] = r % b[m]; r /= b[m]; }
+            for (int m = 0; m < 4; m++) {
+                nbk[2 * m] = y[m] + 1 < b[m] ? yl + stride : yl;
+                nbk[2 * m + 1] = y[m] > 0 ? yl - stride : yl;
+                stride *= b[m];
+            }
+            np.h_tile_pos[2 * k] = make_int4(np.h_site_off[yl], yl, nbk[0] | (nbk[1] << 16), nbk[2] | (nbk[3] << 16));
+            np.h_tile_pos[2 * k + 1] = make_int4(nbk[4] | (nbk[5] << 16), nbk[6] | (nbk[7] << 16), 0, 0);
+        }
+        return np.vol < (1 << 16) ? QCD_OK : QCD_ERR_ARG;
+    }
+    // the thread form on request (min_ctas = -1), FP32 storage, the block spinor in one CTA
+    if (min_ctas == -1 && !half) {
         make_chunks(np, 1, 1 << 20, false);  // one chunk per level, in level order
         const size_t smem = (size_t)np.vol * kTsY * 4 + sizeof(int) * ((np.nchunks + 1 + 3) & ~3) +
                             sizeof(int2) * ((np.vol + 1) & ~1);
@@ -1433,7 +1458,8 @@ size_t sap_table_bytes(const SapPlan &p) {
            up16(sizeof(int) * p.h_origin_site[0].size()) + up16(sizeof(int) * p.h_origin_site[1].size()) +
            up16(sizeof(int) * p.h_chunk_ptr.size()) + up16(sizeof(int2) * p.h_chunk_site.size()) +
            up16(sizeof(int) * p.h_site_off.size()) + up16(p.h_flags.size()) + up16(sizeof(int) * p.h_own.size()) +
-           up16(sizeof(int) * p.h_own_off.size()) + up16(sizeof(int) * p.h_pos.size());
+           up16(sizeof(int) * p.h_own_off.size()) + up16(sizeof(int) * p.h_pos.size()) +
+           up16(sizeof(int4) * p.h_tile_pos.size()) + (p.tile ? up16(sizeof(int) * p.h_step_ptr.size()) : 0);
 }
 
 // Copies every table of the plan into one device region (sap_table_bytes long) on the
@@ -1463,8 +1489,11 @@ int sap_upload_tables(qcd_ctx *c, SapPlan &p, void *region) {
     p.d_own = (int *)put(p.h_own.data(), sizeof(int) * p.h_own.size());
     p.d_own_off = (int *)put(p.h_own_off.data(), sizeof(int) * p.h_own_off.size());
     p.d_pos = p.h_pos.empty() ? nullptr : (int *)put(p.h_pos.data(), sizeof(int) * p.h_pos.size());
+    p.d_tile_pos = p.tile ? (int4 *)put(p.h_tile_pos.data(), sizeof(int4) * p.h_tile_pos.size()) : nullptr;
+    p.d_lev_ptr = p.tile ? (int *)put(p.h_step_ptr.data(), sizeof(int) * p.h_step_ptr.size()) : nullptr;
     if (!p.d_origin[0] || !p.d_origin[1] || !p.d_origin_site[0] || !p.d_origin_site[1] || !p.d_chunk_ptr ||
-        !p.d_chunk_site || !p.d_site_off || !p.d_flags || !p.d_own || !p.d_own_off || (p.thread && !p.d_pos))
+        !p.d_chunk_site || !p.d_site_off || !p.d_flags || !p.d_own || !p.d_own_off || (p.thread && !p.d_pos) ||
+        (p.tile && (!p.d_tile_pos || !p.d_lev_ptr)))
         return cuda_fail(c, cudaGetLastError(), "cudaMemcpyAsync(SAP tables)");
     // the host vectors may be released only once the copies have consumed them
     QCD_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -1472,6 +1501,8 @@ int sap_upload_tables(qcd_ctx *c, SapPlan &p, void *region) {
 }
 
 size_t sap_record_bytes(const SapPlan &p) {
+    if (p.tile)
+        return (size_t)(p.nblk[0] + p.nblk[1]) * p.vol * (p.half ? kTileRecordBytesHalf : kTileRecordBytes);
     if (p.thread) return (size_t)(p.nblk[0] + p.nblk[1]) * p.vol * kSoaBytesPerSite;
     return (size_t)(p.nblk[0] + p.nblk[1]) * p.vol * (p.half ? Rec<true>::words : Rec<false>::words) * sizeof(float);
 }
@@ -1487,7 +1518,10 @@ int sap_build_records(qcd_ctx *c, SapPlan &p, float *rec) {
     const long total = (long)(p.nblk[0] + p.nblk[1]) * p.vol;
     cudaEvent_t ev;
     prof_begin(c, QCD_K_OTHER, &ev);
-    if (p.thread) {
+    if (p.tile) {
+        int trc = tile_build_records(c, p, rec);
+        if (trc) return trc;
+    } else if (p.thread) {
         float2 *lk = reinterpret_cast<float2 *>(rec);
         float4 *cl = reinterpret_cast<float4 *>(lk + (size_t)total * kSoaLinks);
         k_sap_soa<<<(unsigned)((total + 127) / 128), 128, 0, c->stream>>>(lk, cl, c->U32, c->F32, g, bg, p.d_pos,
@@ -1605,7 +1639,7 @@ int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
                 QCD_CUDA(c, cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
             }
             QCD_CUDA(c, cudaFuncSetAttribute(k_ssor_soa, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
-            return QCD_OK;
+            return tile_set_attributes(c);
         }))
         return arc;
     SsorArgs a;
@@ -1663,7 +1697,10 @@ int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
             cfg.blockDim = dim3(32 * (oct ? w_oct : p.nwarps));
             prof_begin(c, QCD_K_SSOR, &ev);
             cudaError_t e;
-            if (p.thread) {
+            if (p.tile) {
+                if ((rc = tile_launch(c, p, col, y, r, nsweep, omega, nrhs, gate))) return rc;
+                e = cudaSuccess;
+            } else if (p.thread) {
                 SsorArgs at = a;
                 at.rec = reinterpret_cast<const float4 *>(p.d_rec);
                 at.gb0 = col ? p.nblk[0] : 0;

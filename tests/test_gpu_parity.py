@@ -130,10 +130,11 @@ SAP_CASES = [
     ((8, 4, 4, 8), (4, 2, 2, 4), (2, 1, 2, 2), 1.2, 2, 3),
     ((8, 8, 8, 8), (4, 4, 4, 4), (2, 2, 2, 2), 1.0, 3, 2),
     ((12, 12, 12, 24), (6, 6, 6, 12), (3, 3, 3, 6), 1.0, 4, 4),  # the 12^3 x 24 configuration
+    ((12, 12, 12, 24), (6, 6, 6, 6), (3, 3, 3, 3), 1.0, 4, 4),   # the paper's 6^4 blocks, 3^4 sub-blocks (Sec. 3)
 ]
 
 
-@pytest.mark.parametrize("case", SAP_CASES, ids=lambda c: "x".join(map(str, c[0])))
+@pytest.mark.parametrize("case", SAP_CASES, ids=lambda c: "x".join(map(str, c[0])) + "_b" + "x".join(map(str, c[1])))
 def test_sap_vs_oracle(case):
     dims, b, sb, omega, nsweep, nsap = case
     kappa = 0.12

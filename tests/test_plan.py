@@ -121,7 +121,7 @@ def check_schedule(b, s, t):
 
 
 @pytest.mark.parametrize("half", [False, True], ids=["f32", "f16"])
-@pytest.mark.parametrize("ctas", [0, 1, 2, 3, 8, 16, -1])
+@pytest.mark.parametrize("ctas", [0, 1, 2, 3, 8, 16, -1, -2])
 @pytest.mark.parametrize("geom", GEOMS, ids=lambda g: "x".join(map(str, g[1])) + "/" + "x".join(map(str, g[2])))
 def test_ssor_schedule_is_consistent(geom, ctas, half):
     dims, b, s = geom
@@ -129,12 +129,19 @@ def test_ssor_schedule_is_consistent(geom, ctas, half):
         t = q.qcd_sap_plan_tables(dims, b, s, sap_ctas=ctas, half=half, sms=152)
     except q.QcdError:
         # a fixed width whose shared memory does not fit is rejected; the automatic one never is
-        assert ctas not in (0, -1)
+        assert ctas not in (0, -1, -2)
         return
     if ctas >= 1:
         assert t["ctas"] >= ctas
     if ctas == -1:
         assert t["thread"] == (0 if half else t["thread"])
+    if ctas == -2:
+        # the tile form holds one right-hand side's block spinor in one CTA (12 or 24 words per
+        # site), else the automatic cluster form stands in
+        fits = np.prod(b) * (48 if half else 96) <= 200 * 1024
+        assert t["thread"] == (2 if fits else 0)
+        if fits:
+            assert t["ctas"] == 1 and t["chunks"] == t["levels"]
     check_schedule(b, s, t)
 
 
@@ -171,13 +178,13 @@ def random_geometries(n, seed=7):
 
 
 @pytest.mark.parametrize("geom", random_geometries(24), ids=lambda g: "x".join(map(str, g[1])) + "/" + "x".join(map(str, g[2])))
-@pytest.mark.parametrize("ctas,half", [(0, False), (3, False), (0, True), (-1, False)])
+@pytest.mark.parametrize("ctas,half", [(0, False), (3, False), (0, True), (-1, False), (-2, True)])
 def test_ssor_schedule_random_shapes(geom, ctas, half):
     dims, b, s = geom
     try:
         t = q.qcd_sap_plan_tables(dims, b, s, sap_ctas=ctas, half=half, sms=152)
     except q.QcdError:
-        assert ctas not in (0, -1)
+        assert ctas not in (0, -1, -2)
         return
     check_schedule(b, s, t)
 
