@@ -213,7 +213,7 @@ void qcd_destroy(qcd_ctx *c) {
     else cudaDeviceSynchronize();
     void *bufs[] = {c->net.W, c->net.grad, c->net.m, c->net.v, c->net.B, c->net.P, c->net.scal, c->net.act,
                     c->net.pairs,
-                    c->U64, c->U32, c->F64, c->F32, c->U16, c->F16, c->U12, c->d_status, c->d_red, c->d_scalars, c->d_bicg, c->d_mask,
+                    c->U64, c->U32, c->F64, c->F32, c->U16, c->F16, c->U12, c->d_status, c->d_red, c->d_red_tiles, c->d_scalars, c->d_bicg, c->d_mask,
                     c->ws64, c->ws32,
                     c->d_io, c->bench_in, c->bench_out, c->plan.d_origin[0] /* the plan's table region */,
                     c->plan.d_rec};

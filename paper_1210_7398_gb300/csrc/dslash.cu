@@ -9,6 +9,8 @@
 // (links) per plane, coalesced across the warp; neighbours of consecutive
 // threads are consecutive, so neighbour re-reads hit L1/L2 and the HBM traffic
 // stays close to one read of each field (768 B/site in FP32).
+#include <algorithm>
+
 #include "fields.cuh"
 #include "qcd_internal.h"
 
@@ -99,18 +101,73 @@ __global__ void __launch_bounds__(128, MINB) dslash_kernel(SP *__restrict__ out,
     store_spinor(out + (long)rhs * PLANES * g.V, g.V, n, psi);
 }
 
-// The same with NR right-hand sides per thread.
-template <int MINB, int NR, typename R, typename SP, typename LK, typename CL>
+template <int NR, int MODE, typename R, typename SP, typename LK, typename CL>
+__device__ __forceinline__ void dslash_site(SP *__restrict__ out, const SP *__restrict__ in,
+                                            const LK *__restrict__ U, const CL *__restrict__ F, R kappa,
+                                            const Geo &g, long n, int r0, const bool act[NR],
+                                            const SP *__restrict__ other, float part[NR][3]);
+
+// The same with NR right-hand sides per thread (each link and the clover field loaded once for
+// all of them).  MODE fuses the inner products the BiCGStab step after D needs into the
+// epilogue: 1: <other, out> and |out|^2, 2: <out, other> and |out|^2, 0: none; each CTA (128
+// consecutive sites) sums its sites per right-hand side by a fixed tree (a butterfly within each
+// warp, then the four warps in order) into partial[rhs][3][blockIdx.x], so a right-hand side's
+// inner products do not depend on which others share its threads.  Right-hand sides inactive
+// in gate (may be null) are skipped, their partials zero.
+template <int MINB, int NR, typename R, typename SP, typename LK, typename CL, int MODE = 0>
 __global__ void __launch_bounds__(128, MINB) dslash_kernel_nr(SP *__restrict__ out, const SP *__restrict__ in,
                                                      const LK *__restrict__ U, const CL *__restrict__ F,
-                                                     R kappa, Geo g, int nrhs) {
+                                                     R kappa, Geo g, int nrhs,
+                                                     const SP *__restrict__ other = nullptr,
+                                                     double *__restrict__ partial = nullptr,
+                                                     const BicgScalars *__restrict__ gate = nullptr) {
     using C = typename CT<R>::C;
     const long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (n >= g.V) return;
     const int r0 = blockIdx.y * NR;
-    const int nr = nrhs - r0 < NR ? nrhs - r0 : NR;
+    float part[NR][3];
+#pragma unroll
+    for (int r = 0; r < NR; r++) part[r][0] = part[r][1] = part[r][2] = 0.f;
+    bool act[NR];
+#pragma unroll
+    for (int r = 0; r < NR; r++) act[r] = r0 + r < nrhs && (!gate || gate[r0 + r].active);
+    if (n < g.V) dslash_site<NR, MODE>(out, in, U, F, kappa, g, n, r0, act, other, part);
+    if (MODE) {
+        __shared__ float sh[NR][3][4];
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+        for (int r = 0; r < NR; r++)
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                float v = part[r][q];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) sh[r][q][warp] = v;
+            }
+        __syncthreads();
+        if (threadIdx.x < NR * 3) {
+            const int r = threadIdx.x / 3, q = threadIdx.x % 3;
+            if (r0 + r < nrhs) {
+                double t = 0;
+                for (int w = 0; w < 4; w++) t += sh[r][q][w];
+                partial[((long)(r0 + r) * 3 + q) * gridDim.x + blockIdx.x] = t;
+            }
+        }
+    }
+}
+
+// one site of dslash_kernel_nr for its right-hand sides r0 .. r0 + NR - 1 (those with act set)
+template <int NR, int MODE, typename R, typename SP, typename LK, typename CL>
+__device__ __forceinline__ void dslash_site(SP *__restrict__ out, const SP *__restrict__ in,
+                                            const LK *__restrict__ U, const CL *__restrict__ F, R kappa,
+                                            const Geo &g, long n, int r0, const bool act[NR],
+                                            const SP *__restrict__ other, float part[NR][3]) {
+    using C = typename CT<R>::C;
     constexpr int PLANES = sizeof(C) * 12 / sizeof(SP);
     const SP *src = in + (long)r0 * PLANES * g.V;
+    bool any = false;
+#pragma unroll
+    for (int r = 0; r < NR; r++) any |= act[r];
+    if (!any) return;
     int x[4];
     site_coords(g, n, x);
     C acc[NR][12];
@@ -125,7 +182,7 @@ __global__ void __launch_bounds__(128, MINB) dslash_kernel_nr(SP *__restrict__ o
     {                                                                                   \
         const long m = FWD ? nbr_fwd<MU>(g, n, x) : nbr_bwd<MU>(g, n, x);               \
         load_link(U, g.V, FWD ? n : m, MU, u);                                           \
-        _Pragma("unroll") for (int r = 0; r < NR; r++) if (NR == 1 || r < nr) {         \
+        _Pragma("unroll") for (int r = 0; r < NR; r++) if (act[r]) {                     \
             load_spinor(src + (long)r * PLANES * g.V, g.V, m, psi);                      \
             hop_term<MU, FWD>(psi, u, SGN, acc[r]);                                      \
         }                                                                               \
@@ -143,7 +200,7 @@ __global__ void __launch_bounds__(128, MINB) dslash_kernel_nr(SP *__restrict__ o
     load_clover(F, g.V, n, f);
 #pragma unroll
     for (int r = 0; r < NR; r++) {
-        if (NR == 1 || r < nr) {
+        if (act[r]) {
             C fa[12];
             clover_mul<R, C>(f, acc[r], fa);
             load_spinor(src + (long)r * PLANES * g.V, g.V, n, psi);
@@ -153,6 +210,17 @@ __global__ void __launch_bounds__(128, MINB) dslash_kernel_nr(SP *__restrict__ o
                 psi[k].y = fma(-kappa, fa[k].y, psi[k].y);
             }
             store_spinor(out + (long)(r0 + r) * PLANES * g.V, g.V, n, psi);
+            if constexpr (MODE != 0) {
+                C o[12];
+                load_spinor(other + (long)(r0 + r) * PLANES * g.V, g.V, n, o);
+#pragma unroll
+                for (int k = 0; k < 12; k++) {
+                    const C a = MODE == 1 ? o[k] : psi[k], b = MODE == 1 ? psi[k] : o[k];
+                    part[r][0] = fmaf(a.x, b.x, fmaf(a.y, b.y, part[r][0]));   // Re conj(a) b
+                    part[r][1] = fmaf(a.x, b.y, fmaf(-a.y, b.x, part[r][1]));  // Im conj(a) b
+                    part[r][2] = fmaf(psi[k].x, psi[k].x, fmaf(psi[k].y, psi[k].y, part[r][2]));
+                }
+            }
         }
     }
 }
@@ -200,6 +268,25 @@ int dslash64(qcd_ctx *c, double2 *out, const double2 *in, int nrhs) {
     return prof_end(c, QCD_K_DSLASH64, ev);
 }
 
+template <int MODE>
+static int dslash32_tile(qcd_ctx *c, float4 *out, const float4 *in, int nrhs, const float4 *other, double *red,
+                         const BicgScalars *gate) {
+    Geo g = geo_of(c);
+    const unsigned nblk = (unsigned)((g.V + 127) / 128);
+    double *part = MODE ? c->d_red_tiles : nullptr;
+    cudaEvent_t ev;
+    prof_begin(c, QCD_K_DSLASH32, &ev);
+    if (nrhs == 1)
+        dslash_kernel_nr<7, 1, float, float4, float2, float4, MODE><<<dim3(nblk, 1), 128, 0, c->stream>>>(
+            out, in, c->U32, c->F32, (float)c->kappa, g, 1, other, part, gate);
+    else
+        dslash_kernel_nr<4, 2, float, float4, float2, float4, MODE><<<dim3(nblk, (nrhs + 1) / 2), 128, 0, c->stream>>>(
+            out, in, c->U32, c->F32, (float)c->kappa, g, nrhs, other, part, gate);
+    int rc = prof_end(c, QCD_K_DSLASH32, ev);
+    if (rc || !MODE) return rc;
+    return reduce_tiles(c, part, nblk, nrhs, red);
+}
+
 int dslash32(qcd_ctx *c, float4 *out, const float4 *in, int nrhs) {
     Geo g = geo_of(c);
     cudaEvent_t ev;
@@ -213,6 +300,13 @@ int dslash32(qcd_ctx *c, float4 *out, const float4 *in, int nrhs) {
                                                                                      (float)c->kappa, g, nrhs);
     }
     return prof_end(c, QCD_K_DSLASH32, ev);
+}
+
+int dslash32_dot(qcd_ctx *c, float4 *out, const float4 *in, int nrhs, const float4 *other, int mode, double *red,
+                 const BicgScalars *gate) {
+    if (mode == 1) return dslash32_tile<1>(c, out, in, nrhs, other, red, gate);
+    if (mode == 2) return dslash32_tile<2>(c, out, in, nrhs, other, red, gate);
+    return dslash32_tile<0>(c, out, in, nrhs, nullptr, nullptr, gate);
 }
 
 int dslash16(qcd_ctx *c, float4 *out, const float4 *in, int nrhs) {

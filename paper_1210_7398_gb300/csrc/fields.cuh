@@ -225,11 +225,11 @@ __device__ __forceinline__ void hop_term(const C psi[12], const C u[9], decltype
 }
 
 // The same hop with the transport matrix given as it acts: W = U_mu(n) forward and
-// W = U_mu(n-mu)^dag backward, both as W h (row-major W[a][b]).
+// W = U_mu(n-mu)^dag backward, both as W h (row-major W[a][b]); sgn as above.
 template <int MU, bool FWD, typename C>
-__device__ __forceinline__ void hop_term_w(const C psi[12], const C W[9], C acc[12]) {
+__device__ __forceinline__ void hop_term_w(const C psi[12], const C W[9], C acc[12], decltype(C::x) sgn = 1) {
     C h[6];
-    hop_project<MU, FWD>(psi, (decltype(C::x))1, h);
+    hop_project<MU, FWD>(psi, sgn, h);
     C w[6];
 #pragma unroll
     for (int a = 0; a < 3; a++) {

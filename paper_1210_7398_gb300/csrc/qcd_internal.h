@@ -153,6 +153,7 @@ struct qcd_ctx {
     void *ws32 = nullptr;
     size_t ws32_bytes = 0;
     double *d_red = nullptr;      // reduction partials [nrhs][3][kRedMaxBlocks]
+    double *d_red_tiles = nullptr;  // per-CTA partials of the fused D [nrhs][3][V / 128]
     double *d_scalars = nullptr;  // reduction results [nrhs][3]
     double *h_scalars = nullptr;  // pinned host mirror
     int red_rhs = 0;              // right-hand sides d_red / d_scalars are sized for
@@ -215,10 +216,17 @@ int links_to_internal(qcd_ctx *c, const double2 *canon);
 int build_clover(qcd_ctx *c, double kappa, double csw);
 
 // operator D (dslash.cu)
+struct BicgScalars;
 int dslash64(qcd_ctx *c, double2 *out, const double2 *in, int nrhs);
 int dslash32(qcd_ctx *c, float4 *out, const float4 *in, int nrhs);
 int dslash16(qcd_ctx *c, float4 *out, const float4 *in, int nrhs);
 int dslash12(qcd_ctx *c, float4 *out, const float4 *in, int nrhs);
+// FP32 D (two right-hand sides per thread when there are several) fused with the inner
+// products of the BiCGStab step that follows: mode 1: red[rhs] = <other, out>, |out|^2; mode 2:
+// <out, other>, |out|^2; mode 0: none.  Right-hand sides inactive in gate (may be null) are
+// skipped.  Every right-hand side's result is independent of the batch, bit for bit.
+int dslash32_dot(qcd_ctx *c, float4 *out, const float4 *in, int nrhs, const float4 *other, int mode, double *red,
+                 const BicgScalars *gate);
 
 // SSOR form for a call whose params carry sap_ctas (0: the context's qcd_set_sap_ctas setting);
 // rebuilds the SAP plan when it changes (api.cu)
@@ -255,12 +263,13 @@ constexpr size_t kSapRecordBytesPerSite = 1200;
 size_t sap_record_bytes(const SapPlan &plan);
 int sap_build_records(qcd_ctx *c, SapPlan &plan, float *rec);
 
-// RHS-tiled thread form of the SSOR block solve (ssor_tile.cu): one CTA per (block, tile of up
-// to kTileMaxRhs right-hand sides), one thread per site update, the block spinors of the tile
-// in shared memory; per-site records of kTileRecordBytes (FP32) / kTileRecordBytesHalf (FP16)
+// RHS-tiled thread form of the SAP cycle (ssor_tile.cu): one CTA per (block, tile of up to
+// kTileMaxRhs right-hand sides), one thread per site update, the block spinors of the tile in
+// shared memory; per-site records of kTileRecordBytes (FP32) / kTileRecordBytesHalf (FP16)
 constexpr int kTileMaxThreads = 256;
 constexpr int kTileMaxRhs = 8;
 constexpr size_t kTileSmemLimit = 200 * 1024;
+constexpr size_t kTileSmemPerSm = 228 * 1024;
 constexpr int kTileRecordBytes = 672;
 constexpr int kTileRecordBytesHalf = 336;
 size_t tile_smem_bytes(int vol, bool half, int R);
@@ -268,8 +277,11 @@ int tile_build_records(qcd_ctx *c, const SapPlan &p, void *rec);
 int tile_set_attributes(qcd_ctx *c);
 // right-hand sides per CTA, threads per CTA and shared memory of a tile launch for nrhs right-hand sides
 int tile_choose(const SapPlan &p, int nrhs, int *R, int *threads, size_t *smem);
-int tile_launch(qcd_ctx *c, const SapPlan &p, int col, float4 *y, const float4 *f, int nsweep, double omega,
-                int nrhs, const BicgScalars *gate);
+// x = M_SAP v with the tile form: one launch per colour and cycle, each applying the pending
+// hops between blocks, the SSOR sweeps and the residual and solution updates itself; r and y
+// are work fields of nrhs right-hand sides
+int tile_sap_apply(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, float4 *r, float4 *y, double omega,
+                   int nsweep, int nsap, int nrhs, const BicgScalars *gate);
 
 // BLAS (blas.cu), batched: vectors [nrhs][n] complex (double2 or float2), scalars per
 // right-hand side in device memory.  A right-hand side whose scalars say inactive is skipped.
@@ -286,6 +298,11 @@ int reduce64(qcd_ctx *c, int kind, const double2 *a, const double2 *b, long n, i
              const BicgScalars *gate);
 int reduce32(qcd_ctx *c, int kind, const float2 *a, const float2 *b, long n, int nrhs, double *out,
              const BicgScalars *gate);
+// out[rhs][3] = the sums over nblk of the partials [rhs][3][nblk] in c->d_red, in index order
+int reduce_partials(qcd_ctx *c, int nblk, int nrhs, double *out);
+// the same for ntiles partials [rhs][3][ntiles] anywhere in device memory (two fixed levels:
+// contiguous chunks into c->d_red, then those in index order)
+int reduce_tiles(qcd_ctx *c, const double *part, long ntiles, int nrhs, double *out);
 // one scalar step of BiCGStab (SC_*) for every right-hand side; SC_INIT: gate (may be null)
 // deactivates right-hand sides that are inactive in the outer solver
 int scalars(qcd_ctx *c, int stage, BicgScalars *S, const double *red, int nrhs, double tol, const BicgScalars *gate);
@@ -302,6 +319,9 @@ int blas_xr_update64(qcd_ctx *c, double2 *x, double2 *r, const double2 *ph, cons
                      const double2 *t, const BicgScalars *S, long n, int nrhs);
 int blas_xr_update32(qcd_ctx *c, float2 *x, float2 *r, const float2 *ph, const float2 *sh, const float2 *s,
                      const float2 *t, const BicgScalars *S, long n, int nrhs);
+// the same, and out[rhs] = <rh, r>, |r|^2 of the new r (the reduction fused into the update)
+int blas_xr_update_dot32(qcd_ctx *c, float2 *x, float2 *r, const float2 *ph, const float2 *sh, const float2 *s,
+                         const float2 *t, const float2 *rh, const BicgScalars *S, long n, int nrhs, double *out);
 // r = b - w where mask[rhs] (all when mask is null)
 int blas_sub64(qcd_ctx *c, double2 *r, const double2 *b, const double2 *w, const int *mask, long n, int nrhs);
 // rh = r, p = v = 0 where mask[rhs]

@@ -1389,21 +1389,21 @@ int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &np,
         np.smem_bytes = tile_smem_bytes(np.vol, half, 1);
         make_flags(np);
         // per level position: global offset, block-local site and its 8 in-block neighbours
-        // (d = 2 mu + backward; the site itself where the hop leaves the block)
+        // (d = 2 mu + backward; the zero slot vol where the hop leaves the block)
         np.h_tile_pos.assign(2 * (size_t)np.vol, make_int4(0, 0, 0, 0));
         for (int k = 0; k < np.vol; k++) {
             const int yl = np.h_step_site[k];
             int y[4], r = yl, nbk[8], stride = 1;
             for (int m = 0; m < 4; m++) { y[m] = r % b[m]; r /= b[m]; }
             for (int m = 0; m < 4; m++) {
-                nbk[2 * m] = y[m] + 1 < b[m] ? yl + stride : yl;
-                nbk[2 * m + 1] = y[m] > 0 ? yl - stride : yl;
+                nbk[2 * m] = y[m] + 1 < b[m] ? yl + stride : np.vol;
+                nbk[2 * m + 1] = y[m] > 0 ? yl - stride : np.vol;
                 stride *= b[m];
             }
             np.h_tile_pos[2 * k] = make_int4(np.h_site_off[yl], yl, nbk[0] | (nbk[1] << 16), nbk[2] | (nbk[3] << 16));
             np.h_tile_pos[2 * k + 1] = make_int4(nbk[4] | (nbk[5] << 16), nbk[6] | (nbk[7] << 16), 0, 0);
         }
-        return np.vol < (1 << 16) ? QCD_OK : QCD_ERR_ARG;
+        return np.vol < (1 << 16) - 1 ? QCD_OK : QCD_ERR_ARG;
     }
     // the thread form on request (min_ctas = -1), FP32 storage, the block spinor in one CTA
     if (min_ctas == -1 && !half) {
@@ -1683,6 +1683,7 @@ int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int rc;
+    if (p.tile) return tile_sap_apply(c, p, x, v, r, y, omega, nsweep, nsap, nrhs, gate);
     if ((rc = blas_copy(c, r, v, sizeof(float4) * 6 * V * nrhs))) return rc;
     if ((rc = blas_zero(c, x, sizeof(float4) * 6 * V * nrhs))) return rc;
     for (int j = 0; j < nsap; j++) {
@@ -1697,10 +1698,7 @@ int sap_apply_plan(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
             cfg.blockDim = dim3(32 * (oct ? w_oct : p.nwarps));
             prof_begin(c, QCD_K_SSOR, &ev);
             cudaError_t e;
-            if (p.tile) {
-                if ((rc = tile_launch(c, p, col, y, r, nsweep, omega, nrhs, gate))) return rc;
-                e = cudaSuccess;
-            } else if (p.thread) {
+            if (p.thread) {
                 SsorArgs at = a;
                 at.rec = reinterpret_cast<const float4 *>(p.d_rec);
                 at.gb0 = col ? p.nblk[0] : 0;

@@ -50,17 +50,16 @@ int inner_iteration(qcd_ctx *c, const Ws &w, const qcd_params *p) {
     TRY(blas_p_update32(c, f2(w.ip), f2(w.ir), f2(w.iv), w.Si, n, R));
     TRY(sap_apply(c, w.ipt, w.ip, w.sapw, p->omega, p->nsweep, p->nsap, R, w.Si, p->block_solver));
     if (p->learned) TRY(learned_correct(c, w.ipt, w.ip, w.iv, reinterpret_cast<float4 *>(c->net.tmp), R));
-    TRY(dslash32(c, w.iv, w.ipt, R));
-    TRY(reduce32(c, RED_DOT_NORM, f2(w.irh), f2(w.iv), n, R, w.red, w.Si));
+    TRY(dslash32_dot(c, w.iv, w.ipt, R, w.irh, 1, w.red, w.Si));  // v = D p~; <rh, v>, |v|^2
     TRY(scalars(c, SC_ALPHA, w.Si, w.red, R, p->inner_tol, nullptr));
     TRY(blas_s_update32(c, f2(w.is), f2(w.ir), f2(w.iv), w.Si, n, R));
     TRY(sap_apply(c, w.ist, w.is, w.sapw, p->omega, p->nsweep, p->nsap, R, w.Si, p->block_solver));
     if (p->learned) TRY(learned_correct(c, w.ist, w.is, w.it, reinterpret_cast<float4 *>(c->net.tmp), R));
-    TRY(dslash32(c, w.it, w.ist, R));
-    TRY(reduce32(c, RED_DOT_NORMA, f2(w.it), f2(w.is), n, R, w.red, w.Si));
+    TRY(dslash32_dot(c, w.it, w.ist, R, w.is, 2, w.red, w.Si));  // t = D s~; <t, s>, |t|^2
     TRY(scalars(c, SC_OMEGA, w.Si, w.red, R, p->inner_tol, nullptr));
-    TRY(blas_xr_update32(c, f2(w.y), f2(w.ir), f2(w.ipt), f2(w.ist), f2(w.is), f2(w.it), w.Si, n, R));
-    TRY(reduce32(c, RED_DOT_NORM, f2(w.irh), f2(w.ir), n, R, w.red, w.Si));
+    // y += alpha p~ + omega s~, r = s - omega t; <rh, r>, |r|^2
+    TRY(blas_xr_update_dot32(c, f2(w.y), f2(w.ir), f2(w.ipt), f2(w.ist), f2(w.is), f2(w.it), f2(w.irh), w.Si, n, R,
+                             w.red));
     TRY(scalars(c, SC_RHO, w.Si, w.red, R, p->inner_tol, nullptr));
     return QCD_OK;
 }
@@ -168,7 +167,10 @@ int workspace(qcd_ctx *c, int nrhs, int block_solver, Ws *w) {
         c->d_bicg = c->h_bicg = nullptr;
         c->d_mask = c->h_mask = nullptr;
         c->red_rhs = 0;
+        dev_free(c, c->d_red_tiles);
+        c->d_red_tiles = nullptr;
         TRY(dev_alloc(c, (void **)&c->d_red, sizeof(double) * 3 * kRedMaxBlocks * nrhs));
+        TRY(dev_alloc(c, (void **)&c->d_red_tiles, sizeof(double) * 3 * ((V + 127) / 128) * nrhs));
         TRY(dev_alloc(c, (void **)&c->d_scalars, sizeof(double) * 3 * nrhs));
         TRY(dev_alloc(c, &c->d_bicg, sizeof(BicgScalars) * 2 * nrhs));
         TRY(dev_alloc(c, (void **)&c->d_mask, sizeof(int) * nrhs));
@@ -216,18 +218,25 @@ int solve(qcd_ctx *c, double2 *x, const double2 *b, const qcd_params *p, int nrh
 
     TRY(blas_copy(c, w.b, b, b64));
     TRY(blas_copy(c, w.x, x, b64));
-    // |b|^2 per rhs
+    // |b|^2 and |x0|^2 per rhs
     TRY(reduce64(c, RED_NORM, w.b, nullptr, n, R, w.red, nullptr));
-    std::vector<double> bn2(R);
-    {
-        std::vector<double> h(3 * R);
-        QCD_CUDA(c, cudaMemcpyAsync(h.data(), w.red, sizeof(double) * 3 * R, cudaMemcpyDeviceToHost, c->stream));
-        QCD_CUDA(c, cudaStreamSynchronize(c->stream));
-        for (int k = 0; k < R; k++) bn2[k] = h[3 * k + 2];
+    std::vector<double> bn2(R), h(6 * R);
+    QCD_CUDA(c, cudaMemcpyAsync(h.data(), w.red, sizeof(double) * 3 * R, cudaMemcpyDeviceToHost, c->stream));
+    TRY(reduce64(c, RED_NORM, w.x, nullptr, n, R, w.red, nullptr));
+    QCD_CUDA(c, cudaMemcpyAsync(h.data() + 3 * R, w.red, sizeof(double) * 3 * R, cudaMemcpyDeviceToHost, c->stream));
+    QCD_CUDA(c, cudaStreamSynchronize(c->stream));
+    bool x0_zero = true;
+    for (int k = 0; k < R; k++) {
+        bn2[k] = h[3 * k + 2];
+        x0_zero = x0_zero && h[3 * (R + k) + 2] == 0.0;
     }
-    // r = b - D x; rh = r; p = v = 0
-    TRY(dslash64(c, w.tmp, w.x, R));
-    TRY(blas_sub64(c, w.r, w.b, w.tmp, nullptr, n, R));
+    // r = b - D x (r = b when every initial guess is zero); rh = r; p = v = 0
+    if (x0_zero) {
+        TRY(blas_copy(c, w.r, w.b, b64));
+    } else {
+        TRY(dslash64(c, w.tmp, w.x, R));
+        TRY(blas_sub64(c, w.r, w.b, w.tmp, nullptr, n, R));
+    }
     TRY(blas_copy(c, w.rh, w.r, b64));
     TRY(blas_zero(c, w.p, b64));
     TRY(blas_zero(c, w.v, b64));

@@ -14,9 +14,11 @@
 //
 // Records, per block in level order (the order the threads of a level walk), 16-byte aligned:
 // the 8 transport matrices W_d (d = 2 mu + backward: U_mu(n) forward, U_mu(n - mu)^dag
-// backward, zero when the hop leaves the block) as their first two rows (Table 1's 12-real
-// form; the third row is the conjugate cross product of the first two), then the two packed
-// Hermitian chiral blocks of F/2 (72 reals).  FP32: 672 bytes per site; FP16 storage: 336.
+// backward) as their first two rows (Table 1's 12-real form; the third row is the conjugate
+// cross product of the first two), then the two packed Hermitian chiral blocks of F/2 (72
+// reals).  FP32: 672 bytes per site; FP16 storage: 336.  Inside the block a hop that leaves it
+// reads an all-zero spinor slot, so D_BB needs no masks; the same matrices serve the hops
+// between blocks of opposite colour.
 // With FP16 storage the block spinor of each right-hand side is kept in units of the largest
 // |component| of its source on the block (the SSOR iteration is linear), so no rescaling is
 // needed inside the sweep; arithmetic is FP32 throughout.
@@ -120,23 +122,39 @@ template <bool HALF> __device__ __forceinline__ void ld_clover(const uint4 *rec,
 }
 
 struct TileArgs {
-    float4 *y;                 // out: block solutions, plane layout [nrhs][6][V]
-    const float4 *f;           // source (the SAP residual), plane layout
+    float4 *x;                 // M_SAP v being accumulated, plane layout [nrhs][6][V]
+    float4 *r;                 // SAP residual (this colour's sites read and rewritten)
+    float4 *y;                 // block solutions: this colour's sites written, the other colour's read
+    const float4 *v;           // the SAP input (read in the first cycle)
     const uint4 *rec;          // records of this colour's blocks, [block][vol] x TileRec::bytes
     const int4 *pos;           // [vol][2] per level position: (global offset from the block origin,
-                               // block-local site, neighbours 0|1 << 16, 2|3 << 16), (4|5 << 16, 6|7 << 16, 0, 0)
+                               // block-local site, neighbours 0|1 << 16, 2|3 << 16), (4|5 << 16, 6|7 << 16, 0, 0);
+                               // a neighbour outside the block is the zero slot vol
     const int *lev_ptr;        // [nlev + 1] first level position of each level
     const int *origin_site;    // [blocks of this colour] global index of the block origin
+    const int *origin;         // [blocks of this colour][4] coordinates of the block origin
     const BicgScalars *gate;   // per right-hand side; inactive ones are skipped (null: all active)
     float kappa, omega;
     long V;
+    int L[4], bc_t;
     int vol, nlev, nsweep, nrhs;
+    int first;                 // first SAP cycle: the residual starts as v, x as y
+    int cross;                 // add the hops from the other colour's last block solutions first
+    int store_r;               // the residual is needed by a later cycle
+    int store_y;               // the block solutions are needed by the next launch
 };
 
-// y = A_BB f (nsweep SSOR sweeps from 0) on every block of one colour, for the right-hand
-// sides blockIdx.y * R ... + R - 1
+// One colour of one SAP cycle (Eq. (4), Alg. 1, in residual form) on every block of that colour,
+// for the right-hand sides blockIdx.y * R ... + R - 1:
+//   prologue  f = r_c (v in the first cycle) + kappa F H_{cc'} y_{c'}   (the hops from the other
+//             colour's last block solutions, skipped before any exist), written back to r
+//   sweeps    y_c = A_cc f: nsweep SSOR sweeps from 0 in ll order, level by level
+//   epilogue  x_c += y_c (x_c = y_c in the first cycle), r_c = f - D_cc y_c, y_c stored for the
+//             next launch's prologue
+// which is Alg. 1's y = K r, w = D y, x += y, r -= w term by term, with the cross hops of each
+// colour applied by the launch that next reads them.
 template <bool HALF, int R>
-__global__ void __launch_bounds__(kTileMaxThreads, 2) k_ssor_tile(TileArgs a) {
+__global__ void __launch_bounds__(kTileMaxThreads, 2) k_sap_tile(TileArgs a) {
     using L = TileRec<HALF>;
     extern __shared__ __align__(16) float sm[];
     __shared__ float scale_s[R];
@@ -155,39 +173,99 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_ssor_tile(TileArgs a) {
     if (!any) return;  // uniform over the CTA
     const long n0 = a.origin_site[blk];
     const uint4 *recb = a.rec + (size_t)blk * a.vol * L::chunks;
-    float *ys = sm;  // [vol][R][y_words], block-local site order
+    float *ys = sm;  // [vol + 1][R][y_words], block-local site order; site vol is the zero slot
     {
         float4 *y4 = reinterpret_cast<float4 *>(ys);
-        const int nz = a.vol * R * L::y_chunks;
+        const int nz = (a.vol + 1) * R * L::y_chunks;
         for (int i = tid; i < nz; i += T) y4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     const int r_me = tid % R;  // every item this thread takes has right-hand side r_me (T % R == 0)
-    const float4 *fr = a.f + (size_t)(rhs0 + r_me) * 6 * a.V + n0;
-    float inv_scale = 1.f, my_scale = 1.f;
-    if constexpr (HALF) {
-        // largest |component| of each right-hand side's source on the block
-        float m = 0.f;
-        if (act_s[r_me])
-            for (int i = tid; i < a.vol * R; i += T) {
-                const int off = __ldg(a.pos + 2 * (i / R)).x;
+    const bool me_active = act_s[r_me] != 0;
+    const size_t roff = (size_t)(rhs0 + r_me) * 6 * a.V + n0;
+    float4 *rr = a.r + roff;  // this right-hand side's residual, from the block origin
+    const int *org = a.origin + 4 * blk;
+
+    // ---- prologue: f = r (or v) + kappa F H_{cc'} y_{c'} on the block's sites, into r ----
+    float m = 0.f;  // largest |component| of f seen by this thread (FP16 scale)
+    if (me_active)
+        for (int i = tid; i < a.vol * R; i += T) {
+            const int pos = i / R;
+            const int4 pa = __ldg(a.pos + 2 * pos), pb = __ldg(a.pos + 2 * pos + 1);
+            float2 f[12];
+            if (a.first) load_spinor(a.v + roff, a.V, pa.x, f);
+            else load_spinor_rw(rr, a.V, pa.x, f);
+            if (a.cross) {
+                const int nb[8] = {pa.z & 0xffff, pa.z >> 16, pa.w & 0xffff, pa.w >> 16,
+                                   pb.x & 0xffff, pb.x >> 16, pb.y & 0xffff, pb.y >> 16};
+                if (nb[0] == a.vol || nb[1] == a.vol || nb[2] == a.vol || nb[3] == a.vol || nb[4] == a.vol ||
+                    nb[5] == a.vol || nb[6] == a.vol || nb[7] == a.vol) {
+                    // the offset from the block origin, sum_mu y_mu st_mu with 0 <= y_mu < L_mu, gives
+                    // the block-local coordinates y_mu
+                    const long st[4] = {1, a.L[0], (long)a.L[0] * a.L[1], (long)a.L[0] * a.L[1] * a.L[2]};
+                    int xg[4];
+                    long off = pa.x;
+                    for (int mu = 3; mu >= 0; mu--) {
+                        xg[mu] = org[mu] + (int)(off / st[mu]);
+                        off %= st[mu];
+                    }
+                    const uint4 *rec = recb + (size_t)pos * L::chunks;
+                    const float4 *yr = a.y + (size_t)(rhs0 + r_me) * 6 * a.V;
+                    float2 acc[12], psi[12], Wf[9], Wb[9];
 #pragma unroll
-                for (int k = 0; k < 6; k++) {
-                    const float4 v = __ldg(fr + (long)k * a.V + off);
-                    m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+                    for (int k = 0; k < 12; k++) acc[k] = make_float2(0.f, 0.f);
+#define QCD_TILE_CROSS(MU)                                                                          \
+                    if (nb[2 * MU] == a.vol || nb[2 * MU + 1] == a.vol) {                            \
+                        ld_links<HALF>(rec, MU, Wf, Wb);                                             \
+                        if (nb[2 * MU] == a.vol) {                                                   \
+                            const bool wrap = xg[MU] == a.L[MU] - 1;                                 \
+                            const long mm = n0 + pa.x + (wrap ? -(long)(a.L[MU] - 1) * st[MU] : st[MU]); \
+                            load_spinor(yr, a.V, mm, psi);                                           \
+                            hop_term_w<MU, true>(psi, Wf, acc, (MU == 3 && wrap) ? (float)a.bc_t : 1.f); \
+                        }                                                                            \
+                        if (nb[2 * MU + 1] == a.vol) {                                               \
+                            const bool wrap = xg[MU] == 0;                                           \
+                            const long mm = n0 + pa.x + (wrap ? (long)(a.L[MU] - 1) * st[MU] : -st[MU]); \
+                            load_spinor(yr, a.V, mm, psi);                                           \
+                            hop_term_w<MU, false>(psi, Wb, acc, (MU == 3 && wrap) ? (float)a.bc_t : 1.f); \
+                        }                                                                            \
+                    }
+                    QCD_TILE_CROSS(0)
+                    QCD_TILE_CROSS(1)
+                    QCD_TILE_CROSS(2)
+                    QCD_TILE_CROSS(3)
+#undef QCD_TILE_CROSS
+                    float fc[72];
+                    ld_clover<HALF>(rec, fc);
+                    float2 fa[12];
+                    clover_mul<float, float2>(fc, acc, fa);
+#pragma unroll
+                    for (int k = 0; k < 12; k++) {
+                        f[k].x = fmaf(a.kappa, fa[k].x, f[k].x);
+                        f[k].y = fmaf(a.kappa, fa[k].y, f[k].y);
+                    }
                 }
             }
+            store_spinor(rr, a.V, pa.x, f);
+            if constexpr (HALF) {
+#pragma unroll
+                for (int k = 0; k < 12; k++) m = fmaxf(m, fmaxf(fabsf(f[k].x), fabsf(f[k].y)));
+            }
+        }
+    float inv_scale = 1.f, my_scale = 1.f;
+    if constexpr (HALF) {
 #pragma unroll
         for (int o = 16; o >= R; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
         if ((tid & 31) < R) atomicMax(reinterpret_cast<int *>(&scale_s[tid & 31]), __float_as_int(m));
-        __syncthreads();
+    }
+    __syncthreads();  // f is in r (and the FP16 scales are known) for every site of the block
+    if constexpr (HALF) {
         my_scale = scale_s[r_me] > 0.f ? scale_s[r_me] : 1.f;
         inv_scale = 1.f / my_scale;
     }
-    const bool me_active = act_s[r_me] != 0;
-    __syncthreads();
 
-    auto update = [&](int pos) {
-        const int4 pa = __ldg(a.pos + 2 * pos), pb = __ldg(a.pos + 2 * pos + 1);
+    // the in-block hop sum (D_BB without its diagonal) of the block spinor at level position pos,
+    // with the clover term applied: fa = F H_BB y (FP16: in the units of the right-hand side's scale)
+    auto block_FH = [&](int pos, const int4 &pa, const int4 &pb, float2 fa[12]) {
         const int nb[8] = {pa.z & 0xffff, pa.z >> 16, pa.w & 0xffff, pa.w >> 16,
                            pb.x & 0xffff, pb.x >> 16, pb.y & 0xffff, pb.y >> 16};
         const uint4 *rec = recb + (size_t)pos * L::chunks;
@@ -195,7 +273,7 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_ssor_tile(TileArgs a) {
 #pragma unroll
         for (int k = 0; k < 12; k++) acc[k] = make_float2(0.f, 0.f);
         float2 psi[12], Wf[9], Wb[9];
-        // in-block hops only (D_BB): an out-of-block direction has a zero matrix and points at the site itself
+        // a direction leaving the block reads the zero slot, so it adds nothing
 #define QCD_TILE_HOP(MU)                                                                  \
         ld_links<HALF>(rec, MU, Wf, Wb);                                                  \
         ld_y<HALF>(ys + (nb[2 * MU] * R + r_me) * L::y_words, psi);                       \
@@ -209,10 +287,16 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_ssor_tile(TileArgs a) {
 #undef QCD_TILE_HOP
         float fc[72];
         ld_clover<HALF>(rec, fc);
-        float2 fa[12];
         clover_mul<float, float2>(fc, acc, fa);
+    };
+
+    // one SSOR site update: y <- y + omega (f + kappa F H_BB y - y)
+    auto update = [&](int pos) {
+        const int4 pa = __ldg(a.pos + 2 * pos), pb = __ldg(a.pos + 2 * pos + 1);
+        float2 fa[12];
+        block_FH(pos, pa, pb, fa);
         float2 fv[12];
-        load_spinor(fr, a.V, pa.x, fv);
+        load_spinor_rw(rr, a.V, pa.x, fv);
         float *yp = ys + (pa.y * R + r_me) * L::y_words;
         float2 yo[12];
         ld_y<HALF>(yp, yo);
@@ -238,18 +322,42 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_ssor_tile(TileArgs a) {
                 for (int i = tid; i < cnt; i += T) update(p0 + i / R);
         }
     __syncthreads();
-    // the block solutions of the active right-hand sides, back to the lattice
-    for (int i = tid; i < a.vol * R; i += T) {
-        if (!me_active) break;
-        const int4 pa = __ldg(a.pos + 2 * (i / R));
-        float2 v[12];
-        ld_y<HALF>(ys + (pa.y * R + r_me) * L::y_words, v);
-        float4 *yo = a.y + (size_t)(rhs0 + r_me) * 6 * a.V + n0 + pa.x;
+
+    // ---- epilogue: x += y, r = f - D_BB y = f - y + kappa F H_BB y, y to the lattice ----
+    if (me_active) {
+        float4 *xr = a.x + roff;
+        float4 *yo4 = a.y + roff;
+        for (int i = tid; i < a.vol * R; i += T) {
+            const int pos = i / R;
+            const int4 pa = __ldg(a.pos + 2 * pos), pb = __ldg(a.pos + 2 * pos + 1);
+            float2 yv[12];
+            ld_y<HALF>(ys + (pa.y * R + r_me) * L::y_words, yv);
+            if constexpr (HALF) {
 #pragma unroll
-        for (int k = 0; k < 6; k++) {
-            float2 lo = v[2 * k], hi = v[2 * k + 1];
-            if constexpr (HALF) { lo = cscale(lo, my_scale); hi = cscale(hi, my_scale); }
-            yo[(long)k * a.V] = make_float4(lo.x, lo.y, hi.x, hi.y);
+                for (int k = 0; k < 12; k++) yv[k] = cscale(yv[k], my_scale);
+            }
+            if (a.store_r) {
+                float2 fa[12], f[12];
+                block_FH(pos, pa, pb, fa);
+                load_spinor_rw(rr, a.V, pa.x, f);
+#pragma unroll
+                for (int k = 0; k < 12; k++) {
+                    if constexpr (HALF) fa[k] = cscale(fa[k], my_scale);
+                    f[k].x = fmaf(a.kappa, fa[k].x, f[k].x - yv[k].x);
+                    f[k].y = fmaf(a.kappa, fa[k].y, f[k].y - yv[k].y);
+                }
+                store_spinor(rr, a.V, pa.x, f);
+            }
+            if (a.first) {
+                store_spinor(xr, a.V, pa.x, yv);
+            } else {
+                float2 xv[12];
+                load_spinor_rw(xr, a.V, pa.x, xv);
+#pragma unroll
+                for (int k = 0; k < 12; k++) xv[k] = cadd(xv[k], yv[k]);
+                store_spinor(xr, a.V, pa.x, xv);
+            }
+            if (a.store_y) store_spinor(yo4, a.V, pa.x, yv);
         }
     }
 }
@@ -274,18 +382,16 @@ __global__ void k_tile_records(uint4 *__restrict__ rec, const float2 *__restrict
     for (int d = 0; d < 8; d++) {
         const int mu = d >> 1;
         const bool fwd = (d & 1) == 0;
-        const bool in = fwd ? y[mu] + 1 < b[mu] : y[mu] > 0;
-        const long src = fwd ? n : n - gs[mu];
+        // the backward link of a site on the lattice's lower face wraps around (periodic links)
+        const long src = fwd ? n : (o[mu] + y[mu] == 0 ? n + (long)(g.L[mu] - 1) * gs[mu] : n - gs[mu]);
         for (int k = 0; k < 6; k++) {  // rows 0, 1 of W
             const int ra = k / 3, cb = k % 3;
-            float2 w = make_float2(0.f, 0.f);
-            if (in) {
-                if (fwd) {
-                    w = U[(long)(mu * 9 + ra * 3 + cb) * g.V + src];
-                } else {
-                    w = U[(long)(mu * 9 + cb * 3 + ra) * g.V + src];
-                    w.y = -w.y;
-                }
+            float2 w;
+            if (fwd) {
+                w = U[(long)(mu * 9 + ra * 3 + cb) * g.V + src];
+            } else {
+                w = U[(long)(mu * 9 + cb * 3 + ra) * g.V + src];
+                w.y = -w.y;
             }
             if constexpr (HALF) reinterpret_cast<unsigned *>(R + d * L::link_bytes)[k] = f2h(w);
             else reinterpret_cast<float2 *>(R + d * L::link_bytes)[k] = w;
@@ -307,7 +413,8 @@ template <bool HALF> constexpr int y_bytes_per_site() { return TileRec<HALF>::y_
 }  // namespace
 
 size_t tile_smem_bytes(int vol, bool half, int R) {
-    return (size_t)vol * R * (half ? y_bytes_per_site<true>() : y_bytes_per_site<false>());
+    // the block spinors of R right-hand sides and the zero slot
+    return (size_t)(vol + 1) * R * (half ? y_bytes_per_site<true>() : y_bytes_per_site<false>());
 }
 
 int tile_build_records(qcd_ctx *c, const SapPlan &p, void *rec) {
@@ -328,18 +435,21 @@ int tile_build_records(qcd_ctx *c, const SapPlan &p, void *rec) {
 }
 
 int tile_set_attributes(qcd_ctx *c) {
-    const void *ks[] = {(const void *)k_ssor_tile<false, 1>, (const void *)k_ssor_tile<false, 2>,
-                        (const void *)k_ssor_tile<false, 4>, (const void *)k_ssor_tile<false, 8>,
-                        (const void *)k_ssor_tile<true, 1>,  (const void *)k_ssor_tile<true, 2>,
-                        (const void *)k_ssor_tile<true, 4>,  (const void *)k_ssor_tile<true, 8>};
+    const void *ks[] = {(const void *)k_sap_tile<false, 1>, (const void *)k_sap_tile<false, 2>,
+                        (const void *)k_sap_tile<false, 4>, (const void *)k_sap_tile<false, 8>,
+                        (const void *)k_sap_tile<true, 1>,  (const void *)k_sap_tile<true, 2>,
+                        (const void *)k_sap_tile<true, 4>,  (const void *)k_sap_tile<true, 8>};
     for (const void *k : ks)
         QCD_CUDA(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemLimit));
     return QCD_OK;
 }
 
 int tile_choose(const SapPlan &p, int nrhs, int *R, int *threads, size_t *smem) {
+    // the most right-hand sides per CTA (up to 8) that still let two CTAs share an SM (the
+    // registers allow two of 256 threads); one per CTA up to the whole shared memory otherwise
+    const size_t two_per_sm = kTileSmemPerSm / 2 - 1024;
     int r = 1;
-    while (r * 2 <= kTileMaxRhs && r * 2 <= nrhs && tile_smem_bytes(p.vol, p.half, r * 2) <= kTileSmemLimit) r *= 2;
+    while (r * 2 <= kTileMaxRhs && r * 2 <= nrhs && tile_smem_bytes(p.vol, p.half, r * 2) <= two_per_sm) r *= 2;
     if (tile_smem_bytes(p.vol, p.half, r) > kTileSmemLimit) return QCD_ERR_ARG;
     int t = ((p.max_step * r + 31) / 32) * 32;
     t = std::max(32, std::min(t, kTileMaxThreads));
@@ -349,37 +459,53 @@ int tile_choose(const SapPlan &p, int nrhs, int *R, int *threads, size_t *smem) 
     return QCD_OK;
 }
 
-int tile_launch(qcd_ctx *c, const SapPlan &p, int col, float4 *y, const float4 *f, int nsweep, double omega,
-                int nrhs, const BicgScalars *gate) {
+int tile_sap_apply(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, float4 *r, float4 *y, double omega,
+                   int nsweep, int nsap, int nrhs, const BicgScalars *gate) {
     int R = 1, T = 32;
     size_t smem = 0;
     if (tile_choose(p, nrhs, &R, &T, &smem)) return fail(c, QCD_ERR_ARG, "SAP block too large for the tile form");
     TileArgs a;
+    a.x = x;
+    a.r = r;
     a.y = y;
-    a.f = f;
-    a.rec = reinterpret_cast<const uint4 *>(p.d_rec) + (size_t)(col ? p.nblk[0] : 0) * p.vol *
-                                                           ((p.half ? kTileRecordBytesHalf : kTileRecordBytes) / 16);
+    a.v = v;
     a.pos = p.d_tile_pos;
     a.lev_ptr = p.d_lev_ptr;
-    a.origin_site = p.d_origin_site[col];
     a.gate = gate;
     a.kappa = (float)c->kappa;
     a.omega = (float)omega;
     a.V = c->lat.V;
+    for (int m = 0; m < 4; m++) a.L[m] = c->lat.L[m];
+    a.bc_t = c->bc_t;
     a.vol = p.vol;
     a.nlev = p.nsteps;
     a.nsweep = nsweep;
     a.nrhs = nrhs;
-    const dim3 grid(p.nblk[col], (nrhs + R - 1) / R);
     void (*k)(TileArgs) = nullptr;
     switch (R) {
-        case 1: k = p.half ? k_ssor_tile<true, 1> : k_ssor_tile<false, 1>; break;
-        case 2: k = p.half ? k_ssor_tile<true, 2> : k_ssor_tile<false, 2>; break;
-        case 4: k = p.half ? k_ssor_tile<true, 4> : k_ssor_tile<false, 4>; break;
-        default: k = p.half ? k_ssor_tile<true, 8> : k_ssor_tile<false, 8>; break;
+        case 1: k = p.half ? k_sap_tile<true, 1> : k_sap_tile<false, 1>; break;
+        case 2: k = p.half ? k_sap_tile<true, 2> : k_sap_tile<false, 2>; break;
+        case 4: k = p.half ? k_sap_tile<true, 4> : k_sap_tile<false, 4>; break;
+        default: k = p.half ? k_sap_tile<true, 8> : k_sap_tile<false, 8>; break;
     }
-    k<<<grid, T, smem, c->stream>>>(a);
-    return check_launch(c, "launch of the tile SSOR kernel");
+    const size_t rec_words = (size_t)p.vol * ((p.half ? kTileRecordBytesHalf : kTileRecordBytes) / 16);
+    for (int j = 0; j < nsap; j++)
+        for (int col = 0; col < 2; col++) {
+            const bool last = j == nsap - 1;
+            a.rec = reinterpret_cast<const uint4 *>(p.d_rec) + (size_t)(col ? p.nblk[0] : 0) * rec_words;
+            a.origin_site = p.d_origin_site[col];
+            a.origin = p.d_origin[col];
+            a.first = j == 0;
+            a.cross = !(j == 0 && col == 0);
+            a.store_r = !last;
+            a.store_y = !(last && col == 1);
+            cudaEvent_t ev;
+            prof_begin(c, QCD_K_SSOR, &ev);
+            k<<<dim3(p.nblk[col], (nrhs + R - 1) / R), T, smem, c->stream>>>(a);
+            int rc = prof_end(c, QCD_K_SSOR, ev);
+            if (rc) return rc;
+        }
+    return QCD_OK;
 }
 
 }  // namespace qcd

@@ -138,7 +138,7 @@ def test_ssor_schedule_is_consistent(geom, ctas, half):
     if ctas == -2:
         # the tile form holds one right-hand side's block spinor in one CTA (12 or 24 words per
         # site), else the automatic cluster form stands in
-        fits = np.prod(b) * (48 if half else 96) <= 200 * 1024
+        fits = (np.prod(b) + 1) * (48 if half else 96) <= 200 * 1024
         assert t["thread"] == (2 if fits else 0)
         if fits:
             assert t["ctas"] == 1 and t["chunks"] == t["levels"]
