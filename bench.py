@@ -1,16 +1,20 @@
-"""Benchmark: time to solve D x = b to a true relative residual of 1e-10 on
-the 12^3 x 24 lattice (plain method: FP64 outer / FP32 inner nested BiCGStab,
-SAP blocks 6^3 x 12, ll sub-blocks 3^3 x 6, SSOR omega = 1, 4 sweeps, 4 SAP
-cycles), plus the bandwidth of the operator D on lattices larger than L2.
+"""Benchmark: time to solve D x = b to a true relative residual of 1e-10 for the
+12 spin-colour point sources on the 48^3 x 96 lattice (kappa 0.122, c_SW 1.6,
+links exp(i 0.3 X)): the chosen set-up (autotuned SAP geometry and kernel form,
+FP16 storage inside SAP, FP32 inner / FP64 outer BiCGStab) against the plain one
+(6^3 x 12 blocks, 3^3 x 6 ll sub-blocks, FP32 SAP, 4 sweeps, 4 cycles), plus the
+bandwidth of the operator D.
 
-One step = one full solve from x0 = 0 (every kernel of the solver runs in
-the step).  Prints one JSON line.  ``--impl reference`` times the FP64 CPU
-oracle instead: each step is one full oracle solve of the same workload on
-the host cores (10-20 s of CPU work).
+One step = one complete solve of all 12 sources from x0 = 0 (every kernel of the
+solver runs in the step; the sources are solved in right-hand-side groups that
+fit the GPU's memory).  Prints one JSON line.  ``--impl reference`` times the
+FP64 CPU oracle instead, on a bounded sample of the same workload, scaled to the
+same unit.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -23,31 +27,59 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "solve time to rel. residual 1e-10, chosen vs plain; D GB/s vs HBM peak"
-WORKLOAD = dict(name="12^3x24 plain nested BiCGStab + SAP(6^3x12 blocks, 3^3x6 ll sub-blocks)",
-                dims=(12, 12, 12, 24), kappa=0.12, csw=1.6, eps=0.3, gauge_seed=1001, source_seed=2001,
-                block=(6, 6, 6, 12), subblock=(3, 3, 3, 6), omega=1.0, nsweep=4, nsap=4, tol=1e-10,
-                inner_tol=1e-5)
+HEADLINE = dict(name="48^3x96 kappa 0.122 c_SW 1.6, 12 spin-colour point sources, nested BiCGStab to 1e-10 "
+                     "(chosen SAP set-up)",
+                dims=(48, 48, 48, 96), kappa=0.122, csw=1.6, eps=0.3, gauge_seed=1004, sources=12, rhs_group=4,
+                tol=1e-10, inner_tol=1e-5,
+                plain=dict(block=(6, 6, 6, 12), subblock=(3, 3, 3, 6), omega=1.0, nsweep=4, nsap=4))
+# the autotuner runs on a 16 times smaller lattice of the same family (same kappa, c_SW, link
+# roughness), and its winner is applied to the headline lattice
+TUNE = dict(dims=(24, 24, 24, 48), gauge_seed=1003, sources=4, candidates=40)
+# extra line items: the 12^3 x 24 workload (plain = its literal set-up) and the D bandwidths
+SMALL = dict(dims=(12, 12, 12, 24), kappa=0.12, csw=1.6, eps=0.3, gauge_seed=1001, source_seed=2001,
+             block=(6, 6, 6, 12), subblock=(3, 3, 3, 6), omega=1.0, nsweep=4, nsap=4, tol=1e-10, inner_tol=1e-5)
+# bounded oracle sample for the CPU legs: point-source solves on an 8^3 x 16 lattice of the same
+# family with a fixed SAP set-up of the kind the tuner picks (4^4 blocks, 2^4 sub-blocks, 2
+# sweeps, 2 cycles), scaled to the headline by the site count and the number of sources
+ORACLE_SAMPLE = dict(dims=(8, 8, 8, 16), gauge_seed=1005, kappa=0.122, csw=1.6, block=(4, 4, 4, 4),
+                     subblock=(2, 2, 2, 2), omega=1.0, nsweep=2, nsap=2, tol=1e-10, inner_tol=1e-5)
 TABLE1_FLOP_PER_SITE = 1896  # flop per site of the clover hopping matrix without SU(3) reconstruction (Table 1)
 D_BYTES_PER_SITE = {"f32": 768, "f64": 1536, "f16": 480, "su3": 672}  # in + out spinor, 4 links (each shared by 2 sites), clover
-L2_FLUSH_BYTES = 512 << 20
-# DRAM bytes (read + write) per launch of a kernel class on this workload, from one ncu capture
-# of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum); None where not captured
-NCU_TRAFFIC = {"ssor": 28918016 + 0}
-# warp instructions per launch and SMs the launch occupies, from the ncu capture of the plain
-# workload's SSOR kernel (profiles/ssor_level_12x12x12x24_c8.md): 64 CTAs, one per SM
-NCU_ISSUE = {"ssor": (66.6e6, 64)}
+L2_BYTES = 126 << 20
+# DRAM bytes (read + write) per unit of work of a kernel, from one ncu capture of the kernel
+# source identified by its SHA-256 prefix; reported only while the source is unchanged
+NCU_TRAFFIC = {}
 
 
-def issue_model(cls, avg_ms, sm_mhz):
-    """The instruction-issue floor of a kernel class: its warp instructions per launch issued at
-    4 per cycle (one per SM sub-partition) on the SMs it occupies, against the measured launch
-    time.  None when the class has no instruction count."""
-    if cls not in NCU_ISSUE or not avg_ms or not sm_mhz:
-        return None
-    instr, sms = NCU_ISSUE[cls]
-    floor_ms = instr / (sms * 4.0 * sm_mhz * 1e6) * 1e3
-    return {"warp_instructions_per_launch": instr, "sms": sms, "issue_per_cycle_per_sm": 4,
-            "floor_ms": floor_ms, "avg_launch_ms": avg_ms, "frac": floor_ms / avg_ms}
+def volume(dims):
+    V = 1
+    for L in dims:
+        V *= L
+    return V
+
+
+def source_sha(rel):
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def sap_flop_per_launch(V, nrhs, nsweep):
+    """Algorithmic flops of one launch of the tile SAP kernel (one colour): V/2 sites x nrhs x
+    (2 nsweep SSOR site updates + the residual's in-block operator) x Table 1's 1896 flop."""
+    return (V / 2) * nrhs * (2 * nsweep + 1) * TABLE1_FLOP_PER_SITE
+
+
+def kernel_model(cls, V, nrhs, prm, peaks):
+    """(bound, algorithmic units per launch, unit, peak, peak source) for a kernel class; nrhs
+    right-hand sides per launch."""
+    if cls == "ssor":
+        return ("alu", sap_flop_per_launch(V, nrhs, prm["nsweep"]) / 1e12, "TFLOP/s", peaks["fp32_tflops"],
+                peaks["fp32_source"])
+    if cls == "dslash32":
+        return "hbm", V * (192 * nrhs + 576) / 1e9, "GB/s", peaks["hbm_gbs"], peaks["source"]
+    if cls == "dslash64":
+        return "hbm", V * (384 * nrhs + 1152) / 1e9, "GB/s", peaks["hbm_gbs"], peaks["source"]
+    return None
 
 
 def read_peaks():
@@ -55,9 +87,13 @@ def read_peaks():
     try:
         with open(path) as f:
             p = json.load(f)
-        return dict(hbm_gbs=float(p["hbm_gbs"]), sm_max_mhz=float(p.get("sm_max_mhz", 2070.0)), source="measured")
+        out = dict(hbm_gbs=float(p["hbm_gbs"]), sm_max_mhz=float(p.get("sm_max_mhz", 2070.0)), source="measured")
     except Exception:
-        return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
+        out = dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
+    # derived FP32 peak, replaced by the measured one in the GPU arm
+    out["fp32_tflops"] = 152 * 128 * 2 * out["sm_max_mhz"] * 1e6 / 1e12
+    out["fp32_source"] = "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"
+    return out
 
 
 class ClockSampler:
@@ -128,54 +164,72 @@ def max_over_ranks(value: float, world: int, device: str = "cuda") -> float:
     return float(t.item())
 
 
+def cores_used():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle sample (cpu_baseline leg and --impl reference)
 # ---------------------------------------------------------------------------
 
-def oracle_setup():
+def oracle_sample_setup():
+    import numpy as np
+
     import oracle
     import qcd_inputs as qi
-    w = WORKLOAD
-    U = qi.gauge_field(w["dims"], w["eps"], seed=w["gauge_seed"])
+    w = ORACLE_SAMPLE
+    U = qi.gauge_field(w["dims"], 0.3, seed=w["gauge_seed"])
     _, F = oracle.clover(w["dims"], U, w["csw"], w["kappa"])
-    b = qi.gaussian_spinor(w["dims"], seed=w["source_seed"])[0]
-    return U, F, b
+    pts = qi.point_sources(w["dims"])
+    return U, F, np.ascontiguousarray(pts)
 
 
-def oracle_solve_seconds(U, F, b):
-    """Wall seconds of one full oracle solve of the workload (FP64 outer and inner)."""
+def oracle_point_solve(U, F, pts, k):
+    """Wall seconds and stats of one oracle solve of point source k on the sample lattice."""
     import oracle
-    w = WORKLOAD
+    w = ORACLE_SAMPLE
     t0 = time.perf_counter()
     _, status, st = oracle.solve(w["dims"], U, F, w["kappa"], w["block"], w["subblock"], w["omega"], w["nsweep"],
-                                 w["nsap"], b, tol=w["tol"], inner_tol=w["inner_tol"])
+                                 w["nsap"], pts[k], tol=w["tol"], inner_tol=w["inner_tol"])
     return time.perf_counter() - t0, status, st
 
 
-def cores_used():
-    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+def oracle_scale():
+    """Seconds of one sample solve -> seconds of the headline's 12-source solve (site ratio x sources)."""
+    return volume(HEADLINE["dims"]) / volume(ORACLE_SAMPLE["dims"]) * HEADLINE["sources"]
+
+
+def oracle_sample_text(what):
+    w = ORACLE_SAMPLE
+    return ("%s FP64 oracle solve(s) to 1e-10 of spin-colour point sources on %s (kappa %.3f, blocks %s, sub-blocks "
+            "%s, %d sweeps, %d cycles), seconds per solve scaled by the site ratio %d and by %d sources: an "
+            "estimate of the oracle on the headline workload, not a measurement of it (its iteration counts "
+            "grow with the volume)" % (what, "x".join(map(str, w["dims"])), w["kappa"], "x".join(map(str, w["block"])),
+                                       "x".join(map(str, w["subblock"])), w["nsweep"], w["nsap"],
+                                       volume(HEADLINE["dims"]) // volume(ORACLE_SAMPLE["dims"]),
+                                       HEADLINE["sources"]))
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    U, F, b = oracle_setup()
-    for _ in range(args.warmup):
-        oracle_solve_seconds(U, F, b)
-    vals = []
-    for _ in range(args.steps):
-        t, status, st = oracle_solve_seconds(U, F, b)
+    U, F, pts = oracle_sample_setup()
+    for i in range(args.warmup):
+        oracle_point_solve(U, F, pts, i % 12)
+    vals, its = [], []
+    for i in range(args.steps):
+        t, status, st = oracle_point_solve(U, F, pts, i % 12)
         vals.append(t)
-    v = statistics.mean(vals)
-    sample = ("per step: one full FP64 oracle solve of the 12^3x24 workload from x0 = 0 to 1e-10 "
-              "(outer %d, inner %d iterations, true rel. residual %.1e)" % (st["outer"], st["inner"],
-                                                                             st["true_rel_res"]))
+        its.append((st["outer"], st["inner"]))
+    v = statistics.mean(vals) * oracle_scale()
+    sample = "per step: " + oracle_sample_text("one") + "; iterations (outer, inner) per step %s" % its[:12]
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1000 * v, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD["name"], "lattice": "12x12x12x24", "kappa": WORKLOAD["kappa"],
-                      "csw": WORKLOAD["csw"], "tol": WORKLOAD["tol"]},
+           "config": {"workload": HEADLINE["name"], "lattice": "x".join(map(str, HEADLINE["dims"])),
+                      "kappa": HEADLINE["kappa"], "csw": HEADLINE["csw"], "sources": HEADLINE["sources"],
+                      "tol": HEADLINE["tol"]},
            "cpu_baseline": {"value": v, "unit": "s", "cores": cores_used(), "kind": "oracle", "sample": sample},
            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -186,33 +240,38 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def kernel_model(cls, V, nrhs_steps, prm, peaks):
-    """(bound, algorithmic units per launch, unit, peak) for a kernel class."""
-    fp32_tflops = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
-    if cls == "dslash32":
-        return "hbm", V * D_BYTES_PER_SITE["f32"] / 1e9, "GB/s", peaks["hbm_gbs"]
-    if cls == "dslash64":
-        return "hbm", V * D_BYTES_PER_SITE["f64"] / 1e9, "GB/s", peaks["hbm_gbs"]
-    if cls == "ssor":
-        # one launch: the V/2 sites of one colour, 2 passes per sweep, Table-1 flops per site update
-        return "alu", (V / 2) * 2 * prm["nsweep"] * TABLE1_FLOP_PER_SITE / 1e12, "TFLOP/s", fp32_tflops
-    if cls == "saphop":
-        return "hbm", V * D_BYTES_PER_SITE["f32"] / 1e9, "GB/s", peaks["hbm_gbs"]
-    return None
+def point_sources_torch(torch, dims, first, count):
+    """Spin-colour point sources first..first+count-1 at the origin, complex128 on the device."""
+    b = torch.zeros((count, volume(dims), 4, 3), dtype=torch.complex128, device="cuda")
+    for j in range(count):
+        k = first + j
+        b[j, 0, k // 3, k % 3] = 1.0
+    return b
 
 
-def dslash_bandwidth(q, torch, dims, iters, peaks, seed=1002, variants=(("f32", 1),)):
-    """GB/s of the operator D (K1) on internal-layout buffers, CUDA events on the context stream,
-    for each (precision, right-hand sides) variant."""
-    import qcd_inputs as qi
-    V = qi.volume(dims)
+def event_ms(torch, stream, fn):
+    """Device milliseconds of fn() on the stream (CUDA events, synchronised), and fn's result."""
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    r = fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b), r
+
+
+def dslash_bandwidth(q, qi, torch, stream, dims, iters, peaks, seed=1002, variants=(("f32", 1),)):
+    """GB/s of the operator D (internal layout, no conversions) for each (precision, right-hand
+    sides) variant; CUDA events on the context stream, L2 flushed before every launch."""
+    V = volume(dims)
     U = qi.gauge_field(dims, 0.3, seed=seed, device="cuda")
-    s = q.Solver(dims)
+    torch.cuda.synchronize()
+    s = q.Solver(dims, stream=stream.cuda_stream)
     s.load_gauge(U)
     del U
     s.build_clover(0.12, 1.6)
-    stream = torch.cuda.current_stream()
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     out = []
     for prec, nrhs in variants:
         pc = {"f32": q.QCD_F32, "f64": q.QCD_F64, "f16": q.QCD_F16, "su3": q.QCD_F32_SU3}[prec]
@@ -220,15 +279,9 @@ def dslash_bandwidth(q, torch, dims, iters, peaks, seed=1002, variants=(("f32", 
         times = []
         for _ in range(iters):
             flush.fill_(1.0)
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            q.qcd_bench_dslash(s.ctx, pc, nrhs, 1)
-            b.record(stream)
-            torch.cuda.synchronize()
-            times.append(a.elapsed_time(b))
+            ms, _ = event_ms(torch, stream, lambda: q.qcd_bench_dslash(s.ctx, pc, nrhs, 1))
+            times.append(ms)
         ms = statistics.median(times)
-        # per right-hand side: both spinors; links and clover once per launch
         spin = 384 if prec == "f64" else 192  # FP16 storage keeps FP32 spinors
         field = D_BYTES_PER_SITE[prec] - spin
         byts = V * (spin * nrhs + field)
@@ -242,6 +295,63 @@ def dslash_bandwidth(q, torch, dims, iters, peaks, seed=1002, variants=(("f32", 
     torch.cuda.empty_cache()
     return out
 
+
+def oracle_true_residuals(dims, U_dev, kappa, csw, x, b):
+    """||b - D x|| / ||b|| per right-hand side under the oracle's FP64 D (host), x and b
+    complex128 [n][V][4][3] device tensors; the links copied from the device."""
+    import numpy as np
+
+    import oracle
+    U = U_dev.cpu().numpy()
+    _, F = oracle.clover(dims, U, csw, kappa)
+    out = []
+    for k in range(x.shape[0]):
+        xk, bk = x[k].cpu().numpy(), b[k].cpu().numpy()
+        r = bk - oracle.apply_D(dims, U, F, kappa, xk)
+        out.append(float(np.linalg.norm(r) / np.linalg.norm(bk)))
+    return out
+
+
+def host_bytes_available():
+    try:
+        return os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    except (ValueError, OSError):
+        return 0
+
+
+def tune_chosen(q, qi, torch, stream, args):
+    """The chosen set-up: qcd_autotune on the 24^3 x 48 lattice of the same family (kappa 0.122,
+    four point sources), its solutions checked under the oracle's D."""
+    w = HEADLINE
+    dims = TUNE["dims"]
+    U = qi.gauge_field(dims, w["eps"], seed=TUNE["gauge_seed"], device="cuda")
+    torch.cuda.synchronize()
+    sv = q.Solver(dims, stream=stream.cuda_stream)
+    sv.load_gauge(U)
+    sv.build_clover(w["kappa"], w["csw"])
+    b = point_sources_torch(torch, dims, 0, TUNE["sources"])
+    p = w["plain"]
+    base = q.make_params(w["kappa"], w["csw"], p["block"], p["subblock"], omega=p["omega"], nsweep=p["nsweep"],
+                         nsap=p["nsap"], tol=w["tol"], inner_tol=w["inner_tol"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    best, best_ms = q.qcd_autotune(sv.ctx, b, base, nrhs=TUNE["sources"], max_candidates=args.tune_candidates)
+    t_tune = time.perf_counter() - t0
+    x = torch.zeros_like(b)
+    st = sv.solve(x, b, best, nrhs=TUNE["sources"])
+    info = {"lattice": "x".join(map(str, dims)), "sources": TUNE["sources"], "seconds": t_tune,
+            "candidates": args.tune_candidates, "best_ms": best_ms, "params": q.params_dict(best),
+            "outer_iters": st["outer_iters"], "inner_iters": st["inner_iters"],
+            "true_rel_res_library": st["true_rel_res"]}
+    if not args.skip_cpu:
+        info["true_rel_res_oracle"] = oracle_true_residuals(dims, U, w["kappa"], w["csw"], x, b)
+    sv.close()
+    del U, b, x
+    torch.cuda.empty_cache()
+    return best, info
+
+
+# ---- optional sections (flags) ----
 
 def learned_section(q, qi, torch, s, dims, prm, b, nrhs, npairs, epochs, lr=3e-3, batch=8):
     """Trains the learned correction on npairs (residual, error) pairs of the plain SAP set-up prm
@@ -269,18 +379,6 @@ def timed(torch, fn):
     r = fn()
     torch.cuda.synchronize()
     return time.perf_counter() - t0, r
-
-
-def point_sources_torch(torch, dims, first, count):
-    """Spin-colour point sources first..first+count-1 at the origin, complex128 on the device."""
-    V = 1
-    for L in dims:
-        V *= L
-    b = torch.zeros((count, V, 4, 3), dtype=torch.complex128, device="cuda")
-    for j in range(count):
-        k = first + j
-        b[j, 0, k // 3, k % 3] = 1.0
-    return b
 
 
 def batched_section(q, qi, torch, csw, eps, tol, inner_tol, candidates):
@@ -452,48 +550,57 @@ def block_solver_section(q, qi, torch, s, w, b):
     return out
 
 
-def headline_section(q, qi, torch, w, group, candidates):
-    """48^3 x 96, kappa 0.122, the 12 spin-colour point sources in right-hand-side groups of `group`:
-    plain FP32 SAP (the workload's literal set-up) against the autotuned set-up."""
-    dims = (48, 48, 48, 96)
-    st = torch.cuda.Stream()
-    sv = q.Solver(dims, stream=st.cuda_stream)
-    Ug = qi.gauge_field(dims, w["eps"], seed=1004, device="cuda")
-    torch.cuda.synchronize()  # made on torch's stream, read on the context's
-    sv.load_gauge(Ug)
-    del Ug
-    torch.cuda.empty_cache()
-    sv.build_clover(0.122, w["csw"])
-    plain = q.make_params(0.122, w["csw"], w["block"], w["subblock"], omega=w["omega"], nsweep=w["nsweep"],
-                          nsap=w["nsap"], tol=w["tol"], inner_tol=w["inner_tol"])
-    g = qi.gaussian_spinor_torch(dims, 2004, 1, "cuda").contiguous()
-    torch.cuda.synchronize()
-    t_tune, (best, _) = timed(torch, lambda: q.qcd_autotune(sv.ctx, g, plain, max_candidates=candidates))
-    del g
-    out = {"lattice": "48x48x48x96", "kappa": 0.122, "sources": 12, "rhs_group": group,
-           "tuning_seconds": t_tune, "chosen_params": q.params_dict(best)}
-    for name, p in (("plain", plain), ("chosen", best)):
-        total, iters, res = 0.0, [], 0.0
-        for k0 in range(0, 12, group):
-            b = point_sources_torch(torch, dims, k0, group)
-            x = torch.zeros_like(b)
-            torch.cuda.synchronize()
-            t, stt = timed(torch, lambda: sv.solve(x, b, p, nrhs=group))
-            total += t
-            iters.append((stt["outer_iters"], stt["inner_iters"]))
-            res = max(res, stt["true_rel_res"])
-            del b, x
-            torch.cuda.empty_cache()
-        out[name] = {"seconds": total, "seconds_per_source": total / 12, "iters_per_group": iters,
-                     "true_rel_res_max": res}
-    out["speedup_chosen_vs_plain"] = out["plain"]["seconds"] / out["chosen"]["seconds"]
-    sv.close()
-    torch.cuda.empty_cache()
+
+
+# ---- the headline and the small-lattice extras ----
+
+def small_section(q, qi, torch, stream, args):
+    """The 12^3 x 24 workload (one Gaussian source): plain (its literal set-up) and autotuned."""
+    w = SMALL
+    dims = w["dims"]
+    U = qi.gauge_field(dims, w["eps"], seed=w["gauge_seed"])
+    b = torch.from_numpy(qi.gaussian_spinor(dims, seed=w["source_seed"])).cuda()
+    s = q.Solver(dims, stream=stream.cuda_stream)
+    s.load_gauge(torch.from_numpy(U).cuda())
+    s.build_clover(w["kappa"], w["csw"])
+    prm = q.make_params(w["kappa"], w["csw"], w["block"], w["subblock"], omega=w["omega"], nsweep=w["nsweep"],
+                        nsap=w["nsap"], tol=w["tol"], inner_tol=w["inner_tol"])
+    x = torch.zeros_like(b)
+    out = {"lattice": "12x12x12x24", "kappa": w["kappa"], "source": "Gaussian, seed %d" % w["source_seed"]}
+    for name, p in (("plain", prm), ("chosen", None)):
+        if p is None:
+            p, _ = q.qcd_autotune(s.ctx, b, prm, max_candidates=args.tune_candidates)
+        for _ in range(3):
+            x.zero_()
+            s.solve(x, b, p)
+        ms = []
+        for _ in range(5):
+            x.zero_()
+            t, st = event_ms(torch, stream, lambda: s.solve(x, b, p))
+            ms.append(t)
+        out[name] = {"ms": statistics.median(ms), "params": q.params_dict(p), "outer_iters": st["outer_iters"],
+                     "inner_iters": st["inner_iters"], "true_rel_res": st["true_rel_res"]}
+    out["speedup_chosen_vs_plain"] = out["plain"]["ms"] / out["chosen"]["ms"]
+    if args.block_solvers:
+        out["block_solvers"] = block_solver_section(q, qi, torch, s, w, b)
+    if args.geometry_sweep:
+        out["geometry_sweep"] = geometry_section(q, qi, torch, s, w, b)
+    s.close()
     return out
 
 
+def headline_params(q, chosen):
+    w = HEADLINE
+    p = w["plain"]
+    plain = q.make_params(w["kappa"], w["csw"], p["block"], p["subblock"], omega=p["omega"], nsweep=p["nsweep"],
+                          nsap=p["nsap"], tol=w["tol"], inner_tol=w["inner_tol"], rhs_group=w["rhs_group"])
+    ch = q.make_params(w["kappa"], w["csw"], tuple(chosen.block), tuple(chosen.subblock), omega=chosen.omega,
+                       nsweep=chosen.nsweep, nsap=chosen.nsap, tol=w["tol"], inner_tol=w["inner_tol"],
+                       sap_storage=chosen.sap_storage, sap_ctas=chosen.sap_ctas, rhs_group=w["rhs_group"])
+    return plain, ch
+
+
 def run_gpu(args):
-    import numpy as np
     import torch
 
     rank, world, local = dist_env()
@@ -507,83 +614,54 @@ def run_gpu(args):
     import paper_1210_7398_gb300 as q
     import qcd_inputs as qi
 
-    peaks = read_peaks()
-    # all work of this run on one non-default stream: the library replays its captured inner
-    # iteration only there, and torch's fills and copies stay ordered with the solves
+    # all work on one non-default stream: the library replays its captured inner iteration only
+    # there, and torch's fills and copies stay ordered with the solves
     side = torch.cuda.Stream()
     with torch.cuda.stream(side):
-        return run_gpu_on_stream(args, q, qi, torch, np, peaks, rank, world, local)
+        out = run_gpu_on_stream(args, q, qi, torch, side, rank, world, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
 
 
-def run_gpu_on_stream(args, q, qi, torch, np, peaks, rank, world, local):
-    if args.only_dslash:  # profiling aid: the FP32 D on 24^3 x 48 alone
-        print(json.dumps({"dslash": dslash_bandwidth(q, torch, (24, 24, 24, 48), 5, peaks)}))
-        return 0
-    if args.only_learned:  # profiling aid: the learned correction's three layers on 24^3 x 48
-        dl = (24, 24, 24, 48)
-        sl = q.Solver(dl)
-        sl.load_gauge(qi.gauge_field(dl, 0.3, seed=1003, device="cuda"))
-        sl.build_clover(0.122, 1.6)
-        q.qcd_learned_set_weights(sl.ctx, q.learned_init_weights(4000, scale_last=1.0))
-        xin = qi.gaussian_spinor_torch(dl, 2003, 1, "cuda").to(torch.complex64).contiguous()
-        yout = torch.empty_like(xin)
-        for _ in range(3):
-            q.qcd_learned_apply(sl.ctx, yout, xin)
-        q.qcd_set_profiling(sl.ctx, True)
-        for k in range(len(q.KERNEL_CLASSES)):
-            q.qcd_kernel_stats(sl.ctx, k, reset=True)
-        for _ in range(5):
-            q.qcd_learned_apply(sl.ctx, yout, xin)
-        n, ms = q.qcd_kernel_stats(sl.ctx, q.KERNEL_CLASSES.index("learned"), reset=True)
-        q.qcd_set_profiling(sl.ctx, False)
-        sl.close()
-        print(json.dumps({"learned_layers_24x24x24x48": {"launches": n, "ms": ms, "ms_per_application": ms / 5}}))
-        return 0
-    if args.only_ssor_forms:  # profiling aid: SAP on 24^3 x 48 with the 32-lane, then the 8-lane SSOR
-        dl = (24, 24, 24, 48)
-        sl = q.Solver(dl)
-        sl.load_gauge(qi.gauge_field(dl, 0.3, seed=1003, device="cuda"))
-        sl.build_clover(0.122, 1.6)
-        prm = q.make_params(0.122, 1.6, (4, 4, 4, 4), (2, 2, 2, 2), nsweep=2, nsap=1, sap_storage=q.QCD_F16)
-        xin = qi.gaussian_spinor_torch(dl, 2003, 4, "cuda").to(torch.complex64).contiguous()
-        yout = torch.empty_like(xin)
-        torch.cuda.synchronize()  # made on torch's stream, read on the context's
-        res = {}
-        for form in (1, 2):  # two SSOR launches (one per colour) per application
-            q.qcd_set_sap_form(sl.ctx, form)
-            q.qcd_set_profiling(sl.ctx, True)
-            q.qcd_kernel_stats(sl.ctx, q.QCD_K_SSOR, reset=True)
-            sl.sap_precondition(yout, xin, prm, nrhs=4)
-            n, ms = q.qcd_kernel_stats(sl.ctx, q.QCD_K_SSOR, reset=True)
-            q.qcd_set_profiling(sl.ctx, False)
-            res["lanes_%d" % (32 if form == 1 else 8)] = {"launches": n, "ms_per_launch": ms / max(n, 1)}
-        sl.close()
-        print(json.dumps({"ssor_forms_24x24x24x48_4x4x4x4_f16_nrhs4": res}))
-        return 0
-    w = WORKLOAD
+def run_gpu_on_stream(args, q, qi, torch, stream, rank, world, local):
+    peaks = read_peaks()
+    w = HEADLINE
     dims = w["dims"]
-    V = qi.volume(dims)
-    U = qi.gauge_field(dims, w["eps"], seed=w["gauge_seed"])
-    b = qi.gaussian_spinor(dims, seed=w["source_seed"])
-    s = q.Solver(dims)
-    s.load_gauge(torch.from_numpy(U).cuda())
-    s.build_clover(w["kappa"], w["csw"])
-    prm = q.make_params(w["kappa"], w["csw"], w["block"], w["subblock"], omega=w["omega"], nsweep=w["nsweep"],
-                        nsap=w["nsap"], tol=w["tol"], inner_tol=w["inner_tol"])
-    stream = torch.cuda.current_stream()
-    bd = torch.from_numpy(b).cuda()
-    x = torch.zeros_like(bd)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    V = volume(dims)
+    nsrc = w["sources"]
+    # ---- the chosen set-up, tuned on the smaller lattice of the same family ----
+    chosen, tune_info = tune_chosen(q, qi, torch, stream, args)
+    plain_p, chosen_p = headline_params(q, chosen)
+    # ---- the headline lattice: links made on the device by the same generator ----
+    U = qi.gauge_field(dims, w["eps"], seed=w["gauge_seed"], device="cuda")
+    torch.cuda.synchronize()
+    sv = q.Solver(dims, stream=stream.cuda_stream)
+    sv.load_gauge(U)
+    sv.build_clover(w["kappa"], w["csw"])
+    # the oracle's check needs the links and its dense 12 x 12 clover matrices A and F on the host
+    keep_U = not args.skip_cpu and host_bytes_available() > 1.5 * V * (2 * 144 * 16 + 36 * 16 + 4 * 192)
+    if not keep_U:
+        del U
+    torch.cuda.empty_cache()
+    fp32 = q.qcd_bench_fp32_peak(sv.ctx, 64)
+    peaks["fp32_tflops"], peaks["fp32_source"] = fp32, "measured: FP32 FMA kernel (qcd_bench_fp32_peak) in this run"
+    b = point_sources_torch(torch, dims, 0, nsrc)
+    x = torch.zeros_like(b)
+
+    def solve(p):
+        return sv.solve(x, b, p, nrhs=nsrc)
+
     for _ in range(args.warmup):
         x.zero_()
-        s.solve(x, bd, prm)
+        solve(chosen_p)
     torch.cuda.synchronize()
 
-    # ---- timed region: K solves, L2 flushed between them ----
-    q.qcd_set_profiling(s.ctx, True)
-    for k in range(len(q.KERNEL_CLASSES)):
-        q.qcd_kernel_stats(s.ctx, k, reset=True)
-    launches0 = q.qcd_launch_count(s.ctx)
+    # ---- timed region: K chosen solves of the 12 sources (inputs larger than L2) ----
+    launches0 = q.qcd_launch_count(sv.ctx)
     clocks = ClockSampler(local)
     clocks.start()
     if world > 1:
@@ -592,190 +670,169 @@ def run_gpu_on_stream(args, q, qi, torch, np, peaks, rank, world, local):
     t_wall0 = time.perf_counter()
     step_ms, stats = [], []
     for _ in range(args.steps):
-        flush.fill_(1.0)
         x.zero_()
-        ev_a = torch.cuda.Event(enable_timing=True)
-        ev_b = torch.cuda.Event(enable_timing=True)
-        ev_a.record(stream)
-        st = s.solve(x, bd, prm)
-        ev_b.record(stream)
-        torch.cuda.synchronize()
-        step_ms.append(ev_a.elapsed_time(ev_b))
+        ms, st = event_ms(torch, stream, lambda: solve(chosen_p))
+        step_ms.append(ms)
         stats.append(st)
-    torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
-    launches = q.qcd_launch_count(s.ctx) - launches0
+    launches = q.qcd_launch_count(sv.ctx) - launches0
+    ms_step = max_over_ranks(sum(step_ms) / len(step_ms), world)
+    # the solutions of the last step under the oracle's FP64 D on the host (one source per group)
+    oracle_check = None
+    if keep_U and rank == 0:
+        ks = list(range(0, nsrc, w["rhs_group"]))
+        t0 = time.perf_counter()
+        res = oracle_true_residuals(dims, U, w["kappa"], w["csw"], x[ks], b[ks])
+        oracle_check = {"sources": ks, "true_rel_res_oracle": res, "seconds": time.perf_counter() - t0}
+    if keep_U:
+        del U
+        torch.cuda.empty_cache()
+    elif not args.skip_cpu:
+        oracle_check = {"skipped": "host memory below the oracle's dense clover fields for this lattice"}
+
+    # ---- plain set-up, same sources ----
+    g = w["rhs_group"]
+    xg, bg = x[:g], b[:g]  # leading right-hand sides: contiguous views
+    xg.zero_()
+    sv.solve(xg, bg, plain_p, nrhs=g)  # builds the plain plan and its records
+    plain_ms, plain_st = [], None
+    for _ in range(max(1, min(args.steps, args.plain_steps))):
+        x.zero_()
+        ms, plain_st = event_ms(torch, stream, lambda: solve(plain_p))
+        plain_ms.append(ms)
+    plain_s = max_over_ranks(sum(plain_ms) / len(plain_ms), world) / 1000.0
+
+    # ---- per-class kernel split of one chosen group (a separate, profiled pass) ----
+    q.qcd_set_profiling(sv.ctx, True)
+    for k in range(len(q.KERNEL_CLASSES)):
+        q.qcd_kernel_stats(sv.ctx, k, reset=True)
+    xg.zero_()
+    sv.solve(xg, bg, chosen_p, nrhs=g)
     kstats = {}
     for k, nm in enumerate(q.KERNEL_CLASSES):
-        n, ms = q.qcd_kernel_stats(s.ctx, k, reset=True)
-        kstats[nm] = {"launches": n, "ms": ms}
-    q.qcd_set_profiling(s.ctx, False)
-    ms_step = max_over_ranks(sum(step_ms) / len(step_ms), world)
-
-    # true residual of the last solve, checked with the library's FP64 D
-    xr = x.cpu().numpy()
+        n, ms = q.qcd_kernel_stats(sv.ctx, k, reset=True)
+        if n:
+            kstats[nm] = {"launches": n, "ms": ms}
+    q.qcd_set_profiling(sv.ctx, False)
+    del xg, bg
+    tot_k = sum(v["ms"] for v in kstats.values())
+    for v in kstats.values():
+        v["share"] = v["ms"] / tot_k if tot_k else 0.0
 
     # ---- end to end: host buffers through the C ABI, copies inside the timed region ----
-    b_host = torch.from_numpy(b).pin_memory().numpy()
-    x_host = torch.zeros(b.shape, dtype=torch.complex128).pin_memory().numpy()
-    e2e = []
-    for _ in range(max(1, min(args.steps, 3))):
-        x_host[...] = 0
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        s.solve(x_host, b_host, prm)
-        e2e.append(time.perf_counter() - t0)
-    # ---- chosen: the autotuned SAP set-up, timed like the plain one ----
-    chosen = None
-    if not args.skip_chosen:
-        best, tune_ms = q.qcd_autotune(s.ctx, bd, prm, max_candidates=args.tune_candidates)
-        for _ in range(2):
-            x.zero_()
-            s.solve(x, bd, best)
-        torch.cuda.synchronize()
-        ch_ms, ch_st = [], None
-        for _ in range(args.steps):
-            flush.fill_(1.0)
-            x.zero_()
-            ev_a = torch.cuda.Event(enable_timing=True)
-            ev_b = torch.cuda.Event(enable_timing=True)
-            ev_a.record(stream)
-            ch_st = s.solve(x, bd, best)
-            ev_b.record(stream)
+    e2e = None
+    nbytes = 16 * 12 * V * nsrc
+    if host_bytes_available() > 3 * nbytes:
+        b_host = torch.empty((nsrc, V, 4, 3), dtype=torch.complex128).pin_memory()
+        b_host.copy_(b)
+        x_host = torch.zeros_like(b_host).pin_memory()
+        bh, xh = b_host.numpy(), x_host.numpy()
+        e2e_s = []
+        for _ in range(max(1, min(args.steps, args.e2e_steps))):
+            xh[...] = 0
             torch.cuda.synchronize()
-            ch_ms.append(ev_a.elapsed_time(ev_b))
-        chosen = {"value": sum(ch_ms) / len(ch_ms) / 1000.0, "unit": "s", "params": q.params_dict(best),
-                  "outer_iters": ch_st["outer_iters"], "inner_iters": ch_st["inner_iters"],
-                  "true_rel_res": ch_st["true_rel_res"], "speedup_vs_plain": ms_step / (sum(ch_ms) / len(ch_ms)),
-                  "tuning": "qcd_autotune over block/sub-block splits, then FP16 storage, 2 CTAs per block "
-                            "and (nsweep, nsap) in {2,4}^2 for the 3 fastest; best of timed full solves"}
-        # 12 spin-colour point sources solved together, with the set-up tuned for that batch
-        pts = torch.from_numpy(qi.point_sources(dims)).cuda()
-        torch.cuda.synchronize()
-        best12, _ = q.qcd_autotune(s.ctx, pts, prm, nrhs=12, max_candidates=args.tune_candidates)
-        xp = torch.zeros_like(pts)
-        s.solve(xp, pts, best12, nrhs=12)
-        torch.cuda.synchronize()
-        xp.zero_()
-        ev_a = torch.cuda.Event(enable_timing=True)
-        ev_b = torch.cuda.Event(enable_timing=True)
-        ev_a.record(stream)
-        bst = s.solve(xp, pts, best12, nrhs=12)
-        ev_b.record(stream)
-        torch.cuda.synchronize()
-        tb = ev_a.elapsed_time(ev_b) / 1000.0
-        chosen["batched_12_point_sources"] = {"seconds": tb, "seconds_per_source": tb / 12,
-                                              "params": q.params_dict(best12),
-                                              "outer_iters": bst["outer_iters"], "inner_iters": bst["inner_iters"],
-                                              "true_rel_res_max": bst["true_rel_res"]}
-        # the learned correction on top of the chosen set-up; kept only when it is faster
-        lr_sec = learned_section(q, qi, torch, s, dims, best, bd, 1, 64, 8)
-        chosen["learned"] = lr_sec
-        if lr_sec["verdict"]["use_learned"] and lr_sec["verdict"]["learned_ms"] < chosen["value"] * 1000.0:
-            chosen["value"] = lr_sec["verdict"]["learned_ms"] / 1000.0
-            chosen["params"]["learned"] = 1
-            chosen["speedup_vs_plain"] = ms_step / lr_sec["verdict"]["learned_ms"]
-    block_solvers = None
-    if not args.skip_chosen:
-        block_solvers = block_solver_section(q, qi, torch, s, w, bd)
-    geometry = None
-    if args.geometry_sweep:
-        geometry = geometry_section(q, qi, torch, s, w, bd)
-    batched = None
-    if args.batched_full:
-        batched = batched_section(q, qi, torch, w["csw"], w["eps"], w["tol"], w["inner_tol"], 16)
-    headline = None
-    if args.headline:
-        headline = headline_section(q, qi, torch, w, args.rhs_group, 20)
-    learned_full = None
+            t0 = time.perf_counter()
+            sv.solve(xh, bh, chosen_p, nrhs=nsrc)
+            e2e_s.append(time.perf_counter() - t0)
+        e2e = {"value": max_over_ranks(statistics.mean(e2e_s), world), "unit": "s",
+               "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": nbytes,
+               "note": "qcd_solve with pinned host x (zero) and b, all 12 sources; copies inside the call"}
+        del b_host, x_host, bh, xh
+    sv.close()
+    del b, x
+    torch.cuda.empty_cache()
+    if rank != 0:
+        return None
+
+    # ---- roofline of the dominant kernel class (time from the profiled pass) ----
+    dom = max(kstats, key=lambda nm: kstats[nm]["ms"])
+    roof = None
+    model = kernel_model(dom, V, g, {"nsweep": chosen_p.nsweep}, peaks)
+    if model:
+        bound, units, unit, peak, psrc = model
+        avg_ms = kstats[dom]["ms"] / kstats[dom]["launches"]
+        achieved = units / (avg_ms * 1e-3)
+        roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": None, "avg_launch_ms": avg_ms, "peak_source": psrc,
+                "units_per_launch": units,
+                "model": "tile SAP launch (one colour, %d right-hand sides): V/2 x nrhs x (2 nsweep + 1) x 1896 "
+                         "flop (Table 1), time from a profiled pass of one group of the chosen solve" % g}
+        src = "paper_1210_7398_gb300/csrc/ssor_tile.cu"
+        t = NCU_TRAFFIC.get(dom)
+        if t and t["sha"] == source_sha(src):
+            roof["traffic"] = t["bytes_per_site_rhs"] * (V / 2) * g
+            roof["traffic_source"] = t["capture"]
+    dsl = []
+    if not args.skip_dslash:
+        dsl += dslash_bandwidth(q, qi, torch, stream, dims, 10, peaks, variants=(("f32", 1), ("f32", 4), ("su3", 1)))
+        dsl += dslash_bandwidth(q, qi, torch, stream, (24, 24, 24, 48), 20, peaks,
+                                variants=(("f32", 1), ("f32", 12), ("f16", 1), ("su3", 1), ("f64", 1)))
+        if roof is not None and dsl:
+            d = dsl[0]
+            roof["dslash"] = {"kernel": "D FP32, 48^3x96, 1 right-hand side", "bound": "hbm", "achieved": d["GB_s"],
+                              "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": d["frac_measured"],
+                              "frac_nominal_8TBs": d["frac_nominal_8TBs"], "ms": d["ms"],
+                              "model": "768 B/site: in 96 + out 96 + links 288 + clover 288"}
+    small = None if args.skip_small else small_section(q, qi, torch, stream, args)
+    cpu = None
+    if world == 1 and not args.skip_cpu:
+        try:
+            Uo, Fo, pts = oracle_sample_setup()
+            ts, its = [], []
+            for k in range(nsrc):
+                t, status, st_o = oracle_point_solve(Uo, Fo, pts, k)
+                ts.append(t)
+                its.append((st_o["outer"], st_o["inner"]))
+            cpu = {"value": statistics.mean(ts) * oracle_scale(), "unit": "s", "cores": cores_used(), "kind": "oracle",
+                   "sample": oracle_sample_text("all 12") + "; measured %.2f s for the 12 sample solves, iterations "
+                                                            "(outer, inner) %s" % (sum(ts), its)}
+        except Exception as e:  # the baseline is reported, not required
+            cpu = {"value": None, "unit": "s", "cores": cores_used(), "kind": "oracle", "sample": "failed: %s" % e}
+    learned = None
     if args.learned_full:
-        # 24^3 x 48, kappa 0.122, 12 point sources, 256 training pairs, plain SAP with 4 sweeps
         dl = (24, 24, 24, 48)
-        sl = q.Solver(dl)
+        sl = q.Solver(dl, stream=stream.cuda_stream)
         sl.load_gauge(qi.gauge_field(dl, w["eps"], seed=1003, device="cuda"))
         sl.build_clover(0.122, w["csw"])
         pl = q.make_params(0.122, w["csw"], (4, 4, 4, 4), (2, 2, 2, 2), nsweep=4, nsap=4, tol=w["tol"],
                            inner_tol=w["inner_tol"])
         pts = torch.from_numpy(qi.point_sources(dl)).cuda()
-        learned_full = learned_section(q, qi, torch, sl, dl, pl, pts, 12, 256, 8)
-        learned_full["lattice"] = "24x24x24x48"
+        learned = learned_section(q, qi, torch, sl, dl, pl, pts, 12, 256, 8)
+        learned["lattice"] = "24x24x24x48"
         sl.close()
-        del pts
-    s.close()
-    del flush
-    torch.cuda.empty_cache()
+    batched = None
+    if args.batched_full:
+        batched = batched_section(q, qi, torch, w["csw"], w["eps"], w["tol"], w["inner_tol"], 16)
 
-    out = None
-    if rank == 0:
-        # dominant kernel and its roofline
-        dom = max((nm for nm in kstats if kstats[nm]["launches"]), key=lambda nm: kstats[nm]["ms"])
-        model = kernel_model(dom, V, 1, w, peaks)
-        roof = None
-        if model:
-            bound, units, unit, peak = model
-            avg_ms = kstats[dom]["ms"] / kstats[dom]["launches"]
-            achieved = units / (avg_ms * 1e-3)
-            roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                    "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(dom), "avg_launch_ms": avg_ms,
-                    "peak_source": peaks["source"] if bound == "hbm" else "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
-            sm_mhz = clk.get("sm_mhz") if isinstance(clk, dict) else None
-            iss = issue_model(dom, avg_ms, sm_mhz or peaks["sm_max_mhz"])
-            if iss is not None:
-                roof["issue"] = iss
-        tot_k = sum(v["ms"] for v in kstats.values())
-        for v in kstats.values():
-            v["share"] = v["ms"] / tot_k if tot_k else 0.0
-        dsl = []
-        if not args.skip_dslash:
-            dsl += dslash_bandwidth(q, torch, (24, 24, 24, 48), 20, peaks,
-                                    variants=(("f32", 1), ("f32", 12), ("f16", 1), ("f16", 12), ("su3", 1), ("su3", 12),
-                                              ("f64", 1)))
-            dsl += dslash_bandwidth(q, torch, (48, 48, 48, 96), 20, peaks)
-        cpu = None
-        if world == 1 and not args.skip_cpu:
-            try:
-                Uo, Fo, bo = oracle_setup()
-                t, status, st_o = oracle_solve_seconds(Uo, Fo, bo)
-                cpu = {"value": t, "unit": "s", "cores": cores_used(), "kind": "oracle",
-                       "sample": "one full FP64 oracle solve of the same workload (outer %d, inner %d, "
-                                 "true rel. residual %.1e)" % (st_o["outer"], st_o["inner"], st_o["true_rel_res"])}
-            except Exception as e:  # the baseline is reported, not required
-                cpu = {"value": None, "unit": "s", "cores": cores_used(), "kind": "oracle", "sample": "failed: %s" % e}
-        last = stats[-1]
-        out = {"metric": METRIC, "value": ms_step / 1000.0, "unit": "s", "n_gpus": world, "steps": args.steps,
-               "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
-               "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
-               "config": {"workload": WORKLOAD["name"], "lattice": "12x12x12x24", "kappa": w["kappa"],
-                          "csw": w["csw"], "omega": w["omega"], "nsweep": w["nsweep"], "nsap": w["nsap"],
-                          "tol": w["tol"], "inner_tol": w["inner_tol"], "l2": "flushed (512 MiB write) between steps",
-                          "parallelism": "replicas" if world > 1 else "single GPU"},
-               "solve": {"outer_iters": last["outer_iters"], "inner_iters": last["inner_iters"],
-                         "restarts": last["restarts"], "true_rel_res": last["true_rel_res"],
-                         "solves_per_s_all_gpus": world / (ms_step / 1000.0), "wall_s_timed_region": wall},
-               "e2e": {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": 2 * 16 * 12 * V,
-                       "d2h_bytes_per_step": 16 * 12 * V,
-                       "note": "qcd_solve with pinned host x and b; copies inside the call"},
-               "gpu_launches": launches, "kernels": kstats, "clocks": clk, "roofline": roof,
-               "dslash": dsl, "chosen": chosen, "cpu_baseline": cpu}
-        if learned_full is not None:
-            out["learned_24x24x24x48"] = learned_full
-        if batched is not None:
-            out["batched_uneven"] = batched
-        if geometry is not None:
-            out["geometry_sweep"] = geometry
-        if block_solvers is not None:
-            out["block_solvers"] = block_solvers
-        if headline is not None:
-            out["headline_48x48x48x96"] = headline
-        print(json.dumps(out))
-    if world > 1:
-        torch.distributed.barrier()
-        torch.distributed.destroy_process_group()
-    return 0
+    last = stats[-1]
+    out = {"metric": METRIC, "value": ms_step / 1000.0, "unit": "s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32 SAP and inner solver (FP16 storage), f64 outer solver",
+           "data": "synthetic",
+           "config": {"workload": w["name"], "lattice": "x".join(map(str, dims)), "kappa": w["kappa"],
+                      "csw": w["csw"], "eps": w["eps"], "gauge_seed": w["gauge_seed"], "sources": nsrc,
+                      "rhs_group": w["rhs_group"], "tol": w["tol"], "inner_tol": w["inner_tol"],
+                      "chosen": q.params_dict(chosen_p), "plain": q.params_dict(plain_p),
+                      "l2": "inputs larger than L2 (12 sources, %.1f GB each of b and x; no flush)" % (nbytes / 1e9),
+                      "parallelism": "replicas" if world > 1 else "single GPU"},
+           "plain": {"value": plain_s, "unit": "s", "steps": len(plain_ms),
+                     "outer_iters": plain_st["outer_iters"], "inner_iters": plain_st["inner_iters"],
+                     "true_rel_res": plain_st["true_rel_res"]},
+           "speedup_chosen_vs_plain": plain_s / (ms_step / 1000.0),
+           "solve": {"outer_iters": last["outer_iters"], "inner_iters": last["inner_iters"],
+                     "restarts": last["restarts"], "true_rel_res": last["true_rel_res"],
+                     "wall_s_timed_region": wall},
+           "oracle_check": oracle_check, "tuning": tune_info,
+           "e2e": e2e, "gpu_launches": launches, "kernels": kstats, "clocks": clk, "roofline": roof,
+           "fp32_peak_tflops": fp32, "dslash": dsl, "cpu_baseline": cpu, "small_12x12x12x24": small}
+    if learned is not None:
+        out["learned_24x24x24x48"] = learned
+    if batched is not None:
+        out["batched_uneven"] = batched
+    return out
 
 
 def main():
@@ -784,23 +841,18 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--plain-steps", type=int, default=2, help="timed solves of the plain set-up")
+    ap.add_argument("--e2e-steps", type=int, default=2, help="timed solves through host buffers")
+    ap.add_argument("--tune-candidates", type=int, default=40, help="solves the autotuner may time")
     ap.add_argument("--skip-dslash", action="store_true", help="skip the D bandwidth measurement")
-    ap.add_argument("--skip-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--skip-chosen", action="store_true", help="skip the autotuned (chosen) measurement")
-    ap.add_argument("--tune-candidates", type=int, default=48, help="solves the autotuner may time")
+    ap.add_argument("--skip-cpu", action="store_true", help="skip the CPU oracle legs (baseline and checks)")
+    ap.add_argument("--skip-small", action="store_true", help="skip the 12^3 x 24 extras")
+    ap.add_argument("--block-solvers", action="store_true",
+                    help="also compare ll-SSOR with the even-odd block inverse at equal cost (12^3 x 24, 24^3 x 48)")
+    ap.add_argument("--geometry-sweep", action="store_true",
+                    help="also time the plain 12^3 x 24 solve over SAP block / sub-block geometries")
     ap.add_argument("--batched-full", action="store_true",
                     help="also solve 24^3x48 (12 point sources) + 8^3x16, 12^3x24, 16^3x32 alone and concurrently")
-    ap.add_argument("--geometry-sweep", action="store_true",
-                    help="also time the plain 12^3x24 solve over SAP block / sub-block geometries")
-    ap.add_argument("--headline", action="store_true",
-                    help="also solve 48^3x96 with 12 point sources, plain and autotuned")
-    ap.add_argument("--rhs-group", type=int, default=4, help="right-hand sides per 48^3x96 solve")
-    ap.add_argument("--only-dslash", action="store_true", help="profiling aid: time only the FP32 D on 24^3x48")
-    ap.add_argument("--only-ssor-forms", action="store_true",
-                    help="profiling aid: one SAP application (24^3x48, 4^4 blocks, FP16, 4 RHS) with the "
-                         "32-lane and then the 8-lane SSOR kernel")
-    ap.add_argument("--only-learned", action="store_true",
-                    help="profiling aid: time only the learned correction's layers on 24^3x48")
     ap.add_argument("--learned-full", action="store_true",
                     help="also train and assess the learned correction on 24^3 x 48 with 12 point sources")
     args = ap.parse_args()

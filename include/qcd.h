@@ -105,6 +105,11 @@ typedef struct {
                            block's even sites from 0, then the odd sites
                            (sap_storage QCD_F32 and learned 0 only; subblock must
                            still divide block; omega unused)                         */
+    int rhs_group;      /* qcd_solve: right-hand sides solved together (the batched
+                           iteration); more are solved group after group, each in the
+                           device memory of one group.  0: as many as fit the free device
+                           memory (at least 1).  Results do not depend on it: each
+                           right-hand side's iterates are those of its solve alone      */
 } qcd_params;
 
 typedef struct {
@@ -263,12 +268,25 @@ int qcd_sap_plan_tables(const int dims[4], const int block[4], const int subbloc
  * sap_ctas, nsweep, nsap; omega from base) and its time in *best_ms.  Stage 1
  * tries block splits (L_mu / block_mu in {2, 4, 6, 8}, spatial directions
  * alike) with sub-blocks block/2, block/3 or block, blocks of about 256 sites
- * first; stage 2 refines the three fastest over FP16 storage, the kernel
- * form (sap_ctas 0, -1, 2) and (nsweep, nsap) in {2, 4} x {2, 4}.  At most
- * max_candidates solves are timed (<= 0: 64).
+ * first, each with FP16 storage and the tile form (sap_ctas -2; the cluster form
+ * where the block does not fit); stage 2 refines the three fastest over the
+ * storage (FP32, FP16), the kernel form (sap_ctas -2, 0, 2) and (nsweep, nsap)
+ * in {2, 4} x {2, 4}.  At most max_candidates solves are timed (<= 0: 64).
+ * Stage 3 (nrhs > 1 and base->rhs_group = 0) then times the winner with
+ * right-hand sides in groups of 1, 2, 4 or 8 dividing nrhs, as well as all at
+ * once, and keeps the fastest rhs_group.
  * b: complex128 [nrhs][V][4][3], host or device.  Synchronises. */
 int qcd_autotune(qcd_ctx *ctx, const double *b, int nrhs, const qcd_params *base, qcd_params *best,
                  double *best_ms, int max_candidates);
+
+/* Tuning cache (no counterpart in the paper): with a path set, qcd_autotune first looks for a
+ * result stored under the same key (lattice extents, nrhs, kappa, csw, bc_t, tolerances and
+ * limits, omega, rhs_group, max_candidates, GPU name and SM count, tuner version) and returns it
+ * without timing anything; otherwise it tunes and appends the winner as one JSON object per
+ * line ({"key": ..., "block": [...], "subblock": [...], "sap_storage", "sap_ctas", "nsweep",
+ * "nsap", "rhs_group", "ms"}).  NULL or "" switches the cache off (the default).  Process-wide;
+ * the file is read and appended under a lock.  Always QCD_OK. */
+int qcd_set_tune_cache(const char *path);
 
 /* ---- learned correction (no counterpart in the paper) -----------------------
  * N is a linear, gauge-covariant network of 3 parallel-transport layers with
@@ -342,11 +360,23 @@ int qcd_kernel_stats(qcd_ctx *ctx, int kclass, long *launches, double *ms, int r
 /* Total kernel launches made by this context since creation. */
 long qcd_launch_count(const qcd_ctx *ctx);
 
+/* Test hook: the next `count` outer BiCGStab iterations of qcd_solve start from rho = 0 for
+ * every active right-hand side, the state a vanishing <rhat, r> leaves (a breakdown made on the
+ * host; no device fault is involved).  The solver then takes its breakdown path: true residual,
+ * restart from it, and QCD_ERR_BREAKDOWN after 5 restarts of a right-hand side.  0 disarms. */
+int qcd_debug_inject_breakdown(qcd_ctx *ctx, int count);
+
 /* D on internal-layout buffers only, repeated `iters` times (no layout
  * conversion): the kernel the memory-bandwidth roofline is measured on.
  * prec = QCD_F64, QCD_F32, QCD_F16 or QCD_F32_SU3; nrhs >= 1.  Work buffers are allocated on first
  * use and kept. */
 int qcd_bench_dslash(qcd_ctx *ctx, int prec, int nrhs, int iters);
+
+/* Measured FP32 FMA throughput of the context's GPU in TFLOP/s (2 flop per FMA): independent
+ * FMA chains in registers over every SM, iters x 4096 FMAs per thread, timed with CUDA events on
+ * the context stream.  The denominator of the SAP block kernel's arithmetic roofline.
+ * Synchronises. */
+int qcd_bench_fp32_peak(qcd_ctx *ctx, int iters, double *tflops);
 
 #ifdef __cplusplus
 }

@@ -28,7 +28,8 @@ EXPORTS = ("qcd_create", "qcd_destroy", "qcd_last_error", "qcd_set_boundary", "q
            "qcd_kernel_stats", "qcd_launch_count", "qcd_bench_dslash", "qcd_sap_precondition_noalloc",
            "qcd_set_sap_ctas", "qcd_set_sap_form", "qcd_sap_plan_tables", "qcd_set_graphs", "qcd_autotune", "qcd_learned_weight_count",
            "qcd_learned_set_weights", "qcd_learned_get_weights", "qcd_learned_apply", "qcd_learned_loss_grad",
-           "qcd_learned_train", "qcd_learned_evaluate", "qcd_solve_multi")
+           "qcd_learned_train", "qcd_learned_evaluate", "qcd_solve_multi", "qcd_set_tune_cache", "qcd_bench_fp32_peak",
+           "qcd_debug_inject_breakdown")
 
 
 class QcdError(RuntimeError):
@@ -44,7 +45,8 @@ class qcd_params(ctypes.Structure):
                 ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
                 ("max_outer", ctypes.c_int), ("max_inner", ctypes.c_int),
                 ("bc_t", ctypes.c_int), ("sap_storage", ctypes.c_int),
-                ("learned", ctypes.c_int), ("sap_ctas", ctypes.c_int), ("block_solver", ctypes.c_int)]
+                ("learned", ctypes.c_int), ("sap_ctas", ctypes.c_int), ("block_solver", ctypes.c_int),
+                ("rhs_group", ctypes.c_int)]
 
 
 class qcd_learned_verdict(ctypes.Structure):
@@ -108,6 +110,9 @@ def load_library(path: str = LIB_PATH):
         "qcd_kernel_stats": (I, [P, I, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(D), I]),
         "qcd_launch_count": (ctypes.c_long, [P]),
         "qcd_bench_dslash": (I, [P, I, I, I]),
+        "qcd_set_tune_cache": (I, [ctypes.c_char_p]),
+        "qcd_bench_fp32_peak": (I, [P, I, ctypes.POINTER(D)]),
+        "qcd_debug_inject_breakdown": (I, [P, I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -257,11 +262,17 @@ def qcd_autotune(ctx, b, base: qcd_params, nrhs: int = 1, max_candidates: int = 
     return best, ms.value
 
 
+def qcd_set_tune_cache(path):
+    """Tuning results are looked up in, and appended to, this JSON-lines file (None: off)."""
+    return load_library().qcd_set_tune_cache(path.encode() if path else None)
+
+
 def params_dict(p: qcd_params) -> dict:
     return {"block": list(p.block), "subblock": list(p.subblock), "omega": p.omega, "nsweep": p.nsweep,
             "nsap": p.nsap, "sap_storage": {QCD_F32: "f32", QCD_F16: "f16"}.get(p.sap_storage, p.sap_storage),
             "sap_ctas": p.sap_ctas, "learned": p.learned,
-            "block_solver": {0: "ll-ssor", 1: "even-odd mr"}.get(p.block_solver, p.block_solver)}
+            "block_solver": {0: "ll-ssor", 1: "even-odd mr"}.get(p.block_solver, p.block_solver),
+            "rhs_group": p.rhs_group}
 
 
 LEARNED_CHANS = (1, 8, 8, 1)
@@ -350,9 +361,21 @@ def qcd_bench_dslash(ctx, prec: int, nrhs: int, iters: int):
     return _check(ctx, load_library().qcd_bench_dslash(ctx, int(prec), int(nrhs), int(iters)))
 
 
+def qcd_debug_inject_breakdown(ctx, count: int):
+    """Test hook: the next count outer iterations start from rho = 0 (a host-made breakdown)."""
+    return _check(ctx, load_library().qcd_debug_inject_breakdown(ctx, int(count)))
+
+
+def qcd_bench_fp32_peak(ctx, iters: int = 64) -> float:
+    """Measured FP32 FMA throughput of the context's GPU, TFLOP/s."""
+    t = ctypes.c_double()
+    _check(ctx, load_library().qcd_bench_fp32_peak(ctx, int(iters), ctypes.byref(t)))
+    return t.value
+
+
 def make_params(kappa, csw, block, subblock, omega=1.0, nsweep=4, nsap=4, tol=1e-10, inner_tol=1e-5,
                 max_outer=100, max_inner=500, bc_t=1, sap_storage=QCD_F32, sap_ctas=0,
-                block_solver=0) -> qcd_params:
+                block_solver=0, rhs_group=0) -> qcd_params:
     p = qcd_params()
     p.kappa, p.csw = float(kappa), float(csw)
     p.block = (ctypes.c_int * 4)(*block)
@@ -362,6 +385,7 @@ def make_params(kappa, csw, block, subblock, omega=1.0, nsweep=4, nsap=4, tol=1e
     p.max_outer, p.max_inner = int(max_outer), int(max_inner)
     p.bc_t, p.sap_storage, p.learned, p.sap_ctas = int(bc_t), int(sap_storage), 0, int(sap_ctas)
     p.block_solver = int(block_solver)
+    p.rhs_group = int(rhs_group)
     return p
 
 

@@ -365,38 +365,58 @@ int qcd_solve(qcd_ctx *c, double *x, const double *b, const qcd_params *p, int n
     if ((rc = check_params(c, p))) return rc;
     if (!(p->tol > 0) || !(p->inner_tol > 0) || p->max_outer < 1 || p->max_inner < 1)
         return fail(c, QCD_ERR_ARG, "tol, inner_tol, max_outer, max_inner must be positive");
+    if (p->rhs_group < 0) return fail(c, QCD_ERR_ARG, "rhs_group must be >= 0");
     if ((rc = sap_prepare(c, p->block, p->subblock, p->sap_storage == QCD_F16))) return rc;
     qcd_stats local;
     std::memset(&local, 0, sizeof(local));
     local.status = QCD_OK;
     const long V = c->lat.V;
-    const size_t bytes = 16 * 12 * V * (size_t)nrhs;  // all right-hand sides, complex128
+    const size_t per = 16 * 12 * (size_t)V;  // one right-hand side, complex128
     const bool dev_x = is_device_ptr(x), dev_b = is_device_ptr(b);
     if ((dev_x && !aligned16(x)) || (dev_b && !aligned16(b)))
         return fail(c, QCD_ERR_ARG, "device spinors must be 16-byte aligned");
-    if ((rc = ensure_io(c, 4 * bytes))) return rc;
-    char *io = (char *)c->d_io;
-    double2 *xi = (double2 *)io, *bi = (double2 *)(io + bytes);
-    char *sx = io + 2 * bytes, *sb = io + 3 * bytes;
-    const char *bsrc = (const char *)b, *xsrc = (const char *)x;
-    if (!dev_b) {
-        QCD_CUDA(c, cudaMemcpyAsync(sb, b, bytes, cudaMemcpyHostToDevice, c->stream));
-        bsrc = sb;
+    // right-hand sides per group: as asked, or as many as the free device memory holds (the
+    // solver's FP64 and FP32 vectors, the internal copies of x and b, host staging)
+    int g = p->rhs_group > 0 ? std::min(p->rhs_group, nrhs) : nrhs;
+    if (p->rhs_group == 0) {
+        size_t fr = 0, tot = 0;
+        QCD_CUDA(c, cudaMemGetInfo(&fr, &tot));
+        const size_t held = c->ws64_bytes + c->ws32_bytes + c->d_io_bytes;
+        const size_t margin = (size_t)1 << 30;
+        const size_t avail = fr + held > margin + tot / 50 ? fr + held - margin - tot / 50 : 0;
+        const size_t need = 16 * 12 * (size_t)V * 11 + 16 * 6 * (size_t)V * (10 + sap_work_fields(p->block_solver)) +
+                            per * (dev_x && dev_b ? 2 : 4);
+        g = (int)std::max<size_t>(1, std::min<size_t>((size_t)nrhs, avail / need));
     }
-    if (!dev_x) {
-        QCD_CUDA(c, cudaMemcpyAsync(sx, x, bytes, cudaMemcpyHostToDevice, c->stream));
-        xsrc = sx;
-    }
-    if ((rc = spinor64_to_internal(c, bi, (const double2 *)bsrc, nrhs))) return rc;
-    if ((rc = spinor64_to_internal(c, xi, (const double2 *)xsrc, nrhs))) return rc;
     // learned = 1 falls back to plain SAP when the last evaluation found the correction slower
     qcd_params pe = *p;
     pe.learned = (p->learned == 2 || (p->learned == 1 && c->net.verdict != 0)) ? 1 : 0;
-    int status = solve(c, xi, bi, &pe, nrhs, &local);
-    if (status == QCD_ERR_CUDA || status == QCD_ERR_OOM || status == QCD_ERR_STATE || status == QCD_ERR_ARG)
-        return status;
-    if ((rc = spinor64_from_internal(c, (double2 *)(dev_x ? (char *)x : sx), xi, nrhs))) return rc;
-    if (!dev_x) QCD_CUDA(c, cudaMemcpyAsync(x, sx, bytes, cudaMemcpyDeviceToHost, c->stream));
+    int status = QCD_OK;
+    for (int k0 = 0; k0 < nrhs; k0 += g) {
+        const int n = std::min(g, nrhs - k0);
+        const size_t bytes = per * n;
+        if ((rc = ensure_io(c, 4 * per * g))) return rc;
+        char *io = (char *)c->d_io;
+        double2 *xi = (double2 *)io, *bi = (double2 *)(io + bytes);
+        char *sx = io + 2 * bytes, *sb = io + 3 * bytes;
+        const char *bsrc = (const char *)b + per * k0, *xsrc = (const char *)x + per * k0;
+        if (!dev_b) {
+            QCD_CUDA(c, cudaMemcpyAsync(sb, bsrc, bytes, cudaMemcpyHostToDevice, c->stream));
+            bsrc = sb;
+        }
+        if (!dev_x) {
+            QCD_CUDA(c, cudaMemcpyAsync(sx, xsrc, bytes, cudaMemcpyHostToDevice, c->stream));
+            xsrc = sx;
+        }
+        if ((rc = spinor64_to_internal(c, bi, (const double2 *)bsrc, n))) return rc;
+        if ((rc = spinor64_to_internal(c, xi, (const double2 *)xsrc, n))) return rc;
+        const int s = solve(c, xi, bi, &pe, n, &local);
+        if (s == QCD_ERR_CUDA || s == QCD_ERR_OOM || s == QCD_ERR_STATE || s == QCD_ERR_ARG) return s;
+        if (s != QCD_OK && (status == QCD_OK || s == QCD_ERR_BREAKDOWN)) status = s;
+        char *xdst = dev_x ? (char *)x + per * k0 : sx;
+        if ((rc = spinor64_from_internal(c, (double2 *)xdst, xi, n))) return rc;
+        if (!dev_x) QCD_CUDA(c, cudaMemcpyAsync((char *)x + per * k0, sx, bytes, cudaMemcpyDeviceToHost, c->stream));
+    }
     QCD_CUDA(c, cudaStreamSynchronize(c->stream));
     local.status = status;
     local.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -451,6 +471,14 @@ int qcd_set_sap_ctas(qcd_ctx *c, int min_ctas) {
     QCD_CUDA(c, c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
     c->sap_ctas_user = min_ctas;
     use_sap_ctas(c, 0);
+    return QCD_OK;
+}
+
+int qcd_debug_inject_breakdown(qcd_ctx *c, int count) {
+    int rc = ready(c);
+    if (rc) return rc;
+    if (count < 0) return fail(c, QCD_ERR_ARG, "count must be >= 0");
+    c->inject_breakdown = count;
     return QCD_OK;
 }
 

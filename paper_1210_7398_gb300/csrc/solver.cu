@@ -339,6 +339,16 @@ int solve(qcd_ctx *c, double2 *x, const double2 *b, const qcd_params *p, int nrh
         for (int k = 0; k < R; k++) any |= h_active[k] != 0;
         if (!any || outer >= p->max_outer) break;
         // one outer iteration for every active rhs
+        if (c->inject_breakdown > 0) {
+            // test hook: rho = 0 in the scalar state of every active rhs, as a vanishing <rh, r>
+            // would leave it; the beta step then reports the breakdown
+            c->inject_breakdown--;
+            QCD_CUDA(c, cudaMemcpyAsync(w.hSo, w.So, sizeof(BicgScalars) * R, cudaMemcpyDeviceToHost, c->stream));
+            QCD_CUDA(c, cudaStreamSynchronize(c->stream));
+            for (int k = 0; k < R; k++)
+                if (w.hSo[k].active) w.hSo[k].rho = make_double2(0.0, 0.0);
+            QCD_CUDA(c, cudaMemcpyAsync(w.So, w.hSo, sizeof(BicgScalars) * R, cudaMemcpyHostToDevice, c->stream));
+        }
         TRY(scalars(c, SC_BETA, w.So, w.red, R, p->tol, nullptr));
         TRY(blas_p_update64(c, w.p, w.r, w.v, w.So, n, R));
         int its = 0;

@@ -4,7 +4,10 @@
 // counts), so candidates are compared by measured time to solution.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "qcd_internal.h"
@@ -27,7 +30,8 @@ bool valid_block(const qcd_ctx *c, const int b[4], const int s[4]) {
     return true;
 }
 
-// time one complete solve (x0 = 0) of the internal-layout right-hand sides bi
+// time one complete solve (x0 = 0) of the internal-layout right-hand sides bi, in groups of
+// p->rhs_group right-hand sides (0: all at once) as qcd_solve runs them
 int time_solve(qcd_ctx *c, double2 *xi, const double2 *bi, int nrhs, const qcd_params *p, double *ms, bool *ok) {
     *ok = false;
     use_sap_ctas(c, p->sap_ctas);  // sap_ctas 0: the context's setting, not the last candidate's
@@ -45,7 +49,13 @@ int time_solve(qcd_ctx *c, double2 *xi, const double2 *bi, int nrhs, const qcd_p
     QCD_CUDA(c, cudaEventRecord(e0, c->stream));
     qcd_stats st;
     std::memset(&st, 0, sizeof(st));
-    int s = solve(c, xi, bi, p, nrhs, &st);
+    const int g = p->rhs_group > 0 ? std::min(p->rhs_group, nrhs) : nrhs;
+    int s = QCD_OK;
+    for (int k0 = 0; k0 < nrhs && (s == QCD_OK || s == QCD_ERR_NOCONV || s == QCD_ERR_BREAKDOWN); k0 += g) {
+        const int n = std::min(g, nrhs - k0);
+        const int sg = solve(c, xi + (size_t)12 * c->lat.V * k0, bi + (size_t)12 * c->lat.V * k0, p, n, &st);
+        if (sg != QCD_OK && s == QCD_OK) s = sg;
+    }
     QCD_CUDA(c, cudaEventRecord(e1, c->stream));
     QCD_CUDA(c, cudaEventSynchronize(e1));
     float t = 0;
@@ -58,10 +68,87 @@ int time_solve(qcd_ctx *c, double2 *xi, const double2 *bi, int nrhs, const qcd_p
     return QCD_OK;
 }
 
+// ---- on-disk cache of tuning results (one JSON object per line) ----
+std::mutex g_cache_mu;
+std::string g_cache_path;
+constexpr const char *kTunerVersion = "sap-tile-2";
+
+std::string cache_key(qcd_ctx *c, int nrhs, const qcd_params *b, int max_candidates) {
+    cudaDeviceProp prop;
+    std::string gpu = "unknown";
+    int sms = 0;
+    if (cudaGetDeviceProperties(&prop, c->device) == cudaSuccess) {
+        gpu = prop.name;
+        sms = prop.multiProcessorCount;
+    } else {
+        cudaGetLastError();
+    }
+    for (char &ch : gpu)
+        if (ch == '"' || ch == ';' || ch == '\\') ch = '_';
+    char buf[512];
+    std::snprintf(buf, sizeof(buf),
+                  "%s;dims=%dx%dx%dx%d;nrhs=%d;kappa=%.17g;csw=%.17g;bc_t=%d;tol=%.17g;inner_tol=%.17g;"
+                  "max=%d/%d;omega=%.17g;rhs_group=%d;cands=%d;gpu=%s;sms=%d",
+                  kTunerVersion, c->lat.L[0], c->lat.L[1], c->lat.L[2], c->lat.L[3], nrhs, b->kappa, b->csw, b->bc_t,
+                  b->tol, b->inner_tol, b->max_outer, b->max_inner, b->omega, b->rhs_group, max_candidates,
+                  gpu.c_str(), sms);
+    return buf;
+}
+
+// the cached winner for key, if the cache file holds one
+bool cache_lookup(const std::string &key, const qcd_params *base, qcd_params *best, double *ms) {
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    if (g_cache_path.empty()) return false;
+    FILE *f = std::fopen(g_cache_path.c_str(), "r");
+    if (!f) return false;
+    const std::string head = "{\"key\": \"" + key + "\", ";
+    char line[2048];
+    bool found = false;
+    while (std::fgets(line, sizeof(line), f)) {
+        if (std::strncmp(line, head.c_str(), head.size()) != 0) continue;
+        qcd_params p = *base;
+        double t = 0;
+        const int n = std::sscanf(line + head.size(),
+                                  "\"block\": [%d, %d, %d, %d], \"subblock\": [%d, %d, %d, %d], "
+                                  "\"sap_storage\": %d, \"sap_ctas\": %d, \"nsweep\": %d, \"nsap\": %d, "
+                                  "\"rhs_group\": %d, \"ms\": %lf",
+                                  &p.block[0], &p.block[1], &p.block[2], &p.block[3], &p.subblock[0], &p.subblock[1],
+                                  &p.subblock[2], &p.subblock[3], &p.sap_storage, &p.sap_ctas, &p.nsweep, &p.nsap,
+                                  &p.rhs_group, &t);
+        if (n == 14) {
+            *best = p;
+            *ms = t;
+            found = true;  // the last matching line wins
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+void cache_store(const std::string &key, const qcd_params *p, double ms) {
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    if (g_cache_path.empty()) return;
+    FILE *f = std::fopen(g_cache_path.c_str(), "a");
+    if (!f) return;
+    std::fprintf(f,
+                 "{\"key\": \"%s\", \"block\": [%d, %d, %d, %d], \"subblock\": [%d, %d, %d, %d], "
+                 "\"sap_storage\": %d, \"sap_ctas\": %d, \"nsweep\": %d, \"nsap\": %d, \"rhs_group\": %d, "
+                 "\"ms\": %.6f}\n",
+                 key.c_str(), p->block[0], p->block[1], p->block[2], p->block[3], p->subblock[0], p->subblock[1],
+                 p->subblock[2], p->subblock[3], p->sap_storage, p->sap_ctas, p->nsweep, p->nsap, p->rhs_group, ms);
+    std::fclose(f);
+}
+
 }  // namespace
 }  // namespace qcd
 
 using namespace qcd;
+
+extern "C" int qcd_set_tune_cache(const char *path) {
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    g_cache_path = path ? path : "";
+    return QCD_OK;
+}
 
 extern "C" int qcd_autotune(qcd_ctx *c, const double *b, int nrhs, const qcd_params *base, qcd_params *best,
                             double *best_ms, int max_candidates) {
@@ -72,6 +159,14 @@ extern "C" int qcd_autotune(qcd_ctx *c, const double *b, int nrhs, const qcd_par
     if (base->kappa != c->kappa || base->csw != c->csw || base->bc_t != c->bc_t)
         return fail(c, QCD_ERR_ARG, "params kappa/csw/bc_t differ from the context");
     if (max_candidates <= 0) max_candidates = 64;
+    const std::string key = cache_key(c, nrhs, base, max_candidates);
+    {
+        double cms = 0;
+        if (cache_lookup(key, base, best, &cms)) {
+            if (best_ms) *best_ms = cms;
+            return QCD_OK;
+        }
+    }
     const long V = c->lat.V;
     const size_t bytes = sizeof(double2) * 12 * V * nrhs;
     // right-hand sides in the internal layout, solution buffer
@@ -113,9 +208,12 @@ extern "C" int qcd_autotune(qcd_ctx *c, const double *b, int nrhs, const qcd_par
                 cd.p = *base;
                 std::memcpy(cd.p.block, blk, sizeof(blk));
                 std::memcpy(cd.p.subblock, sub, sizeof(sub));
-                cd.p.sap_storage = QCD_F32;
-                cd.p.sap_ctas = 0;
+                // ranked with the fast form: the tile form with FP16 storage, the cluster form
+                // where a block's spinor does not fit one CTA
+                cd.p.sap_storage = QCD_F16;
+                cd.p.sap_ctas = -2;
                 cd.p.block_solver = 0;  // the tuner explores the ll-SSOR set-ups
+                cd.p.rhs_group = base->rhs_group;
                 cands.push_back(cd);
             }
         }
@@ -154,7 +252,7 @@ extern "C" int qcd_autotune(qcd_ctx *c, const double *b, int nrhs, const qcd_par
         for (size_t i = 0; i < cands.size() && i < 3; i++) {
             if (!cands[i].ok) continue;
             for (int storage : {QCD_F32, QCD_F16})
-                for (int ctas : {0, -1, 2})
+                for (int ctas : {-2, 0, 2})
                     for (int ns : {2, 4})
                         for (int np : {2, 4}) {
                             Cand cd = cands[i];
@@ -172,6 +270,27 @@ extern "C" int qcd_autotune(qcd_ctx *c, const double *b, int nrhs, const qcd_par
             if ((rc = run(cd))) break;
         cands.insert(cands.end(), more.begin(), more.end());
     }
+    if (!rc && nrhs > 1 && base->rhs_group == 0) {
+        // stage 3: right-hand sides per group for the fastest set-up (all at once, or groups of
+        // 1, 2, 4 or 8 that divide them)
+        const Cand *w0 = nullptr;
+        for (auto &cd : cands)
+            if (cd.ok && (!w0 || cd.ms < w0->ms)) w0 = &cd;
+        if (w0) {
+            std::vector<Cand> more;
+            for (int g : {1, 2, 4, 8})
+                if (g < nrhs && nrhs % g == 0) {
+                    Cand cd = *w0;
+                    cd.p.rhs_group = g;
+                    more.push_back(cd);
+                }
+            for (auto &cd : more) {
+                tried = std::min(tried, max_candidates - 1);  // always time the group sizes
+                if ((rc = run(cd))) break;
+            }
+            cands.insert(cands.end(), more.begin(), more.end());
+        }
+    }
     c->prof.on = old_prof;
     use_sap_ctas(c, 0);
     if (rc) return rc;
@@ -181,5 +300,6 @@ extern "C" int qcd_autotune(qcd_ctx *c, const double *b, int nrhs, const qcd_par
     if (!win) return fail(c, QCD_ERR_NOCONV, "autotune: no candidate converged");
     *best = win->p;
     if (best_ms) *best_ms = win->ms;
+    cache_store(key, &win->p, win->ms);
     return QCD_OK;
 }

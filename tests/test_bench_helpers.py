@@ -1,27 +1,29 @@
-"""Host-side helpers of bench.py (no GPU): the kernel models behind the roofline fields."""
+"""Host-side helpers of bench.py (no GPU): the kernel models behind the roofline fields and the
+scaling of the bounded oracle sample."""
 import math
 
 import bench
 
 
-def test_issue_floor_of_the_ssor_kernel():
-    # 66.6 M warp instructions on 64 SMs at 4 per cycle and 2070 MHz: 125.7 us per launch
-    r = bench.issue_model("ssor", 0.2486, 2070.0)
-    assert math.isclose(r["floor_ms"], 66.6e6 / (64 * 4 * 2070e6) * 1e3, rel_tol=1e-12)
-    assert math.isclose(r["floor_ms"], 0.1257, rel_tol=1e-3)
-    assert math.isclose(r["frac"], r["floor_ms"] / 0.2486, rel_tol=1e-12)
-    assert bench.issue_model("dslash32", 0.1, 2070.0) is None
-    assert bench.issue_model("ssor", 0.0, 2070.0) is None
-
-
-def test_ssor_flop_model_counts_table1_flops_per_update():
-    peaks = {"hbm_gbs": 6764.0, "sm_max_mhz": 2070.0, "source": "measured"}
-    V = 12 * 12 * 12 * 24
-    bound, units, unit, peak = bench.kernel_model("ssor", V, 1, {"nsweep": 4}, peaks)
-    assert (bound, unit) == ("alu", "TFLOP/s")
-    # one launch: V/2 sites x 2 passes x 4 sweeps x 1896 flop
-    assert math.isclose(units, V / 2 * 2 * 4 * 1896 / 1e12, rel_tol=1e-12)
-    assert math.isclose(peak, 152 * 128 * 2 * 2070e6 / 1e12, rel_tol=1e-12)
-    bound, units, unit, peak = bench.kernel_model("dslash32", V, 1, {"nsweep": 4}, peaks)
-    assert (bound, unit, peak) == ("hbm", "GB/s", 6764.0)
+def test_sap_flop_model_counts_table1_flops_per_update():
+    peaks = {"hbm_gbs": 6789.0, "sm_max_mhz": 2070.0, "source": "measured", "fp32_tflops": 70.0,
+             "fp32_source": "measured"}
+    V = 48 * 48 * 48 * 96
+    bound, units, unit, peak, src = bench.kernel_model("ssor", V, 4, {"nsweep": 2}, peaks)
+    assert (bound, unit, peak) == ("alu", "TFLOP/s", 70.0)
+    # one launch: V/2 sites x 4 right-hand sides x (2 passes x 2 sweeps + 1 residual) x 1896 flop
+    assert math.isclose(units, V / 2 * 4 * 5 * 1896 / 1e12, rel_tol=1e-12)
+    bound, units, unit, peak, src = bench.kernel_model("dslash32", V, 1, {"nsweep": 2}, peaks)
+    assert (bound, unit, peak) == ("hbm", "GB/s", 6789.0)
     assert math.isclose(units, V * 768 / 1e9, rel_tol=1e-12)
+    # k right-hand sides: both spinors each, links and clover once
+    _, units, _, _, _ = bench.kernel_model("dslash32", V, 12, {"nsweep": 2}, peaks)
+    assert math.isclose(units, V * (12 * 192 + 576) / 1e9, rel_tol=1e-12)
+    assert bench.kernel_model("blas", V, 1, {"nsweep": 2}, peaks) is None
+
+
+def test_derived_fp32_peak_and_oracle_scale():
+    p = bench.read_peaks()
+    assert math.isclose(p["fp32_tflops"], 152 * 128 * 2 * p["sm_max_mhz"] * 1e6 / 1e12, rel_tol=1e-12)
+    # 48^3 x 96 has 1296 times the sites of 8^3 x 16; 12 sources
+    assert bench.oracle_scale() == 1296 * 12

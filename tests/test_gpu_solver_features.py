@@ -1,0 +1,118 @@
+"""GPU tests of solver features around the method: right-hand-side groups, the tuning cache,
+the breakdown path of the outer BiCGStab (Sec. 2) under a breakdown made on the host, and the
+FP32 peak measurement hook."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import qcd_inputs as qi
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1210_7398_gb300 as q  # noqa: E402
+
+CSW = 1.6
+
+
+def make_solver(dims, kappa, seed):
+    U = qi.gauge_field(dims, 0.3, seed=seed)
+    s = q.Solver(dims)
+    s.load_gauge(torch.from_numpy(U).cuda())
+    s.build_clover(kappa, CSW)
+    return s, U
+
+
+def test_rhs_groups_give_the_batched_solutions_bit_for_bit():
+    """Each right-hand side's iterates do not depend on which others share its batch, so solving
+    five sources in groups of 1, 2 or all at once gives identical solutions."""
+    dims, kappa = (8, 8, 8, 8), 0.12
+    s, U = make_solver(dims, kappa, seed=1011)
+    b = torch.from_numpy(qi.gaussian_spinor(dims, seed=2011, nrhs=5)).cuda()
+    outs = []
+    for g in (0, 5, 2, 1):
+        prm = q.make_params(kappa, CSW, (4, 4, 4, 4), (2, 2, 2, 2), nsweep=2, nsap=2, tol=1e-10,
+                            sap_storage=q.QCD_F16, sap_ctas=-2, rhs_group=g)
+        x = torch.zeros_like(b)
+        st = s.solve(x, b, prm, nrhs=5)
+        assert st["true_rel_res"] <= 1e-10
+        outs.append(x)
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+    with pytest.raises(q.QcdError) as e:
+        s.solve(torch.zeros_like(b), b, q.make_params(kappa, CSW, (4, 4, 4, 4), (2, 2, 2, 2), rhs_group=-1), nrhs=5)
+    assert e.value.code == q.QCD_ERR_ARG
+    s.close()
+
+
+def test_tuning_cache_round_trip(tmp_path):
+    dims, kappa = (8, 8, 8, 8), 0.12
+    s, _ = make_solver(dims, kappa, seed=1012)
+    b = torch.from_numpy(qi.gaussian_spinor(dims, seed=2012, nrhs=2)).cuda()
+    base = q.make_params(kappa, CSW, (4, 4, 4, 4), (2, 2, 2, 2), tol=1e-10)
+    path = str(tmp_path / "tune.jsonl")
+    q.qcd_set_tune_cache(path)
+    try:
+        best1, ms1 = q.qcd_autotune(s.ctx, b, base, nrhs=2, max_candidates=6)
+        lines = open(path).read().splitlines()
+        assert len(lines) == 1
+        rec = json.loads(lines[0])
+        assert rec["block"] == list(best1.block) and rec["rhs_group"] == best1.rhs_group
+        best2, ms2 = q.qcd_autotune(s.ctx, b, base, nrhs=2, max_candidates=6)  # served from the file
+        assert q.params_dict(best2) == q.params_dict(best1)
+        assert abs(ms2 - ms1) <= 1e-6 * max(1.0, ms1)
+        assert len(open(path).read().splitlines()) == 1
+        # another key (nrhs) is tuned and appended
+        q.qcd_autotune(s.ctx, b[:1].contiguous(), base, nrhs=1, max_candidates=4)
+        assert len(open(path).read().splitlines()) == 2
+    finally:
+        q.qcd_set_tune_cache(None)
+    s.close()
+
+
+def test_breakdown_made_on_the_host_restarts_and_converges():
+    """rho = 0 at the start of the first outer iteration: the solver takes the breakdown path
+    (true residual, restart from it) and still reaches 1e-10 under the oracle's D."""
+    dims, kappa = (4, 4, 4, 4), 0.12
+    s, U = make_solver(dims, kappa, seed=1000)
+    b = qi.gaussian_spinor(dims, seed=2000, nrhs=2)
+    prm = q.make_params(kappa, CSW, (2, 2, 2, 2), (1, 1, 1, 1), nsweep=4, nsap=4, tol=1e-10)
+    q.qcd_debug_inject_breakdown(s.ctx, 1)
+    x = np.zeros_like(b)
+    st = s.solve(x, b, prm, nrhs=2)
+    assert st["status"] == q.QCD_OK and st["restarts"] >= 2  # one per right-hand side
+    _, F = oracle.clover(dims, U, CSW, kappa)
+    for k in range(2):
+        r = b[k] - oracle.apply_D(dims, U, F, kappa, x[k])
+        assert np.linalg.norm(r) / np.linalg.norm(b[k]) <= 1e-10
+    s.close()
+
+
+def test_persistent_breakdown_ends_in_qcd_err_breakdown():
+    """Breakdowns at every outer iteration: after 5 restarts the solve reports
+    QCD_ERR_BREAKDOWN, x stays finite, and the context keeps working."""
+    dims, kappa = (4, 4, 4, 4), 0.12
+    s, U = make_solver(dims, kappa, seed=1000)
+    b = qi.gaussian_spinor(dims, seed=2000)
+    prm = q.make_params(kappa, CSW, (2, 2, 2, 2), (1, 1, 1, 1), nsweep=4, nsap=4, tol=1e-10)
+    q.qcd_debug_inject_breakdown(s.ctx, 1000)
+    x = np.zeros_like(b)
+    st = s.solve(x, b, prm, check=False)
+    assert st["rc"] == q.QCD_ERR_BREAKDOWN and st["status"] == q.QCD_ERR_BREAKDOWN
+    assert st["restarts"] == 6
+    assert np.all(np.isfinite(x))
+    q.qcd_debug_inject_breakdown(s.ctx, 0)
+    x[...] = 0
+    st = s.solve(x, b, prm)
+    assert st["true_rel_res"] <= 1e-10
+    s.close()
+
+
+def test_fp32_peak_hook():
+    s = q.Solver((4, 4, 4, 4))
+    t = q.qcd_bench_fp32_peak(s.ctx, 8)
+    assert 10.0 < t < 200.0, t  # GB300: 152 SMs x 128 lanes x 2 flop x about 2 GHz
+    s.close()
