@@ -268,6 +268,7 @@ int sap_build_records(qcd_ctx *c, SapPlan &plan, float *rec);
 // kTileMaxRhs right-hand sides), one thread per site update, the block spinors of the tile in
 // shared memory; per-site records of kTileRecordBytes (FP32) / kTileRecordBytesHalf (FP16)
 constexpr int kTileMaxThreads = 256;
+constexpr int kTileMinBlocks = 2;  // resident CTAs per SM the register allocation is made for (128 registers)
 constexpr int kTileMaxRhs = 8;
 constexpr size_t kTileSmemLimit = 200 * 1024;
 constexpr size_t kTileSmemPerSm = 228 * 1024;

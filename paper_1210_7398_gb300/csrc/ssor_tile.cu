@@ -81,43 +81,110 @@ template <bool HALF> __device__ __forceinline__ void st_y(float *p, const float2
     }
 }
 
-// the two transport matrices of direction mu (forward, backward), first two rows each, the third rebuilt
-template <bool HALF> __device__ __forceinline__ void ld_links(const uint4 *rec, int mu, float2 Wf[9], float2 Wb[9]) {
+// one transport matrix W_d (first two rows; the third rebuilt): loaded direction by direction,
+// so that only one matrix is live at a time
+template <bool HALF, int D> __device__ __forceinline__ void ld_link(const uint4 *rec, float2 W[9]) {
     if constexpr (HALF) {
-        const uint4 *p = rec + 3 * mu;  // 48 bytes: 6 half2 forward, 6 half2 backward
-        const uint4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
-        Wf[0] = h2f(a.x); Wf[1] = h2f(a.y); Wf[2] = h2f(a.z); Wf[3] = h2f(a.w); Wf[4] = h2f(b.x); Wf[5] = h2f(b.y);
-        Wb[0] = h2f(b.z); Wb[1] = h2f(b.w); Wb[2] = h2f(c.x); Wb[3] = h2f(c.y); Wb[4] = h2f(c.z); Wb[5] = h2f(c.w);
+        const unsigned char *p = reinterpret_cast<const unsigned char *>(rec) + D * 24;
+        unsigned w[6];
+        if constexpr ((D & 1) == 0) {  // 16-byte aligned: 16 + 8 bytes
+            const uint4 a = __ldg(reinterpret_cast<const uint4 *>(p));
+            const uint2 b = __ldg(reinterpret_cast<const uint2 *>(p + 16));
+            w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w; w[4] = b.x; w[5] = b.y;
+        } else {  // 8-byte aligned: 8 + 16 bytes
+            const uint2 a = __ldg(reinterpret_cast<const uint2 *>(p));
+            const uint4 b = __ldg(reinterpret_cast<const uint4 *>(p + 8));
+            w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y; w[4] = b.z; w[5] = b.w;
+        }
+#pragma unroll
+        for (int k = 0; k < 6; k++) W[k] = h2f(w[k]);
     } else {
-        const float4 *p = reinterpret_cast<const float4 *>(rec) + 6 * mu;
+        const float4 *p = reinterpret_cast<const float4 *>(rec) + 3 * D;
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-            const float4 v = __ldg(p + k), w = __ldg(p + 3 + k);
-            Wf[2 * k] = make_float2(v.x, v.y); Wf[2 * k + 1] = make_float2(v.z, v.w);
-            Wb[2 * k] = make_float2(w.x, w.y); Wb[2 * k + 1] = make_float2(w.z, w.w);
+            const float4 v = __ldg(p + k);
+            W[2 * k] = make_float2(v.x, v.y);
+            W[2 * k + 1] = make_float2(v.z, v.w);
         }
     }
-    su3_third_row(Wf);
-    su3_third_row(Wb);
+    su3_third_row(W);
 }
 
-template <bool HALF> __device__ __forceinline__ void ld_clover(const uint4 *rec, float f[72]) {
+// y = H x for chiral block B (0 or 1) of the record's packed clover (6 real diagonal entries,
+// then the 15 complex entries below the diagonal in row order).  FP16: 18 half2 words, the first
+// three holding the diagonal and each later one a complex entry, converted as they are used.
+template <bool HALF, int B> __device__ __forceinline__ void herm6_rec(const uint4 *rec, const float2 x[6], float2 y[6]) {
+    float d[6];
+    float2 o[15];
     if constexpr (HALF) {
-        const uint4 *p = rec + TileRec<true>::clover_off / 16;
+        const unsigned char *p = reinterpret_cast<const unsigned char *>(rec) + TileRec<true>::clover_off + 72 * B;
+        unsigned w[18];
+        if constexpr (B == 0) {  // 16-byte aligned: 4 x 16 + 8 bytes
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p) + k);
+                w[4 * k] = v.x; w[4 * k + 1] = v.y; w[4 * k + 2] = v.z; w[4 * k + 3] = v.w;
+            }
+            const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p + 64));
+            w[16] = v.x; w[17] = v.y;
+        } else {  // 8-byte aligned: 8 + 4 x 16 bytes
+            const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
+            w[0] = v.x; w[1] = v.y;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const uint4 u = __ldg(reinterpret_cast<const uint4 *>(p + 8) + k);
+                w[2 + 4 * k] = u.x; w[3 + 4 * k] = u.y; w[4 + 4 * k] = u.z; w[5 + 4 * k] = u.w;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const float2 t = h2f(w[k]);
+            d[2 * k] = t.x;
+            d[2 * k + 1] = t.y;
+        }
+#pragma unroll
+        for (int k = 0; k < 15; k++) o[k] = h2f(w[3 + k]);
+    } else {
+        const float4 *p = reinterpret_cast<const float4 *>(rec) + TileRec<false>::clover_off / 16 + 9 * B;
+        float f[36];
 #pragma unroll
         for (int k = 0; k < 9; k++) {
-            const uint4 v = __ldg(p + k);
-            const float2 a = h2f(v.x), b = h2f(v.y), c = h2f(v.z), d = h2f(v.w);
-            f[8 * k] = a.x; f[8 * k + 1] = a.y; f[8 * k + 2] = b.x; f[8 * k + 3] = b.y;
-            f[8 * k + 4] = c.x; f[8 * k + 5] = c.y; f[8 * k + 6] = d.x; f[8 * k + 7] = d.y;
-        }
-    } else {
-        const float4 *p = reinterpret_cast<const float4 *>(rec) + TileRec<false>::clover_off / 16;
-#pragma unroll
-        for (int k = 0; k < 18; k++) {
             const float4 v = __ldg(p + k);
             f[4 * k] = v.x; f[4 * k + 1] = v.y; f[4 * k + 2] = v.z; f[4 * k + 3] = v.w;
         }
+#pragma unroll
+        for (int k = 0; k < 6; k++) d[k] = f[k];
+#pragma unroll
+        for (int k = 0; k < 15; k++) o[k] = make_float2(f[6 + 2 * k], f[7 + 2 * k]);
+    }
+#pragma unroll
+    for (int i = 0; i < 6; i++) y[i] = cscale(x[i], d[i]);
+    int k = 0;
+#pragma unroll
+    for (int i = 1; i < 6; i++) {
+#pragma unroll
+        for (int j = 0; j < i; j++) {
+            y[i] = cfma(o[k], x[j], y[i]);   // row i gets H_ij x_j
+            y[j] = cfmac(o[k], x[i], y[j]);  // row j gets conj(H_ij) x_i
+            k++;
+        }
+    }
+}
+
+// out = F v for a Dirac-basis spinor (the chiral blocks of F/2 applied to v_u -/+ v_l), one
+// chiral block at a time
+template <bool HALF> __device__ __forceinline__ void clover_rec(const uint4 *rec, const float2 v[12], float2 out[12]) {
+    float2 c[6], e0[6], e1[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) c[k] = csub(v[k], v[k + 6]);
+    herm6_rec<HALF, 0>(rec, c, e0);
+#pragma unroll
+    for (int k = 0; k < 6; k++) c[k] = cadd(v[k], v[k + 6]);
+    herm6_rec<HALF, 1>(rec, c, e1);
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+        out[k] = cadd(e0[k], e1[k]);
+        out[k + 6] = csub(e1[k], e0[k]);
     }
 }
 
@@ -154,7 +221,7 @@ struct TileArgs {
 // which is Alg. 1's y = K r, w = D y, x += y, r -= w term by term, with the cross hops of each
 // colour applied by the launch that next reads them.
 template <bool HALF, int R>
-__global__ void __launch_bounds__(kTileMaxThreads, 2) k_sap_tile(TileArgs a) {
+__global__ void __launch_bounds__(kTileMaxThreads, kTileMinBlocks) k_sap_tile(TileArgs a) {
     using L = TileRec<HALF>;
     extern __shared__ __align__(16) float sm[];
     __shared__ float scale_s[R];
@@ -192,8 +259,8 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_sap_tile(TileArgs a) {
             const int pos = i / R;
             const int4 pa = __ldg(a.pos + 2 * pos), pb = __ldg(a.pos + 2 * pos + 1);
             float2 f[12];
-            if (a.first) load_spinor(a.v + roff, a.V, pa.x, f);
-            else load_spinor_rw(rr, a.V, pa.x, f);
+#pragma unroll
+            for (int k = 0; k < 12; k++) f[k] = make_float2(0.f, 0.f);
             if (a.cross) {
                 const int nb[8] = {pa.z & 0xffff, pa.z >> 16, pa.w & 0xffff, pa.w >> 16,
                                    pb.x & 0xffff, pb.x >> 16, pb.y & 0xffff, pb.y >> 16};
@@ -210,39 +277,42 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_sap_tile(TileArgs a) {
                     }
                     const uint4 *rec = recb + (size_t)pos * L::chunks;
                     const float4 *yr = a.y + (size_t)(rhs0 + r_me) * 6 * a.V;
-                    float2 acc[12], psi[12], Wf[9], Wb[9];
+                    float2 acc[12];
 #pragma unroll
                     for (int k = 0; k < 12; k++) acc[k] = make_float2(0.f, 0.f);
 #define QCD_TILE_CROSS(MU)                                                                          \
-                    if (nb[2 * MU] == a.vol || nb[2 * MU + 1] == a.vol) {                            \
-                        ld_links<HALF>(rec, MU, Wf, Wb);                                             \
-                        if (nb[2 * MU] == a.vol) {                                                   \
-                            const bool wrap = xg[MU] == a.L[MU] - 1;                                 \
-                            const long mm = n0 + pa.x + (wrap ? -(long)(a.L[MU] - 1) * st[MU] : st[MU]); \
-                            load_spinor(yr, a.V, mm, psi);                                           \
-                            hop_term_w<MU, true>(psi, Wf, acc, (MU == 3 && wrap) ? (float)a.bc_t : 1.f); \
-                        }                                                                            \
-                        if (nb[2 * MU + 1] == a.vol) {                                               \
-                            const bool wrap = xg[MU] == 0;                                           \
-                            const long mm = n0 + pa.x + (wrap ? (long)(a.L[MU] - 1) * st[MU] : -st[MU]); \
-                            load_spinor(yr, a.V, mm, psi);                                           \
-                            hop_term_w<MU, false>(psi, Wb, acc, (MU == 3 && wrap) ? (float)a.bc_t : 1.f); \
-                        }                                                                            \
+                    if (nb[2 * MU] == a.vol) {                                                       \
+                        float2 W[9], psi[12];                                                        \
+                        ld_link<HALF, 2 * MU>(rec, W);                                               \
+                        const bool wrap = xg[MU] == a.L[MU] - 1;                                     \
+                        const long mm = n0 + pa.x + (wrap ? -(long)(a.L[MU] - 1) * st[MU] : st[MU]); \
+                        load_spinor(yr, a.V, mm, psi);                                               \
+                        hop_term_w<MU, true>(psi, W, acc, (MU == 3 && wrap) ? (float)a.bc_t : 1.f);  \
+                    }                                                                                \
+                    if (nb[2 * MU + 1] == a.vol) {                                                   \
+                        float2 W[9], psi[12];                                                        \
+                        ld_link<HALF, 2 * MU + 1>(rec, W);                                           \
+                        const bool wrap = xg[MU] == 0;                                               \
+                        const long mm = n0 + pa.x + (wrap ? (long)(a.L[MU] - 1) * st[MU] : -st[MU]); \
+                        load_spinor(yr, a.V, mm, psi);                                               \
+                        hop_term_w<MU, false>(psi, W, acc, (MU == 3 && wrap) ? (float)a.bc_t : 1.f); \
                     }
                     QCD_TILE_CROSS(0)
                     QCD_TILE_CROSS(1)
                     QCD_TILE_CROSS(2)
                     QCD_TILE_CROSS(3)
 #undef QCD_TILE_CROSS
-                    float fc[72];
-                    ld_clover<HALF>(rec, fc);
-                    float2 fa[12];
-                    clover_mul<float, float2>(fc, acc, fa);
+                    clover_rec<HALF>(rec, acc, f);  // f = F H_{cc'} y for now
+                }
+            }
+            {
+                float2 base[12];
+                if (a.first) load_spinor(a.v + roff, a.V, pa.x, base);
+                else load_spinor_rw(rr, a.V, pa.x, base);
 #pragma unroll
-                    for (int k = 0; k < 12; k++) {
-                        f[k].x = fmaf(a.kappa, fa[k].x, f[k].x);
-                        f[k].y = fmaf(a.kappa, fa[k].y, f[k].y);
-                    }
+                for (int k = 0; k < 12; k++) {
+                    f[k].x = fmaf(a.kappa, f[k].x, base[k].x);
+                    f[k].y = fmaf(a.kappa, f[k].y, base[k].y);
                 }
             }
             store_spinor(rr, a.V, pa.x, f);
@@ -272,22 +342,24 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_sap_tile(TileArgs a) {
         float2 acc[12];
 #pragma unroll
         for (int k = 0; k < 12; k++) acc[k] = make_float2(0.f, 0.f);
-        float2 psi[12], Wf[9], Wb[9];
         // a direction leaving the block reads the zero slot, so it adds nothing
-#define QCD_TILE_HOP(MU)                                                                  \
-        ld_links<HALF>(rec, MU, Wf, Wb);                                                  \
-        ld_y<HALF>(ys + (nb[2 * MU] * R + r_me) * L::y_words, psi);                       \
-        hop_term_w<MU, true>(psi, Wf, acc);                                               \
-        ld_y<HALF>(ys + (nb[2 * MU + 1] * R + r_me) * L::y_words, psi);                   \
-        hop_term_w<MU, false>(psi, Wb, acc);
+#define QCD_TILE_HOP(D)                                                                   \
+        {                                                                                 \
+            float2 W[9], psi[12];                                                         \
+            ld_link<HALF, D>(rec, W);                                                     \
+            ld_y<HALF>(ys + (nb[D] * R + r_me) * L::y_words, psi);                        \
+            hop_term_w<D / 2, (D & 1) == 0>(psi, W, acc);                                 \
+        }
         QCD_TILE_HOP(0)
         QCD_TILE_HOP(1)
         QCD_TILE_HOP(2)
         QCD_TILE_HOP(3)
+        QCD_TILE_HOP(4)
+        QCD_TILE_HOP(5)
+        QCD_TILE_HOP(6)
+        QCD_TILE_HOP(7)
 #undef QCD_TILE_HOP
-        float fc[72];
-        ld_clover<HALF>(rec, fc);
-        clover_mul<float, float2>(fc, acc, fa);
+        clover_rec<HALF>(rec, acc, fa);
     };
 
     // one SSOR site update: y <- y + omega (f + kappa F H_BB y - y)
@@ -330,23 +402,33 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_sap_tile(TileArgs a) {
         for (int i = tid; i < a.vol * R; i += T) {
             const int pos = i / R;
             const int4 pa = __ldg(a.pos + 2 * pos), pb = __ldg(a.pos + 2 * pos + 1);
+            if (a.store_r) {
+                float2 f[12];
+                block_FH(pos, pa, pb, f);  // F H_BB y, then f - y + kappa F H_BB y
+                {
+                    float2 base[12];
+                    load_spinor_rw(rr, a.V, pa.x, base);
+#pragma unroll
+                    for (int k = 0; k < 12; k++) {
+                        if constexpr (HALF) f[k] = cscale(f[k], my_scale);
+                        f[k].x = fmaf(a.kappa, f[k].x, base[k].x);
+                        f[k].y = fmaf(a.kappa, f[k].y, base[k].y);
+                    }
+                }
+                float2 yv[12];
+                ld_y<HALF>(ys + (pa.y * R + r_me) * L::y_words, yv);
+#pragma unroll
+                for (int k = 0; k < 12; k++) {
+                    if constexpr (HALF) yv[k] = cscale(yv[k], my_scale);
+                    f[k] = csub(f[k], yv[k]);
+                }
+                store_spinor(rr, a.V, pa.x, f);
+            }
             float2 yv[12];
             ld_y<HALF>(ys + (pa.y * R + r_me) * L::y_words, yv);
             if constexpr (HALF) {
 #pragma unroll
                 for (int k = 0; k < 12; k++) yv[k] = cscale(yv[k], my_scale);
-            }
-            if (a.store_r) {
-                float2 fa[12], f[12];
-                block_FH(pos, pa, pb, fa);
-                load_spinor_rw(rr, a.V, pa.x, f);
-#pragma unroll
-                for (int k = 0; k < 12; k++) {
-                    if constexpr (HALF) fa[k] = cscale(fa[k], my_scale);
-                    f[k].x = fmaf(a.kappa, fa[k].x, f[k].x - yv[k].x);
-                    f[k].y = fmaf(a.kappa, fa[k].y, f[k].y - yv[k].y);
-                }
-                store_spinor(rr, a.V, pa.x, f);
             }
             if (a.first) {
                 store_spinor(xr, a.V, pa.x, yv);
@@ -445,11 +527,12 @@ int tile_set_attributes(qcd_ctx *c) {
 }
 
 int tile_choose(const SapPlan &p, int nrhs, int *R, int *threads, size_t *smem) {
-    // the most right-hand sides per CTA (up to 8) that still let two CTAs share an SM (the
-    // registers allow two of 256 threads); one per CTA up to the whole shared memory otherwise
-    const size_t two_per_sm = kTileSmemPerSm / 2 - 1024;
+    // the most right-hand sides per CTA (up to 8) that still let kTileMinBlocks CTAs share an
+    // SM (the registers allow that many of 256 threads); one per CTA up to the whole shared
+    // memory otherwise
+    const size_t share = kTileSmemPerSm / kTileMinBlocks - 1024;
     int r = 1;
-    while (r * 2 <= kTileMaxRhs && r * 2 <= nrhs && tile_smem_bytes(p.vol, p.half, r * 2) <= two_per_sm) r *= 2;
+    while (r * 2 <= kTileMaxRhs && r * 2 <= nrhs && tile_smem_bytes(p.vol, p.half, r * 2) <= share) r *= 2;
     if (tile_smem_bytes(p.vol, p.half, r) > kTileSmemLimit) return QCD_ERR_ARG;
     int t = ((p.max_step * r + 31) / 32) * 32;
     t = std::max(32, std::min(t, kTileMaxThreads));
