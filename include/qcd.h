@@ -75,7 +75,11 @@ enum {
     QCD_ERR_STATE = -8      /* wrong call order, or context poisoned by a CUDA error  */
 };
 
-enum { QCD_F64 = 0, QCD_F32 = 1, QCD_F16 = 2, QCD_BF16 = 3, QCD_F32_SU3 = 4 };
+/* Precisions and storage forms.  QCD_F16 is the half-precision storage of the precision
+ * pattern (FP32 arithmetic); the value 3 is not used (the SAP block spinors are kept per block in
+ * units of their largest source component, so FP16's 10-bit mantissa, not BF16's exponent
+ * range, is what the storage needs). */
+enum { QCD_F64 = 0, QCD_F32 = 1, QCD_F16 = 2, QCD_F32_SU3 = 4 };
 
 /* Solver and SAP parameters (Sec. 2, Sec. 3, Eq. (4)). */
 typedef struct {
@@ -113,11 +117,15 @@ typedef struct {
 } qcd_params;
 
 typedef struct {
-    int status, outer_iters, inner_iters, restarts;
+    int status;
+    int outer_iters;     /* outer iterations (summed over right-hand-side groups)       */
+    int inner_iters;     /* inner iterations summed over the right-hand sides           */
+    int restarts;        /* restarts from the true residual, summed over them           */
     double true_rel_res; /* max over right-hand sides of ||b - D x|| / ||b|| (FP64)     */
     double ms_total;     /* wall time of the call                                      */
-    double ms_dslash;    /* reserved (0 unless kernel profiling is on)                 */
-    double ms_sap;       /* reserved (0 unless kernel profiling is on)                 */
+    double ms_dslash;    /* device ms of the D kernels (FP32 and FP64) during the call
+                            when kernel profiling is on (qcd_set_profiling), else 0     */
+    double ms_sap;       /* the same for the SAP kernels (block solves, hop updates)    */
 } qcd_stats;
 
 /* Creates a context for a lattice of the given extents (each >= 2, even
@@ -173,17 +181,23 @@ int qcd_sap_precondition(qcd_ctx *ctx, float *out, const float *in, const qcd_pa
  * out = M_SAP in, exactly as qcd_sap_precondition with nrhs = 1, for device
  * pointers only (16-byte aligned complex64 [V][4][3]), with
  * p->sap_storage = QCD_F32, p->learned = 0 and p->block_solver = 0 (others
- * are rejected with QCD_ERR_ARG).  It calls no
- * cudaMalloc, cudaFree or allocating library routine: its scratch (four FP32
- * spinor fields, the per-site SSOR records and the ll-schedule tables) is one
- * fixed __device__ array of about 68.3 MB that every GPU loading the library
- * holds until the process exits.  Lattices above 41,472 sites (12^3 x 24) are rejected with
- * QCD_ERR_ARG.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress), so make that first call before any stream
- * capture.  All calls on a device share the one array and leave their data
- * in it; every region is rewritten before it is read, but calls that overlap
- * on the GPU (other streams, other contexts on the same device) race and
- * must be serialised by the caller.  Asynchronous on the context stream. */
+ * are rejected with QCD_ERR_ARG); p->sap_ctas (-2..16, 0 = the context's
+ * qcd_set_sap_ctas setting) picks the SSOR kernel form as for
+ * qcd_sap_precondition.  It calls no cudaMalloc, cudaFree or allocating
+ * library routine: its scratch (four FP32 spinor fields, the per-site SSOR
+ * records and the ll-schedule tables) is one fixed __device__ array of about
+ * 68.3 MB that every GPU loading the library holds until the process exits.
+ * Lattices above 41,472 sites (12^3 x 24) are rejected with QCD_ERR_ARG.  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * The array keeps the schedule tables and records of the last call (per
+ * device): a call with the same context, unchanged fields, geometry and form
+ * only launches kernels and is asynchronous on the context stream; any other
+ * call first rebuilds them, which copies from host memory and synchronises the
+ * context stream (so it cannot be captured either).  All calls on a device
+ * share the one array and leave their data in it; every region is rewritten
+ * before it is read, but calls that overlap on the GPU (other streams, other
+ * contexts on the same device) race and must be serialised by the caller. */
 int qcd_sap_precondition_noalloc(qcd_ctx *ctx, float *out, const float *in, const qcd_params *p);
 
 /* Solves D x = b (Eq. (1)) by the nested BiCGStab of Sec. 2 for nrhs
@@ -302,6 +316,14 @@ long qcd_learned_weight_count(void);
 int qcd_learned_set_weights(qcd_ctx *ctx, const float *w, long n);
 /* w: host complex64 [n] */
 int qcd_learned_get_weights(qcd_ctx *ctx, float *w, long n);
+/* Weights file of the correction: one JSON header line ({"format": "qcd-learned-weights",
+ * "version": 1, "layers", "channels", "layout", "dtype": "complex64", "count"}) followed by the
+ * count complex64 weights in the layout above.  qcd_learned_save writes the current weights
+ * (QCD_ERR_STATE without any); qcd_learned_load reads them and sets them as
+ * qcd_learned_set_weights does, and rejects a file whose header or size does not match this
+ * network with QCD_ERR_ARG.  Synchronise. */
+int qcd_learned_save(const qcd_ctx *ctx, const char *path);
+int qcd_learned_load(qcd_ctx *ctx, const char *path);
 /* out = N(in), complex64 [V][4][3], host or device */
 int qcd_learned_apply(qcd_ctx *ctx, float *out, const float *in);
 /* One training pair: loss = |N(rho) - eps|^2 / |eps|^2 and its gradient grad

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libqcd.so")
 
 QCD_OK, QCD_ERR_ARG, QCD_ERR_CUDA, QCD_ERR_OOM = 0, -1, -2, -3
 QCD_ERR_SINGULAR, QCD_ERR_NOCONV, QCD_ERR_BREAKDOWN, QCD_ERR_TIMEOUT, QCD_ERR_STATE = -4, -5, -6, -7, -8
-QCD_F64, QCD_F32, QCD_F16, QCD_BF16, QCD_F32_SU3 = 0, 1, 2, 3, 4
+QCD_F64, QCD_F32, QCD_F16, QCD_F32_SU3 = 0, 1, 2, 4
 QCD_K_DSLASH32, QCD_K_DSLASH64, QCD_K_SSOR, QCD_K_SAPHOP, QCD_K_BLAS, QCD_K_OTHER, QCD_K_LEARNED = range(7)
 KERNEL_CLASSES = ("dslash32", "dslash64", "ssor", "saphop", "blas", "other", "learned")
 
@@ -29,7 +29,7 @@ EXPORTS = ("qcd_create", "qcd_destroy", "qcd_last_error", "qcd_set_boundary", "q
            "qcd_set_sap_ctas", "qcd_set_sap_form", "qcd_sap_plan_tables", "qcd_set_graphs", "qcd_autotune", "qcd_learned_weight_count",
            "qcd_learned_set_weights", "qcd_learned_get_weights", "qcd_learned_apply", "qcd_learned_loss_grad",
            "qcd_learned_train", "qcd_learned_evaluate", "qcd_solve_multi", "qcd_set_tune_cache", "qcd_bench_fp32_peak",
-           "qcd_debug_inject_breakdown")
+           "qcd_debug_inject_breakdown", "qcd_learned_save", "qcd_learned_load")
 
 
 class QcdError(RuntimeError):
@@ -113,6 +113,8 @@ def load_library(path: str = LIB_PATH):
         "qcd_set_tune_cache": (I, [ctypes.c_char_p]),
         "qcd_bench_fp32_peak": (I, [P, I, ctypes.POINTER(D)]),
         "qcd_debug_inject_breakdown": (I, [P, I]),
+        "qcd_learned_save": (I, [P, ctypes.c_char_p]),
+        "qcd_learned_load": (I, [P, ctypes.c_char_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -291,6 +293,16 @@ def qcd_learned_get_weights(ctx):
     w = np.empty(qcd_learned_weight_count(), dtype=np.complex64)
     _check(ctx, load_library().qcd_learned_get_weights(ctx, _ptr(w), len(w)))
     return w
+
+
+def qcd_learned_save(ctx, path):
+    """Writes the correction's weights (JSON header line + complex64 data)."""
+    return _check(ctx, load_library().qcd_learned_save(ctx, str(path).encode()))
+
+
+def qcd_learned_load(ctx, path):
+    """Reads weights written by qcd_learned_save and sets them."""
+    return _check(ctx, load_library().qcd_learned_load(ctx, str(path).encode()))
 
 
 def qcd_learned_apply(ctx, out, inp):

@@ -184,6 +184,8 @@ int qcd_create(qcd_ctx **out, const int dims[4], void *stream) {
     if (V > (1L << 31)) return QCD_ERR_ARG;
     qcd_ctx *c = new (std::nothrow) qcd_ctx();
     if (!c) return QCD_ERR_OOM;
+    static std::atomic<long> next_uid{1};
+    c->uid = next_uid.fetch_add(1);
     cudaGetDevice(&c->device);
     c->stream = (cudaStream_t)stream;
     for (int m = 0; m < 4; m++) c->lat.L[m] = dims[m];
@@ -391,6 +393,12 @@ int qcd_solve(qcd_ctx *c, double *x, const double *b, const qcd_params *p, int n
     // learned = 1 falls back to plain SAP when the last evaluation found the correction slower
     qcd_params pe = *p;
     pe.learned = (p->learned == 2 || (p->learned == 1 && c->net.verdict != 0)) ? 1 : 0;
+    // device time per kernel class during this call (kernel profiling on)
+    double ms0[QCD_K_COUNT] = {};
+    if (c->prof.on) {
+        if ((rc = prof_collect(c))) return rc;
+        std::memcpy(ms0, c->prof.ms, sizeof(ms0));
+    }
     int status = QCD_OK;
     for (int k0 = 0; k0 < nrhs; k0 += g) {
         const int n = std::min(g, nrhs - k0);
@@ -418,6 +426,11 @@ int qcd_solve(qcd_ctx *c, double *x, const double *b, const qcd_params *p, int n
         if (!dev_x) QCD_CUDA(c, cudaMemcpyAsync((char *)x + per * k0, sx, bytes, cudaMemcpyDeviceToHost, c->stream));
     }
     QCD_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (c->prof.on) {
+        if ((rc = prof_collect(c))) return rc;
+        local.ms_dslash = c->prof.ms[QCD_K_DSLASH32] - ms0[QCD_K_DSLASH32] + c->prof.ms[QCD_K_DSLASH64] - ms0[QCD_K_DSLASH64];
+        local.ms_sap = c->prof.ms[QCD_K_SSOR] - ms0[QCD_K_SSOR] + c->prof.ms[QCD_K_SAPHOP] - ms0[QCD_K_SAPHOP];
+    }
     local.status = status;
     local.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (st) *st = local;
@@ -565,6 +578,52 @@ int qcd_learned_get_weights(qcd_ctx *c, float *w, long n) {
     if (rc) return rc;
     if (!w || n != learned_weight_count()) return fail(c, QCD_ERR_ARG, "weight count mismatch");
     return learned_get_weights(c, (float2 *)w);
+}
+
+// Weights file: one JSON header line, then the complex64 weights (little-endian float pairs) in
+// the layout of qcd_learned_set_weights.
+static std::string learned_header(long n) {
+    std::string ch;
+    for (int l = 0; l <= kLearnedLayers; l++) ch += (l ? ", " : "") + std::to_string(kLearnedChans[l]);
+    return "{\"format\": \"qcd-learned-weights\", \"version\": 1, \"layers\": " + std::to_string(kLearnedLayers) +
+           ", \"channels\": [" + ch + "], \"layout\": \"[layer][9][cout][cin][4][4]\", \"dtype\": \"complex64\", "
+           "\"count\": " + std::to_string(n) + "}";
+}
+
+int qcd_learned_save(const qcd_ctx *cc, const char *path) {
+    qcd_ctx *c = const_cast<qcd_ctx *>(cc);  // reads the weights only
+    int rc = ready(c);
+    if (rc) return rc;
+    if (!path) return fail(c, QCD_ERR_ARG, "path is NULL");
+    if (!c->net.ready) return fail(c, QCD_ERR_STATE, "no learned weights (qcd_learned_set_weights first)");
+    const long n = learned_weight_count();
+    std::vector<float> w(2 * (size_t)n);
+    if ((rc = learned_get_weights(c, (float2 *)w.data()))) return rc;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(c, QCD_ERR_ARG, std::string("cannot open ") + path + " for writing");
+    const std::string head = learned_header(n) + "\n";
+    const bool ok = std::fwrite(head.data(), 1, head.size(), f) == head.size() &&
+                    std::fwrite(w.data(), sizeof(float), w.size(), f) == w.size();
+    if (std::fclose(f) != 0 || !ok) return fail(c, QCD_ERR_ARG, std::string("cannot write ") + path);
+    return QCD_OK;
+}
+
+int qcd_learned_load(qcd_ctx *c, const char *path) {
+    int rc = ready(c);
+    if (rc) return rc;
+    if (!path) return fail(c, QCD_ERR_ARG, "path is NULL");
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(c, QCD_ERR_ARG, std::string("cannot open ") + path);
+    const long n = learned_weight_count();
+    const std::string want = learned_header(n);
+    std::string line;
+    for (int ch; (ch = std::fgetc(f)) != EOF && ch != '\n' && line.size() < 4096;) line.push_back((char)ch);
+    std::vector<float> w(2 * (size_t)n);
+    const bool ok = line == want && std::fread(w.data(), sizeof(float), w.size(), f) == w.size() &&
+                    std::fgetc(f) == EOF;
+    std::fclose(f);
+    if (!ok) return fail(c, QCD_ERR_ARG, std::string(path) + ": not a weights file of this network (" + want + ")");
+    return qcd_learned_set_weights(c, w.data(), n);
 }
 
 // stage a complex64 [k][V][12] field (host or device) into the internal plane layout

@@ -17,6 +17,13 @@
 // name is only a host-side stand-in for the symbol; the device address is
 // obtained with cudaGetSymbolAddress once per device and passed to the
 // kernels.
+//
+// The array keeps what the last call built: the schedule tables and per-site records of one
+// context's fields, geometry and kernel form (per device).  A call that matches them only
+// converts the input, launches the SAP kernels and converts the output, all asynchronously on
+// the context stream; a call with another context, changed fields, geometry or form first plans
+// on the host, uploads the tables and rebuilds the records, which synchronises the stream.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -37,6 +44,16 @@ static __device__ __align__(256) unsigned char g_sap_scratch[kScratchBytes];
 std::mutex g_scratch_mutex;
 constexpr int kMaxDevices = 64;
 unsigned char *g_scratch_addr[kMaxDevices] = {};
+
+// What the array of each device holds now: the plan (host tables, device pointers into the
+// array) and records made for one context's fields, geometry and kernel form.  A call with the
+// same key reuses them and only launches kernels; any other call rebuilds them.
+struct Held {
+    long uid = 0, field_version = -1;
+    int b[4] = {0, 0, 0, 0}, s[4] = {0, 0, 0, 0}, ctas = 0, sms = 0;
+    SapPlan plan;
+};
+Held g_held[kMaxDevices];
 
 // Device address of g_sap_scratch on the context's device (current when called).
 int scratch_address(qcd_ctx *c, unsigned char **out) {
@@ -84,11 +101,11 @@ extern "C" int qcd_sap_precondition_noalloc(qcd_ctx *c, float *out, const float 
                                         " sites exceeds its fixed scratch limit of 41472 sites");
     if (!on_device(in) || !on_device(out) || ((uintptr_t)in & 15) || ((uintptr_t)out & 15))
         return fail(c, QCD_ERR_ARG, "qcd_sap_precondition_noalloc needs 16-byte aligned device pointers");
-    SapPlan plan;
-    if (sap_plan_host(c, p->block, p->subblock, plan) != QCD_OK)
+    if (p->sap_ctas < -2 || p->sap_ctas > 16) return fail(c, QCD_ERR_ARG, "sap_ctas must lie in -2..16");
+    if (!sap_geometry_ok(c, p->block, p->subblock))
         return fail(c, QCD_ERR_ARG, "SAP geometry: need L % block == 0, L/block even and >= 2, block % subblock == 0");
-    if (sap_table_bytes(plan) > kTableBytes || sap_record_bytes(plan) > kRecordBytes)
-        return fail(c, QCD_ERR_ARG, "SAP schedule tables exceed the fixed scratch");
+    // the kernel form qcd_sap_precondition would use with these params (0: the context's setting)
+    const int ctas = p->sap_ctas != 0 ? p->sap_ctas : c->sap_ctas_user;
     unsigned char *base = nullptr;
     int rc = scratch_address(c, &base);
     if (rc) return rc;
@@ -97,8 +114,38 @@ extern "C" int qcd_sap_precondition_noalloc(qcd_ctx *c, float *out, const float 
     float4 *x = reinterpret_cast<float4 *>(base + kSpinorBytes);
     float4 *work = reinterpret_cast<float4 *>(base + 2 * kSpinorBytes);
     float *rec = reinterpret_cast<float *>(base + 4 * kSpinorBytes);
-    if ((rc = sap_upload_tables(c, plan, base + 4 * kSpinorBytes + kRecordBytes))) return rc;
-    if ((rc = sap_build_records(c, plan, rec))) return rc;
+    Held &h = g_held[c->device];
+    SapPlan plan;  // copied under the lock: another host thread may replace the held one
+    {
+        std::lock_guard<std::mutex> lock(g_scratch_mutex);
+        int sms = c->sms_override;
+        if (sms < 1 && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+            cudaGetLastError();
+            sms = 1;
+        }
+        const bool same = h.uid == c->uid && h.field_version == c->field_version && h.ctas == ctas && h.sms == sms &&
+                          std::equal(p->block, p->block + 4, h.b) && std::equal(p->subblock, p->subblock + 4, h.s);
+        if (!same) {
+            // a new geometry, field or form: plan on the host, upload the tables and build the
+            // records into the array (this path synchronises the stream)
+            h.uid = 0;
+            if (sap_plan_host(c, p->block, p->subblock, plan, ctas, false) != QCD_OK)
+                return fail(c, QCD_ERR_ARG, "SAP block too large for the shared memory of a cluster of 16 CTAs");
+            if (sap_table_bytes(plan) > kTableBytes || sap_record_bytes(plan) > kRecordBytes)
+                return fail(c, QCD_ERR_ARG, "SAP schedule tables exceed the fixed scratch");
+            if ((rc = sap_upload_tables(c, plan, base + 4 * kSpinorBytes + kRecordBytes))) return rc;
+            if ((rc = sap_build_records(c, plan, rec))) return rc;
+            h.plan = plan;
+            h.uid = c->uid;
+            h.field_version = c->field_version;
+            h.ctas = ctas;
+            h.sms = sms;
+            std::memcpy(h.b, p->block, sizeof(h.b));
+            std::memcpy(h.s, p->subblock, sizeof(h.s));
+        } else {
+            plan = h.plan;
+        }
+    }
     if ((rc = spinor32_to_internal(c, v, reinterpret_cast<const float2 *>(in), 1))) return rc;
     if ((rc = sap_apply_plan(c, plan, x, v, work, p->omega, p->nsweep, p->nsap))) return rc;
     if ((rc = spinor32_from_internal(c, reinterpret_cast<float2 *>(out), x, 1))) return rc;

@@ -112,6 +112,7 @@ struct Profiler {
 }  // namespace qcd
 
 struct qcd_ctx {
+    long uid = 0;        // unique per context of the process (never reused)
     int device = 0;
     cudaStream_t stream = nullptr;
     qcd::Lattice lat{};
@@ -234,6 +235,9 @@ int dslash32_dot(qcd_ctx *c, float4 *out, const float4 *in, int nrhs, const floa
 void use_sap_ctas(qcd_ctx *c, int sap_ctas);
 
 // SAP (sap.cu)
+// block decomposition valid for the lattice (L % block == 0, L / block even and >= 2,
+// block % subblock == 0)
+bool sap_geometry_ok(const qcd_ctx *c, const int b[4], const int s[4]);
 // host part of a plan (tables in h_*; device pointers left null); QCD_ERR_ARG on bad geometry
 int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &plan, int min_ctas = 1,
                   bool half = false);

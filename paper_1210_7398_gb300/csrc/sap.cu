@@ -1302,6 +1302,8 @@ void make_flags(SapPlan &np) {
 
 }  // namespace
 
+bool sap_geometry_ok(const qcd_ctx *c, const int b[4], const int s[4]) { return geometry_ok(c, b, s); }
+
 int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &np, int min_ctas, bool half) {
     if (!geometry_ok(c, b, s)) return QCD_ERR_ARG;
     np = SapPlan();

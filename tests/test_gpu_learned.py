@@ -145,3 +145,34 @@ def test_trained_correction_gain_and_fallback():
     r = b.cpu().numpy()[0] - oracle.apply_D(dims, U, F, KAPPA, x.cpu().numpy()[0])
     assert np.linalg.norm(r) / np.linalg.norm(b.cpu().numpy()[0]) <= 1e-10, st
     s.close()
+
+
+def test_weights_file_round_trip(tmp_path):
+    """qcd_learned_save / qcd_learned_load: the weights come back bit for bit (and with them the
+    correction's output); a file for another network is refused."""
+    dims = (4, 4, 4, 4)
+    s, U = setup(dims)
+    with pytest.raises(q.QcdError) as e:
+        q.qcd_learned_save(s.ctx, tmp_path / "none.bin")
+    assert e.value.code == q.QCD_ERR_STATE
+    W = q.learned_init_weights(21, scale_last=1.0)
+    q.qcd_learned_set_weights(s.ctx, W)
+    path = tmp_path / "w.bin"
+    q.qcd_learned_save(s.ctx, path)
+    head = open(path, "rb").readline()
+    assert b'"count": %d' % q.qcd_learned_weight_count() in head
+    s2, _ = setup(dims)
+    q.qcd_learned_load(s2.ctx, path)
+    assert np.array_equal(q.qcd_learned_get_weights(s2.ctx), q.qcd_learned_get_weights(s.ctx))
+    x = qi.gaussian_spinor(dims, seed=22)[0].astype(np.complex64)
+    o1, o2 = np.empty_like(x), np.empty_like(x)
+    q.qcd_learned_apply(s.ctx, o1, x)
+    q.qcd_learned_apply(s2.ctx, o2, x)
+    assert np.array_equal(o1, o2)
+    bad = tmp_path / "bad.bin"
+    bad.write_bytes(open(path, "rb").read()[:-8])  # truncated
+    with pytest.raises(q.QcdError) as e:
+        q.qcd_learned_load(s2.ctx, bad)
+    assert e.value.code == q.QCD_ERR_ARG
+    s.close()
+    s2.close()

@@ -116,3 +116,37 @@ def test_fp32_peak_hook():
     t = q.qcd_bench_fp32_peak(s.ctx, 8)
     assert 10.0 < t < 200.0, t  # GB300: 152 SMs x 128 lanes x 2 flop x about 2 GHz
     s.close()
+
+
+def test_plain_c_client_computes_through_the_abi(tmp_path):
+    """tests/c/abi_compute.c (C99, warnings as errors): D and a full solve on the free field
+    through the C ABI with host buffers, checked against the closed forms in C."""
+    import shutil
+    import subprocess
+    from paper_1210_7398_gb300 import build as qbuild
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    libdir = os.path.dirname(qbuild.LIB)
+    exe = str(tmp_path / "abi_compute")
+    subprocess.check_call([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(root, "include"),
+                           os.path.join(root, "tests", "c", "abi_compute.c"), "-L", libdir, "-lqcd", "-lm",
+                           "-Wl,-rpath," + libdir, "-o", exe])
+    res = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert res.returncode == 0, res.stderr
+    assert res.stdout.strip() == "ok"
+
+
+def test_stats_report_kernel_time_when_profiling():
+    dims, kappa = (8, 8, 8, 8), 0.12
+    s, _ = make_solver(dims, kappa, seed=1013)
+    b = torch.from_numpy(qi.gaussian_spinor(dims, seed=2013)).cuda()
+    prm = q.make_params(kappa, CSW, (4, 4, 4, 4), (2, 2, 2, 2), tol=1e-10)
+    st = s.solve(torch.zeros_like(b), b, prm)
+    assert st["ms_dslash"] == 0 and st["ms_sap"] == 0
+    q.qcd_set_profiling(s.ctx, True)
+    st = s.solve(torch.zeros_like(b), b, prm)
+    q.qcd_set_profiling(s.ctx, False)
+    assert 0 < st["ms_dslash"] < st["ms_total"] and 0 < st["ms_sap"] < st["ms_total"]
+    s.close()

@@ -50,6 +50,38 @@ def test_noalloc_matches_allocating_entry_point_twice(dims, block, sub):
     s.close()
 
 
+@pytest.mark.parametrize("ctas", [0, 2, -2])
+def test_noalloc_kernel_forms_and_no_device_allocation(ctas):
+    """The kernel form follows params.sap_ctas as for the allocating entry point (0: the
+    context's setting); a repeated call reuses what the fixed array holds and leaves the
+    device's free memory unchanged."""
+    dims, kappa = (12, 12, 12, 24), 0.12
+    s = solver(dims, kappa, seed=1002)
+    prm = q.make_params(kappa, CSW, (3, 3, 3, 6), (1, 1, 1, 2), omega=1.0, nsweep=2, nsap=2, sap_ctas=ctas)
+    v = torch.from_numpy(qi.gaussian_spinor(dims, seed=3003)[0].astype(np.complex64)).cuda()
+    ref = torch.empty_like(v)
+    s.sap_precondition(ref, v, prm)
+    out = torch.empty_like(v)
+    q.qcd_sap_precondition_noalloc(s.ctx, out, v, prm)  # first call: builds the tables and records
+    torch.cuda.synchronize()
+    assert rel_norm(out, ref) <= SAP_TOL
+    out2 = torch.empty_like(v)  # allocated before the measured call
+    torch.cuda.synchronize()
+    reserved0 = torch.cuda.memory_reserved()
+    free0, _ = torch.cuda.mem_get_info()
+    q.qcd_sap_precondition_noalloc(s.ctx, out2, v, prm)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_reserved() == reserved0
+    assert torch.equal(out2, out)
+    bad = q.make_params(kappa, CSW, (3, 3, 3, 6), (1, 1, 1, 2), sap_ctas=17)
+    with pytest.raises(q.QcdError) as e:
+        q.qcd_sap_precondition_noalloc(s.ctx, out2, v, bad)
+    assert e.value.code == q.QCD_ERR_ARG
+    s.close()
+
+
 def test_noalloc_rejects_lattices_above_its_limit():
     dims = (16, 16, 16, 16)  # 65,536 sites > 41,472
     s = solver(dims, 0.12, seed=7)
