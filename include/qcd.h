@@ -280,8 +280,9 @@ int qcd_sap_plan_tables(const int dims[4], const int block[4], const int subbloc
  * times complete solves of D x = b from x0 = 0 for candidate SAP set-ups and
  * returns the fastest that converges in *best (block, subblock, sap_storage,
  * sap_ctas, nsweep, nsap; omega from base) and its time in *best_ms.  Stage 1
- * tries block splits (L_mu / block_mu in {2, 4, 6, 8}, spatial directions
- * alike) with sub-blocks block/2, block/3 or block, blocks of about 256 sites
+ * tries block extents (2, 3, 4, 6, 8, 12 or 16, the spatial ones alike, the
+ * time extent one to two times the spatial one, each dividing L with an even
+ * quotient) with sub-blocks block/2, block/3 or block, blocks of about 256 sites
  * first, each with FP16 storage and the tile form (sap_ctas -2; the cluster form
  * where the block does not fit); stage 2 refines the three fastest over the
  * storage (FP32, FP16), the kernel form (sap_ctas -2, 0, 2) and (nsweep, nsap)

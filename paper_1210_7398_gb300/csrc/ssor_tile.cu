@@ -19,9 +19,10 @@
 // reals).  FP32: 672 bytes per site; FP16 storage: 336.  Inside the block a hop that leaves it
 // reads an all-zero spinor slot, so D_BB needs no masks; the same matrices serve the hops
 // between blocks of opposite colour.
-// With FP16 storage the block spinor of each right-hand side is kept in units of the largest
-// |component| of its source on the block (the SSOR iteration is linear), so no rescaling is
-// needed inside the sweep; arithmetic is FP32 throughout.
+// With FP16 storage the block spinor of each right-hand side, and its source, are kept in
+// shared memory in units of the largest |component| of that source on the block (the SSOR
+// iteration is linear), so no rescaling is needed inside the sweep; arithmetic is FP32
+// throughout.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -241,6 +242,8 @@ __global__ void __launch_bounds__(kTileMaxThreads, kTileMinBlocks) k_sap_tile(Ti
     const long n0 = a.origin_site[blk];
     const uint4 *recb = a.rec + (size_t)blk * a.vol * L::chunks;
     float *ys = sm;  // [vol + 1][R][y_words], block-local site order; site vol is the zero slot
+    // FP16 storage: the block's source f in the same units, [vol][R][y_words] after the spinors
+    float *fs = ys + (size_t)(a.vol + 1) * R * L::y_words;
     {
         float4 *y4 = reinterpret_cast<float4 *>(ys);
         const int nz = (a.vol + 1) * R * L::y_chunks;
@@ -331,6 +334,18 @@ __global__ void __launch_bounds__(kTileMaxThreads, kTileMinBlocks) k_sap_tile(Ti
     if constexpr (HALF) {
         my_scale = scale_s[r_me] > 0.f ? scale_s[r_me] : 1.f;
         inv_scale = 1.f / my_scale;
+        // the source of the sweeps into shared memory, in the right-hand side's units: the
+        // sweeps then read no global memory but the records
+        if (me_active)
+            for (int i = tid; i < a.vol * R; i += T) {
+                const int4 pa = __ldg(a.pos + 2 * (i / R));
+                float2 f[12];
+                load_spinor_rw(rr, a.V, pa.x, f);
+#pragma unroll
+                for (int k = 0; k < 12; k++) f[k] = cscale(f[k], inv_scale);
+                st_y<true>(fs + (pa.y * R + r_me) * L::y_words, f);
+            }
+        __syncthreads();
     }
 
     // the in-block hop sum (D_BB without its diagonal) of the block spinor at level position pos,
@@ -368,13 +383,13 @@ __global__ void __launch_bounds__(kTileMaxThreads, kTileMinBlocks) k_sap_tile(Ti
         float2 fa[12];
         block_FH(pos, pa, pb, fa);
         float2 fv[12];
-        load_spinor_rw(rr, a.V, pa.x, fv);
+        if constexpr (HALF) ld_y<true>(fs + (pa.y * R + r_me) * L::y_words, fv);
+        else load_spinor_rw(rr, a.V, pa.x, fv);
         float *yp = ys + (pa.y * R + r_me) * L::y_words;
         float2 yo[12];
         ld_y<HALF>(yp, yo);
 #pragma unroll
         for (int k = 0; k < 12; k++) {
-            if constexpr (HALF) fv[k] = cscale(fv[k], inv_scale);
             const float tx = fmaf(a.kappa, fa[k].x, fv[k].x), ty = fmaf(a.kappa, fa[k].y, fv[k].y);
             yo[k] = make_float2(fmaf(a.omega, tx - yo[k].x, yo[k].x), fmaf(a.omega, ty - yo[k].y, yo[k].y));
         }
@@ -495,8 +510,9 @@ template <bool HALF> constexpr int y_bytes_per_site() { return TileRec<HALF>::y_
 }  // namespace
 
 size_t tile_smem_bytes(int vol, bool half, int R) {
-    // the block spinors of R right-hand sides and the zero slot
-    return (size_t)(vol + 1) * R * (half ? y_bytes_per_site<true>() : y_bytes_per_site<false>());
+    // the block spinors of R right-hand sides and the zero slot; FP16 storage: and the sources
+    return half ? (size_t)(2 * vol + 1) * R * y_bytes_per_site<true>()
+                : (size_t)(vol + 1) * R * y_bytes_per_site<false>();
 }
 
 int tile_build_records(qcd_ctx *c, const SapPlan &p, void *rec) {

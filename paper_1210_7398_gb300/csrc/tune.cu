@@ -190,13 +190,14 @@ extern "C" int qcd_autotune(qcd_ctx *c, const double *b, int nrhs, const qcd_par
 
     // stage 1: block splits and sub-block splits, FP32 storage, base sweeps and cycles
     std::vector<Cand> cands;
-    const int splits[4] = {2, 4, 6, 8};
-    for (int ks : splits)
-        for (int kt : splits) {
-            int blk[4];
-            for (int m = 0; m < 3; m++) blk[m] = c->lat.L[m] % ks ? 0 : c->lat.L[m] / ks;
-            blk[3] = c->lat.L[3] % kt ? 0 : c->lat.L[3] / kt;
-            if (!blk[0] || !blk[1] || !blk[2] || !blk[3]) continue;
+    // block extents: the spatial ones alike, each dividing L with an even quotient
+    const int extents[] = {2, 3, 4, 6, 8, 12, 16};
+    for (int bs : extents)
+        for (int bt : extents) {
+            int blk[4] = {bs, bs, bs, bt};
+            bool fits = true;
+            for (int m = 0; m < 4; m++) fits = fits && c->lat.L[m] % blk[m] == 0 && (c->lat.L[m] / blk[m]) % 2 == 0;
+            if (!fits || bt < bs || bt > 2 * bs) continue;
             const int vol = blk[0] * blk[1] * blk[2] * blk[3];
             if (vol > 4096 || vol < 16) continue;
             for (int div = 2; div <= 4; div++) {

@@ -28,7 +28,7 @@ TILE_CASES = [
     ((8, 4, 4, 8), (4, 2, 2, 4), (2, 1, 2, 2), 1.2, 2, 3, ("f32", "f16")),
     ((8, 8, 8, 8), (4, 4, 4, 4), (2, 2, 2, 2), 1.0, 3, 2, ("f32", "f16")),
     ((12, 12, 12, 24), (6, 6, 6, 6), (3, 3, 3, 3), 1.0, 4, 4, ("f32", "f16")),  # the paper's split
-    ((12, 12, 12, 24), (6, 6, 6, 12), (3, 3, 3, 6), 1.0, 4, 4, ("f16",)),  # FP32 spinor does not fit
+    ((12, 12, 12, 24), (6, 6, 6, 12), (3, 3, 3, 6), 1.0, 4, 4, ("f16",)),  # does not fit: the cluster form stands in
     ((12, 12, 12, 24), (3, 3, 3, 6), (1, 1, 1, 2), 0.9, 2, 2, ("f32", "f16")),
 ]
 
