@@ -32,9 +32,6 @@ HEADLINE = dict(name="48^3x96 kappa 0.122 c_SW 1.6, 12 spin-colour point sources
                 dims=(48, 48, 48, 96), kappa=0.122, csw=1.6, eps=0.3, gauge_seed=1004, sources=12, rhs_group=4,
                 tol=1e-10, inner_tol=1e-5,
                 plain=dict(block=(6, 6, 6, 12), subblock=(3, 3, 3, 6), omega=1.0, nsweep=4, nsap=4))
-# the autotuner runs on a 16 times smaller lattice of the same family (same kappa, c_SW, link
-# roughness), and its winner is applied to the headline lattice
-TUNE = dict(dims=(24, 24, 24, 48), gauge_seed=1003, sources=4, candidates=40)
 # extra line items: the 12^3 x 24 workload (plain = its literal set-up) and the D bandwidths
 SMALL = dict(dims=(12, 12, 12, 24), kappa=0.12, csw=1.6, eps=0.3, gauge_seed=1001, source_seed=2001,
              block=(6, 6, 6, 12), subblock=(3, 3, 3, 6), omega=1.0, nsweep=4, nsap=4, tol=1e-10, inner_tol=1e-5)
@@ -319,37 +316,51 @@ def host_bytes_available():
         return 0
 
 
-def tune_chosen(q, qi, torch, stream, args):
-    """The chosen set-up: qcd_autotune on the 24^3 x 48 lattice of the same family (kappa 0.122,
-    four point sources), its solutions checked under the oracle's D."""
+def tune_chosen(q, sv, b, args):
+    """The chosen set-up: qcd_autotune on the headline lattice itself, timing full solves of the
+    first right-hand-side group of point sources."""
     w = HEADLINE
-    dims = TUNE["dims"]
-    U = qi.gauge_field(dims, w["eps"], seed=TUNE["gauge_seed"], device="cuda")
+    p = w["plain"]
+    base = q.make_params(w["kappa"], w["csw"], p["block"], p["subblock"], omega=p["omega"], nsweep=p["nsweep"],
+                         nsap=p["nsap"], tol=w["tol"], inner_tol=w["inner_tol"], rhs_group=w["rhs_group"])
+    g = w["rhs_group"]
+    t0 = time.perf_counter()
+    best, best_ms = q.qcd_autotune(sv.ctx, b[:g], base, nrhs=g, max_candidates=args.tune_candidates)
+    return best, {"lattice": "x".join(map(str, w["dims"])), "sources": g, "seconds": time.perf_counter() - t0,
+                  "candidates": args.tune_candidates, "best_ms": best_ms, "params": q.params_dict(best)}
+
+
+def sources24_section(q, qi, torch, stream, chosen, args):
+    """The 12 spin-colour point sources on 24^3 x 48 (kappa 0.120, the batched configuration's
+    main instance) in one batched solve with the chosen set-up (retuned there if its blocks do
+    not divide the lattice), every solution checked under the oracle's D."""
+    w = HEADLINE
+    dims, kappa = (24, 24, 24, 48), 0.120
+    U = qi.gauge_field(dims, w["eps"], seed=1002, device="cuda")
     torch.cuda.synchronize()
     sv = q.Solver(dims, stream=stream.cuda_stream)
     sv.load_gauge(U)
-    sv.build_clover(w["kappa"], w["csw"])
-    b = point_sources_torch(torch, dims, 0, TUNE["sources"])
-    p = w["plain"]
-    base = q.make_params(w["kappa"], w["csw"], p["block"], p["subblock"], omega=p["omega"], nsweep=p["nsweep"],
-                         nsap=p["nsap"], tol=w["tol"], inner_tol=w["inner_tol"])
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    best, best_ms = q.qcd_autotune(sv.ctx, b, base, nrhs=TUNE["sources"], max_candidates=args.tune_candidates)
-    t_tune = time.perf_counter() - t0
+    sv.build_clover(kappa, w["csw"])
+    b = point_sources_torch(torch, dims, 0, 12)
     x = torch.zeros_like(b)
-    st = sv.solve(x, b, best, nrhs=TUNE["sources"])
-    info = {"lattice": "x".join(map(str, dims)), "sources": TUNE["sources"], "seconds": t_tune,
-            "candidates": args.tune_candidates, "best_ms": best_ms, "params": q.params_dict(best),
-            "outer_iters": st["outer_iters"], "inner_iters": st["inner_iters"],
-            "true_rel_res_library": st["true_rel_res"]}
+    p = q.make_params(kappa, w["csw"], tuple(chosen.block), tuple(chosen.subblock), omega=chosen.omega,
+                      nsweep=chosen.nsweep, nsap=chosen.nsap, tol=w["tol"], inner_tol=w["inner_tol"],
+                      sap_storage=chosen.sap_storage, sap_ctas=chosen.sap_ctas)
+    fits = all(L % bl == 0 and (L // bl) % 2 == 0 for L, bl in zip(dims, chosen.block))
+    if not fits:
+        p, _ = q.qcd_autotune(sv.ctx, b[:4], p, nrhs=4, max_candidates=args.tune_candidates)
+    sv.solve(x, b, p, nrhs=12)  # plan, records, graph
+    x.zero_()
+    ms, st = event_ms(torch, stream, lambda: sv.solve(x, b, p, nrhs=12))
+    out = {"lattice": "24x24x24x48", "kappa": kappa, "sources": 12, "seconds": ms / 1000.0,
+           "params": q.params_dict(p), "outer_iters": st["outer_iters"], "inner_iters": st["inner_iters"],
+           "true_rel_res_library": st["true_rel_res"]}
     if not args.skip_cpu:
-        info["true_rel_res_oracle"] = oracle_true_residuals(dims, U, w["kappa"], w["csw"], x, b)
+        out["true_rel_res_oracle"] = oracle_true_residuals(dims, U, kappa, w["csw"], x, b)
     sv.close()
     del U, b, x
     torch.cuda.empty_cache()
-    return best, info
-
+    return out
 
 # ---- optional sections (flags) ----
 
@@ -633,9 +644,6 @@ def run_gpu_on_stream(args, q, qi, torch, stream, rank, world, local):
     dims = w["dims"]
     V = volume(dims)
     nsrc = w["sources"]
-    # ---- the chosen set-up, tuned on the smaller lattice of the same family ----
-    chosen, tune_info = tune_chosen(q, qi, torch, stream, args)
-    plain_p, chosen_p = headline_params(q, chosen)
     # ---- the headline lattice: links made on the device by the same generator ----
     U = qi.gauge_field(dims, w["eps"], seed=w["gauge_seed"], device="cuda")
     torch.cuda.synchronize()
@@ -650,6 +658,9 @@ def run_gpu_on_stream(args, q, qi, torch, stream, rank, world, local):
     fp32 = q.qcd_bench_fp32_peak(sv.ctx, 64)
     peaks["fp32_tflops"], peaks["fp32_source"] = fp32, "measured: FP32 FMA kernel (qcd_bench_fp32_peak) in this run"
     b = point_sources_torch(torch, dims, 0, nsrc)
+    # ---- the chosen set-up, tuned on one group of the headline's sources ----
+    chosen, tune_info = tune_chosen(q, sv, b, args)
+    plain_p, chosen_p = headline_params(q, chosen)
     x = torch.zeros_like(b)
 
     def solve(p):
@@ -777,6 +788,7 @@ def run_gpu_on_stream(args, q, qi, torch, stream, rank, world, local):
                               "frac_nominal_8TBs": d["frac_nominal_8TBs"], "ms": d["ms"],
                               "model": "768 B/site: in 96 + out 96 + links 288 + clover 288"}
     small = None if args.skip_small else small_section(q, qi, torch, stream, args)
+    src24 = None if args.skip_small else sources24_section(q, qi, torch, stream, chosen_p, args)
     cpu = None
     if world == 1 and not args.skip_cpu:
         try:
@@ -827,7 +839,8 @@ def run_gpu_on_stream(args, q, qi, torch, stream, rank, world, local):
                      "wall_s_timed_region": wall},
            "oracle_check": oracle_check, "tuning": tune_info,
            "e2e": e2e, "gpu_launches": launches, "kernels": kstats, "clocks": clk, "roofline": roof,
-           "fp32_peak_tflops": fp32, "dslash": dsl, "cpu_baseline": cpu, "small_12x12x12x24": small}
+           "fp32_peak_tflops": fp32, "dslash": dsl, "cpu_baseline": cpu, "small_12x12x12x24": small,
+           "point_sources_24x24x24x48": src24}
     if learned is not None:
         out["learned_24x24x24x48"] = learned
     if batched is not None:
@@ -843,7 +856,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--plain-steps", type=int, default=2, help="timed solves of the plain set-up")
     ap.add_argument("--e2e-steps", type=int, default=2, help="timed solves through host buffers")
-    ap.add_argument("--tune-candidates", type=int, default=40, help="solves the autotuner may time")
+    ap.add_argument("--tune-candidates", type=int, default=16, help="solves the autotuner may time")
     ap.add_argument("--skip-dslash", action="store_true", help="skip the D bandwidth measurement")
     ap.add_argument("--skip-cpu", action="store_true", help="skip the CPU oracle legs (baseline and checks)")
     ap.add_argument("--skip-small", action="store_true", help="skip the 12^3 x 24 extras")

@@ -286,7 +286,8 @@ int qcd_sap_plan_tables(const int dims[4], const int block[4], const int subbloc
  * first, each with FP16 storage and the tile form (sap_ctas -2; the cluster form
  * where the block does not fit); stage 2 refines the three fastest over the
  * storage (FP32, FP16), the kernel form (sap_ctas -2, 0, 2) and (nsweep, nsap)
- * in {2, 4} x {2, 4}.  At most max_candidates solves are timed (<= 0: 64).
+ * in {2, 4} x {2, 4}.  At most max_candidates solves are timed (<= 0: 64), at
+ * most half of them in stage 1.
  * Stage 3 (nrhs > 1 and base->rhs_group = 0) then times the winner with
  * right-hand sides in groups of 1, 2, 4 or 8 dividing nrhs, as well as all at
  * once, and keeps the fastest rhs_group.

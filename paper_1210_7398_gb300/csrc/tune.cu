@@ -244,15 +244,20 @@ extern "C" int qcd_autotune(qcd_ctx *c, const double *b, int nrhs, const qcd_par
         cd.ms = ok ? ms : 1e300;
         return QCD_OK;
     };
-    for (auto &cd : cands)
+    // stage 1 takes at most half the budget, so that stage 2 can refine
+    const int stage1 = std::max(1, (max_candidates + 1) / 2);
+    for (auto &cd : cands) {
+        if (tried >= stage1) break;
         if ((rc = run(cd))) break;
+    }
     if (!rc) {
         std::sort(cands.begin(), cands.end(), [](const Cand &u, const Cand &v) { return u.ms < v.ms; });
-        // stage 2: refine the three fastest
+        // stage 2: refine the three fastest, the likeliest variants first (FP16 tile form with other
+        // sweep and cycle counts, then the other forms and storage)
         std::vector<Cand> more;
         for (size_t i = 0; i < cands.size() && i < 3; i++) {
             if (!cands[i].ok) continue;
-            for (int storage : {QCD_F32, QCD_F16})
+            for (int storage : {QCD_F16, QCD_F32})
                 for (int ctas : {-2, 0, 2})
                     for (int ns : {2, 4})
                         for (int np : {2, 4}) {
