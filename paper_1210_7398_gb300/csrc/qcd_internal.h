@@ -71,9 +71,10 @@ struct SapPlan {
     int *d_own_off = nullptr;
     int *d_pos = nullptr;
     int *d_origin_site[2] = {nullptr, nullptr};
-    std::vector<int4> h_tile_pos;   // tile form: [vol][2] per level position (offset, site, neighbours)
+    std::vector<int4> h_tile_pos;   // tile form: [vol][2] per level position (offset, slots, site)
     int4 *d_tile_pos = nullptr;
     int *d_lev_ptr = nullptr;       // tile form: [nsteps + 1] level boundaries (h_step_ptr)
+    int tile_zslots = 1;            // tile form: zero slots after the vol site slots
     float *d_rec = nullptr;         // per-site records (links, clover, neighbour codes), V x 912 bytes
     long rec_version = -1;          // field version the records were built from
 };
@@ -278,7 +279,16 @@ constexpr size_t kTileSmemLimit = 200 * 1024;
 constexpr size_t kTileSmemPerSm = 228 * 1024;
 constexpr int kTileRecordBytes = 672;
 constexpr int kTileRecordBytesHalf = 336;
-size_t tile_smem_bytes(int vol, bool half, int R);
+// zero slots of the tile form (one per bank class that an out-of-block hop may need)
+constexpr int kTileZeroSlotsHalf = 4;
+constexpr int kTileZeroSlots = 2;
+// shared memory of a tile CTA with R right-hand sides
+size_t tile_smem_bytes(const SapPlan &p, int R);
+// tile form: h_tile_pos from the level schedule, the positions of a level ordered against
+// shared-memory bank conflicts (needs h_step_site, h_step_ptr, h_site_off, b, vol, half)
+void tile_make_positions(SapPlan &p);
+// the host check of h_tile_pos that the tile kernel relies on for in-bounds shared memory
+bool tile_positions_valid(const SapPlan &p);
 int tile_build_records(qcd_ctx *c, const SapPlan &p, void *rec);
 int tile_set_attributes(qcd_ctx *c);
 // right-hand sides per CTA, threads per CTA and shared memory of a tile launch for nrhs right-hand sides

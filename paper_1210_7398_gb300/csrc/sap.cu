@@ -1384,28 +1384,20 @@ int sap_plan_host(const qcd_ctx *c, const int b[4], const int s[4], SapPlan &np,
     }
     // the right-hand-side tiled thread form on request (min_ctas == -2), the block spinor of
     // one right-hand side in one CTA
-    if (min_ctas == -2 && tile_smem_bytes(np.vol, half, 1) <= kTileSmemLimit) {
+    if (min_ctas == -2) {
         make_chunks(np, 1, 1 << 20, false);  // one chunk per level, in level order (diagnostics)
-        np.tile = true;
-        np.nwarps = 0;
-        np.smem_bytes = tile_smem_bytes(np.vol, half, 1);
-        make_flags(np);
-        // per level position: global offset, block-local site and its 8 in-block neighbours
-        // (d = 2 mu + backward; the zero slot vol where the hop leaves the block)
-        np.h_tile_pos.assign(2 * (size_t)np.vol, make_int4(0, 0, 0, 0));
-        for (int k = 0; k < np.vol; k++) {
-            const int yl = np.h_step_site[k];
-            int y[4], r = yl, nbk[8], stride = 1;
-            for (int m = 0; m < 4; m++) { y[m] = r % b[m]; r /= b[m]; }
-            for (int m = 0; m < 4; m++) {
-                nbk[2 * m] = y[m] + 1 < b[m] ? yl + stride : np.vol;
-                nbk[2 * m + 1] = y[m] > 0 ? yl - stride : np.vol;
-                stride *= b[m];
+        if (np.vol + kTileZeroSlotsHalf < (1 << 16)) {  // slots are 16-bit
+            tile_make_positions(np);
+            if (tile_positions_valid(np) && tile_smem_bytes(np, 1) <= kTileSmemLimit) {
+                np.tile = true;
+                np.nwarps = 0;
+                np.smem_bytes = tile_smem_bytes(np, 1);
+                make_flags(np);
+                return QCD_OK;
             }
-            np.h_tile_pos[2 * k] = make_int4(np.h_site_off[yl], yl, nbk[0] | (nbk[1] << 16), nbk[2] | (nbk[3] << 16));
-            np.h_tile_pos[2 * k + 1] = make_int4(nbk[4] | (nbk[5] << 16), nbk[6] | (nbk[7] << 16), 0, 0);
         }
-        return np.vol < (1 << 16) - 1 ? QCD_OK : QCD_ERR_ARG;
+        // the block spinor does not fit one CTA: the cluster form stands in
+        np.h_tile_pos.clear();
     }
     // the thread form on request (min_ctas = -1), FP32 storage, the block spinor in one CTA
     if (min_ctas == -1 && !half) {

@@ -206,6 +206,8 @@ struct TileArgs {
     long V;
     int L[4], bc_t;
     int vol, nlev, nsweep, nrhs;
+    int stride;                // 4-byte words per site in shared memory (the R spinors)
+    int zslots;                // zero slots after the vol site slots (out-of-block hops read them)
     int first;                 // first SAP cycle: the residual starts as v, x as y
     int cross;                 // add the hops from the other colour's last block solutions first
     int store_r;               // the residual is needed by a later cycle
@@ -241,12 +243,14 @@ __global__ void __launch_bounds__(kTileMaxThreads, kTileMinBlocks) k_sap_tile(Ti
     if (!any) return;  // uniform over the CTA
     const long n0 = a.origin_site[blk];
     const uint4 *recb = a.rec + (size_t)blk * a.vol * L::chunks;
-    float *ys = sm;  // [vol + 1][R][y_words], block-local site order; site vol is the zero slot
-    // FP16 storage: the block's source f in the same units, [vol][R][y_words] after the spinors
-    float *fs = ys + (size_t)(a.vol + 1) * R * L::y_words;
+    // [vol + zslots][R spinors]: a site's slot (pa.y) is a permutation of the block-local sites
+    // chosen against bank conflicts; slots vol ... vol + zslots - 1 stay zero
+    float *ys = sm;
+    // FP16 storage: the block's source f in the same units and slots after the spinors
+    float *fs = ys + (size_t)(a.vol + a.zslots) * a.stride;
     {
         float4 *y4 = reinterpret_cast<float4 *>(ys);
-        const int nz = (a.vol + 1) * R * L::y_chunks;
+        const int nz = (a.vol + a.zslots) * a.stride / 4;
         for (int i = tid; i < nz; i += T) y4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     const int r_me = tid % R;  // every item this thread takes has right-hand side r_me (T % R == 0)
@@ -267,8 +271,8 @@ __global__ void __launch_bounds__(kTileMaxThreads, kTileMinBlocks) k_sap_tile(Ti
             if (a.cross) {
                 const int nb[8] = {pa.z & 0xffff, pa.z >> 16, pa.w & 0xffff, pa.w >> 16,
                                    pb.x & 0xffff, pb.x >> 16, pb.y & 0xffff, pb.y >> 16};
-                if (nb[0] == a.vol || nb[1] == a.vol || nb[2] == a.vol || nb[3] == a.vol || nb[4] == a.vol ||
-                    nb[5] == a.vol || nb[6] == a.vol || nb[7] == a.vol) {
+                if (nb[0] >= a.vol || nb[1] >= a.vol || nb[2] >= a.vol || nb[3] >= a.vol || nb[4] >= a.vol ||
+                    nb[5] >= a.vol || nb[6] >= a.vol || nb[7] >= a.vol) {
                     // the offset from the block origin, sum_mu y_mu st_mu with 0 <= y_mu < L_mu, gives
                     // the block-local coordinates y_mu
                     const long st[4] = {1, a.L[0], (long)a.L[0] * a.L[1], (long)a.L[0] * a.L[1] * a.L[2]};
@@ -284,7 +288,7 @@ __global__ void __launch_bounds__(kTileMaxThreads, kTileMinBlocks) k_sap_tile(Ti
 #pragma unroll
                     for (int k = 0; k < 12; k++) acc[k] = make_float2(0.f, 0.f);
 #define QCD_TILE_CROSS(MU)                                                                          \
-                    if (nb[2 * MU] == a.vol) {                                                       \
+                    if (nb[2 * MU] >= a.vol) {                                                       \
                         float2 W[9], psi[12];                                                        \
                         ld_link<HALF, 2 * MU>(rec, W);                                               \
                         const bool wrap = xg[MU] == a.L[MU] - 1;                                     \
@@ -292,7 +296,7 @@ __global__ void __launch_bounds__(kTileMaxThreads, kTileMinBlocks) k_sap_tile(Ti
                         load_spinor(yr, a.V, mm, psi);                                               \
                         hop_term_w<MU, true>(psi, W, acc, (MU == 3 && wrap) ? (float)a.bc_t : 1.f);  \
                     }                                                                                \
-                    if (nb[2 * MU + 1] == a.vol) {                                                   \
+                    if (nb[2 * MU + 1] >= a.vol) {                                                   \
                         float2 W[9], psi[12];                                                        \
                         ld_link<HALF, 2 * MU + 1>(rec, W);                                           \
                         const bool wrap = xg[MU] == 0;                                               \
@@ -343,7 +347,7 @@ __global__ void __launch_bounds__(kTileMaxThreads, kTileMinBlocks) k_sap_tile(Ti
                 load_spinor_rw(rr, a.V, pa.x, f);
 #pragma unroll
                 for (int k = 0; k < 12; k++) f[k] = cscale(f[k], inv_scale);
-                st_y<true>(fs + (pa.y * R + r_me) * L::y_words, f);
+                st_y<true>(fs + pa.y * a.stride + r_me * L::y_words, f);
             }
         __syncthreads();
     }
@@ -357,12 +361,12 @@ __global__ void __launch_bounds__(kTileMaxThreads, kTileMinBlocks) k_sap_tile(Ti
         float2 acc[12];
 #pragma unroll
         for (int k = 0; k < 12; k++) acc[k] = make_float2(0.f, 0.f);
-        // a direction leaving the block reads the zero slot, so it adds nothing
+        // a direction leaving the block reads a zero slot, so it adds nothing
 #define QCD_TILE_HOP(D)                                                                   \
         {                                                                                 \
             float2 W[9], psi[12];                                                         \
             ld_link<HALF, D>(rec, W);                                                     \
-            ld_y<HALF>(ys + (nb[D] * R + r_me) * L::y_words, psi);                        \
+            ld_y<HALF>(ys + nb[D] * a.stride + r_me * L::y_words, psi);                   \
             hop_term_w<D / 2, (D & 1) == 0>(psi, W, acc);                                 \
         }
         QCD_TILE_HOP(0)
@@ -383,9 +387,9 @@ __global__ void __launch_bounds__(kTileMaxThreads, kTileMinBlocks) k_sap_tile(Ti
         float2 fa[12];
         block_FH(pos, pa, pb, fa);
         float2 fv[12];
-        if constexpr (HALF) ld_y<true>(fs + (pa.y * R + r_me) * L::y_words, fv);
+        if constexpr (HALF) ld_y<true>(fs + pa.y * a.stride + r_me * L::y_words, fv);
         else load_spinor_rw(rr, a.V, pa.x, fv);
-        float *yp = ys + (pa.y * R + r_me) * L::y_words;
+        float *yp = ys + pa.y * a.stride + r_me * L::y_words;
         float2 yo[12];
         ld_y<HALF>(yp, yo);
 #pragma unroll
@@ -431,7 +435,7 @@ __global__ void __launch_bounds__(kTileMaxThreads, kTileMinBlocks) k_sap_tile(Ti
                     }
                 }
                 float2 yv[12];
-                ld_y<HALF>(ys + (pa.y * R + r_me) * L::y_words, yv);
+                ld_y<HALF>(ys + pa.y * a.stride + r_me * L::y_words, yv);
 #pragma unroll
                 for (int k = 0; k < 12; k++) {
                     if constexpr (HALF) yv[k] = cscale(yv[k], my_scale);
@@ -440,7 +444,7 @@ __global__ void __launch_bounds__(kTileMaxThreads, kTileMinBlocks) k_sap_tile(Ti
                 store_spinor(rr, a.V, pa.x, f);
             }
             float2 yv[12];
-            ld_y<HALF>(ys + (pa.y * R + r_me) * L::y_words, yv);
+            ld_y<HALF>(ys + pa.y * a.stride + r_me * L::y_words, yv);
             if constexpr (HALF) {
 #pragma unroll
                 for (int k = 0; k < 12; k++) yv[k] = cscale(yv[k], my_scale);
@@ -470,7 +474,7 @@ __global__ void k_tile_records(uint4 *__restrict__ rec, const float2 *__restrict
     const int gb = (int)(i / vol), p = (int)(i % vol);
     const int *o = gb < nblk0 ? org0 + 4 * gb : org1 + 4 * (gb - nblk0);
     const int b[4] = {bdim.x, bdim.y, bdim.z, bdim.w};
-    int y[4], r = __ldg(pos + 2 * p).y;
+    int y[4], r = __ldg(pos + 2 * p + 1).z;  // the block-local site of the position
     for (int m = 0; m < 4; m++) { y[m] = r % b[m]; r /= b[m]; }
     const long gs[4] = {1, g.L[0], (long)g.L[0] * g.L[1], (long)g.L[0] * g.L[1] * g.L[2]};
     long n = 0;
@@ -509,10 +513,189 @@ template <bool HALF> constexpr int y_bytes_per_site() { return TileRec<HALF>::y_
 
 }  // namespace
 
-size_t tile_smem_bytes(int vol, bool half, int R) {
-    // the block spinors of R right-hand sides and the zero slot; FP16 storage: and the sources
-    return half ? (size_t)(2 * vol + 1) * R * y_bytes_per_site<true>()
-                : (size_t)(vol + 1) * R * y_bytes_per_site<false>();
+size_t tile_smem_bytes(const SapPlan &p, int R) {
+    // the block spinors of R right-hand sides and the zero slots; FP16 storage: and the sources
+    return p.half ? (size_t)(2 * p.vol + p.tile_zslots) * R * y_bytes_per_site<true>()
+                  : (size_t)(p.vol + p.tile_zslots) * R * y_bytes_per_site<false>();
+}
+
+namespace {
+
+// Shared-memory wavefronts of the kernel's 16-byte spinor loads with R right-hand sides, for
+// the positions and slots in p.h_tile_pos.  The loads of a warp go in four phases of eight
+// consecutive lanes, and the lanes of a level take its (position, right-hand side) items in
+// order, so a phase is eight consecutive items of one level; its wavefronts are the most
+// distinct 16-byte addresses that fall on one group of four banks.  Counted for the 8
+// neighbour reads and the site's own read.
+long tile_bank_cost(const SapPlan &p, int R) {
+    const int yw = p.half ? TileRec<true>::y_words : TileRec<false>::y_words, S = R * yw;
+    long cost = 0;
+    for (int l = 0; l < p.nsteps; l++) {
+        const int p0 = p.h_step_ptr[l], n = (p.h_step_ptr[l + 1] - p0) * R;
+        for (int i0 = 0; i0 < n; i0 += 8)
+            for (int pat = 0; pat < 9; pat++) {
+                int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0}, addr[8], na = 0;
+                for (int i = i0; i < n && i < i0 + 8; i++) {
+                    const int pos = p0 + i / R, r = i % R;
+                    const int4 pa = p.h_tile_pos[2 * pos], pb = p.h_tile_pos[2 * pos + 1];
+                    const int nb[9] = {pa.z & 0xffff, pa.z >> 16, pa.w & 0xffff, pa.w >> 16,
+                                       pb.x & 0xffff, pb.x >> 16, pb.y & 0xffff, pb.y >> 16, pa.y};
+                    const int a = nb[pat] * S + r * yw;
+                    bool seen = false;
+                    for (int k = 0; k < na; k++) seen = seen || addr[k] == a;
+                    if (!seen) {
+                        addr[na++] = a;
+                        cnt[(a / 4) % 8]++;
+                    }
+                }
+                cost += *std::max_element(cnt, cnt + 8);
+            }
+    }
+    return cost;
+}
+
+// One arrangement of the tile positions: the order of the sites within each level, the slot of
+// every site, and the residue (mod 8) that the zero slot of each out-of-block hop should have.
+struct TileLayout {
+    std::vector<int> order, slot;
+    std::vector<int> zres;  // [vol][8]
+};
+
+// p.h_tile_pos from a layout: per position (offset, slot, neighbour slots d = 0..3) and
+// (neighbour slots d = 4..7, site, 0), d = 2 mu + backward; an out-of-block hop reads the zero
+// slot vol + k, 0 <= k < zslots, with vol + k = zres mod zslots.
+void tile_fill_positions(SapPlan &p, const TileLayout &t) {
+    const int Z = p.tile_zslots;
+    p.h_tile_pos.assign(2 * (size_t)p.vol, make_int4(0, 0, 0, 0));
+    for (int k = 0; k < p.vol; k++) {
+        const int yl = t.order[k];
+        int y[4], r = yl, nbk[8], stride = 1;
+        for (int m = 0; m < 4; m++) { y[m] = r % p.b[m]; r /= p.b[m]; }
+        for (int m = 0; m < 4; m++) {
+            const int zf = p.vol + (((t.zres[8 * yl + 2 * m] - p.vol) % Z) + Z) % Z;
+            const int zb = p.vol + (((t.zres[8 * yl + 2 * m + 1] - p.vol) % Z) + Z) % Z;
+            nbk[2 * m] = y[m] + 1 < p.b[m] ? t.slot[yl + stride] : zf;
+            nbk[2 * m + 1] = y[m] > 0 ? t.slot[yl - stride] : zb;
+            stride *= p.b[m];
+        }
+        p.h_tile_pos[2 * k] = make_int4(p.h_site_off[yl], t.slot[yl], nbk[0] | (nbk[1] << 16), nbk[2] | (nbk[3] << 16));
+        p.h_tile_pos[2 * k + 1] = make_int4(nbk[4] | (nbk[5] << 16), nbk[6] | (nbk[7] << 16), yl, 0);
+    }
+}
+
+}  // namespace
+
+// The tile kernel reads, for the lanes of a phase (consecutive positions of one level), the
+// slots of their sites and of the same neighbour of each.  A spinor of slot q starts at bank
+// group (q R y_words / 4 + 3 r) mod 8 for right-hand side r, which with the FP16 spinor
+// (12 words) depends on q mod 2 for R = 4, q mod 4 for R = 2 and q mod 8 for R = 1: the reads of
+// a phase are free of conflicts when its positions' slots, and their neighbours' slots, fall in
+// distinct classes.  Two layouts are weighed by the simulated wavefronts:
+//  - the ll order itself, slot = block-local site;
+//  - by sub-block class: with Y the sub-block coordinate and z the site's place in its
+//    sub-block, a site's class is g = (Y_0 + 2 Y_1 + 4 Y_2) mod 8 and its slot is 8 times its
+//    rank among the sites of its class plus g (when the classes are equally large).  The sites
+//    of a level are taken by z, and within one z round-robin over the classes.  Sites of equal
+//    z hop alike: within their sub-blocks (class kept) or into the next (class shifted by the
+//    same 1, 2, 4 or 0), so the neighbour reads of a phase stay in distinct classes too, and an
+//    out-of-block hop reads the zero slot of the class it would have reached.
+// The order of the sites within a level is free: no site of a level depends on another of it.
+void tile_make_positions(SapPlan &p) {
+    const int vol = p.vol;
+    p.tile_zslots = p.half ? kTileZeroSlotsHalf : kTileZeroSlots;
+    int st[4];
+    st[0] = 1;
+    for (int m = 1; m < 4; m++) st[m] = st[m - 1] * p.b[m - 1];
+    TileLayout ll;
+    ll.order.assign(p.h_step_site.begin(), p.h_step_site.end());
+    ll.slot.resize(vol);
+    ll.zres.resize(8 * (size_t)vol);
+    for (int yl = 0; yl < vol; yl++) {
+        ll.slot[yl] = yl;
+        for (int m = 0; m < 4; m++) {
+            ll.zres[8 * yl + 2 * m] = yl + st[m];  // the slot the hop would reach if the block went on
+            ll.zres[8 * yl + 2 * m + 1] = yl - st[m];
+        }
+    }
+    tile_fill_positions(p, ll);
+    const long cost_ll = tile_bank_cost(p, 1) + tile_bank_cost(p, 2) + tile_bank_cost(p, 4) + tile_bank_cost(p, 8);
+
+    const int coef[4] = {1, 2, 4, 0};
+    TileLayout sb;
+    std::vector<int> cls(vol), zpos(vol);
+    int count[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int yl = 0; yl < vol; yl++) {
+        int y[4], r = yl, g = 0, z = 0, zs = 1;
+        for (int m = 0; m < 4; m++) { y[m] = r % p.b[m]; r /= p.b[m]; }
+        for (int m = 0; m < 4; m++) {
+            g += coef[m] * (y[m] / p.s[m]);
+            z += zs * (y[m] % p.s[m]);
+            zs *= p.s[m];
+        }
+        cls[yl] = g & 7;
+        zpos[yl] = z;
+        count[cls[yl]]++;
+    }
+    bool balanced = vol % 8 == 0;
+    for (int k = 0; k < 8; k++) balanced = balanced && count[k] == vol / 8;
+    if (!balanced) return;  // the ll layout stands
+    sb.slot.resize(vol);
+    sb.zres.resize(8 * (size_t)vol);
+    int rank[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int yl = 0; yl < vol; yl++) {
+        sb.slot[yl] = 8 * rank[cls[yl]]++ + cls[yl];
+        for (int m = 0; m < 4; m++) {
+            sb.zres[8 * yl + 2 * m] = cls[yl] + coef[m];
+            sb.zres[8 * yl + 2 * m + 1] = cls[yl] - coef[m];
+        }
+    }
+    sb.order.reserve(vol);
+    for (int l = 0; l < p.nsteps; l++) {
+        // the level's sites grouped by z (groups in order of first appearance), each group
+        // round-robin over the classes
+        std::vector<int> zorder;
+        std::vector<std::vector<int>> groups;
+        for (int k = p.h_step_ptr[l]; k < p.h_step_ptr[l + 1]; k++) {
+            const int yl = ll.order[k];
+            size_t gi = std::find(zorder.begin(), zorder.end(), zpos[yl]) - zorder.begin();
+            if (gi == zorder.size()) {
+                zorder.push_back(zpos[yl]);
+                groups.emplace_back();
+            }
+            groups[gi].push_back(yl);
+        }
+        for (const auto &grp : groups) {
+            std::vector<int> byc[8];
+            for (int yl : grp) byc[cls[yl]].push_back(yl);
+            size_t taken[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (size_t n = 0; n < grp.size();)
+                for (int c = 0; c < 8; c++)
+                    if (taken[c] < byc[c].size()) {
+                        sb.order.push_back(byc[c][taken[c]++]);
+                        n++;
+                    }
+        }
+    }
+    tile_fill_positions(p, sb);
+    const long cost_sb = tile_bank_cost(p, 1) + tile_bank_cost(p, 2) + tile_bank_cost(p, 4) + tile_bank_cost(p, 8);
+    if (cost_ll <= cost_sb) tile_fill_positions(p, ll);
+}
+
+bool tile_positions_valid(const SapPlan &p) {
+    // every site once, slots a permutation of 0 .. vol - 1, every neighbour slot below vol + zslots
+    if (p.h_tile_pos.size() != 2 * (size_t)p.vol || p.tile_zslots < 1) return false;
+    std::vector<char> site(p.vol, 0), slot(p.vol, 0);
+    for (int k = 0; k < p.vol; k++) {
+        const int4 pa = p.h_tile_pos[2 * k], pb = p.h_tile_pos[2 * k + 1];
+        if (pb.z < 0 || pb.z >= p.vol || site[pb.z] || pa.y < 0 || pa.y >= p.vol || slot[pa.y]) return false;
+        site[pb.z] = slot[pa.y] = 1;
+        if (pa.x != p.h_site_off[pb.z]) return false;
+        const int nb[8] = {pa.z & 0xffff, pa.z >> 16, pa.w & 0xffff, pa.w >> 16,
+                           pb.x & 0xffff, pb.x >> 16, pb.y & 0xffff, pb.y >> 16};
+        for (int d = 0; d < 8; d++)
+            if (nb[d] < 0 || nb[d] >= p.vol + p.tile_zslots) return false;
+    }
+    return true;
 }
 
 int tile_build_records(qcd_ctx *c, const SapPlan &p, void *rec) {
@@ -548,13 +731,13 @@ int tile_choose(const SapPlan &p, int nrhs, int *R, int *threads, size_t *smem) 
     // memory otherwise
     const size_t share = kTileSmemPerSm / kTileMinBlocks - 1024;
     int r = 1;
-    while (r * 2 <= kTileMaxRhs && r * 2 <= nrhs && tile_smem_bytes(p.vol, p.half, r * 2) <= share) r *= 2;
-    if (tile_smem_bytes(p.vol, p.half, r) > kTileSmemLimit) return QCD_ERR_ARG;
+    while (r * 2 <= kTileMaxRhs && r * 2 <= nrhs && tile_smem_bytes(p, r * 2) <= share) r *= 2;
+    if (tile_smem_bytes(p, r) > kTileSmemLimit) return QCD_ERR_ARG;
     int t = ((p.max_step * r + 31) / 32) * 32;
     t = std::max(32, std::min(t, kTileMaxThreads));
     *R = r;
     *threads = t;
-    *smem = tile_smem_bytes(p.vol, p.half, r);
+    *smem = tile_smem_bytes(p, r);
     return QCD_OK;
 }
 
@@ -580,6 +763,8 @@ int tile_sap_apply(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
     a.nlev = p.nsteps;
     a.nsweep = nsweep;
     a.nrhs = nrhs;
+    a.stride = R * (p.half ? TileRec<true>::y_words : TileRec<false>::y_words);
+    a.zslots = p.tile_zslots;
     void (*k)(TileArgs) = nullptr;
     switch (R) {
         case 1: k = p.half ? k_sap_tile<true, 1> : k_sap_tile<false, 1>; break;

@@ -136,14 +136,16 @@ def test_ssor_schedule_is_consistent(geom, ctas, half):
     if ctas == -1:
         assert t["thread"] == (0 if half else t["thread"])
     if ctas == -2:
-        # the tile form holds one right-hand side's block spinor (plus a zero slot) in one CTA,
-        # with FP16 storage its source as well (12 words per site each, 24 for an FP32 spinor),
-        # else the automatic cluster form stands in
+        # the tile form holds one right-hand side's block spinor (plus 4 zero slots, 2 with FP32
+        # storage) in one CTA, with FP16 storage its source as well (12 words per site each, 24
+        # for an FP32 spinor), else the automatic cluster form stands in
         vol = int(np.prod(b))
-        fits = ((2 * vol + 1) * 48 if half else (vol + 1) * 96) <= 200 * 1024
+        size = (2 * vol + 4) * 48 if half else (vol + 2) * 96
+        fits = size <= 200 * 1024
         assert t["thread"] == (2 if fits else 0)
         if fits:
             assert t["ctas"] == 1 and t["chunks"] == t["levels"]
+            assert t["smem_bytes"] == size
     check_schedule(b, s, t)
 
 
