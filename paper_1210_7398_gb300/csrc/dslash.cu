@@ -60,15 +60,23 @@ __device__ __forceinline__ void load_link(const float4 *__restrict__ U, long V, 
 // (7 blocks of 128 threads); the FP64 kernel is bound by GB300's FP64 rate and
 // keeps its registers.  NR: right-hand sides per thread; each link and the
 // clover field are loaded once and applied to all of them, so the field bytes
-// per right-hand side drop from 576 to 576 / NR (FP32).
+// per right-hand side drop from 576 to 576 / NR (FP32).  Over the grid the
+// right-hand side (tile) index varies fastest, so the CTAs of one site block run
+// close together and the field bytes come from HBM about once for all of them.
+// With FP32 fields two right-hand sides per thread (4 blocks of 128 threads) are
+// faster than one (7 blocks, the fields then read once per right-hand side from
+// L2); with FP16 or two-row fields one per thread is, so those launch NR = 1.
 template <int MINB, typename R, typename SP, typename LK, typename CL>
 __global__ void __launch_bounds__(128, MINB) dslash_kernel(SP *__restrict__ out, const SP *__restrict__ in,
                                                      const LK *__restrict__ U, const CL *__restrict__ F,
                                                      R kappa, Geo g, int nrhs) {
     using C = typename CT<R>::C;
-    const long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    // the right-hand side varies fastest over the (1-D) grid: the CTAs of one site block run
+    // together and share its links and clover field through L2
+    const long sblk = blockIdx.x / nrhs;
+    const int rhs = (int)(blockIdx.x - sblk * nrhs);
+    const long n = sblk * blockDim.x + threadIdx.x;
     if (n >= g.V) return;
-    const int rhs = blockIdx.y;
     constexpr int PLANES = sizeof(C) * 12 / sizeof(SP);
     const SP *src = in + (long)rhs * PLANES * g.V;
     int x[4];
@@ -112,7 +120,7 @@ __device__ __forceinline__ void dslash_site(SP *__restrict__ out, const SP *__re
 // epilogue: 1: <other, out> and |out|^2, 2: <out, other> and |out|^2, 0: none; each CTA (128
 // consecutive sites) sums its sites per right-hand side by a fixed tree (a butterfly within each
 // warp, then the four warps in order) into partial[rhs][3][blockIdx.x], so a right-hand side's
-// inner products do not depend on which others share its threads.  Right-hand sides inactive
+// inner products do not depend on which others share its threads.  partial[rhs][3][site block].  Right-hand sides inactive
 // in gate (may be null) are skipped, their partials zero.
 template <int MINB, int NR, typename R, typename SP, typename LK, typename CL, int MODE = 0>
 __global__ void __launch_bounds__(128, MINB) dslash_kernel_nr(SP *__restrict__ out, const SP *__restrict__ in,
@@ -122,8 +130,12 @@ __global__ void __launch_bounds__(128, MINB) dslash_kernel_nr(SP *__restrict__ o
                                                      double *__restrict__ partial = nullptr,
                                                      const BicgScalars *__restrict__ gate = nullptr) {
     using C = typename CT<R>::C;
-    const long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    const int r0 = blockIdx.y * NR;
+    // the right-hand-side tile varies fastest over the (1-D) grid: the CTAs of one site block
+    // run together and share its links and clover field through L2
+    const int ntile = (nrhs + NR - 1) / NR;
+    const long sblk = blockIdx.x / ntile;
+    const int r0 = (int)(blockIdx.x - sblk * ntile) * NR;
+    const long n = sblk * blockDim.x + threadIdx.x;
     float part[NR][3];
 #pragma unroll
     for (int r = 0; r < NR; r++) part[r][0] = part[r][1] = part[r][2] = 0.f;
@@ -149,7 +161,7 @@ __global__ void __launch_bounds__(128, MINB) dslash_kernel_nr(SP *__restrict__ o
             if (r0 + r < nrhs) {
                 double t = 0;
                 for (int w = 0; w < 4; w++) t += sh[r][q][w];
-                partial[((long)(r0 + r) * 3 + q) * gridDim.x + blockIdx.x] = t;
+                partial[((long)(r0 + r) * 3 + q) * (gridDim.x / ntile) + sblk] = t;
             }
         }
     }
@@ -260,7 +272,7 @@ static Geo geo_of(const qcd_ctx *c) {
 
 int dslash64(qcd_ctx *c, double2 *out, const double2 *in, int nrhs) {
     Geo g = geo_of(c);
-    dim3 grid((unsigned)((g.V + 127) / 128), nrhs);
+    dim3 grid((unsigned)((g.V + 127) / 128 * nrhs));
     cudaEvent_t ev;
     prof_begin(c, QCD_K_DSLASH64, &ev);
     dslash_kernel<3, double, double2, double2, double2><<<grid, 128, 0, c->stream>>>(out, in, c->U64, c->F64,
@@ -277,10 +289,11 @@ static int dslash32_tile(qcd_ctx *c, float4 *out, const float4 *in, int nrhs, co
     cudaEvent_t ev;
     prof_begin(c, QCD_K_DSLASH32, &ev);
     if (nrhs == 1)
-        dslash_kernel_nr<7, 1, float, float4, float2, float4, MODE><<<dim3(nblk, 1), 128, 0, c->stream>>>(
+        dslash_kernel_nr<7, 1, float, float4, float2, float4, MODE><<<dim3(nblk), 128, 0, c->stream>>>(
             out, in, c->U32, c->F32, (float)c->kappa, g, 1, other, part, gate);
     else
-        dslash_kernel_nr<4, 2, float, float4, float2, float4, MODE><<<dim3(nblk, (nrhs + 1) / 2), 128, 0, c->stream>>>(
+        dslash_kernel_nr<4, 2, float, float4, float2, float4, MODE><<<dim3(nblk * ((nrhs + 1) / 2)), 128, 0,
+                                                                       c->stream>>>(
             out, in, c->U32, c->F32, (float)c->kappa, g, nrhs, other, part, gate);
     int rc = prof_end(c, QCD_K_DSLASH32, ev);
     if (rc || !MODE) return rc;
@@ -295,7 +308,7 @@ int dslash32(qcd_ctx *c, float4 *out, const float4 *in, int nrhs) {
         dslash_kernel<7, float, float4, float2, float4><<<dim3((unsigned)((g.V + 127) / 128), 1), 128, 0, c->stream>>>(
             out, in, c->U32, c->F32, (float)c->kappa, g, 1);
     } else {
-        dim3 grid((unsigned)((g.V + 127) / 128), (nrhs + 1) / 2);
+        dim3 grid((unsigned)((g.V + 127) / 128 * ((nrhs + 1) / 2)));
         dslash_kernel_nr<4, 2, float, float4, float2, float4><<<grid, 128, 0, c->stream>>>(out, in, c->U32, c->F32,
                                                                                      (float)c->kappa, g, nrhs);
     }
@@ -327,8 +340,8 @@ int dslash16(qcd_ctx *c, float4 *out, const float4 *in, int nrhs) {
         dslash_kernel<7, float, float4, __half2, uint2><<<dim3((unsigned)((g.V + 127) / 128), 1), 128, 0, c->stream>>>(
             out, in, c->U16, c->F16, (float)c->kappa, g, 1);
     } else {
-        dim3 grid((unsigned)((g.V + 127) / 128), (nrhs + 1) / 2);
-        dslash_kernel_nr<4, 2, float, float4, __half2, uint2><<<grid, 128, 0, c->stream>>>(out, in, c->U16, c->F16,
+        dim3 grid((unsigned)((g.V + 127) / 128 * nrhs));
+        dslash_kernel_nr<7, 1, float, float4, __half2, uint2><<<grid, 128, 0, c->stream>>>(out, in, c->U16, c->F16,
                                                                                      (float)c->kappa, g, nrhs);
     }
     return prof_end(c, QCD_K_DSLASH32, ev);
@@ -351,8 +364,8 @@ int dslash12(qcd_ctx *c, float4 *out, const float4 *in, int nrhs) {
         dslash_kernel<7, float, float4, float4, float4><<<dim3((unsigned)((g.V + 127) / 128), 1), 128, 0, c->stream>>>(
             out, in, c->U12, c->F32, (float)c->kappa, g, 1);
     } else {
-        dim3 grid((unsigned)((g.V + 127) / 128), (nrhs + 1) / 2);
-        dslash_kernel_nr<4, 2, float, float4, float4, float4><<<grid, 128, 0, c->stream>>>(out, in, c->U12, c->F32,
+        dim3 grid((unsigned)((g.V + 127) / 128 * nrhs));
+        dslash_kernel_nr<7, 1, float, float4, float4, float4><<<grid, 128, 0, c->stream>>>(out, in, c->U12, c->F32,
                                                                                      (float)c->kappa, g, nrhs);
     }
     return prof_end(c, QCD_K_DSLASH32, ev);
