@@ -728,6 +728,16 @@ def run_gpu_on_stream(args, q, qi, torch, stream, rank, world, local):
         if n:
             kstats[nm] = {"launches": n, "ms": ms}
     q.qcd_set_profiling(sv.ctx, False)
+    # ---- the outer operator's precision: FP64 D (as timed) against the FP32 D for v = D p^ and
+    # t = D s^ with FP64 left to the true residual, the dots and x; one group of sources ----
+    outer_prec = {}
+    for name, op in (("f64", q.QCD_F64), ("f32", q.QCD_F32)):
+        pp = q.qcd_params.from_buffer_copy(chosen_p)
+        pp.outer_precision = op
+        xg.zero_()
+        ms, st = event_ms(torch, stream, lambda: sv.solve(xg, bg, pp, nrhs=g))
+        outer_prec[name] = {"ms": ms, "sources": g, "outer_iters": st["outer_iters"], "inner_iters": st["inner_iters"],
+                            "restarts": st["restarts"], "true_rel_res": st["true_rel_res"], "status": st["status"]}
     del xg, bg
     tot_k = sum(v["ms"] for v in kstats.values())
     for v in kstats.values():
@@ -837,6 +847,7 @@ def run_gpu_on_stream(args, q, qi, torch, stream, rank, world, local):
            "solve": {"outer_iters": last["outer_iters"], "inner_iters": last["inner_iters"],
                      "restarts": last["restarts"], "true_rel_res": last["true_rel_res"],
                      "wall_s_timed_region": wall},
+           "outer_precision": outer_prec,
            "oracle_check": oracle_check, "tuning": tune_info,
            "e2e": e2e, "gpu_launches": launches, "kernels": kstats, "clocks": clk, "roofline": roof,
            "fp32_peak_tflops": fp32, "dslash": dsl, "cpu_baseline": cpu, "small_12x12x12x24": small,

@@ -114,6 +114,13 @@ typedef struct {
                            device memory of one group.  0: as many as fit the free device
                            memory (at least 1).  Results do not depend on it: each
                            right-hand side's iterates are those of its solve alone      */
+    int outer_precision; /* qcd_solve, the outer BiCGStab's v = D p^ and t = D s^ (Sec. 2):
+                           QCD_F64 (0, the default): the FP64 D.  QCD_F32: the FP32 D
+                           applied to the inner solver's FP32 solution, widened to FP64;
+                           FP64 then serves only the true residual b - D x, the dot
+                           products and norms, and x.  The recursive residual then
+                           carries the FP32 error of D, so reaching tol takes restarts
+                           from the true residual                                     */
 } qcd_params;
 
 typedef struct {
@@ -222,9 +229,13 @@ int qcd_solve(qcd_ctx *ctx, double *x, const double *b, const qcd_params *p, int
 int qcd_solve_multi(int n, qcd_ctx *const *ctxs, double *const *x, const double *const *b, const qcd_params *params,
                     const int *nrhs, qcd_stats *stats);
 
-/* on != 0 (default): qcd_solve captures one inner BiCGStab iteration as a CUDA
- * graph and replays it, when the context stream is not the legacy default
- * stream and kernel profiling is off.  Results do not depend on it. */
+/* on != 0 (default): when the context stream is not the legacy default stream
+ * and kernel profiling is off, qcd_solve captures each inner BiCGStab solve as
+ * one CUDA graph: a conditional while node repeats the inner iteration until a
+ * kernel finds no right-hand side active or max_inner reached, so convergence
+ * is decided on the device and the host waits once per inner solve (where the
+ * driver has no conditional nodes, one iteration is captured and replayed, the
+ * host reading the active flags after each).  Results do not depend on it. */
 int qcd_set_graphs(qcd_ctx *ctx, int on);
 
 /* Tuning knob of the SAP block kernel; results do not depend on it.  The

@@ -46,7 +46,7 @@ class qcd_params(ctypes.Structure):
                 ("max_outer", ctypes.c_int), ("max_inner", ctypes.c_int),
                 ("bc_t", ctypes.c_int), ("sap_storage", ctypes.c_int),
                 ("learned", ctypes.c_int), ("sap_ctas", ctypes.c_int), ("block_solver", ctypes.c_int),
-                ("rhs_group", ctypes.c_int)]
+                ("rhs_group", ctypes.c_int), ("outer_precision", ctypes.c_int)]
 
 
 class qcd_learned_verdict(ctypes.Structure):
@@ -274,7 +274,7 @@ def params_dict(p: qcd_params) -> dict:
             "nsap": p.nsap, "sap_storage": {QCD_F32: "f32", QCD_F16: "f16"}.get(p.sap_storage, p.sap_storage),
             "sap_ctas": p.sap_ctas, "learned": p.learned,
             "block_solver": {0: "ll-ssor", 1: "even-odd mr"}.get(p.block_solver, p.block_solver),
-            "rhs_group": p.rhs_group}
+            "rhs_group": p.rhs_group, "outer_precision": {QCD_F64: "f64", QCD_F32: "f32"}.get(p.outer_precision)}
 
 
 LEARNED_CHANS = (1, 8, 8, 1)
@@ -387,7 +387,7 @@ def qcd_bench_fp32_peak(ctx, iters: int = 64) -> float:
 
 def make_params(kappa, csw, block, subblock, omega=1.0, nsweep=4, nsap=4, tol=1e-10, inner_tol=1e-5,
                 max_outer=100, max_inner=500, bc_t=1, sap_storage=QCD_F32, sap_ctas=0,
-                block_solver=0, rhs_group=0) -> qcd_params:
+                block_solver=0, rhs_group=0, outer_precision=0) -> qcd_params:
     p = qcd_params()
     p.kappa, p.csw = float(kappa), float(csw)
     p.block = (ctypes.c_int * 4)(*block)
@@ -398,6 +398,7 @@ def make_params(kappa, csw, block, subblock, omega=1.0, nsweep=4, nsap=4, tol=1e
     p.bc_t, p.sap_storage, p.learned, p.sap_ctas = int(bc_t), int(sap_storage), 0, int(sap_ctas)
     p.block_solver = int(block_solver)
     p.rhs_group = int(rhs_group)
+    p.outer_precision = int(outer_precision)
     return p
 
 

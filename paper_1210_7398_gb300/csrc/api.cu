@@ -163,6 +163,8 @@ int check_params(qcd_ctx *c, const qcd_params *p) {
         return fail(c, QCD_ERR_ARG, "params.kappa/csw differ from the clover field built");
     if (p->sap_ctas < -2 || p->sap_ctas > 16) return fail(c, QCD_ERR_ARG, "sap_ctas must lie in -2..16");
     if (p->block_solver < 0 || p->block_solver > 1) return fail(c, QCD_ERR_ARG, "block_solver must be 0 or 1");
+    if (p->outer_precision != QCD_F64 && p->outer_precision != QCD_F32)
+        return fail(c, QCD_ERR_ARG, "outer_precision must be QCD_F64 or QCD_F32");
     if (p->block_solver == 1 && (p->sap_storage != QCD_F32 || p->learned != 0))
         return fail(c, QCD_ERR_ARG, "block_solver 1 needs sap_storage QCD_F32 and learned 0");
     use_sap_ctas(c, p->sap_ctas);
@@ -216,7 +218,7 @@ void qcd_destroy(qcd_ctx *c) {
     void *bufs[] = {c->net.W, c->net.grad, c->net.m, c->net.v, c->net.B, c->net.P, c->net.scal, c->net.act,
                     c->net.pairs,
                     c->U64, c->U32, c->F64, c->F32, c->U16, c->F16, c->U12, c->d_status, c->d_red, c->d_red_tiles, c->d_scalars, c->d_bicg, c->d_mask,
-                    c->ws64, c->ws32,
+                    c->d_loop, c->ws64, c->ws32,
                     c->d_io, c->bench_in, c->bench_out, c->plan.d_origin[0] /* the plan's table region */,
                     c->plan.d_rec};
     for (void *p : bufs)

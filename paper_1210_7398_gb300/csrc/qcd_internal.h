@@ -165,6 +165,8 @@ struct qcd_ctx {
     int *d_mask = nullptr;        // per right-hand side masks [2][nrhs]
     int *h_mask = nullptr;
     bool use_graphs = true;       // replay the inner iteration as a CUDA graph when possible
+    bool cond_graphs = true;      // the whole inner solve as one graph with a device-decided while loop
+    int *d_loop = nullptr;        // that loop's iteration counter (device)
     // host staging for host-pointer calls
     void *d_io = nullptr;
     size_t d_io_bytes = 0;

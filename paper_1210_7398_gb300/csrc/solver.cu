@@ -8,8 +8,12 @@
 // restarts that right-hand side from its true residual (at most 5 restarts).
 //
 // One inner iteration is a fixed sequence of launches that reads its scalars
-// from device memory, so on a capturable stream it is captured once per call
-// as a CUDA graph and replayed; the host reads only the active flags.
+// from device memory, so on a capturable stream the inner solve is captured once
+// per call as a CUDA graph whose while node repeats the iteration until a kernel
+// at its end finds no right-hand side active (or max_inner reached): one graph
+// launch and one read of the scalars per inner solve.  Where conditional nodes
+// are unavailable the iteration alone is captured and replayed, the host reading
+// the active flags after each.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -86,6 +90,57 @@ bool capturable(qcd_ctx *c) {
     return st == cudaStreamCaptureStatusNone;
 }
 
+// the condition of the inner loop's graph: another iteration while any right-hand side is
+// active and fewer than max_inner have run (the counter starts at 0 with each launch)
+__global__ void k_inner_continue(cudaGraphConditionalHandle h, const BicgScalars *__restrict__ S, int nrhs,
+                                 int *__restrict__ iter, int max_inner) {
+    if (threadIdx.x != 0) return;
+    int any = 0;
+    for (int k = 0; k < nrhs; k++) any |= S[k].active;
+    const int it = ++*iter;
+    cudaGraphSetConditional(h, (any && it < max_inner) ? 1u : 0u);
+}
+
+// The inner solve as one graph: a while node whose body is one inner iteration followed by
+// k_inner_continue, so the loop runs on the device with no host round trip per iteration.
+// Returns cudaSuccess, or the error of the first graph call that failed (the caller then
+// replays the iteration graph from the host instead).
+cudaError_t build_loop_graph(qcd_ctx *c, const Ws &w, const qcd_params *p, cudaGraphExec_t *graph, int *rc) {
+    *rc = QCD_OK;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return e;
+    cudaGraphConditionalHandle h;
+    e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const long l0 = c->total_launches;
+            *rc = inner_iteration(c, w, p);
+            if (!*rc) {
+                k_inner_continue<<<1, 32, 0, c->stream>>>(h, w.Si, w.nrhs, c->d_loop, p->max_inner);
+                c->total_launches++;
+            }
+            c->graph_launches = c->total_launches - l0;
+            c->total_launches = l0;
+            cudaGraph_t captured = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(c->stream, &captured);
+            if (e == cudaSuccess) e = e2;
+        }
+    }
+    if (e == cudaSuccess && !*rc) e = cudaGraphInstantiate(graph, g, 0);
+    cudaGraphDestroy(g);
+    return e;
+}
+
 // inner FP32 BiCGStab for every right-hand side active in the outer solver:
 // y ~ D^{-1} q with right preconditioner M_SAP; returns the iterations summed over rhs
 int inner_solve(qcd_ctx *c, const Ws &w, const qcd_params *p, cudaGraphExec_t *graph, int *iters) {
@@ -102,6 +157,29 @@ int inner_solve(qcd_ctx *c, const Ws &w, const qcd_params *p, cudaGraphExec_t *g
     *iters = 0;
     bool any = false;
     TRY(any_active(c, w, w.Si, w.hSi, &any, nullptr));
+    if (any && graph && c->cond_graphs) {
+        // the whole loop in one graph launch; the host reads the scalars once at the end
+        if (!*graph) {
+            int rc = QCD_OK;
+            const cudaError_t e = build_loop_graph(c, w, p, graph, &rc);
+            if (rc) return rc;
+            if (e != cudaSuccess) {
+                cudaGetLastError();  // no conditional nodes here: replay the iteration from the host
+                if (*graph) cudaGraphExecDestroy(*graph);
+                *graph = nullptr;
+                c->cond_graphs = false;
+            }
+        }
+        if (*graph) {
+            int ran = 0;
+            QCD_CUDA(c, cudaMemsetAsync(c->d_loop, 0, sizeof(int), c->stream));
+            QCD_CUDA(c, cudaGraphLaunch(*graph, c->stream));
+            QCD_CUDA(c, cudaMemcpyAsync(&ran, c->d_loop, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+            TRY(any_active(c, w, w.Si, w.hSi, &any, iters));
+            c->total_launches += c->graph_launches * ran;
+            return QCD_OK;
+        }
+    }
     for (int it = 0; any && it < p->max_inner; it++) {
         if (graph) {
             if (!*graph) {
@@ -139,6 +217,16 @@ int precondition(qcd_ctx *c, const Ws &w, const qcd_params *p, const double2 *in
     TRY(inner_solve(c, w, p, graph, iters));
     TRY(spinor32_to_64(c, out, w.y, w.nrhs));
     return QCD_OK;
+}
+
+// out = D y for the outer iteration, y the preconditioner's output (its FP32 original still in
+// w.y): the FP64 D, or with outer_precision QCD_F32 the FP32 D widened to FP64
+int outer_D(qcd_ctx *c, const Ws &w, const qcd_params *p, double2 *out, const double2 *y) {
+    if (p->outer_precision == QCD_F32) {
+        TRY(dslash32(c, w.iv, w.y, w.nrhs));
+        return spinor32_to_64(c, out, w.iv, w.nrhs);
+    }
+    return dslash64(c, out, y, w.nrhs);
 }
 
 int ensure(qcd_ctx *c, void **ptr, size_t *have, size_t need) {
@@ -181,6 +269,7 @@ int workspace(qcd_ctx *c, int nrhs, int block_solver, Ws *w) {
         }
         c->red_rhs = nrhs;
     }
+    if (!c->d_loop) TRY(dev_alloc(c, (void **)&c->d_loop, sizeof(int)));
     w->nrhs = nrhs;
     w->V = V;
     double2 *base = (double2 *)c->ws64;
@@ -354,13 +443,13 @@ int solve(qcd_ctx *c, double2 *x, const double2 *b, const qcd_params *p, int nrh
         int its = 0;
         TRY(precondition(c, w, p, w.p, w.ph, gp, &its));
         inner += its;
-        TRY(dslash64(c, w.v, w.ph, R));
+        TRY(outer_D(c, w, p, w.v, w.ph));
         TRY(reduce64(c, RED_DOT_NORM, w.rh, w.v, n, R, w.red, w.So));
         TRY(scalars(c, SC_ALPHA, w.So, w.red, R, p->tol, nullptr));
         TRY(blas_s_update64(c, w.s, w.r, w.v, w.So, n, R));
         TRY(precondition(c, w, p, w.s, w.sh, gp, &its));
         inner += its;
-        TRY(dslash64(c, w.t, w.sh, R));
+        TRY(outer_D(c, w, p, w.t, w.sh));
         TRY(reduce64(c, RED_DOT_NORMA, w.t, w.s, n, R, w.red, w.So));
         TRY(scalars(c, SC_OMEGA, w.So, w.red, R, p->tol, nullptr));
         TRY(blas_xr_update64(c, w.x, w.r, w.ph, w.sh, w.s, w.t, w.So, n, R));

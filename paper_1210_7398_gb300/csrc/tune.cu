@@ -88,10 +88,10 @@ std::string cache_key(qcd_ctx *c, int nrhs, const qcd_params *b, int max_candida
     char buf[512];
     std::snprintf(buf, sizeof(buf),
                   "%s;dims=%dx%dx%dx%d;nrhs=%d;kappa=%.17g;csw=%.17g;bc_t=%d;tol=%.17g;inner_tol=%.17g;"
-                  "max=%d/%d;omega=%.17g;rhs_group=%d;cands=%d;gpu=%s;sms=%d",
+                  "max=%d/%d;omega=%.17g;rhs_group=%d;outer=%d;cands=%d;gpu=%s;sms=%d",
                   kTunerVersion, c->lat.L[0], c->lat.L[1], c->lat.L[2], c->lat.L[3], nrhs, b->kappa, b->csw, b->bc_t,
-                  b->tol, b->inner_tol, b->max_outer, b->max_inner, b->omega, b->rhs_group, max_candidates,
-                  gpu.c_str(), sms);
+                  b->tol, b->inner_tol, b->max_outer, b->max_inner, b->omega, b->rhs_group, b->outer_precision,
+                  max_candidates, gpu.c_str(), sms);
     return buf;
 }
 

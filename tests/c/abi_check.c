@@ -18,9 +18,10 @@ static int failures = 0;
 int main(void)
 {
     /* layouts the Python binding mirrors */
-    CHECK(sizeof(qcd_params) == 112);
+    CHECK(sizeof(qcd_params) == 120);
     CHECK(offsetof(qcd_params, block_solver) == 104);
     CHECK(offsetof(qcd_params, rhs_group) == 108);
+    CHECK(offsetof(qcd_params, outer_precision) == 112);
     CHECK(sizeof(qcd_stats) == 48);
     CHECK(sizeof(qcd_learned_verdict) == 56);
     /* argument errors are returned, never fatal */

@@ -37,8 +37,8 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_binding_structs_match_header():
-    # qcd_params: 2 doubles, 8 ints, 1 double, 2 ints, 2 doubles, 7 ints (with padding)
-    assert ctypes.sizeof(q.qcd_params) == 112
+    # qcd_params: 2 doubles, 8 ints, 1 double, 2 ints, 2 doubles, 9 ints (with padding)
+    assert ctypes.sizeof(q.qcd_params) == 120
     assert ctypes.sizeof(q.qcd_stats) == 48
     # qcd_learned_verdict: 4 doubles, 6 ints
     assert ctypes.sizeof(q.qcd_learned_verdict) == 56

@@ -479,24 +479,31 @@ def test_non_finite_rhs_is_reported_and_isolated():
     s.close()
 
 
-def test_graph_replay_equals_direct_launches():
-    """The inner iteration replayed as a CUDA graph (non-default stream) gives the
-    same solution, bitwise, as direct launches."""
+@pytest.mark.parametrize("ctas,storage", [(0, "f32"), (-2, "f16")])
+def test_graph_replay_equals_direct_launches(ctas, storage):
+    """The inner solve run as one CUDA graph whose while node the device ends (non-default
+    stream) gives the same solution, bitwise, as direct launches with the host deciding each
+    iteration; the graph path launches one condition kernel per iteration on top."""
     dims, kappa = (8, 8, 8, 8), 0.12
     side = torch.cuda.Stream()
     with torch.cuda.stream(side):
         s, U, F = make_solver(dims, kappa, seed=1005)
         b = torch.from_numpy(qi.gaussian_spinor(dims, seed=2005, nrhs=2)).cuda()
-        prm = q.make_params(kappa, CSW, (4, 4, 4, 4), (2, 2, 2, 2), tol=1e-10)
+        prm = q.make_params(kappa, CSW, (4, 4, 4, 4), (2, 2, 2, 2), tol=1e-10, sap_ctas=ctas,
+                            sap_storage=q.QCD_F16 if storage == "f16" else q.QCD_F32)
         xg = torch.zeros_like(b)
         l0 = q.qcd_launch_count(s.ctx)
-        s.solve(xg, b, prm, nrhs=2)
+        stg = s.solve(xg, b, prm, nrhs=2)
+        l1 = q.qcd_launch_count(s.ctx)
         q.qcd_set_graphs(s.ctx, False)
         xd = torch.zeros_like(b)
-        s.solve(xd, b, prm, nrhs=2)
+        std = s.solve(xd, b, prm, nrhs=2)
+        l2 = q.qcd_launch_count(s.ctx)
     torch.cuda.synchronize()
     assert torch.equal(xg, xd)
-    assert q.qcd_launch_count(s.ctx) > l0
+    assert stg["inner_iters"] == std["inner_iters"] and stg["outer_iters"] == std["outer_iters"]
+    # the device loop adds its condition kernel to every iteration: strictly more launches
+    assert l1 - l0 > l2 - l1 > 0
     s.close()
 
 

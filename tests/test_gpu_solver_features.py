@@ -150,3 +150,31 @@ def test_stats_report_kernel_time_when_profiling():
     q.qcd_set_profiling(s.ctx, False)
     assert 0 < st["ms_dslash"] < st["ms_total"] and 0 < st["ms_sap"] < st["ms_total"]
     s.close()
+
+
+def test_fp32_outer_operator_reaches_tolerance_through_restarts():
+    """outer_precision = QCD_F32: v = D p^ and t = D s^ in FP32, FP64 only for the true residual,
+    the dots and x.  The recursive residual drifts by the FP32 error of D, so the solve restarts
+    from the true residual and still ends at 1e-10 under the oracle's D; the default FP64 outer
+    needs no restart here."""
+    dims, kappa = (8, 8, 8, 8), 0.12
+    s, U = make_solver(dims, kappa, seed=1014)
+    b = qi.gaussian_spinor(dims, seed=2014, nrhs=2)
+    _, F = oracle.clover(dims, U, CSW, kappa)
+    stats = {}
+    for name, op in (("f64", q.QCD_F64), ("f32", q.QCD_F32)):
+        prm = q.make_params(kappa, CSW, (4, 4, 4, 4), (2, 2, 2, 2), nsweep=2, nsap=2, tol=1e-10,
+                            outer_precision=op)
+        x = np.zeros_like(b)
+        st = s.solve(x, b, prm, nrhs=2)
+        assert st["status"] == q.QCD_OK and st["true_rel_res"] <= 1e-10
+        for k in range(2):
+            r = b[k] - oracle.apply_D(dims, U, F, kappa, x[k])
+            assert np.linalg.norm(r) / np.linalg.norm(b[k]) <= 1e-10
+        stats[name] = st
+    assert stats["f64"]["restarts"] == 0
+    assert stats["f32"]["outer_iters"] >= stats["f64"]["outer_iters"]
+    with pytest.raises(q.QcdError) as e:
+        s.solve(np.zeros_like(b), b, q.make_params(kappa, CSW, (4, 4, 4, 4), (2, 2, 2, 2), outer_precision=2), nrhs=2)
+    assert e.value.code == q.QCD_ERR_ARG
+    s.close()
