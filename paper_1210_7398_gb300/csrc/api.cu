@@ -198,6 +198,10 @@ int qcd_create(qcd_ctx **out, const int dims[4], void *stream) {
     if (!rc) rc = dev_alloc(c, (void **)&c->F64, sizeof(double2) * 36 * V);
     if (!rc) rc = dev_alloc(c, (void **)&c->F32, sizeof(float4) * 18 * V);
     if (!rc) rc = dev_alloc(c, (void **)&c->d_status, sizeof(int) * 16);
+    if (!rc && cudaMemset(c->d_status, 0, sizeof(int) * 16) != cudaSuccess) {
+        cudaGetLastError();
+        rc = QCD_ERR_CUDA;
+    }
     if (!rc && cudaMallocHost((void **)&c->h_scalars, sizeof(double) * 16) != cudaSuccess) {
         cudaGetLastError();
         rc = QCD_ERR_OOM;
@@ -433,6 +437,7 @@ int qcd_solve(qcd_ctx *c, double *x, const double *b, const qcd_params *p, int n
         local.ms_dslash = c->prof.ms[QCD_K_DSLASH32] - ms0[QCD_K_DSLASH32] + c->prof.ms[QCD_K_DSLASH64] - ms0[QCD_K_DSLASH64];
         local.ms_sap = c->prof.ms[QCD_K_SSOR] - ms0[QCD_K_SSOR] + c->prof.ms[QCD_K_SAPHOP] - ms0[QCD_K_SAPHOP];
     }
+    if (p->learned && (rc = learned_tc_status(c))) return rc;
     local.status = status;
     local.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (st) *st = local;
@@ -653,8 +658,7 @@ int qcd_learned_apply(qcd_ctx *c, float *out, const float *in) {
     const bool dev_out = is_device_ptr(out);
     if ((rc = spinor32_from_internal(c, (float2 *)(dev_out ? (char *)out : io + 2 * bytes), y, 1))) return rc;
     if (!dev_out) QCD_CUDA(c, cudaMemcpyAsync(out, io + 2 * bytes, bytes, cudaMemcpyDeviceToHost, c->stream));
-    QCD_CUDA(c, cudaStreamSynchronize(c->stream));
-    return QCD_OK;
+    return learned_tc_status(c);  // synchronises
 }
 
 int qcd_learned_loss_grad(qcd_ctx *c, const float *rho, const float *eps, double *loss, float *grad) {
@@ -674,12 +678,10 @@ int qcd_learned_loss_grad(qcd_ctx *c, const float *rho, const float *eps, double
     double l = 0;
     if ((rc = learned_loss_grad(c, r, es, &l, y))) return rc;
     if (loss) *loss = l;
-    if (grad) {
+    if (grad)
         QCD_CUDA(c, cudaMemcpyAsync(grad, c->net.grad, sizeof(float2) * learned_weight_count(),
                                     cudaMemcpyDeviceToHost, c->stream));
-        QCD_CUDA(c, cudaStreamSynchronize(c->stream));
-    }
-    return QCD_OK;
+    return learned_tc_status(c);  // synchronises
 }
 
 int qcd_learned_train(qcd_ctx *c, const float *sources, int npairs, const qcd_params *p, int epochs, int batch,
@@ -777,8 +779,7 @@ int qcd_learned_train(qcd_ctx *c, const float *sources, int npairs, const qcd_pa
         }
         if (history) history[e + 1] = total / npairs;
     }
-    QCD_CUDA(c, cudaStreamSynchronize(c->stream));
-    return QCD_OK;
+    return learned_tc_status(c);  // synchronises
 }
 
 int qcd_learned_evaluate(qcd_ctx *c, const double *b, int nrhs, const qcd_params *p, qcd_learned_verdict *out) {

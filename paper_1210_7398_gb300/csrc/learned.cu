@@ -862,7 +862,7 @@ int learned_forward(qcd_ctx *c, float4 *y, const float4 *x) {
     int rc = ensure_net(c);
     if (rc) return rc;
     if ((rc = launch_layer<1, 8, PLANE32, SITE16>(c, L.a1, x, L.B + layer_boff(0, false)))) return rc;
-    if ((rc = launch_layer<8, 8, SITE16, SITE16>(c, L.a2, L.a1, L.B + layer_boff(1, false)))) return rc;
+    if ((rc = learned_layer_tc(c, L.a2, L.a1, L.B + layer_boff(1, false), false))) return rc;
     return launch_layer_wfirst<8, SITE16, PLANE32>(c, y, L.a2, L.B + layer_boff(2, false));
 }
 
@@ -896,7 +896,7 @@ int learned_loss_grad(qcd_ctx *c, const float4 *rho, const float2 *eps, double *
     if ((rc = wgrad_layer(2, [&]() { return launch_wgrad<8, 1, SITE16>(c, L.P, L.a2, L.g3); }))) return rc;
     if ((rc = launch_layer<1, 8, SITE32, SITE32>(c, L.g2, L.g3, L.B + layer_boff(2, true)))) return rc;
     if ((rc = wgrad_layer(1, [&]() { return launch_wgrad<8, 8, SITE16>(c, L.P, L.a1, L.g2); }))) return rc;
-    if ((rc = launch_layer<8, 8, SITE32, SITE32>(c, L.g1, L.g2, L.B + layer_boff(1, true)))) return rc;
+    if ((rc = learned_layer_tc(c, L.g1, L.g2, L.B + layer_boff(1, true), true))) return rc;
     if ((rc = wgrad_layer(0, [&]() { return launch_wgrad<1, 8, PLANE32>(c, L.P, rho, L.g1); }))) return rc;
     if (loss_out) {
         double h = 0;

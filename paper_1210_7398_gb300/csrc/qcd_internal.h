@@ -359,6 +359,12 @@ int learned_zero_grad(qcd_ctx *c);
 int learned_adam(qcd_ctx *c, float lr);
 // out += N(v - D out) per right-hand side; w1, w2 scratch of nrhs fields
 int learned_correct(qcd_ctx *c, float4 *out, const float4 *v, float4 *w1, float4 *w2, int nrhs);
+// the hidden 8 -> 8 layer on the tcgen05 tensor cores (BF16 site records in and out, or FP32 with
+// fp32_io); Bt: its [9][64][64] BF16 B matrices
+int learned_layer_tc(qcd_ctx *c, void *y, const void *x, const __nv_bfloat16 *Bt, bool fp32_io);
+// QCD_ERR_TIMEOUT (and the flag cleared) if a tensor-core layer gave up a wait since the last
+// check; synchronises the stream
+int learned_tc_status(qcd_ctx *c);
 int sub_plane(qcd_ctx *c, float4 *r, const float4 *a, const float4 *b, int nrhs);
 int plane_to_site(qcd_ctx *c, float2 *out, const float4 *in);
 

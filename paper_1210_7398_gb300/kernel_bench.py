@@ -1,11 +1,13 @@
 """Kernel micro-benchmarks of the library: one SAP application (M_SAP v, Eq. (4) with the
-ll-SSOR block inverse of Sec. 3) or one application of D (Eq. (2)) on a synthetic lattice,
-repeated, with per-class device times from the library's profiler.  For tuning by hand and for
-profilers (ncu), which need a short program that runs one kernel family on a small case.
+ll-SSOR block inverse of Sec. 3), one application of D (Eq. (2)) or one application of the
+learned correction N (three gauge-covariant layers) on a synthetic lattice, repeated, with
+per-class device times from the library's profiler.  For tuning by hand and for profilers (ncu),
+which need a short program that runs one kernel family on a small case.
 
     python -m paper_1210_7398_gb300.kernel_bench sap --dims 24x24x24x48 --block 4x4x4x6 \\
         --subblock 2x2x2x3 --nrhs 4 --storage f16 --ctas -2 --reps 3
     python -m paper_1210_7398_gb300.kernel_bench dslash --dims 24x24x24x48 --prec f32 --nrhs 1
+    python -m paper_1210_7398_gb300.kernel_bench learned --dims 24x24x24x48 --reps 3
 
 Prints one JSON line.  Links: exp(i 0.3 X) from the seeded generator; sources Gaussian.
 """
@@ -30,7 +32,7 @@ def dims_arg(s):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("what", choices=["sap", "dslash"])
+    ap.add_argument("what", choices=["sap", "dslash", "learned"])
     ap.add_argument("--dims", type=dims_arg, default=(24, 24, 24, 48))
     ap.add_argument("--kappa", type=float, default=0.122)
     ap.add_argument("--csw", type=float, default=1.6)
@@ -73,6 +75,17 @@ def main(argv=None):
             for _ in range(a.reps):
                 s.sap_precondition(y, v, prm, nrhs=a.nrhs)
             out["params"] = q.params_dict(prm)
+        elif a.what == "learned":
+            q.qcd_learned_set_weights(s.ctx, q.learned_init_weights(7))
+            v = qi.gaussian_spinor_torch(a.dims, 2004, 1, "cuda")[0].to(torch.complex64).contiguous()
+            y = torch.empty_like(v)
+            q.qcd_learned_apply(s.ctx, y, v)
+            q.qcd_set_profiling(s.ctx, True)
+            for k in range(len(q.KERNEL_CLASSES)):
+                q.qcd_kernel_stats(s.ctx, k, reset=True)
+            for _ in range(a.reps):
+                q.qcd_learned_apply(s.ctx, y, v)
+            out["nrhs"] = 1
         else:
             pc = {"f32": q.QCD_F32, "f64": q.QCD_F64, "f16": q.QCD_F16, "su3": q.QCD_F32_SU3}[a.prec]
             q.qcd_bench_dslash(s.ctx, pc, a.nrhs, 1)
