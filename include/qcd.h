@@ -401,6 +401,13 @@ long qcd_launch_count(const qcd_ctx *ctx);
  * restart from it, and QCD_ERR_BREAKDOWN after 5 restarts of a right-hand side.  0 disarms. */
 int qcd_debug_inject_breakdown(qcd_ctx *ctx, int count);
 
+/* Test hook of the tensor-core learned layer: with on != 0 its kernel issues no MMA and commits
+ * nothing to its mbarriers, so its first wait for a commit finds none.  Every such wait is
+ * bounded (about a second); the kernel stops, frees its tensor memory and returns, and the call
+ * that launched it reports QCD_ERR_TIMEOUT, leaving the context usable.  The failure path is
+ * exercised without a device fault.  0 disarms. */
+int qcd_debug_tc_skip_commit(qcd_ctx *ctx, int on);
+
 /* D on internal-layout buffers only, repeated `iters` times (no layout
  * conversion): the kernel the memory-bandwidth roofline is measured on.
  * prec = QCD_F64, QCD_F32, QCD_F16 or QCD_F32_SU3; nrhs >= 1.  Work buffers are allocated on first

@@ -29,7 +29,7 @@ EXPORTS = ("qcd_create", "qcd_destroy", "qcd_last_error", "qcd_set_boundary", "q
            "qcd_set_sap_ctas", "qcd_set_sap_form", "qcd_sap_plan_tables", "qcd_set_graphs", "qcd_autotune", "qcd_learned_weight_count",
            "qcd_learned_set_weights", "qcd_learned_get_weights", "qcd_learned_apply", "qcd_learned_loss_grad",
            "qcd_learned_train", "qcd_learned_evaluate", "qcd_solve_multi", "qcd_set_tune_cache", "qcd_bench_fp32_peak",
-           "qcd_debug_inject_breakdown", "qcd_learned_save", "qcd_learned_load")
+           "qcd_debug_inject_breakdown", "qcd_learned_save", "qcd_learned_load", "qcd_debug_tc_skip_commit")
 
 
 class QcdError(RuntimeError):
@@ -113,6 +113,7 @@ def load_library(path: str = LIB_PATH):
         "qcd_set_tune_cache": (I, [ctypes.c_char_p]),
         "qcd_bench_fp32_peak": (I, [P, I, ctypes.POINTER(D)]),
         "qcd_debug_inject_breakdown": (I, [P, I]),
+        "qcd_debug_tc_skip_commit": (I, [P, I]),
         "qcd_learned_save": (I, [P, ctypes.c_char_p]),
         "qcd_learned_load": (I, [P, ctypes.c_char_p]),
     }
@@ -376,6 +377,11 @@ def qcd_bench_dslash(ctx, prec: int, nrhs: int, iters: int):
 def qcd_debug_inject_breakdown(ctx, count: int):
     """Test hook: the next count outer iterations start from rho = 0 (a host-made breakdown)."""
     return _check(ctx, load_library().qcd_debug_inject_breakdown(ctx, int(count)))
+
+
+def qcd_debug_tc_skip_commit(ctx, on: bool):
+    """Test hook: the tensor-core learned layer commits nothing, so its bounded waits run out."""
+    return _check(ctx, load_library().qcd_debug_tc_skip_commit(ctx, 1 if on else 0))
 
 
 def qcd_bench_fp32_peak(ctx, iters: int = 64) -> float:

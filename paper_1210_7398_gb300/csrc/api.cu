@@ -502,6 +502,13 @@ int qcd_debug_inject_breakdown(qcd_ctx *c, int count) {
     return QCD_OK;
 }
 
+int qcd_debug_tc_skip_commit(qcd_ctx *c, int on) {
+    int rc = ready(c);
+    if (rc) return rc;
+    c->tc_skip_commit = on != 0;
+    return QCD_OK;
+}
+
 int qcd_set_sap_form(qcd_ctx *c, int form) {
     int rc = ready(c);
     if (rc) return rc;

@@ -216,7 +216,7 @@ __device__ __forceinline__ void tc_transport(unsigned char *Ab, const void *x, c
 template <int FIN, int FOUT>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_layer_tc(void *y, const void *x, const float2 *__restrict__ U, const __nv_bfloat16 *__restrict__ Bt, Geo g,
-               int ntiles, int *status) {
+               int ntiles, int *status, int skip_commit) {
     extern __shared__ unsigned char tc_raw[];
     unsigned char *sm = tc_raw + ((1024u - (smem_u32(tc_raw) & 1023u)) & 1023u);
     unsigned char *Bs = sm + kOffB, *As = sm + kOffA;
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 break;
             }
             tc_fence_after();
-            if (tid == 0) {
+            if (tid == 0 && !skip_commit) {
                 const uint32_t a_base = smem_u32(Ab);
 #pragma unroll
                 for (int a = 0; a < 3; a++)
@@ -391,7 +391,8 @@ int launch_tc(qcd_ctx *c, void *y, const void *x, const __nv_bfloat16 *Bt) {
     g.bc_t = c->bc_t;
     cudaEvent_t ev;
     prof_begin(c, QCD_K_LEARNED, &ev);
-    k_layer_tc<FIN, FOUT><<<grid, kTcThreads, kTcSmem, c->stream>>>(y, x, c->U32, Bt, g, (int)tiles, c->d_status);
+    k_layer_tc<FIN, FOUT><<<grid, kTcThreads, kTcSmem, c->stream>>>(y, x, c->U32, Bt, g, (int)tiles, c->d_status,
+                                                                   c->tc_skip_commit ? 1 : 0);
     return prof_end(c, QCD_K_LEARNED, ev);
 }
 

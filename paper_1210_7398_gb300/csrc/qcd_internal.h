@@ -148,6 +148,7 @@ struct qcd_ctx {
     int sms_override = 0;    // SM count the SAP plan is made for (0: ask the device); diagnostics
     int sap_form = 0;        // SSOR lanes per site update: 0 by occupancy, 1 warp form (32), 2 octet form (8)
     int inject_breakdown = 0;  // test hook: outer iterations still to start from rho = 0 (a host-made breakdown)
+    bool tc_skip_commit = false;  // test hook: the tensor-core layer issues no MMA or commit (its waits run out)
 
     // workspace, grown on demand
     std::vector<void *> allocations;

@@ -176,3 +176,25 @@ def test_weights_file_round_trip(tmp_path):
     assert e.value.code == q.QCD_ERR_ARG
     s.close()
     s2.close()
+
+
+def test_tensor_core_layer_wait_runs_out_cleanly():
+    """The tcgen05 8 -> 8 layer with its MMA commits withheld (a test hook; no device fault):
+    its bounded mbarrier waits run out, it frees its tensor memory and returns, the call reports
+    QCD_ERR_TIMEOUT, and the same context then computes the correction exactly as before."""
+    dims = (8, 8, 8, 8)
+    s, _ = setup(dims)
+    q.qcd_learned_set_weights(s.ctx, q.learned_init_weights(3))
+    v = torch.from_numpy(qi.gaussian_spinor(dims, seed=2017)[0].astype(np.complex64)).cuda()
+    y0 = torch.empty_like(v)
+    q.qcd_learned_apply(s.ctx, y0, v)
+    q.qcd_debug_tc_skip_commit(s.ctx, True)
+    with pytest.raises(q.QcdError) as e:
+        q.qcd_learned_apply(s.ctx, torch.empty_like(v), v)
+    assert e.value.code == q.QCD_ERR_TIMEOUT
+    q.qcd_debug_tc_skip_commit(s.ctx, False)
+    y1 = torch.empty_like(v)
+    q.qcd_learned_apply(s.ctx, y1, v)
+    torch.cuda.synchronize()
+    assert torch.equal(y1, y0)
+    s.close()
