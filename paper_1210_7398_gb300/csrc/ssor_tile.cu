@@ -196,8 +196,9 @@ struct TileArgs {
     const float4 *v;           // the SAP input (read in the first cycle)
     const uint4 *rec;          // records of this colour's blocks, [block][vol] x TileRec::bytes
     const int4 *pos;           // [vol][2] per level position: (global offset from the block origin,
-                               // block-local site, neighbours 0|1 << 16, 2|3 << 16), (4|5 << 16, 6|7 << 16, 0, 0);
-                               // a neighbour outside the block is the zero slot vol
+                               // shared-memory slot, neighbour slots 0|1 << 16, 2|3 << 16),
+                               // (4|5 << 16, 6|7 << 16, block-local site, 0); a neighbour outside
+                               // the block is a zero slot (>= vol)
     const int *lev_ptr;        // [nlev + 1] first level position of each level
     const int *origin_site;    // [blocks of this colour] global index of the block origin
     const int *origin;         // [blocks of this colour][4] coordinates of the block origin
@@ -212,7 +213,35 @@ struct TileArgs {
     int cross;                 // add the hops from the other colour's last block solutions first
     int store_r;               // the residual is needed by a later cycle
     int store_y;               // the block solutions are needed by the next launch
+    // FP16 storage: the block solutions y as FP16 site records [rhs][V] x 48 bytes (the words of
+    // the block spinor in shared memory) and their scales [block of either colour][rhs]; the
+    // values are y16 x scale, exactly those the kernel holds
+    uint4 *y16;
+    float *yscale;
+    int b[4], nb[4];           // block extents, blocks per direction
+    int blk_base, other_base;  // index in yscale of this colour's first block, of the other colour's
 };
+
+// the other colour's block solution at site mm (coordinates xn) for one right-hand side: FP32 in
+// the lattice layout, or (FP16 storage) the FP16 record times its block's scale
+template <bool HALF>
+__device__ __forceinline__ void load_y_other(const TileArgs &a, int rhs, long mm, const int xn[4], float2 psi[12]) {
+    if constexpr (HALF) {
+        // blocks of one colour are listed in lexicographic order (x fastest) and alternate in
+        // colour along x, whose block count is even: the rank among its colour is lex / 2
+        const int lex = xn[0] / a.b[0] + a.nb[0] * (xn[1] / a.b[1] + a.nb[1] * (xn[2] / a.b[2] + a.nb[2] * (xn[3] / a.b[3])));
+        const float sc = a.yscale[(size_t)(a.other_base + (lex >> 1)) * a.nrhs + rhs];
+        const uint4 *q = a.y16 + ((size_t)rhs * a.V + mm) * 3;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const uint4 v = q[k];
+            psi[4 * k] = cscale(h2f(v.x), sc); psi[4 * k + 1] = cscale(h2f(v.y), sc);
+            psi[4 * k + 2] = cscale(h2f(v.z), sc); psi[4 * k + 3] = cscale(h2f(v.w), sc);
+        }
+    } else {
+        load_spinor(a.y + (size_t)rhs * 6 * a.V, a.V, mm, psi);
+    }
+}
 
 // One colour of one SAP cycle (Eq. (4), Alg. 1, in residual form) on every block of that colour,
 // for the right-hand sides blockIdx.y * R ... + R - 1:
@@ -283,7 +312,6 @@ __global__ void __launch_bounds__(kTileMaxThreads, kTileMinBlocks) k_sap_tile(Ti
                         off %= st[mu];
                     }
                     const uint4 *rec = recb + (size_t)pos * L::chunks;
-                    const float4 *yr = a.y + (size_t)(rhs0 + r_me) * 6 * a.V;
                     float2 acc[12];
 #pragma unroll
                     for (int k = 0; k < 12; k++) acc[k] = make_float2(0.f, 0.f);
@@ -293,7 +321,9 @@ __global__ void __launch_bounds__(kTileMaxThreads, kTileMinBlocks) k_sap_tile(Ti
                         ld_link<HALF, 2 * MU>(rec, W);                                               \
                         const bool wrap = xg[MU] == a.L[MU] - 1;                                     \
                         const long mm = n0 + pa.x + (wrap ? -(long)(a.L[MU] - 1) * st[MU] : st[MU]); \
-                        load_spinor(yr, a.V, mm, psi);                                               \
+                        int xn[4] = {xg[0], xg[1], xg[2], xg[3]};                                    \
+                        xn[MU] = wrap ? 0 : xg[MU] + 1;                                              \
+                        load_y_other<HALF>(a, rhs0 + r_me, mm, xn, psi);                             \
                         hop_term_w<MU, true>(psi, W, acc, (MU == 3 && wrap) ? (float)a.bc_t : 1.f);  \
                     }                                                                                \
                     if (nb[2 * MU + 1] >= a.vol) {                                                   \
@@ -301,7 +331,9 @@ __global__ void __launch_bounds__(kTileMaxThreads, kTileMinBlocks) k_sap_tile(Ti
                         ld_link<HALF, 2 * MU + 1>(rec, W);                                           \
                         const bool wrap = xg[MU] == 0;                                               \
                         const long mm = n0 + pa.x + (wrap ? (long)(a.L[MU] - 1) * st[MU] : -st[MU]); \
-                        load_spinor(yr, a.V, mm, psi);                                               \
+                        int xn[4] = {xg[0], xg[1], xg[2], xg[3]};                                    \
+                        xn[MU] = wrap ? a.L[MU] - 1 : xg[MU] - 1;                                    \
+                        load_y_other<HALF>(a, rhs0 + r_me, mm, xn, psi);                             \
                         hop_term_w<MU, false>(psi, W, acc, (MU == 3 && wrap) ? (float)a.bc_t : 1.f); \
                     }
                     QCD_TILE_CROSS(0)
@@ -458,8 +490,23 @@ __global__ void __launch_bounds__(kTileMaxThreads, kTileMinBlocks) k_sap_tile(Ti
                 for (int k = 0; k < 12; k++) xv[k] = cadd(xv[k], yv[k]);
                 store_spinor(xr, a.V, pa.x, xv);
             }
-            if (a.store_y) store_spinor(yo4, a.V, pa.x, yv);
+            if (a.store_y) {
+                if constexpr (HALF) {
+                    // the FP16 words as they are; the scale is written once per block below
+                    const uint4 *src = reinterpret_cast<const uint4 *>(ys + pa.y * a.stride + r_me * L::y_words);
+                    uint4 *dst = a.y16 + ((size_t)(rhs0 + r_me) * a.V + n0 + pa.x) * 3;
+                    dst[0] = src[0];
+                    dst[1] = src[1];
+                    dst[2] = src[2];
+                } else {
+                    store_spinor(yo4, a.V, pa.x, yv);
+                }
+            }
         }
+    }
+    if constexpr (HALF) {
+        if (a.store_y && tid < R && act_s[tid])
+            a.yscale[(size_t)(a.blk_base + blk) * a.nrhs + rhs0 + tid] = scale_s[tid] > 0.f ? scale_s[tid] : 1.f;
     }
 }
 
@@ -765,6 +812,13 @@ int tile_sap_apply(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
     a.nrhs = nrhs;
     a.stride = R * (p.half ? TileRec<true>::y_words : TileRec<false>::y_words);
     a.zslots = p.tile_zslots;
+    // FP16 storage: y's FP16 records in the first half of the y field, the scales after them
+    a.y16 = reinterpret_cast<uint4 *>(y);
+    a.yscale = reinterpret_cast<float *>(a.y16 + (size_t)nrhs * c->lat.V * 3);
+    for (int m = 0; m < 4; m++) {
+        a.b[m] = p.b[m];
+        a.nb[m] = p.nb[m];
+    }
     void (*k)(TileArgs) = nullptr;
     switch (R) {
         case 1: k = p.half ? k_sap_tile<true, 1> : k_sap_tile<false, 1>; break;
@@ -783,6 +837,8 @@ int tile_sap_apply(qcd_ctx *c, const SapPlan &p, float4 *x, const float4 *v, flo
             a.cross = !(j == 0 && col == 0);
             a.store_r = !last;
             a.store_y = !(last && col == 1);
+            a.blk_base = col ? p.nblk[0] : 0;
+            a.other_base = col ? 0 : p.nblk[0];
             cudaEvent_t ev;
             prof_begin(c, QCD_K_SSOR, &ev);
             k<<<dim3(p.nblk[col], (nrhs + R - 1) / R), T, smem, c->stream>>>(a);
