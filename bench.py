@@ -70,6 +70,16 @@ def sap_flop_per_launch(V, nrhs, nsweep):
     return (V / 2) * nrhs * (2 * nsweep + 1) * TABLE1_FLOP_PER_SITE
 
 
+def sap_smem_bytes_per_launch(V, nrhs, nsweep, half=True):
+    """Shared-memory bytes one launch of the tile SAP kernel moves (one colour): per site and
+    right-hand side, each of the 2 nsweep site updates reads its 8 neighbours, its own y and f and
+    writes y (11 spinors); the epilogue's in-block operator reads 9; the FP16 source is written
+    once.  A spinor is 48 B in FP16 storage (96 B in FP32, which keeps f in global memory)."""
+    sp = 48 if half else 96
+    per_update = 11 if half else 10
+    return (V / 2) * nrhs * (2 * nsweep * per_update + 9 + (1 if half else 0)) * sp
+
+
 def kernel_model(cls, V, nrhs, prm, peaks):
     """(bound, algorithmic units per launch, unit, peak, peak source) for a kernel class; nrhs
     right-hand sides per launch."""
@@ -667,6 +677,7 @@ def run_gpu_on_stream(args, q, qi, torch, stream, rank, world, local):
     torch.cuda.empty_cache()
     fp32 = q.qcd_bench_fp32_peak(sv.ctx, 64)
     peaks["fp32_tflops"], peaks["fp32_source"] = fp32, "measured: FP32 FMA kernel (qcd_bench_fp32_peak) in this run"
+    smem_gbs = q.qcd_bench_smem_peak(sv.ctx, 256)
     b = point_sources_torch(torch, dims, 0, nsrc)
     # ---- the chosen set-up, tuned on one group of the headline's sources ----
     chosen, tune_info = tune_chosen(q, sv, b, args)
@@ -791,6 +802,13 @@ def run_gpu_on_stream(args, q, qi, torch, stream, rank, world, local):
                 "units_per_launch": units,
                 "model": "tile SAP launch (one colour, %d right-hand sides): V/2 x nrhs x (2 nsweep + 1) x 1896 "
                          "flop (Table 1), time from a profiled pass of one group of the chosen solve" % g}
+        if dom == "ssor":
+            sb = sap_smem_bytes_per_launch(V, g, chosen_p.nsweep, chosen_p.sap_storage == q.QCD_F16)
+            roof["smem"] = {"achieved": sb / (avg_ms * 1e-3) / 1e9, "peak": smem_gbs, "unit": "GB/s",
+                            "frac": sb / (avg_ms * 1e-3) / 1e9 / smem_gbs,
+                            "peak_source": "measured: conflict-free 16-byte shared loads (qcd_bench_smem_peak)",
+                            "model": "per (site, right-hand side): 2 nsweep x 11 spinors (8 neighbours, y, f read, "
+                                     "y written) + 9 in the epilogue + 1 source write, 48 B each in FP16 storage"}
         src = "paper_1210_7398_gb300/csrc/ssor_tile.cu"
         t = NCU_TRAFFIC.get(dom)
         if t and t["sha"] == source_sha(src):
@@ -860,7 +878,7 @@ def run_gpu_on_stream(args, q, qi, torch, stream, rank, world, local):
            "outer_precision": outer_prec,
            "oracle_check": oracle_check, "tuning": tune_info,
            "e2e": e2e, "gpu_launches": launches, "kernels": kstats, "clocks": clk, "roofline": roof,
-           "fp32_peak_tflops": fp32, "dslash": dsl, "cpu_baseline": cpu, "small_12x12x12x24": small,
+           "fp32_peak_tflops": fp32, "smem_peak_gbs": smem_gbs, "dslash": dsl, "cpu_baseline": cpu, "small_12x12x12x24": small,
            "point_sources_24x24x24x48": src24}
     if learned is not None:
         out["learned_24x24x24x48"] = learned

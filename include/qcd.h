@@ -420,6 +420,11 @@ int qcd_bench_dslash(qcd_ctx *ctx, int prec, int nrhs, int iters);
  * Synchronises. */
 int qcd_bench_fp32_peak(qcd_ctx *ctx, int iters, double *tflops);
 
+/* Measures the shared-memory load bandwidth of the GPU (GB/s, all SMs): conflict-free 16-byte
+ * loads from a 32 KB buffer, four CTAs of 512 threads per SM; iters scales the run time
+ * (64 is about a millisecond).  Synchronises. */
+int qcd_bench_smem_peak(qcd_ctx *ctx, int iters, double *gbs);
+
 #ifdef __cplusplus
 }
 #endif

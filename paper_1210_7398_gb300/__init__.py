@@ -28,7 +28,7 @@ EXPORTS = ("qcd_create", "qcd_destroy", "qcd_last_error", "qcd_set_boundary", "q
            "qcd_kernel_stats", "qcd_launch_count", "qcd_bench_dslash", "qcd_sap_precondition_noalloc",
            "qcd_set_sap_ctas", "qcd_set_sap_form", "qcd_sap_plan_tables", "qcd_set_graphs", "qcd_autotune", "qcd_learned_weight_count",
            "qcd_learned_set_weights", "qcd_learned_get_weights", "qcd_learned_apply", "qcd_learned_loss_grad",
-           "qcd_learned_train", "qcd_learned_evaluate", "qcd_solve_multi", "qcd_set_tune_cache", "qcd_bench_fp32_peak",
+           "qcd_learned_train", "qcd_learned_evaluate", "qcd_solve_multi", "qcd_set_tune_cache", "qcd_bench_fp32_peak", "qcd_bench_smem_peak",
            "qcd_debug_inject_breakdown", "qcd_learned_save", "qcd_learned_load", "qcd_debug_tc_skip_commit")
 
 
@@ -112,6 +112,7 @@ def load_library(path: str = LIB_PATH):
         "qcd_bench_dslash": (I, [P, I, I, I]),
         "qcd_set_tune_cache": (I, [ctypes.c_char_p]),
         "qcd_bench_fp32_peak": (I, [P, I, ctypes.POINTER(D)]),
+        "qcd_bench_smem_peak": (I, [P, I, ctypes.POINTER(D)]),
         "qcd_debug_inject_breakdown": (I, [P, I]),
         "qcd_debug_tc_skip_commit": (I, [P, I]),
         "qcd_learned_save": (I, [P, ctypes.c_char_p]),
@@ -388,6 +389,13 @@ def qcd_bench_fp32_peak(ctx, iters: int = 64) -> float:
     """Measured FP32 FMA throughput of the context's GPU, TFLOP/s."""
     t = ctypes.c_double()
     _check(ctx, load_library().qcd_bench_fp32_peak(ctx, int(iters), ctypes.byref(t)))
+    return t.value
+
+
+def qcd_bench_smem_peak(ctx, iters: int = 64) -> float:
+    """Measured shared-memory load bandwidth of the GPU in GB/s."""
+    t = ctypes.c_double()
+    _check(ctx, load_library().qcd_bench_smem_peak(ctx, int(iters), ctypes.byref(t)))
     return t.value
 
 

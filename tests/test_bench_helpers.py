@@ -27,3 +27,11 @@ def test_derived_fp32_peak_and_oracle_scale():
     assert math.isclose(p["fp32_tflops"], 152 * 128 * 2 * p["sm_max_mhz"] * 1e6 / 1e12, rel_tol=1e-12)
     # 48^3 x 96 has 1296 times the sites of 8^3 x 16; 12 sources
     assert bench.oracle_scale() == 1296 * 12
+
+
+def test_sap_shared_memory_model():
+    V = 24 * 24 * 24 * 48
+    # FP16 storage, 2 sweeps: per (site, right-hand side) 4 x 11 + 9 + 1 spinors of 48 B
+    assert math.isclose(bench.sap_smem_bytes_per_launch(V, 4, 2), V / 2 * 4 * 54 * 48, rel_tol=1e-12)
+    # FP32 storage keeps f in global memory: 4 x 10 + 9 spinors of 96 B
+    assert math.isclose(bench.sap_smem_bytes_per_launch(V, 4, 2, half=False), V / 2 * 4 * 49 * 96, rel_tol=1e-12)

@@ -178,3 +178,10 @@ def test_fp32_outer_operator_reaches_tolerance_through_restarts():
         s.solve(np.zeros_like(b), b, q.make_params(kappa, CSW, (4, 4, 4, 4), (2, 2, 2, 2), outer_precision=2), nrhs=2)
     assert e.value.code == q.QCD_ERR_ARG
     s.close()
+
+
+def test_smem_peak_hook():
+    s = q.Solver((4, 4, 4, 4))
+    t = q.qcd_bench_smem_peak(s.ctx, 64)
+    assert 5000.0 < t < 100000.0, t  # GB300: 152 SMs x 128 B per cycle x about 2 GHz is about 40 TB/s
+    s.close()
