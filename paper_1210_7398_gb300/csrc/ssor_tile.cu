@@ -158,18 +158,56 @@ template <bool HALF, int B> __device__ __forceinline__ void herm6_rec(const uint
 #pragma unroll
         for (int k = 0; k < 15; k++) o[k] = make_float2(f[6 + 2 * k], f[7 + 2 * k]);
     }
+    // packed FP32 pairs: A_i = sum_j Re(H_ij) x_j, E_i = sum_j s_ij Im(H_ij) x_j with s = +1 below
+    // the diagonal (H_ij) and -1 above it (conj(H_ji)); y_i = (A_i.x - E_i.y, A_i.y + E_i.x)
+    float2 A[6], E[6];
 #pragma unroll
-    for (int i = 0; i < 6; i++) y[i] = cscale(x[i], d[i]);
+    for (int i = 0; i < 6; i++) {
+        A[i] = __fmul2_rn(make_float2(d[i], d[i]), x[i]);
+        E[i] = make_float2(0.f, 0.f);
+    }
     int k = 0;
 #pragma unroll
     for (int i = 1; i < 6; i++) {
 #pragma unroll
         for (int j = 0; j < i; j++) {
-            y[i] = cfma(o[k], x[j], y[i]);   // row i gets H_ij x_j
-            y[j] = cfmac(o[k], x[i], y[j]);  // row j gets conj(H_ij) x_i
+            const float2 hr = make_float2(o[k].x, o[k].x), hi = make_float2(o[k].y, o[k].y);
+            A[i] = __ffma2_rn(hr, x[j], A[i]);  // row i gets H_ij x_j
+            E[i] = __ffma2_rn(hi, x[j], E[i]);
+            A[j] = __ffma2_rn(hr, x[i], A[j]);  // row j gets conj(H_ij) x_i
+            E[j] = __ffma2_rn(make_float2(-o[k].y, -o[k].y), x[i], E[j]);
             k++;
         }
     }
+#pragma unroll
+    for (int i = 0; i < 6; i++) y[i] = make_float2(A[i].x - E[i].y, A[i].y + E[i].x);
+}
+
+// The hop of fields.cuh's hop_term_w (W h, W = U_mu(n) forward or U_mu(n-mu)^dag backward, row
+// major) with the colour multiply in packed FP32 pairs: for each row a, p = sum_b Re(W_ab) h_b and
+// q = sum_b Im(W_ab) h_b, and (W h)_a = (p.x - q.y, p.y + q.x).
+template <int MU, bool FWD>
+__device__ __forceinline__ void hop_term_w2(const float2 psi[12], const float2 W[9], float2 acc[12], float sgn = 1.f) {
+    float2 h[6];
+    hop_project<MU, FWD>(psi, sgn, h);
+    float2 w[6];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const float2 r0 = make_float2(W[a * 3].x, W[a * 3].x), i0 = make_float2(W[a * 3].y, W[a * 3].y);
+        float2 p0 = __fmul2_rn(r0, h[0]), q0 = __fmul2_rn(i0, h[0]);
+        float2 p1 = __fmul2_rn(r0, h[3]), q1 = __fmul2_rn(i0, h[3]);
+#pragma unroll
+        for (int b = 1; b < 3; b++) {
+            const float2 rb = make_float2(W[a * 3 + b].x, W[a * 3 + b].x), ib = make_float2(W[a * 3 + b].y, W[a * 3 + b].y);
+            p0 = __ffma2_rn(rb, h[b], p0);
+            q0 = __ffma2_rn(ib, h[b], q0);
+            p1 = __ffma2_rn(rb, h[3 + b], p1);
+            q1 = __ffma2_rn(ib, h[3 + b], q1);
+        }
+        w[a] = make_float2(p0.x - q0.y, p0.y + q0.x);
+        w[3 + a] = make_float2(p1.x - q1.y, p1.y + q1.x);
+    }
+    hop_reconstruct<MU, FWD>(w, acc);
 }
 
 // out = F v for a Dirac-basis spinor (the chiral blocks of F/2 applied to v_u -/+ v_l), one
@@ -324,7 +362,7 @@ __global__ void __launch_bounds__(kTileMaxThreads, kTileMinBlocks) k_sap_tile(Ti
                         int xn[4] = {xg[0], xg[1], xg[2], xg[3]};                                    \
                         xn[MU] = wrap ? 0 : xg[MU] + 1;                                              \
                         load_y_other<HALF>(a, rhs0 + r_me, mm, xn, psi);                             \
-                        hop_term_w<MU, true>(psi, W, acc, (MU == 3 && wrap) ? (float)a.bc_t : 1.f);  \
+                        hop_term_w2<MU, true>(psi, W, acc, (MU == 3 && wrap) ? (float)a.bc_t : 1.f); \
                     }                                                                                \
                     if (nb[2 * MU + 1] >= a.vol) {                                                   \
                         float2 W[9], psi[12];                                                        \
@@ -334,7 +372,7 @@ __global__ void __launch_bounds__(kTileMaxThreads, kTileMinBlocks) k_sap_tile(Ti
                         int xn[4] = {xg[0], xg[1], xg[2], xg[3]};                                    \
                         xn[MU] = wrap ? a.L[MU] - 1 : xg[MU] - 1;                                    \
                         load_y_other<HALF>(a, rhs0 + r_me, mm, xn, psi);                             \
-                        hop_term_w<MU, false>(psi, W, acc, (MU == 3 && wrap) ? (float)a.bc_t : 1.f); \
+                        hop_term_w2<MU, false>(psi, W, acc, (MU == 3 && wrap) ? (float)a.bc_t : 1.f);\
                     }
                     QCD_TILE_CROSS(0)
                     QCD_TILE_CROSS(1)
@@ -399,7 +437,7 @@ __global__ void __launch_bounds__(kTileMaxThreads, kTileMinBlocks) k_sap_tile(Ti
             float2 W[9], psi[12];                                                         \
             ld_link<HALF, D>(rec, W);                                                     \
             ld_y<HALF>(ys + nb[D] * a.stride + r_me * L::y_words, psi);                   \
-            hop_term_w<D / 2, (D & 1) == 0>(psi, W, acc);                                 \
+            hop_term_w2<D / 2, (D & 1) == 0>(psi, W, acc);                                \
         }
         QCD_TILE_HOP(0)
         QCD_TILE_HOP(1)
