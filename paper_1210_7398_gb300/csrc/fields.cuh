@@ -41,6 +41,11 @@ template <typename C> __device__ __forceinline__ C cfmac(C a, C b, C acc) {
 // i*a, -i*a
 template <typename C> __device__ __forceinline__ C cmuli(C a) { return cmk<C>(-a.y, a.x); }
 template <typename C> __device__ __forceinline__ C cmulmi(C a) { return cmk<C>(a.y, -a.x); }
+// FP32 complex sums as one packed FP32x2 add each (the same IEEE sums, half the instructions)
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 caddi(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.y, b.x)); }
+__device__ __forceinline__ float2 csubi(float2 a, float2 b) { return __fadd2_rn(a, make_float2(b.y, -b.x)); }
 
 // ---- loads / stores in the internal layouts ---------------------------------
 

@@ -40,7 +40,6 @@ template <bool HALF> struct TileRec {
     static constexpr int bytes = clover_off + (HALF ? 144 : 288);  // 336 / 672
     static constexpr int chunks = bytes / 16;
     static constexpr int y_words = HALF ? 12 : 24;  // 4-byte words of one site spinor in shared memory
-    static constexpr int y_chunks = y_words / 4;
 };
 static_assert(TileRec<true>::bytes == kTileRecordBytesHalf && TileRec<false>::bytes == kTileRecordBytes,
               "tile record size");
