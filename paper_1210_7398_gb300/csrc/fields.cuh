@@ -46,6 +46,7 @@ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 __device__ __forceinline__ float2 caddi(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.y, b.x)); }
 __device__ __forceinline__ float2 csubi(float2 a, float2 b) { return __fadd2_rn(a, make_float2(b.y, -b.x)); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return __fmul2_rn(a, make_float2(s, s)); }
 
 // ---- loads / stores in the internal layouts ---------------------------------
 
@@ -252,6 +253,20 @@ __device__ __forceinline__ void hop_term_w(const C psi[12], const C W[9], C acc[
 
 // third row of a special unitary 3x3 matrix from its first two: row2 = conj(row0 x row1)
 // (Table 1's reconstruction of a link from 12 reals)
+template <typename C> __device__ __forceinline__ void su3_third_row(C W[9]);
+// FP32: each entry conj(W_k W_{3+l} - W_l W_{3+k}) from packed pairs p = Re(W_k) W_{3+l} -
+// Re(W_l) W_{3+k} and q = Im(W_k) W_{3+l} - Im(W_l) W_{3+k}: the product is (p.x - q.y, p.y + q.x)
+template <> __device__ __forceinline__ void su3_third_row<float2>(float2 W[9]) {
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        const int k = (j + 1) % 3, l = (j + 2) % 3;
+        float2 p = __fmul2_rn(make_float2(W[k].x, W[k].x), W[3 + l]);
+        float2 q = __fmul2_rn(make_float2(W[k].y, W[k].y), W[3 + l]);
+        p = __ffma2_rn(make_float2(-W[l].x, -W[l].x), W[3 + k], p);
+        q = __ffma2_rn(make_float2(-W[l].y, -W[l].y), W[3 + k], q);
+        W[6 + j] = make_float2(p.x - q.y, -(p.y + q.x));
+    }
+}
 template <typename C> __device__ __forceinline__ void su3_third_row(C W[9]) {
 #pragma unroll
     for (int j = 0; j < 3; j++) {

@@ -461,10 +461,12 @@ __global__ void __launch_bounds__(kTileMaxThreads, kTileMinBlocks) k_sap_tile(Ti
         float *yp = ys + pa.y * a.stride + r_me * L::y_words;
         float2 yo[12];
         ld_y<HALF>(yp, yo);
+        // y <- y + omega (f + kappa F H y - y), packed FP32 pairs
+        const float2 kap = make_float2(a.kappa, a.kappa), om = make_float2(a.omega, a.omega);
 #pragma unroll
         for (int k = 0; k < 12; k++) {
-            const float tx = fmaf(a.kappa, fa[k].x, fv[k].x), ty = fmaf(a.kappa, fa[k].y, fv[k].y);
-            yo[k] = make_float2(fmaf(a.omega, tx - yo[k].x, yo[k].x), fmaf(a.omega, ty - yo[k].y, yo[k].y));
+            const float2 t = __ffma2_rn(kap, fa[k], fv[k]);
+            yo[k] = __ffma2_rn(om, __fadd2_rn(t, make_float2(-yo[k].x, -yo[k].y)), yo[k]);
         }
         st_y<HALF>(yp, yo);
     };
