@@ -45,9 +45,9 @@ D_BYTES_PER_SITE = {"f32": 768, "f64": 1536, "f16": 480, "su3": 672}  # in + out
 L2_BYTES = 126 << 20
 # DRAM bytes (read + write) per unit of work of a kernel, from one ncu capture of the kernel
 # source identified by its SHA-256 prefix; reported only while the source is unchanged
-NCU_TRAFFIC = {"ssor": {"sha": "dced587a3d56aa02", "bytes_per_site_rhs": 1039.0,
+NCU_TRAFFIC = {"ssor": {"sha": "08bd50dfec66ed03", "bytes_per_site_rhs": 1059.6,
                          "capture": "ncu, k_sap_tile<FP16, 4> on 24^3x48 (4^4 / 2^4 blocks, 4 right-hand sides): "
-                                    "1.224 GB (colour without cross hops) and 1.430 GB (with) per launch, weighted "
+                                    "1.239 GB (colour without cross hops) and 1.462 GB (with) per launch, weighted "
                                     "1:3 as in a 2-cycle SAP application, per (site, right-hand side) of a colour, "
                                     "scaled to this launch"}}
 
