@@ -316,7 +316,9 @@ __device__ __forceinline__ void transport_item(const unsigned char *xs, const fl
 // fragments read by ldmatrix.
 template <int CIN, int COUT, int FIN, int FOUT>
 __global__ void __launch_bounds__(kLayerWarps * 32, FIN == SITE32 ? 1 : 2) k_layer(void *y, const void *x, const float2 *__restrict__ U,
-                                                               const __nv_bfloat16 *__restrict__ Bt, Geo g) {
+                                                               const __nv_bfloat16 *__restrict__ Bt, Geo g,
+                                                               const BicgScalars *__restrict__ gate = nullptr) {
+    if (gate && !gate->active) return;  // a right-hand side that has left the iteration
     using S = LayerSmem<CIN, COUT, FIN>;
     constexpr int KDP = S::KDP, N = S::N, AS = S::AS, NT = N / 8, XS = S::XS;
     constexpr int NTH = kLayerWarps * 32;
@@ -406,7 +408,9 @@ __global__ void __launch_bounds__(kLayerWarps * 32, FIN == SITE32 ? 1 : 2) k_lay
 template <int CIN, int FIN, int FOUT>
 __global__ void __launch_bounds__(kLayerWarps * 32, 2) k_layer_wfirst(void *y, const void *x,
                                                                       const float2 *__restrict__ U,
-                                                                      const __nv_bfloat16 *__restrict__ Bt, Geo g) {
+                                                                      const __nv_bfloat16 *__restrict__ Bt, Geo g,
+                                                                      const BicgScalars *__restrict__ gate = nullptr) {
+    if (gate && !gate->active) return;  // a right-hand side that has left the iteration
     using S = LayerSmem<CIN, 1, FIN>;
     constexpr int KDP = S::KDP, AS = S::AS, XS = S::XS;
     constexpr int NTH = kLayerWarps * 32;
@@ -612,16 +616,18 @@ __global__ void k_wgrad_finish(float2 *__restrict__ grad, const float *__restric
 
 // r = a - b (plane layout FP32, 6 float4 per site); r may be b (each element is read and
 // written by one thread)
-__global__ void k_sub_plane(float4 *r, const float4 *a, const float4 *b, long n) {
+__global__ void k_sub_plane(float4 *r, const float4 *a, const float4 *b, long n,
+                            const BicgScalars *__restrict__ gate = nullptr) {
     const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || (gate && !gate->active)) return;
     const float4 x = a[i], y = b[i];
     r[i] = make_float4(x.x - y.x, x.y - y.y, x.z - y.z, x.w - y.w);
 }
 // x += y (plane layout FP32)
-__global__ void k_add_plane(float4 *__restrict__ x, const float4 *__restrict__ y, long n) {
+__global__ void k_add_plane(float4 *__restrict__ x, const float4 *__restrict__ y, long n,
+                            const BicgScalars *__restrict__ gate = nullptr) {
     const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || (gate && !gate->active)) return;
     const float4 a = x[i], b = y[i];
     x[i] = make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
 }
@@ -700,7 +706,7 @@ Geo geo(const qcd_ctx *c) {
 }
 
 template <int CIN, int COUT, int FIN, int FOUT>
-int launch_layer(qcd_ctx *c, void *y, const void *x, const __nv_bfloat16 *Bt) {
+int launch_layer(qcd_ctx *c, void *y, const void *x, const __nv_bfloat16 *Bt, const BicgScalars *gate = nullptr) {
     constexpr size_t smem = LayerSmem<CIN, COUT, FIN>::total;
     static std::atomic<unsigned long long> attr{0};
     static std::mutex attr_mu;
@@ -713,12 +719,14 @@ int launch_layer(qcd_ctx *c, void *y, const void *x, const __nv_bfloat16 *Bt) {
     const long tiles = (c->lat.V + kLayerSites - 1) / kLayerSites;
     cudaEvent_t ev;
     prof_begin(c, QCD_K_LEARNED, &ev);
-    k_layer<CIN, COUT, FIN, FOUT><<<(unsigned)tiles, kLayerWarps * 32, smem, c->stream>>>(y, x, c->U32, Bt, geo(c));
+    k_layer<CIN, COUT, FIN, FOUT><<<(unsigned)tiles, kLayerWarps * 32, smem, c->stream>>>(y, x, c->U32, Bt, geo(c),
+                                                                                       gate);
     return prof_end(c, QCD_K_LEARNED, ev);
 }
 
 template <int CIN, int FIN, int FOUT>
-int launch_layer_wfirst(qcd_ctx *c, void *y, const void *x, const __nv_bfloat16 *Bt) {
+int launch_layer_wfirst(qcd_ctx *c, void *y, const void *x, const __nv_bfloat16 *Bt,
+                        const BicgScalars *gate = nullptr) {
     constexpr size_t smem = LayerSmem<CIN, 1, FIN>::total + sizeof(float2) * kLayerRows * 4;
     static std::atomic<unsigned long long> attr{0};
     static std::mutex attr_mu;
@@ -731,7 +739,8 @@ int launch_layer_wfirst(qcd_ctx *c, void *y, const void *x, const __nv_bfloat16 
     const long tiles = (c->lat.V + kLayerSites - 1) / kLayerSites;
     cudaEvent_t ev;
     prof_begin(c, QCD_K_LEARNED, &ev);
-    k_layer_wfirst<CIN, FIN, FOUT><<<(unsigned)tiles, kLayerWarps * 32, smem, c->stream>>>(y, x, c->U32, Bt, geo(c));
+    k_layer_wfirst<CIN, FIN, FOUT><<<(unsigned)tiles, kLayerWarps * 32, smem, c->stream>>>(y, x, c->U32, Bt, geo(c),
+                                                                                        gate);
     return prof_end(c, QCD_K_LEARNED, ev);
 }
 
@@ -855,15 +864,16 @@ int learned_get_weights(qcd_ctx *c, float2 *w_host) {
     return QCD_OK;
 }
 
-// y = N(x) for one right-hand side in the FP32 plane layout (layers 1 -> 8 -> 8 -> 1)
-int learned_forward(qcd_ctx *c, float4 *y, const float4 *x) {
+// y = N(x) for one right-hand side in the FP32 plane layout (layers 1 -> 8 -> 8 -> 1); with
+// gate, every kernel returns at once while that right-hand side is inactive
+int learned_forward(qcd_ctx *c, float4 *y, const float4 *x, const BicgScalars *gate) {
     Learned &L = c->net;
     if (!L.ready) return fail(c, QCD_ERR_STATE, "no learned weights set");
     int rc = ensure_net(c);
     if (rc) return rc;
-    if ((rc = launch_layer<1, 8, PLANE32, SITE16>(c, L.a1, x, L.B + layer_boff(0, false)))) return rc;
-    if ((rc = learned_layer_tc(c, L.a2, L.a1, L.B + layer_boff(1, false), false))) return rc;
-    return launch_layer_wfirst<8, SITE16, PLANE32>(c, y, L.a2, L.B + layer_boff(2, false));
+    if ((rc = launch_layer<1, 8, PLANE32, SITE16>(c, L.a1, x, L.B + layer_boff(0, false), gate))) return rc;
+    if ((rc = learned_layer_tc(c, L.a2, L.a1, L.B + layer_boff(1, false), false, gate))) return rc;
+    return launch_layer_wfirst<8, SITE16, PLANE32>(c, y, L.a2, L.B + layer_boff(2, false), gate);
 }
 
 // loss of one pair (rho: plane layout FP32, eps: site layout FP32) and, with accumulate,
@@ -929,18 +939,21 @@ int learned_zero_grad(qcd_ctx *c) {
 
 // out = out + N(v - D out) for nrhs right-hand sides (plane layout): the learned correction
 // applied after SAP; w1, w2: two scratch spinors of nrhs fields each
-int learned_correct(qcd_ctx *c, float4 *out, const float4 *v, float4 *w1, float4 *w2, int nrhs) {
+int learned_correct(qcd_ctx *c, float4 *out, const float4 *v, float4 *w1, float4 *w2, int nrhs,
+                    const BicgScalars *gate) {
     const long n4 = 6 * c->lat.V;
     int rc;
-    if ((rc = dslash32(c, w1, out, nrhs))) return rc;
+    if ((rc = dslash32_dot(c, w1, out, nrhs, nullptr, 0, nullptr, gate))) return rc;
     for (int k = 0; k < nrhs; k++) {
+        const BicgScalars *gk = gate ? gate + k : nullptr;
         cudaEvent_t ev;
         prof_begin(c, QCD_K_LEARNED, &ev);
-        k_sub_plane<<<(unsigned)((n4 + 255) / 256), 256, 0, c->stream>>>(w1 + k * n4, v + k * n4, w1 + k * n4, n4);
+        k_sub_plane<<<(unsigned)((n4 + 255) / 256), 256, 0, c->stream>>>(w1 + k * n4, v + k * n4, w1 + k * n4, n4,
+                                                                         gk);
         if ((rc = prof_end(c, QCD_K_LEARNED, ev))) return rc;
-        if ((rc = learned_forward(c, w2, w1 + k * n4))) return rc;
+        if ((rc = learned_forward(c, w2, w1 + k * n4, gk))) return rc;
         prof_begin(c, QCD_K_LEARNED, &ev);
-        k_add_plane<<<(unsigned)((n4 + 255) / 256), 256, 0, c->stream>>>(out + k * n4, w2, n4);
+        k_add_plane<<<(unsigned)((n4 + 255) / 256), 256, 0, c->stream>>>(out + k * n4, w2, n4, gk);
         if ((rc = prof_end(c, QCD_K_LEARNED, ev))) return rc;
     }
     return QCD_OK;

@@ -216,7 +216,8 @@ __device__ __forceinline__ void tc_transport(unsigned char *Ab, const void *x, c
 template <int FIN, int FOUT>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_layer_tc(void *y, const void *x, const float2 *__restrict__ U, const __nv_bfloat16 *__restrict__ Bt, Geo g,
-               int ntiles, int *status, int skip_commit) {
+               int ntiles, int *status, int skip_commit, const BicgScalars *__restrict__ gate) {
+    if (gate && !gate->active) return;  // a right-hand side that has left the iteration (uniform)
     extern __shared__ unsigned char tc_raw[];
     unsigned char *sm = tc_raw + ((1024u - (smem_u32(tc_raw) & 1023u)) & 1023u);
     unsigned char *Bs = sm + kOffB, *As = sm + kOffA;
@@ -373,7 +374,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 template <int FIN, int FOUT>
-int launch_tc(qcd_ctx *c, void *y, const void *x, const __nv_bfloat16 *Bt) {
+int launch_tc(qcd_ctx *c, void *y, const void *x, const __nv_bfloat16 *Bt, const BicgScalars *gate) {
     static std::atomic<unsigned long long> attr{0};
     static std::mutex attr_mu;
     if (int arc = once_per_device(attr, attr_mu, c->device, [&]() -> int {
@@ -392,15 +393,16 @@ int launch_tc(qcd_ctx *c, void *y, const void *x, const __nv_bfloat16 *Bt) {
     cudaEvent_t ev;
     prof_begin(c, QCD_K_LEARNED, &ev);
     k_layer_tc<FIN, FOUT><<<grid, kTcThreads, kTcSmem, c->stream>>>(y, x, c->U32, Bt, g, (int)tiles, c->d_status,
-                                                                   c->tc_skip_commit ? 1 : 0);
+                                                                   c->tc_skip_commit ? 1 : 0, gate);
     return prof_end(c, QCD_K_LEARNED, ev);
 }
 
 }  // namespace
 
-int learned_layer_tc(qcd_ctx *c, void *y, const void *x, const __nv_bfloat16 *Bt, bool fp32_io) {
+int learned_layer_tc(qcd_ctx *c, void *y, const void *x, const __nv_bfloat16 *Bt, bool fp32_io,
+                     const BicgScalars *gate) {
     if (c->lat.V >= (1L << 31) - kTcSites) return fail(c, QCD_ERR_ARG, "lattice too large for the learned layer");
-    return fp32_io ? launch_tc<TC_SITE32, TC_SITE32>(c, y, x, Bt) : launch_tc<TC_SITE16, TC_SITE16>(c, y, x, Bt);
+    return fp32_io ? launch_tc<TC_SITE32, TC_SITE32>(c, y, x, Bt, gate) : launch_tc<TC_SITE16, TC_SITE16>(c, y, x, Bt, gate);
 }
 
 int learned_tc_status(qcd_ctx *c) {

@@ -353,16 +353,19 @@ int learned_set_weights(qcd_ctx *c, const float2 *w, bool on_device);
 int learned_get_weights(qcd_ctx *c, float2 *w_host);
 int learned_sync_B(qcd_ctx *c);
 // y = N(x), one right-hand side, plane layout FP32
-int learned_forward(qcd_ctx *c, float4 *y, const float4 *x);
+int learned_forward(qcd_ctx *c, float4 *y, const float4 *x, const BicgScalars *gate = nullptr);
 // loss of one pair (rho plane layout, eps site layout FP32); gradient added to net.grad
 int learned_loss_grad(qcd_ctx *c, const float4 *rho, const float2 *eps, double *loss, float4 *ybuf);
 int learned_zero_grad(qcd_ctx *c);
 int learned_adam(qcd_ctx *c, float lr);
 // out += N(v - D out) per right-hand side; w1, w2 scratch of nrhs fields
-int learned_correct(qcd_ctx *c, float4 *out, const float4 *v, float4 *w1, float4 *w2, int nrhs);
+// out += N(v - D out) for every right-hand side active in gate (may be null: all)
+int learned_correct(qcd_ctx *c, float4 *out, const float4 *v, float4 *w1, float4 *w2, int nrhs,
+                    const BicgScalars *gate = nullptr);
 // the hidden 8 -> 8 layer on the tcgen05 tensor cores (BF16 site records in and out, or FP32 with
 // fp32_io); Bt: its [9][64][64] BF16 B matrices
-int learned_layer_tc(qcd_ctx *c, void *y, const void *x, const __nv_bfloat16 *Bt, bool fp32_io);
+int learned_layer_tc(qcd_ctx *c, void *y, const void *x, const __nv_bfloat16 *Bt, bool fp32_io,
+                     const BicgScalars *gate = nullptr);
 // QCD_ERR_TIMEOUT (and the flag cleared) if a tensor-core layer gave up a wait since the last
 // check; synchronises the stream
 int learned_tc_status(qcd_ctx *c);

@@ -53,12 +53,12 @@ int inner_iteration(qcd_ctx *c, const Ws &w, const qcd_params *p) {
     TRY(scalars(c, SC_BETA, w.Si, w.red, R, p->inner_tol, nullptr));
     TRY(blas_p_update32(c, f2(w.ip), f2(w.ir), f2(w.iv), w.Si, n, R));
     TRY(sap_apply(c, w.ipt, w.ip, w.sapw, p->omega, p->nsweep, p->nsap, R, w.Si, p->block_solver));
-    if (p->learned) TRY(learned_correct(c, w.ipt, w.ip, w.iv, reinterpret_cast<float4 *>(c->net.tmp), R));
+    if (p->learned) TRY(learned_correct(c, w.ipt, w.ip, w.iv, reinterpret_cast<float4 *>(c->net.tmp), R, w.Si));
     TRY(dslash32_dot(c, w.iv, w.ipt, R, w.irh, 1, w.red, w.Si));  // v = D p~; <rh, v>, |v|^2
     TRY(scalars(c, SC_ALPHA, w.Si, w.red, R, p->inner_tol, nullptr));
     TRY(blas_s_update32(c, f2(w.is), f2(w.ir), f2(w.iv), w.Si, n, R));
     TRY(sap_apply(c, w.ist, w.is, w.sapw, p->omega, p->nsweep, p->nsap, R, w.Si, p->block_solver));
-    if (p->learned) TRY(learned_correct(c, w.ist, w.is, w.it, reinterpret_cast<float4 *>(c->net.tmp), R));
+    if (p->learned) TRY(learned_correct(c, w.ist, w.is, w.it, reinterpret_cast<float4 *>(c->net.tmp), R, w.Si));
     TRY(dslash32_dot(c, w.it, w.ist, R, w.is, 2, w.red, w.Si));  // t = D s~; <t, s>, |t|^2
     TRY(scalars(c, SC_OMEGA, w.Si, w.red, R, p->inner_tol, nullptr));
     // y += alpha p~ + omega s~, r = s - omega t; <rh, r>, |r|^2
