@@ -71,7 +71,7 @@ int time_solve(qcd_ctx *c, double2 *xi, const double2 *bi, int nrhs, const qcd_p
 // ---- on-disk cache of tuning results (one JSON object per line) ----
 std::mutex g_cache_mu;
 std::string g_cache_path;
-constexpr const char *kTunerVersion = "sap-tile-2";
+constexpr const char *kTunerVersion = "sap-tile-3";
 
 std::string cache_key(qcd_ctx *c, int nrhs, const qcd_params *b, int max_candidates) {
     cudaDeviceProp prop;
@@ -110,12 +110,12 @@ bool cache_lookup(const std::string &key, const qcd_params *base, qcd_params *be
         double t = 0;
         const int n = std::sscanf(line + head.size(),
                                   "\"block\": [%d, %d, %d, %d], \"subblock\": [%d, %d, %d, %d], "
-                                  "\"sap_storage\": %d, \"sap_ctas\": %d, \"nsweep\": %d, \"nsap\": %d, "
-                                  "\"rhs_group\": %d, \"ms\": %lf",
+                                  "\"omega\": %lf, \"sap_storage\": %d, \"sap_ctas\": %d, \"nsweep\": %d, "
+                                  "\"nsap\": %d, \"rhs_group\": %d, \"ms\": %lf",
                                   &p.block[0], &p.block[1], &p.block[2], &p.block[3], &p.subblock[0], &p.subblock[1],
-                                  &p.subblock[2], &p.subblock[3], &p.sap_storage, &p.sap_ctas, &p.nsweep, &p.nsap,
-                                  &p.rhs_group, &t);
-        if (n == 14) {
+                                  &p.subblock[2], &p.subblock[3], &p.omega, &p.sap_storage, &p.sap_ctas, &p.nsweep,
+                                  &p.nsap, &p.rhs_group, &t);
+        if (n == 15) {
             *best = p;
             *ms = t;
             found = true;  // the last matching line wins
@@ -132,10 +132,11 @@ void cache_store(const std::string &key, const qcd_params *p, double ms) {
     if (!f) return;
     std::fprintf(f,
                  "{\"key\": \"%s\", \"block\": [%d, %d, %d, %d], \"subblock\": [%d, %d, %d, %d], "
-                 "\"sap_storage\": %d, \"sap_ctas\": %d, \"nsweep\": %d, \"nsap\": %d, \"rhs_group\": %d, "
-                 "\"ms\": %.6f}\n",
+                 "\"omega\": %.17g, \"sap_storage\": %d, \"sap_ctas\": %d, \"nsweep\": %d, \"nsap\": %d, "
+                 "\"rhs_group\": %d, \"ms\": %.6f}\n",
                  key.c_str(), p->block[0], p->block[1], p->block[2], p->block[3], p->subblock[0], p->subblock[1],
-                 p->subblock[2], p->subblock[3], p->sap_storage, p->sap_ctas, p->nsweep, p->nsap, p->rhs_group, ms);
+                 p->subblock[2], p->subblock[3], p->omega, p->sap_storage, p->sap_ctas, p->nsweep, p->nsap,
+                 p->rhs_group, ms);
     std::fclose(f);
 }
 
@@ -188,7 +189,8 @@ extern "C" int qcd_autotune(qcd_ctx *c, const double *b, int nrhs, const qcd_par
     const bool old_prof = c->prof.on;
     c->prof.on = false;
 
-    // stage 1: block splits and sub-block splits, FP32 storage, base sweeps and cycles
+    // stage 1: block and sub-block splits, ranked with the fast tile form, FP16 storage, 2 sweeps,
+    // 2 cycles and omega 1
     std::vector<Cand> cands;
     // block extents: the spatial ones alike, each dividing L with an even quotient
     const int extents[] = {2, 3, 4, 6, 8, 12, 16};
@@ -213,6 +215,9 @@ extern "C" int qcd_autotune(qcd_ctx *c, const double *b, int nrhs, const qcd_par
                 // where a block's spinor does not fit one CTA
                 cd.p.sap_storage = QCD_F16;
                 cd.p.sap_ctas = -2;
+                cd.p.nsweep = 2;
+                cd.p.nsap = 2;
+                cd.p.omega = 1.0;
                 cd.p.block_solver = 0;  // the tuner explores the ll-SSOR set-ups
                 cd.p.rhs_group = base->rhs_group;
                 cands.push_back(cd);
@@ -252,28 +257,49 @@ extern "C" int qcd_autotune(qcd_ctx *c, const double *b, int nrhs, const qcd_par
     }
     if (!rc) {
         std::sort(cands.begin(), cands.end(), [](const Cand &u, const Cand &v) { return u.ms < v.ms; });
-        // stage 2: refine the three fastest, the likeliest variants first (FP16 tile form with other
-        // sweep and cycle counts, then the other forms and storage)
+        // stage 2: a coordinate search from the fastest geometry, one parameter at a time, each
+        // move kept only if it is faster: the SSOR relaxation omega upwards in steps of 0.2 while it
+        // improves, then the SAP cycles (1, 3), the SSOR sweeps (3, 1), and last the other
+        // storage and kernel forms
         std::vector<Cand> more;
-        for (size_t i = 0; i < cands.size() && i < 3; i++) {
-            if (!cands[i].ok) continue;
-            for (int storage : {QCD_F16, QCD_F32})
-                for (int ctas : {-2, 0, 2})
-                    for (int ns : {2, 4})
-                        for (int np : {2, 4}) {
-                            Cand cd = cands[i];
-                            cd.p.sap_storage = storage;
-                            cd.p.sap_ctas = ctas;
-                            cd.p.nsweep = ns;
-                            cd.p.nsap = np;
-                            if (storage == cands[i].p.sap_storage && ctas == cands[i].p.sap_ctas &&
-                                ns == cands[i].p.nsweep && np == cands[i].p.nsap)
-                                continue;
-                            more.push_back(cd);
-                        }
+        if (!cands.empty() && cands[0].ok) {
+            Cand cur = cands[0];
+            auto try_move = [&](Cand cd) -> bool {
+                if (tried >= max_candidates || rc) return false;
+                rc = run(cd);
+                more.push_back(cd);
+                if (!rc && cd.ok && cd.ms < cur.ms) {
+                    cur = cd;
+                    return true;
+                }
+                return false;
+            };
+            for (double om = cur.p.omega + 0.2; om < 1.95; om += 0.2) {
+                Cand cd = cur;
+                cd.p.omega = om;
+                if (!try_move(cd)) break;
+            }
+            for (int np : {1, 3})
+                if (np != cur.p.nsap) {
+                    Cand cd = cur;
+                    cd.p.nsap = np;
+                    try_move(cd);
+                }
+            for (int ns : {3, 1})
+                if (ns != cur.p.nsweep) {
+                    Cand cd = cur;
+                    cd.p.nsweep = ns;
+                    try_move(cd);
+                }
+            const int forms[][2] = {{QCD_F32, -2}, {QCD_F16, 0}, {QCD_F32, 0}, {QCD_F16, 2}};
+            for (const auto &f : forms)
+                if (f[0] != cur.p.sap_storage || f[1] != cur.p.sap_ctas) {
+                    Cand cd = cur;
+                    cd.p.sap_storage = f[0];
+                    cd.p.sap_ctas = f[1];
+                    try_move(cd);
+                }
         }
-        for (auto &cd : more)
-            if ((rc = run(cd))) break;
         cands.insert(cands.end(), more.begin(), more.end());
     }
     if (!rc && nrhs > 1 && base->rhs_group == 0) {

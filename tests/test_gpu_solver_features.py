@@ -61,6 +61,7 @@ def test_tuning_cache_round_trip(tmp_path):
         assert len(lines) == 1
         rec = json.loads(lines[0])
         assert rec["block"] == list(best1.block) and rec["rhs_group"] == best1.rhs_group
+        assert rec["omega"] == best1.omega and rec["nsap"] == best1.nsap
         best2, ms2 = q.qcd_autotune(s.ctx, b, base, nrhs=2, max_candidates=6)  # served from the file
         assert q.params_dict(best2) == q.params_dict(best1)
         assert abs(ms2 - ms1) <= 1e-6 * max(1.0, ms1)
