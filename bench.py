@@ -45,11 +45,18 @@ D_BYTES_PER_SITE = {"f32": 768, "f64": 1536, "f16": 480, "su3": 672}  # in + out
 L2_BYTES = 126 << 20
 # DRAM bytes (read + write) per unit of work of a kernel, from one ncu capture of the kernel
 # source identified by its SHA-256 prefix; reported only while the source is unchanged
-NCU_TRAFFIC = {"ssor": {"sha": "08bd50dfec66ed03", "bytes_per_site_rhs": 1059.6,
+NCU_TRAFFIC = {"ssor": {"sha": "08bd50dfec66ed03", "first": 933.5, "cross": 1101.7,
                          "capture": "ncu, k_sap_tile<FP16, 4> on 24^3x48 (4^4 / 2^4 blocks, 4 right-hand sides): "
-                                    "1.239 GB (colour without cross hops) and 1.462 GB (with) per launch, weighted "
-                                    "1:3 as in a 2-cycle SAP application, per (site, right-hand side) of a colour, "
-                                    "scaled to this launch"}}
+                                    "1.239 GB for a colour without cross hops and 1.462 GB for one with them per "
+                                    "launch; per (site, right-hand side) of a colour, weighted by the launch types of "
+                                    "the chosen cycle count (one without cross hops per application) and scaled to "
+                                    "this launch"}}
+
+
+def sap_traffic_per_site_rhs(t, nsap):
+    """DRAM bytes per (site, right-hand side) of an average tile SAP launch: an application of
+    nsap cycles has 2 nsap launches, the first without cross hops."""
+    return (t["first"] + (2 * nsap - 1) * t["cross"]) / (2 * nsap)
 
 
 def volume(dims):
@@ -812,7 +819,7 @@ def run_gpu_on_stream(args, q, qi, torch, stream, rank, world, local):
         src = "paper_1210_7398_gb300/csrc/ssor_tile.cu"
         t = NCU_TRAFFIC.get(dom)
         if t and t["sha"] == source_sha(src):
-            roof["traffic"] = t["bytes_per_site_rhs"] * (V / 2) * g
+            roof["traffic"] = sap_traffic_per_site_rhs(t, chosen_p.nsap) * (V / 2) * g
             roof["traffic_source"] = t["capture"]
     dsl = []
     if not args.skip_dslash:

@@ -35,3 +35,11 @@ def test_sap_shared_memory_model():
     assert math.isclose(bench.sap_smem_bytes_per_launch(V, 4, 2), V / 2 * 4 * 54 * 48, rel_tol=1e-12)
     # FP32 storage keeps f in global memory: 4 x 10 + 9 spinors of 96 B
     assert math.isclose(bench.sap_smem_bytes_per_launch(V, 4, 2, half=False), V / 2 * 4 * 49 * 96, rel_tol=1e-12)
+
+
+def test_sap_traffic_weights_launch_types():
+    t = {"first": 900.0, "cross": 1100.0}
+    # 2 cycles: 4 launches, the first without cross hops
+    assert math.isclose(bench.sap_traffic_per_site_rhs(t, 2), (900 + 3 * 1100) / 4, rel_tol=1e-12)
+    # 1 cycle: one of each
+    assert math.isclose(bench.sap_traffic_per_site_rhs(t, 1), 1000.0, rel_tol=1e-12)
