@@ -41,7 +41,8 @@ SMALL = dict(dims=(12, 12, 12, 24), kappa=0.12, csw=1.6, eps=0.3, gauge_seed=100
 ORACLE_SAMPLE = dict(dims=(8, 8, 8, 16), gauge_seed=1005, kappa=0.122, csw=1.6, block=(4, 4, 4, 4),
                      subblock=(2, 2, 2, 2), omega=1.0, nsweep=2, nsap=2, tol=1e-10, inner_tol=1e-5)
 TABLE1_FLOP_PER_SITE = 1896  # flop per site of the clover hopping matrix without SU(3) reconstruction (Table 1)
-D_BYTES_PER_SITE = {"f32": 768, "f64": 1536, "f16": 480, "su3": 672}  # in + out spinor, 4 links (each shared by 2 sites), clover
+D_BYTES_PER_SITE = {"f32": 768, "f64": 1536, "f16": 480, "su3": 672,  # in + out spinor, 4 links (each shared by 2 sites), clover
+                    "x2": 1440}  # pair-of-FP32 D: FP32 in, FP64 out, hi + lo links and clover (the FP64 bytes)
 L2_BYTES = 126 << 20
 # DRAM bytes (read + write) per unit of work of a kernel, from one ncu capture of the kernel
 # source identified by its SHA-256 prefix; reported only while the source is unchanged
@@ -292,7 +293,7 @@ def dslash_bandwidth(q, qi, torch, stream, dims, iters, peaks, seed=1002, varian
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     out = []
     for prec, nrhs in variants:
-        pc = {"f32": q.QCD_F32, "f64": q.QCD_F64, "f16": q.QCD_F16, "su3": q.QCD_F32_SU3}[prec]
+        pc = {"f32": q.QCD_F32, "f64": q.QCD_F64, "f16": q.QCD_F16, "su3": q.QCD_F32_SU3, "x2": q.QCD_F32X2}[prec]
         q.qcd_bench_dslash(s.ctx, pc, nrhs, 3)
         times = []
         for _ in range(iters):
@@ -300,7 +301,7 @@ def dslash_bandwidth(q, qi, torch, stream, dims, iters, peaks, seed=1002, varian
             ms, _ = event_ms(torch, stream, lambda: q.qcd_bench_dslash(s.ctx, pc, nrhs, 1))
             times.append(ms)
         ms = statistics.median(times)
-        spin = 384 if prec == "f64" else 192  # FP16 storage keeps FP32 spinors
+        spin = {"f64": 384, "x2": 288}.get(prec, 192)  # FP16 storage keeps FP32 spinors
         field = D_BYTES_PER_SITE[prec] - spin
         byts = V * (spin * nrhs + field)
         gbs = byts / (ms * 1e-3) / 1e9
@@ -756,10 +757,11 @@ def run_gpu_on_stream(args, q, qi, torch, stream, rank, world, local):
         if n:
             kstats[nm] = {"launches": n, "ms": ms}
     q.qcd_set_profiling(sv.ctx, False)
-    # ---- the outer operator's precision: FP64 D (as timed) against the FP32 D for v = D p^ and
-    # t = D s^ with FP64 left to the true residual, the dots and x; one group of sources ----
+    # ---- the outer operator's precision: the FP64 D, the pair-of-FP32 D and the FP32 D for
+    # v = D p^ and t = D s^ (FP64 kept for the true residual, the dots and x); one group of
+    # sources with the chosen SAP set-up ----
     outer_prec = {}
-    for name, op in (("f64", q.QCD_F64), ("f32", q.QCD_F32)):
+    for name, op in (("f64", q.QCD_F64), ("f32x2", q.QCD_F32X2), ("f32", q.QCD_F32)):
         pp = q.qcd_params.from_buffer_copy(chosen_p)
         pp.outer_precision = op
         xg.zero_()
@@ -823,9 +825,10 @@ def run_gpu_on_stream(args, q, qi, torch, stream, rank, world, local):
             roof["traffic_source"] = t["capture"]
     dsl = []
     if not args.skip_dslash:
-        dsl += dslash_bandwidth(q, qi, torch, stream, dims, 10, peaks, variants=(("f32", 1), ("f32", 4), ("su3", 1)))
+        dsl += dslash_bandwidth(q, qi, torch, stream, dims, 10, peaks,
+                                variants=(("f32", 1), ("f32", 4), ("su3", 1), ("x2", 1), ("x2", 4)))
         dsl += dslash_bandwidth(q, qi, torch, stream, (24, 24, 24, 48), 20, peaks,
-                                variants=(("f32", 1), ("f32", 12), ("f16", 1), ("su3", 1), ("f64", 1)))
+                                variants=(("f32", 1), ("f32", 12), ("f16", 1), ("su3", 1), ("f64", 1), ("x2", 1)))
         if roof is not None and dsl:
             d = dsl[0]
             roof["dslash"] = {"kernel": "D FP32, 48^3x96, 1 right-hand side", "bound": "hbm", "achieved": d["GB_s"],

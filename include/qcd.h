@@ -78,8 +78,11 @@ enum {
 /* Precisions and storage forms.  QCD_F16 is the half-precision storage of the precision
  * pattern (FP32 arithmetic); the value 3 is not used (the SAP block spinors are kept per block in
  * units of their largest source component, so FP16's 10-bit mantissa, not BF16's exponent
- * range, is what the storage needs). */
-enum { QCD_F64 = 0, QCD_F32 = 1, QCD_F16 = 2, QCD_F32_SU3 = 4 };
+ * range, is what the storage needs).  QCD_F32X2 is pair-of-FP32 arithmetic: each FP64 link and
+ * clover entry held as hi + lo FP32 numbers, products and sums carried without losing the low
+ * part (Dekker's product with the FMA error term, Knuth's TwoSum), on an FP32 input; about 2^-46
+ * relative per site, on the FP32 pipe. */
+enum { QCD_F64 = 0, QCD_F32 = 1, QCD_F16 = 2, QCD_F32_SU3 = 4, QCD_F32X2 = 5 };
 
 /* Solver and SAP parameters (Sec. 2, Sec. 3, Eq. (4)). */
 typedef struct {
@@ -115,7 +118,10 @@ typedef struct {
                            memory (at least 1).  Results do not depend on it: each
                            right-hand side's iterates are those of its solve alone      */
     int outer_precision; /* qcd_solve, the outer BiCGStab's v = D p^ and t = D s^ (Sec. 2):
-                           QCD_F64 (0, the default): the FP64 D.  QCD_F32: the FP32 D
+                           QCD_F64 (0, the default): the FP64 D.  QCD_F32X2: the
+                           pair-of-FP32 D of the inner solver's FP32 output (exact in FP32),
+                           within about 1e-13 of the FP64 D and several times faster on
+                           GB300, whose FP64 rate is 1/64 of its FP32 rate.  QCD_F32: the FP32 D
                            applied to the inner solver's FP32 solution, widened to FP64;
                            FP64 then serves only the true residual b - D x, the dot
                            products and norms, and x.  The recursive residual then
@@ -163,8 +169,10 @@ int qcd_build_clover(qcd_ctx *ctx, double kappa, double csw);
  * FP16 copies are made on first use after each field change); QCD_F32_SU3:
  * complex64 in/out with each link stored as its first two rows and the third
  * rebuilt as the conjugate cross product (SU(3) 12-real form, Table 1: 672
- * instead of 768 bytes per site).  in and out must not overlap.  Requires
- * qcd_build_clover. */
+ * instead of 768 bytes per site); QCD_F32X2: complex64 in, complex128 out, computed in
+ * pair-of-FP32 arithmetic from the FP64 fields (hi + lo copies made on first use after each
+ * field change), within about 1e-13 of the FP64 D of the same input.  in and out must not
+ * overlap.  Requires qcd_build_clover. */
 int qcd_apply_D(qcd_ctx *ctx, void *out, const void *in, int prec, int nrhs);
 
 /* out = M_SAP in (Eq. (4), Alg. 1) in FP32 for nrhs right-hand sides:
@@ -411,8 +419,8 @@ int qcd_debug_tc_skip_commit(qcd_ctx *ctx, int on);
 
 /* D on internal-layout buffers only, repeated `iters` times (no layout
  * conversion): the kernel the memory-bandwidth roofline is measured on.
- * prec = QCD_F64, QCD_F32, QCD_F16 or QCD_F32_SU3; nrhs >= 1.  Work buffers are allocated on first
- * use and kept. */
+ * prec = QCD_F64, QCD_F32, QCD_F16, QCD_F32_SU3 or QCD_F32X2; nrhs >= 1.  Work buffers are
+ * allocated on first use and kept. */
 int qcd_bench_dslash(qcd_ctx *ctx, int prec, int nrhs, int iters);
 
 /* Measured FP32 FMA throughput of the context's GPU in TFLOP/s (2 flop per FMA): independent

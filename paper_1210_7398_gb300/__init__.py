@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libqcd.so")
 
 QCD_OK, QCD_ERR_ARG, QCD_ERR_CUDA, QCD_ERR_OOM = 0, -1, -2, -3
 QCD_ERR_SINGULAR, QCD_ERR_NOCONV, QCD_ERR_BREAKDOWN, QCD_ERR_TIMEOUT, QCD_ERR_STATE = -4, -5, -6, -7, -8
-QCD_F64, QCD_F32, QCD_F16, QCD_F32_SU3 = 0, 1, 2, 4
+QCD_F64, QCD_F32, QCD_F16, QCD_F32_SU3, QCD_F32X2 = 0, 1, 2, 4, 5
 QCD_K_DSLASH32, QCD_K_DSLASH64, QCD_K_SSOR, QCD_K_SAPHOP, QCD_K_BLAS, QCD_K_OTHER, QCD_K_LEARNED = range(7)
 KERNEL_CLASSES = ("dslash32", "dslash64", "ssor", "saphop", "blas", "other", "learned")
 
@@ -276,7 +276,7 @@ def params_dict(p: qcd_params) -> dict:
             "nsap": p.nsap, "sap_storage": {QCD_F32: "f32", QCD_F16: "f16"}.get(p.sap_storage, p.sap_storage),
             "sap_ctas": p.sap_ctas, "learned": p.learned,
             "block_solver": {0: "ll-ssor", 1: "even-odd mr"}.get(p.block_solver, p.block_solver),
-            "rhs_group": p.rhs_group, "outer_precision": {QCD_F64: "f64", QCD_F32: "f32"}.get(p.outer_precision)}
+            "rhs_group": p.rhs_group, "outer_precision": {QCD_F64: "f64", QCD_F32: "f32", QCD_F32X2: "f32x2"}.get(p.outer_precision)}
 
 
 LEARNED_CHANS = (1, 8, 8, 1)

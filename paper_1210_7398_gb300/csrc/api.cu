@@ -163,8 +163,8 @@ int check_params(qcd_ctx *c, const qcd_params *p) {
         return fail(c, QCD_ERR_ARG, "params.kappa/csw differ from the clover field built");
     if (p->sap_ctas < -2 || p->sap_ctas > 16) return fail(c, QCD_ERR_ARG, "sap_ctas must lie in -2..16");
     if (p->block_solver < 0 || p->block_solver > 1) return fail(c, QCD_ERR_ARG, "block_solver must be 0 or 1");
-    if (p->outer_precision != QCD_F64 && p->outer_precision != QCD_F32)
-        return fail(c, QCD_ERR_ARG, "outer_precision must be QCD_F64 or QCD_F32");
+    if (p->outer_precision != QCD_F64 && p->outer_precision != QCD_F32 && p->outer_precision != QCD_F32X2)
+        return fail(c, QCD_ERR_ARG, "outer_precision must be QCD_F64, QCD_F32 or QCD_F32X2");
     if (p->block_solver == 1 && (p->sap_storage != QCD_F32 || p->learned != 0))
         return fail(c, QCD_ERR_ARG, "block_solver 1 needs sap_storage QCD_F32 and learned 0");
     use_sap_ctas(c, p->sap_ctas);
@@ -221,7 +221,7 @@ void qcd_destroy(qcd_ctx *c) {
     else cudaDeviceSynchronize();
     void *bufs[] = {c->net.W, c->net.grad, c->net.m, c->net.v, c->net.B, c->net.P, c->net.scal, c->net.act,
                     c->net.pairs,
-                    c->U64, c->U32, c->F64, c->F32, c->U16, c->F16, c->U12, c->d_status, c->d_red, c->d_red_tiles, c->d_scalars, c->d_bicg, c->d_mask,
+                    c->U64, c->U32, c->F64, c->F32, c->U16, c->F16, c->U12, c->Ux2, c->Fx2, c->d_status, c->d_red, c->d_red_tiles, c->d_scalars, c->d_bicg, c->d_mask,
                     c->d_loop, c->ws64, c->ws32,
                     c->d_io, c->bench_in, c->bench_out, c->plan.d_origin[0] /* the plan's table region */,
                     c->plan.d_rec};
@@ -291,23 +291,31 @@ int qcd_apply_D(qcd_ctx *c, void *out, const void *in, int prec, int nrhs) {
     int rc = ready(c);
     if (rc) return rc;
     if ((rc = need_clover(c))) return rc;
-    if (!out || !in || nrhs < 1 || (prec != QCD_F64 && prec != QCD_F32 && prec != QCD_F16 && prec != QCD_F32_SU3))
+    if (!out || !in || nrhs < 1 ||
+        (prec != QCD_F64 && prec != QCD_F32 && prec != QCD_F16 && prec != QCD_F32_SU3 && prec != QCD_F32X2))
         return fail(c, QCD_ERR_ARG, "qcd_apply_D: bad pointer, nrhs or precision");
     const long V = c->lat.V;
     const size_t elem = (prec == QCD_F64) ? 16 : 8;
     const size_t bytes = elem * 12 * V * nrhs;
+    const size_t obytes = (prec == QCD_F32X2 ? 16 : elem) * 12 * V * nrhs;  // F32X2: complex64 in, complex128 out
     const bool dev_in = is_device_ptr(in), dev_out = is_device_ptr(out);
     if ((dev_in && !aligned16(in)) || (dev_out && !aligned16(out)))
         return fail(c, QCD_ERR_ARG, "device spinors must be 16-byte aligned");
-    if ((rc = ensure_io(c, 3 * bytes))) return rc;
+    if ((rc = ensure_io(c, 3 * obytes))) return rc;  // internal in, internal out, staged host in / out
     char *io = (char *)c->d_io;
     const void *din = in;
-    void *dout = dev_out ? out : io + 2 * bytes;
+    void *dout = dev_out ? out : io + 2 * obytes;
     if (!dev_in) {
-        QCD_CUDA(c, cudaMemcpyAsync(io + 2 * bytes, in, bytes, cudaMemcpyHostToDevice, c->stream));
-        din = io + 2 * bytes;
+        QCD_CUDA(c, cudaMemcpyAsync(io + 2 * obytes, in, bytes, cudaMemcpyHostToDevice, c->stream));
+        din = io + 2 * obytes;
     }
-    if (prec == QCD_F64) {
+    if (prec == QCD_F32X2) {
+        float4 *a = (float4 *)io;
+        double2 *b = (double2 *)(io + obytes);
+        if ((rc = spinor32_to_internal(c, a, (const float2 *)din, nrhs))) return rc;
+        if ((rc = dslash_x2(c, b, a, nrhs))) return rc;
+        if ((rc = spinor64_from_internal(c, (double2 *)dout, b, nrhs))) return rc;
+    } else if (prec == QCD_F64) {
         double2 *a = (double2 *)io, *b = (double2 *)(io + bytes);
         if ((rc = spinor64_to_internal(c, a, (const double2 *)din, nrhs))) return rc;
         if ((rc = dslash64(c, b, a, nrhs))) return rc;
@@ -318,7 +326,7 @@ int qcd_apply_D(qcd_ctx *c, void *out, const void *in, int prec, int nrhs) {
         if ((rc = (prec == QCD_F16 ? dslash16 : prec == QCD_F32_SU3 ? dslash12 : dslash32)(c, b, a, nrhs))) return rc;
         if ((rc = spinor32_from_internal(c, (float2 *)dout, b, nrhs))) return rc;
     }
-    if (!dev_out) QCD_CUDA(c, cudaMemcpyAsync(out, dout, bytes, cudaMemcpyDeviceToHost, c->stream));
+    if (!dev_out) QCD_CUDA(c, cudaMemcpyAsync(out, dout, obytes, cudaMemcpyDeviceToHost, c->stream));
     if (!dev_in || !dev_out) QCD_CUDA(c, cudaStreamSynchronize(c->stream));
     return QCD_OK;
 }
@@ -836,9 +844,10 @@ int qcd_bench_dslash(qcd_ctx *c, int prec, int nrhs, int iters) {
     int rc = ready(c);
     if (rc) return rc;
     if ((rc = need_clover(c))) return rc;
-    if ((prec != QCD_F64 && prec != QCD_F32 && prec != QCD_F16 && prec != QCD_F32_SU3) || nrhs < 1 || iters < 1)
+    if ((prec != QCD_F64 && prec != QCD_F32 && prec != QCD_F16 && prec != QCD_F32_SU3 && prec != QCD_F32X2) ||
+        nrhs < 1 || iters < 1)
         return fail(c, QCD_ERR_ARG, "qcd_bench_dslash: bad precision, nrhs or iters");
-    const size_t bytes = (prec == QCD_F64 ? 16 : 8) * 12 * c->lat.V * (size_t)nrhs;
+    const size_t bytes = (prec == QCD_F64 || prec == QCD_F32X2 ? 16 : 8) * 12 * c->lat.V * (size_t)nrhs;
     if (c->bench_bytes < bytes) {
         dev_free(c, c->bench_in);
         dev_free(c, c->bench_out);
@@ -852,6 +861,7 @@ int qcd_bench_dslash(qcd_ctx *c, int prec, int nrhs, int iters) {
     }
     for (int i = 0; i < iters; i++) {
         if (prec == QCD_F64) rc = dslash64(c, (double2 *)c->bench_out, (const double2 *)c->bench_in, nrhs);
+        else if (prec == QCD_F32X2) rc = dslash_x2(c, (double2 *)c->bench_out, (const float4 *)c->bench_in, nrhs);
         else if (prec == QCD_F16) rc = dslash16(c, (float4 *)c->bench_out, (const float4 *)c->bench_in, nrhs);
         else if (prec == QCD_F32_SU3) rc = dslash12(c, (float4 *)c->bench_out, (const float4 *)c->bench_in, nrhs);
         else rc = dslash32(c, (float4 *)c->bench_out, (const float4 *)c->bench_in, nrhs);

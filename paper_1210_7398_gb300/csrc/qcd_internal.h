@@ -136,6 +136,9 @@ struct qcd_ctx {
     long half_version = -1;  // field_version the FP16 copies were made from
     float4 *U12 = nullptr;   // links as their first two rows [4][3][V] (SU(3) 12-real form), made on first use
     long u12_version = -1;
+    float4 *Ux2 = nullptr;   // links [4][9][V] and clover [36][V] as hi + lo FP32 pairs (pair-arithmetic D)
+    float4 *Fx2 = nullptr;
+    long x2_version = -1;
     int *d_status = nullptr;  // device status word (clover singularity)
 
     // SAP plan cache (one geometry at a time)
@@ -224,6 +227,8 @@ int build_clover(qcd_ctx *c, double kappa, double csw);
 // operator D (dslash.cu)
 struct BicgScalars;
 int dslash64(qcd_ctx *c, double2 *out, const double2 *in, int nrhs);
+// D in pair-of-FP32 arithmetic: FP32 input (internal layout), FP64 output (internal layout)
+int dslash_x2(qcd_ctx *c, double2 *out, const float4 *in, int nrhs);
 int dslash32(qcd_ctx *c, float4 *out, const float4 *in, int nrhs);
 int dslash16(qcd_ctx *c, float4 *out, const float4 *in, int nrhs);
 int dslash12(qcd_ctx *c, float4 *out, const float4 *in, int nrhs);

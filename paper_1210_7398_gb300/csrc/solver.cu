@@ -220,8 +220,10 @@ int precondition(qcd_ctx *c, const Ws &w, const qcd_params *p, const double2 *in
 }
 
 // out = D y for the outer iteration, y the preconditioner's output (its FP32 original still in
-// w.y): the FP64 D, or with outer_precision QCD_F32 the FP32 D widened to FP64
+// w.y): the FP64 D; with outer_precision QCD_F32X2 the pair-of-FP32 D of the FP32 original (about
+// FP64 accuracy, on the FP32 pipe); with QCD_F32 the FP32 D widened to FP64
 int outer_D(qcd_ctx *c, const Ws &w, const qcd_params *p, double2 *out, const double2 *y) {
+    if (p->outer_precision == QCD_F32X2) return dslash_x2(c, out, w.y, w.nrhs);
     if (p->outer_precision == QCD_F32) {
         TRY(dslash32(c, w.iv, w.y, w.nrhs));
         return spinor32_to_64(c, out, w.iv, w.nrhs);

@@ -71,7 +71,7 @@ int time_solve(qcd_ctx *c, double2 *xi, const double2 *bi, int nrhs, const qcd_p
 // ---- on-disk cache of tuning results (one JSON object per line) ----
 std::mutex g_cache_mu;
 std::string g_cache_path;
-constexpr const char *kTunerVersion = "sap-tile-3";
+constexpr const char *kTunerVersion = "sap-tile-4";
 
 std::string cache_key(qcd_ctx *c, int nrhs, const qcd_params *b, int max_candidates) {
     cudaDeviceProp prop;
@@ -111,11 +111,11 @@ bool cache_lookup(const std::string &key, const qcd_params *base, qcd_params *be
         const int n = std::sscanf(line + head.size(),
                                   "\"block\": [%d, %d, %d, %d], \"subblock\": [%d, %d, %d, %d], "
                                   "\"omega\": %lf, \"sap_storage\": %d, \"sap_ctas\": %d, \"nsweep\": %d, "
-                                  "\"nsap\": %d, \"rhs_group\": %d, \"ms\": %lf",
+                                  "\"nsap\": %d, \"rhs_group\": %d, \"outer_precision\": %d, \"ms\": %lf",
                                   &p.block[0], &p.block[1], &p.block[2], &p.block[3], &p.subblock[0], &p.subblock[1],
                                   &p.subblock[2], &p.subblock[3], &p.omega, &p.sap_storage, &p.sap_ctas, &p.nsweep,
-                                  &p.nsap, &p.rhs_group, &t);
-        if (n == 15) {
+                                  &p.nsap, &p.rhs_group, &p.outer_precision, &t);
+        if (n == 16) {
             *best = p;
             *ms = t;
             found = true;  // the last matching line wins
@@ -133,10 +133,10 @@ void cache_store(const std::string &key, const qcd_params *p, double ms) {
     std::fprintf(f,
                  "{\"key\": \"%s\", \"block\": [%d, %d, %d, %d], \"subblock\": [%d, %d, %d, %d], "
                  "\"omega\": %.17g, \"sap_storage\": %d, \"sap_ctas\": %d, \"nsweep\": %d, \"nsap\": %d, "
-                 "\"rhs_group\": %d, \"ms\": %.6f}\n",
+                 "\"rhs_group\": %d, \"outer_precision\": %d, \"ms\": %.6f}\n",
                  key.c_str(), p->block[0], p->block[1], p->block[2], p->block[3], p->subblock[0], p->subblock[1],
                  p->subblock[2], p->subblock[3], p->omega, p->sap_storage, p->sap_ctas, p->nsweep, p->nsap,
-                 p->rhs_group, ms);
+                 p->rhs_group, p->outer_precision, ms);
     std::fclose(f);
 }
 
@@ -258,9 +258,10 @@ extern "C" int qcd_autotune(qcd_ctx *c, const double *b, int nrhs, const qcd_par
     if (!rc) {
         std::sort(cands.begin(), cands.end(), [](const Cand &u, const Cand &v) { return u.ms < v.ms; });
         // stage 2: a coordinate search from the fastest geometry, one parameter at a time, each
-        // move kept only if it is faster: the SSOR relaxation omega upwards in steps of 0.2 while it
-        // improves, then the SAP cycles (1, 3), the SSOR sweeps (3, 1), and last the other
-        // storage and kernel forms
+        // move kept only if it is faster: first the outer operator in pair-of-FP32 arithmetic
+        // where the base asks for the FP64 one (the same accuracy), then the SSOR relaxation omega
+        // upwards in steps of 0.2 while it improves, the SAP cycles (1, 3), the SSOR sweeps (3, 1),
+        // and last the other storage and kernel forms
         std::vector<Cand> more;
         if (!cands.empty() && cands[0].ok) {
             Cand cur = cands[0];
@@ -274,6 +275,11 @@ extern "C" int qcd_autotune(qcd_ctx *c, const double *b, int nrhs, const qcd_par
                 }
                 return false;
             };
+            if (cur.p.outer_precision == QCD_F64) {
+                Cand cd = cur;
+                cd.p.outer_precision = QCD_F32X2;
+                try_move(cd);
+            }
             for (double om = cur.p.omega + 0.2; om < 1.95; om += 0.2) {
                 Cand cd = cur;
                 cd.p.omega = om;

@@ -43,7 +43,7 @@ def main(argv=None):
     ap.add_argument("--nsap", type=int, default=2)
     ap.add_argument("--storage", choices=["f32", "f16"], default="f16")
     ap.add_argument("--ctas", type=int, default=-2, help="SSOR kernel form (qcd_set_sap_ctas)")
-    ap.add_argument("--prec", choices=["f64", "f32", "f16", "su3"], default="f32")
+    ap.add_argument("--prec", choices=["f64", "f32", "f16", "su3", "x2"], default="f32")
     ap.add_argument("--nrhs", type=int, default=4)
     ap.add_argument("--reps", type=int, default=3)
     a = ap.parse_args(argv)
@@ -87,7 +87,8 @@ def main(argv=None):
                 q.qcd_learned_apply(s.ctx, y, v)
             out["nrhs"] = 1
         else:
-            pc = {"f32": q.QCD_F32, "f64": q.QCD_F64, "f16": q.QCD_F16, "su3": q.QCD_F32_SU3}[a.prec]
+            pc = {"f32": q.QCD_F32, "f64": q.QCD_F64, "f16": q.QCD_F16, "su3": q.QCD_F32_SU3,
+                  "x2": q.QCD_F32X2}[a.prec]
             q.qcd_bench_dslash(s.ctx, pc, a.nrhs, 1)
             q.qcd_set_profiling(s.ctx, True)
             for k in range(len(q.KERNEL_CLASSES)):

@@ -61,6 +61,43 @@ def test_dslash_fp64_fp32_vs_oracle(dims, bc_t):
     s.close()
 
 
+
+@pytest.mark.parametrize("dims,bc_t", [((4, 4, 4, 4), 1), ((6, 4, 4, 6), -1), ((8, 8, 8, 16), 1),
+                                       ((2, 6, 4, 2), -1)])
+def test_dslash_pair_fp32_vs_oracle(dims, bc_t):
+    """QCD_F32X2: D of an FP32 input in pair-of-FP32 arithmetic, against the oracle's FP64 D of the
+    same (exactly widened) input.  Hi + lo links and clover carry 2^-48 of each FP64 entry; every
+    product keeps its FMA error and every leading sum its TwoSum error, so what is lost is the FP32
+    rounding of the low parts (about 2^-24 of 2^-24 per term, over some 200 terms a site): the same
+    1e-13 bound as the FP64 D.  Ragged volumes (96 and 576 sites), three right-hand sides, and the
+    hi + lo copies following a change of the clover field."""
+    kappa = 0.12
+    s, U, F = make_solver(dims, kappa, seed=1000, bc_t=bc_t)
+    psi32 = qi.gaussian_spinor(dims, seed=2000, nrhs=3).astype(np.complex64)
+    psi = psi32.astype(np.complex128)
+    ref = np.stack([oracle.apply_D(dims, U, F, kappa, psi[k], bc_t=bc_t) for k in range(3)])
+    dev = torch.from_numpy(psi32).cuda()
+    out = torch.empty(dev.shape, dtype=torch.complex128, device="cuda")
+    s.apply_D(out, dev, q.QCD_F32X2, nrhs=3)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    for k in range(3):
+        assert rel_max(got[k], ref[k]) <= 1e-13
+        assert rel_norm(got[k], ref[k]) <= 1e-13
+    # far closer than the FP32 D: the low parts carry the FP64 fields
+    out32 = torch.empty_like(dev)
+    s.apply_D(out32, dev, q.QCD_F32, nrhs=3)
+    torch.cuda.synchronize()
+    assert rel_norm(got[0], ref[0]) < 1e-5 * rel_norm(out32[0].cpu().numpy().astype(np.complex128), ref[0])
+    # host buffers, and the copies made again after the fields change
+    s.build_clover(0.11, CSW)
+    _, F2 = oracle.clover(dims, U, CSW, 0.11)
+    host_out = np.empty(psi.shape, dtype=np.complex128)
+    s.apply_D(host_out, psi32, q.QCD_F32X2, nrhs=3)
+    ref2 = oracle.apply_D(dims, U, F2, 0.11, psi[1], bc_t=bc_t)
+    assert rel_max(host_out[1], ref2) <= 1e-13
+    s.close()
+
 # FP16 storage of links and clover (FP32 arithmetic and spinors): each stored
 # value carries a relative rounding of at most 2^-11 = 4.9e-4; the hop sum and
 # the clover product add a few of them, so 2e-3 relative in norm.

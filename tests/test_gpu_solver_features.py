@@ -181,6 +181,36 @@ def test_fp32_outer_operator_reaches_tolerance_through_restarts():
     s.close()
 
 
+
+def test_pair_fp32_outer_operator_matches_fp64_outer():
+    """outer_precision = QCD_F32X2: the outer v = D p^ and t = D s^ in pair-of-FP32 arithmetic on
+    the inner solver's FP32 output.  Its error (about 1e-14 of D) is far below the tolerance, so the
+    solve takes the FP64 outer's iterations, needs no restart, and ends at 1e-10 under the oracle's
+    D, with a solution within the tolerance of the FP64-outer one."""
+    dims, kappa = (8, 8, 8, 8), 0.12
+    s, U = make_solver(dims, kappa, seed=1014)
+    b = qi.gaussian_spinor(dims, seed=2014, nrhs=2)
+    _, F = oracle.clover(dims, U, CSW, kappa)
+    xs, stats = {}, {}
+    for name, op in (("f64", q.QCD_F64), ("x2", q.QCD_F32X2)):
+        prm = q.make_params(kappa, CSW, (4, 4, 4, 4), (2, 2, 2, 2), nsweep=2, nsap=2, tol=1e-10,
+                            outer_precision=op)
+        x = np.zeros_like(b)
+        st = s.solve(x, b, prm, nrhs=2)
+        assert st["status"] == q.QCD_OK and st["true_rel_res"] <= 1e-10
+        for k in range(2):
+            r = b[k] - oracle.apply_D(dims, U, F, kappa, x[k])
+            assert np.linalg.norm(r) / np.linalg.norm(b[k]) <= 1e-10
+        xs[name], stats[name] = x, st
+    assert stats["x2"]["restarts"] == 0
+    assert stats["x2"]["outer_iters"] == stats["f64"]["outer_iters"]
+    assert abs(stats["x2"]["inner_iters"] - stats["f64"]["inner_iters"]) <= 2
+    for k in range(2):
+        assert np.linalg.norm(xs["x2"][k] - xs["f64"][k]) <= 1e-8 * np.linalg.norm(xs["f64"][k])
+    assert q.params_dict(q.make_params(kappa, CSW, (4, 4, 4, 4), (2, 2, 2, 2),
+                                       outer_precision=q.QCD_F32X2))["outer_precision"] == "f32x2"
+    s.close()
+
 def test_smem_peak_hook():
     s = q.Solver((4, 4, 4, 4))
     t = q.qcd_bench_smem_peak(s.ctx, 64)
