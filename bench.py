@@ -635,7 +635,8 @@ def headline_params(q, chosen):
                           nsap=p["nsap"], tol=w["tol"], inner_tol=w["inner_tol"], rhs_group=w["rhs_group"])
     ch = q.make_params(w["kappa"], w["csw"], tuple(chosen.block), tuple(chosen.subblock), omega=chosen.omega,
                        nsweep=chosen.nsweep, nsap=chosen.nsap, tol=w["tol"], inner_tol=w["inner_tol"],
-                       sap_storage=chosen.sap_storage, sap_ctas=chosen.sap_ctas, rhs_group=w["rhs_group"])
+                       sap_storage=chosen.sap_storage, sap_ctas=chosen.sap_ctas, rhs_group=w["rhs_group"],
+                       outer_precision=chosen.outer_precision)
     return plain, ch
 
 

@@ -43,3 +43,16 @@ def test_sap_traffic_weights_launch_types():
     assert math.isclose(bench.sap_traffic_per_site_rhs(t, 2), (900 + 3 * 1100) / 4, rel_tol=1e-12)
     # 1 cycle: one of each
     assert math.isclose(bench.sap_traffic_per_site_rhs(t, 1), 1000.0, rel_tol=1e-12)
+
+
+def test_headline_params_keep_every_tuned_knob():
+    """The timed chosen set-up is the tuner's result as a whole, outer operator form included;
+    the plain set-up keeps the FP64 outer operator."""
+    import paper_1210_7398_gb300 as q
+    tuned = q.make_params(0.122, 1.6, (4, 4, 4, 4), (2, 2, 2, 2), omega=1.4, nsweep=2, nsap=1,
+                          sap_storage=q.QCD_F16, sap_ctas=-2, outer_precision=q.QCD_F32X2)
+    plain, chosen = bench.headline_params(q, tuned)
+    for f in ("omega", "nsweep", "nsap", "sap_storage", "sap_ctas", "outer_precision"):
+        assert getattr(chosen, f) == getattr(tuned, f), f
+    assert tuple(chosen.block) == (4, 4, 4, 4) and tuple(chosen.subblock) == (2, 2, 2, 2)
+    assert plain.outer_precision == q.QCD_F64
