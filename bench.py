@@ -46,18 +46,19 @@ D_BYTES_PER_SITE = {"f32": 768, "f64": 1536, "f16": 480, "su3": 672,  # in + out
 L2_BYTES = 126 << 20
 # DRAM bytes (read + write) per unit of work of a kernel, from one ncu capture of the kernel
 # source identified by its SHA-256 prefix; reported only while the source is unchanged
-NCU_TRAFFIC = {"ssor": {"sha": "08bd50dfec66ed03", "first": 933.5, "cross": 1101.7,
-                         "capture": "ncu, k_sap_tile<FP16, 4> on 24^3x48 (4^4 / 2^4 blocks, 4 right-hand sides): "
-                                    "1.239 GB for a colour without cross hops and 1.462 GB for one with them per "
-                                    "launch; per (site, right-hand side) of a colour, weighted by the launch types of "
-                                    "the chosen cycle count (one without cross hops per application) and scaled to "
-                                    "this launch"}}
+NCU_TRAFFIC = {"ssor": {"sha": "08bd50dfec66ed03", "nsap": 1, "nsweep": 2, "per_launch": [634.1, 703.9],
+                         "capture": "ncu, k_sap_tile<FP16, 4> on 24^3x48 (4^4 / 2^4 blocks, 4 right-hand sides, "
+                                    "2 sweeps, 1 cycle): DRAM bytes per (site, right-hand side) of the colour of "
+                                    "each launch of one application, averaged and scaled to this launch"}}
 
 
-def sap_traffic_per_site_rhs(t, nsap):
-    """DRAM bytes per (site, right-hand side) of an average tile SAP launch: an application of
-    nsap cycles has 2 nsap launches, the first without cross hops."""
-    return (t["first"] + (2 * nsap - 1) * t["cross"]) / (2 * nsap)
+def sap_traffic_per_site_rhs(t, nsap, nsweep):
+    """DRAM bytes per (site, right-hand side) of an average tile SAP launch, from the launches of one
+    captured application; None unless the capture's cycle and sweep counts are the chosen ones
+    (the launches of an application differ in cross hops, kept residual and copied-out y)."""
+    if not t.get("per_launch") or (t["nsap"], t["nsweep"]) != (nsap, nsweep):
+        return None
+    return sum(t["per_launch"]) / len(t["per_launch"])
 
 
 def volume(dims):
@@ -72,27 +73,39 @@ def source_sha(rel):
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def sap_flop_per_launch(V, nrhs, nsweep):
-    """Algorithmic flops of one launch of the tile SAP kernel (one colour): V/2 sites x nrhs x
-    (2 nsweep SSOR site updates + the residual's in-block operator) x Table 1's 1896 flop."""
-    return (V / 2) * nrhs * (2 * nsweep + 1) * TABLE1_FLOP_PER_SITE
+def sap_updates_per_launch(nsweep, nsap):
+    """Site updates per (site, right-hand side) of an average tile SAP launch: 2 nsweep SSOR passes,
+    and the residual's in-block operator in the launches whose colour has a later cycle (the first
+    2 (nsap - 1) of the 2 nsap launches of an application; the last cycle keeps no residual)."""
+    return 2 * nsweep + (nsap - 1) / nsap
 
 
-def sap_smem_bytes_per_launch(V, nrhs, nsweep, half=True):
-    """Shared-memory bytes one launch of the tile SAP kernel moves (one colour): per site and
+def sap_flop_per_launch(V, nrhs, nsweep, nsap):
+    """Algorithmic flops of an average launch of the tile SAP kernel (one colour): V/2 sites x nrhs
+    x its site updates x Table 1's 1896 flop."""
+    return (V / 2) * nrhs * sap_updates_per_launch(nsweep, nsap) * TABLE1_FLOP_PER_SITE
+
+
+def sap_smem_bytes_per_launch(V, nrhs, nsweep, nsap, half=True):
+    """Shared-memory bytes an average launch of the tile SAP kernel moves (one colour): per site and
     right-hand side, each of the 2 nsweep site updates reads its 8 neighbours, its own y and f and
-    writes y (11 spinors); the epilogue's in-block operator reads 9; the FP16 source is written
-    once.  A spinor is 48 B in FP16 storage (96 B in FP32, which keeps f in global memory)."""
+    writes y (11 spinors); the epilogue reads y for x += y, and the residual's in-block operator 9
+    more where the residual is kept (2 (nsap - 1) of the 2 nsap launches); with FP16 storage the
+    source is written once and y copied out where the next launch reads it (all but the last
+    launch).  A spinor is 48 B in FP16 storage (96 B in FP32, which keeps f in global memory)."""
     sp = 48 if half else 96
     per_update = 11 if half else 10
-    return (V / 2) * nrhs * (2 * nsweep * per_update + 9 + (1 if half else 0)) * sp
+    spinors = 2 * nsweep * per_update + 1 + 9 * (nsap - 1) / nsap
+    if half:
+        spinors += 1 + (2 * nsap - 1) / (2 * nsap)
+    return (V / 2) * nrhs * spinors * sp
 
 
 def kernel_model(cls, V, nrhs, prm, peaks):
     """(bound, algorithmic units per launch, unit, peak, peak source) for a kernel class; nrhs
     right-hand sides per launch."""
     if cls == "ssor":
-        return ("alu", sap_flop_per_launch(V, nrhs, prm["nsweep"]) / 1e12, "TFLOP/s", peaks["fp32_tflops"],
+        return ("alu", sap_flop_per_launch(V, nrhs, prm["nsweep"], prm["nsap"]) / 1e12, "TFLOP/s", peaks["fp32_tflops"],
                 peaks["fp32_source"])
     if cls == "dslash32":
         return "hbm", V * (192 * nrhs + 576) / 1e9, "GB/s", peaks["hbm_gbs"], peaks["source"]
@@ -802,7 +815,7 @@ def run_gpu_on_stream(args, q, qi, torch, stream, rank, world, local):
     # ---- roofline of the dominant kernel class (time from the profiled pass) ----
     dom = max(kstats, key=lambda nm: kstats[nm]["ms"])
     roof = None
-    model = kernel_model(dom, V, g, {"nsweep": chosen_p.nsweep}, peaks)
+    model = kernel_model(dom, V, g, {"nsweep": chosen_p.nsweep, "nsap": chosen_p.nsap}, peaks)
     if model:
         bound, units, unit, peak, psrc = model
         avg_ms = kstats[dom]["ms"] / kstats[dom]["launches"]
@@ -810,20 +823,25 @@ def run_gpu_on_stream(args, q, qi, torch, stream, rank, world, local):
         roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak, "traffic": None, "avg_launch_ms": avg_ms, "peak_source": psrc,
                 "units_per_launch": units,
-                "model": "tile SAP launch (one colour, %d right-hand sides): V/2 x nrhs x (2 nsweep + 1) x 1896 "
-                         "flop (Table 1), time from a profiled pass of one group of the chosen solve" % g}
+                "model": "average tile SAP launch (one colour, %d right-hand sides): V/2 x nrhs x (2 nsweep + "
+                         "(nsap - 1) / nsap) site updates x 1896 flop (Table 1; the residual's in-block operator "
+                         "only where a later cycle reads it), time from a profiled pass of one group of the "
+                         "chosen solve" % g}
         if dom == "ssor":
-            sb = sap_smem_bytes_per_launch(V, g, chosen_p.nsweep, chosen_p.sap_storage == q.QCD_F16)
+            sb = sap_smem_bytes_per_launch(V, g, chosen_p.nsweep, chosen_p.nsap, chosen_p.sap_storage == q.QCD_F16)
             roof["smem"] = {"achieved": sb / (avg_ms * 1e-3) / 1e9, "peak": smem_gbs, "unit": "GB/s",
                             "frac": sb / (avg_ms * 1e-3) / 1e9 / smem_gbs,
                             "peak_source": "measured: conflict-free 16-byte shared loads (qcd_bench_smem_peak)",
                             "model": "per (site, right-hand side): 2 nsweep x 11 spinors (8 neighbours, y, f read, "
-                                     "y written) + 9 in the epilogue + 1 source write, 48 B each in FP16 storage"}
+                                     "y written), 1 for x += y, 9 for the kept residual, the source write and the "
+                                     "y copy-out, 48 B each in FP16 storage, averaged over an application"}
         src = "paper_1210_7398_gb300/csrc/ssor_tile.cu"
         t = NCU_TRAFFIC.get(dom)
         if t and t["sha"] == source_sha(src):
-            roof["traffic"] = sap_traffic_per_site_rhs(t, chosen_p.nsap) * (V / 2) * g
-            roof["traffic_source"] = t["capture"]
+            per = sap_traffic_per_site_rhs(t, chosen_p.nsap, chosen_p.nsweep)
+            if per is not None:
+                roof["traffic"] = per * (V / 2) * g
+                roof["traffic_source"] = t["capture"]
     dsl = []
     if not args.skip_dslash:
         dsl += dslash_bandwidth(q, qi, torch, stream, dims, 10, peaks,
