@@ -234,8 +234,9 @@ struct TileArgs {
     const uint4 *rec;          // records of this colour's blocks, [block][vol] x TileRec::bytes
     const int4 *pos;           // [vol][2] per level position: (global offset from the block origin,
                                // shared-memory slot, neighbour slots 0|1 << 16, 2|3 << 16),
-                               // (4|5 << 16, 6|7 << 16, block-local site, 0); a neighbour outside
-                               // the block is a zero slot (>= vol)
+                               // (4|5 << 16, 6|7 << 16, block-local site, its coordinates y_mu
+                               // in bytes mu = 0..3); a neighbour outside the block is a zero
+                               // slot (>= vol)
     const int *lev_ptr;        // [nlev + 1] first level position of each level
     const int *origin_site;    // [blocks of this colour] global index of the block origin
     const int *origin;         // [blocks of this colour][4] coordinates of the block origin
@@ -259,15 +260,13 @@ struct TileArgs {
     int blk_base, other_base;  // index in yscale of this colour's first block, of the other colour's
 };
 
-// the other colour's block solution at site mm (coordinates xn) for one right-hand side: FP32 in
-// the lattice layout, or (FP16 storage) the FP16 record times its block's scale
+// the other colour's block solution at site mm, in the neighbouring block of rank nrank among its
+// colour, for one right-hand side: FP32 in the lattice layout, or (FP16 storage) the FP16 record
+// times its block's scale
 template <bool HALF>
-__device__ __forceinline__ void load_y_other(const TileArgs &a, int rhs, long mm, const int xn[4], float2 psi[12]) {
+__device__ __forceinline__ void load_y_other(const TileArgs &a, int rhs, long mm, int nrank, float2 psi[12]) {
     if constexpr (HALF) {
-        // blocks of one colour are listed in lexicographic order (x fastest) and alternate in
-        // colour along x, whose block count is even: the rank among its colour is lex / 2
-        const int lex = xn[0] / a.b[0] + a.nb[0] * (xn[1] / a.b[1] + a.nb[1] * (xn[2] / a.b[2] + a.nb[2] * (xn[3] / a.b[3])));
-        const float sc = a.yscale[(size_t)(a.other_base + (lex >> 1)) * a.nrhs + rhs];
+        const float sc = a.yscale[(size_t)(a.other_base + nrank) * a.nrhs + rhs];
         const uint4 *q = a.y16 + ((size_t)rhs * a.V + mm) * 3;
 #pragma unroll
         for (int k = 0; k < 3; k++) {
@@ -295,12 +294,24 @@ __global__ void __launch_bounds__(kTileMaxThreads, kTileMinBlocks) k_sap_tile(Ti
     extern __shared__ __align__(16) float sm[];
     __shared__ float scale_s[R];
     __shared__ int act_s[R];
+    __shared__ int nrank_s[8];  // rank among its colour of the neighbouring block in direction d
     const int tid = threadIdx.x, T = blockDim.x;
     const int blk = blockIdx.x, rhs0 = blockIdx.y * R;
     if (tid < R) {
         const int r = rhs0 + tid;
         act_s[tid] = r < a.nrhs && (!a.gate || a.gate[r].active);
         scale_s[tid] = 0.f;
+    }
+    if (tid < 8) {
+        // the block one step along mu = tid / 2, forward for even tid (periodic in the block
+        // grid).  Blocks of one colour are listed in lexicographic order (x fastest) and alternate
+        // in colour along x, whose block count is even: the rank among its colour is lex / 2.
+        const int mu = tid >> 1;
+        int cb[4];
+        for (int m = 0; m < 4; m++) cb[m] = a.origin[4 * blk + m] / a.b[m];
+        if (tid & 1) cb[mu] = cb[mu] == 0 ? a.nb[mu] - 1 : cb[mu] - 1;
+        else cb[mu] = cb[mu] + 1 == a.nb[mu] ? 0 : cb[mu] + 1;
+        nrank_s[tid] = (cb[0] + a.nb[0] * (cb[1] + a.nb[1] * (cb[2] + a.nb[2] * cb[3]))) >> 1;
     }
     __syncthreads();
     bool any = false;
@@ -339,15 +350,11 @@ __global__ void __launch_bounds__(kTileMaxThreads, kTileMinBlocks) k_sap_tile(Ti
                                    pb.x & 0xffff, pb.x >> 16, pb.y & 0xffff, pb.y >> 16};
                 if (nb[0] >= a.vol || nb[1] >= a.vol || nb[2] >= a.vol || nb[3] >= a.vol || nb[4] >= a.vol ||
                     nb[5] >= a.vol || nb[6] >= a.vol || nb[7] >= a.vol) {
-                    // the offset from the block origin, sum_mu y_mu st_mu with 0 <= y_mu < L_mu, gives
-                    // the block-local coordinates y_mu
+                    // global coordinates from the block origin and the block-local ones
                     const long st[4] = {1, a.L[0], (long)a.L[0] * a.L[1], (long)a.L[0] * a.L[1] * a.L[2]};
                     int xg[4];
-                    long off = pa.x;
-                    for (int mu = 3; mu >= 0; mu--) {
-                        xg[mu] = org[mu] + (int)(off / st[mu]);
-                        off %= st[mu];
-                    }
+#pragma unroll
+                    for (int mu = 0; mu < 4; mu++) xg[mu] = org[mu] + ((pb.w >> (8 * mu)) & 255);
                     const uint4 *rec = recb + (size_t)pos * L::chunks;
                     float2 acc[12];
 #pragma unroll
@@ -358,9 +365,7 @@ __global__ void __launch_bounds__(kTileMaxThreads, kTileMinBlocks) k_sap_tile(Ti
                         ld_link<HALF, 2 * MU>(rec, W);                                               \
                         const bool wrap = xg[MU] == a.L[MU] - 1;                                     \
                         const long mm = n0 + pa.x + (wrap ? -(long)(a.L[MU] - 1) * st[MU] : st[MU]); \
-                        int xn[4] = {xg[0], xg[1], xg[2], xg[3]};                                    \
-                        xn[MU] = wrap ? 0 : xg[MU] + 1;                                              \
-                        load_y_other<HALF>(a, rhs0 + r_me, mm, xn, psi);                             \
+                        load_y_other<HALF>(a, rhs0 + r_me, mm, nrank_s[2 * MU], psi);                \
                         hop_term_w2<MU, true>(psi, W, acc, (MU == 3 && wrap) ? (float)a.bc_t : 1.f); \
                     }                                                                                \
                     if (nb[2 * MU + 1] >= a.vol) {                                                   \
@@ -368,9 +373,7 @@ __global__ void __launch_bounds__(kTileMaxThreads, kTileMinBlocks) k_sap_tile(Ti
                         ld_link<HALF, 2 * MU + 1>(rec, W);                                           \
                         const bool wrap = xg[MU] == 0;                                               \
                         const long mm = n0 + pa.x + (wrap ? (long)(a.L[MU] - 1) * st[MU] : -st[MU]); \
-                        int xn[4] = {xg[0], xg[1], xg[2], xg[3]};                                    \
-                        xn[MU] = wrap ? a.L[MU] - 1 : xg[MU] - 1;                                    \
-                        load_y_other<HALF>(a, rhs0 + r_me, mm, xn, psi);                             \
+                        load_y_other<HALF>(a, rhs0 + r_me, mm, nrank_s[2 * MU + 1], psi);            \
                         hop_term_w2<MU, false>(psi, W, acc, (MU == 3 && wrap) ? (float)a.bc_t : 1.f);\
                     }
                     QCD_TILE_CROSS(0)
@@ -648,8 +651,10 @@ struct TileLayout {
 };
 
 // p.h_tile_pos from a layout: per position (offset, slot, neighbour slots d = 0..3) and
-// (neighbour slots d = 4..7, site, 0), d = 2 mu + backward; an out-of-block hop reads the zero
-// slot vol + k, 0 <= k < zslots, with vol + k = zres mod zslots.
+// (neighbour slots d = 4..7, site, its coordinates packed in bytes), d = 2 mu + backward; an
+// out-of-block hop reads the zero slot vol + k, 0 <= k < zslots, with vol + k = zres mod zslots.
+// A block extent above 255 does not pack: tile_positions_valid then rejects the table and the
+// plan takes another form.
 void tile_fill_positions(SapPlan &p, const TileLayout &t) {
     const int Z = p.tile_zslots;
     p.h_tile_pos.assign(2 * (size_t)p.vol, make_int4(0, 0, 0, 0));
@@ -665,7 +670,8 @@ void tile_fill_positions(SapPlan &p, const TileLayout &t) {
             stride *= p.b[m];
         }
         p.h_tile_pos[2 * k] = make_int4(p.h_site_off[yl], t.slot[yl], nbk[0] | (nbk[1] << 16), nbk[2] | (nbk[3] << 16));
-        p.h_tile_pos[2 * k + 1] = make_int4(nbk[4] | (nbk[5] << 16), nbk[6] | (nbk[7] << 16), yl, 0);
+        p.h_tile_pos[2 * k + 1] = make_int4(nbk[4] | (nbk[5] << 16), nbk[6] | (nbk[7] << 16), yl,
+                                            y[0] | (y[1] << 8) | (y[2] << 16) | (y[3] << 24));
     }
 }
 
@@ -776,6 +782,12 @@ bool tile_positions_valid(const SapPlan &p) {
         if (pb.z < 0 || pb.z >= p.vol || site[pb.z] || pa.y < 0 || pa.y >= p.vol || slot[pa.y]) return false;
         site[pb.z] = slot[pa.y] = 1;
         if (pa.x != p.h_site_off[pb.z]) return false;
+        // the packed block-local coordinates are those of the site (x fastest)
+        int r = pb.z;
+        for (int m = 0; m < 4; m++) {
+            if (((pb.w >> (8 * m)) & 255) != r % p.b[m]) return false;
+            r /= p.b[m];
+        }
         const int nb[8] = {pa.z & 0xffff, pa.z >> 16, pa.w & 0xffff, pa.w >> 16,
                            pb.x & 0xffff, pb.x >> 16, pb.y & 0xffff, pb.y >> 16};
         for (int d = 0; d < 8; d++)

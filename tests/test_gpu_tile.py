@@ -30,6 +30,10 @@ TILE_CASES = [
     ((12, 12, 12, 24), (6, 6, 6, 6), (3, 3, 3, 3), 1.0, 4, 4, ("f32", "f16")),  # the paper's split
     ((12, 12, 12, 24), (6, 6, 6, 12), (3, 3, 3, 6), 1.0, 4, 4, ("f16",)),  # does not fit: the cluster form stands in
     ((12, 12, 12, 24), (3, 3, 3, 6), (1, 1, 1, 2), 0.9, 2, 2, ("f32", "f16")),
+    # block grids of 6 x 2 x 2 x 4 and 4 x 2 x 2 x 2: the cross hops find the neighbouring block
+    # of the other colour in each direction, across the periodic wrap; one and two SAP cycles
+    ((24, 4, 4, 8), (4, 2, 2, 2), (2, 1, 1, 1), 1.4, 2, 1, ("f32", "f16")),
+    ((16, 8, 8, 12), (4, 4, 4, 6), (2, 2, 2, 3), 1.3, 2, 2, ("f16",)),
 ]
 
 
