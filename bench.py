@@ -46,7 +46,7 @@ D_BYTES_PER_SITE = {"f32": 768, "f64": 1536, "f16": 480, "su3": 672,  # in + out
 L2_BYTES = 126 << 20
 # DRAM bytes (read + write) per unit of work of a kernel, from one ncu capture of the kernel
 # source identified by its SHA-256 prefix; reported only while the source is unchanged
-NCU_TRAFFIC = {"ssor": {"sha": "08bd50dfec66ed03", "nsap": 1, "nsweep": 2, "per_launch": [634.1, 703.9],
+NCU_TRAFFIC = {"ssor": {"sha": "2d5f2563905eaedb", "nsap": 1, "nsweep": 2, "per_launch": [629.6, 703.0],
                          "capture": "ncu, k_sap_tile<FP16, 4> on 24^3x48 (4^4 / 2^4 blocks, 4 right-hand sides, "
                                     "2 sweeps, 1 cycle): DRAM bytes per (site, right-hand side) of the colour of "
                                     "each launch of one application, averaged and scaled to this launch"}}
