@@ -228,6 +228,8 @@ int build_clover(qcd_ctx *c, double kappa, double csw);
 struct BicgScalars;
 int dslash64(qcd_ctx *c, double2 *out, const double2 *in, int nrhs);
 // D in pair-of-FP32 arithmetic: FP32 input (internal layout), FP64 output (internal layout)
+// makes the two-row link copy the inner solver's D reads (before any graph capture of it)
+int dslash32_prepare(qcd_ctx *c);
 int dslash_x2(qcd_ctx *c, double2 *out, const float4 *in, int nrhs);
 int dslash32(qcd_ctx *c, float4 *out, const float4 *in, int nrhs);
 int dslash16(qcd_ctx *c, float4 *out, const float4 *in, int nrhs);

@@ -295,6 +295,7 @@ int workspace(qcd_ctx *c, int nrhs, int block_solver, Ws *w) {
 int solve(qcd_ctx *c, double2 *x, const double2 *b, const qcd_params *p, int nrhs, qcd_stats *st) {
     Ws w;
     TRY(workspace(c, nrhs, p->block_solver, &w));
+    TRY(dslash32_prepare(c));  // the inner D's link copy, made here rather than inside a graph capture
     const long n = 12 * w.V;
     const size_t b64 = sizeof(double2) * n * nrhs;
     const int R = nrhs;
