@@ -298,15 +298,18 @@ int qcd_sap_plan_tables(const int dims[4], const int block[4], const int subbloc
  * sub-blocks).  Starting from *base (kappa, csw, tol, inner_tol, bc_t, limits),
  * times complete solves of D x = b from x0 = 0 for candidate SAP set-ups and
  * returns the fastest that converges in *best (block, subblock, omega,
- * sap_storage, sap_ctas, nsweep, nsap) and its time in *best_ms.  Stage 1
+ * sap_storage, sap_ctas, nsweep, nsap, outer_precision, rhs_group) and its time
+ * in *best_ms.  Stage 1
  * tries block extents (2, 3, 4, 6, 8, 12 or 16, the spatial ones alike, the
  * time extent one to two times the spatial one, each dividing L with an even
  * quotient) with sub-blocks block/2, block/3 or block, blocks of about 256 sites
  * first, each with FP16 storage and the tile form (sap_ctas -2; the cluster form
  * where the block does not fit), 2 sweeps, 2 cycles and omega 1; stage 2 is a
- * coordinate search from the fastest, keeping each move that is faster: omega
- * upwards in steps of 0.2 while it improves, nsap 1 or 3, nsweep 3 or 1, then
- * the storage and kernel forms (FP32 / FP16, sap_ctas -2, 0, 2).  At most
+ * coordinate search from the fastest, keeping each move that is faster: the
+ * outer operator in pair-of-FP32 arithmetic (outer_precision QCD_F32X2, the same
+ * accuracy) where base asks for QCD_F64, omega upwards in steps of 0.2 while it
+ * improves, nsap 1 or 3, nsweep 3 or 1, then the storage and kernel forms
+ * (FP32 / FP16, sap_ctas -2, 0, 2).  At most
  * max_candidates solves are timed (<= 0: 64), at most half of them in stage 1.
  * Stage 3 (nrhs > 1 and base->rhs_group = 0) then times the winner with
  * right-hand sides in groups of 1, 2, 4 or 8 dividing nrhs, as well as all at
@@ -320,7 +323,7 @@ int qcd_autotune(qcd_ctx *ctx, const double *b, int nrhs, const qcd_params *base
  * limits, omega, rhs_group, max_candidates, GPU name and SM count, tuner version) and returns it
  * without timing anything; otherwise it tunes and appends the winner as one JSON object per
  * line ({"key": ..., "block": [...], "subblock": [...], "omega", "sap_storage", "sap_ctas",
- * "nsweep", "nsap", "rhs_group", "ms"}).  NULL or "" switches the cache off (the default).  Process-wide;
+ * "nsweep", "nsap", "rhs_group", "outer_precision", "ms"}).  NULL or "" switches the cache off (the default).  Process-wide;
  * the file is read and appended under a lock.  Always QCD_OK. */
 int qcd_set_tune_cache(const char *path);
 
