@@ -44,6 +44,24 @@ def test_binding_structs_match_header():
     assert ctypes.sizeof(q.qcd_learned_verdict) == 56
 
 
+def test_binding_constants_match_header():
+    """Every QCD_* enumerator of the header has the same value in the binding (precisions and
+    storage forms, error codes, kernel classes)."""
+    text = open(os.path.join(ROOT, "include", "qcd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    consts = {}
+    for body in re.findall(r"enum\s*\{([^}]*)\}", text):
+        for name, val in re.findall(r"\b(QCD_[A-Z0-9_]+)\s*=\s*(-?\d+)", body):
+            consts[name] = int(val)
+    assert consts["QCD_F32X2"] == 5 and consts["QCD_F64"] == 0
+    checked = 0
+    for name, val in consts.items():
+        if hasattr(q, name):
+            assert getattr(q, name) == val, name
+            checked += 1
+    assert checked >= 8
+
+
 def test_null_context_is_rejected(lib):
     q.load_library()
     assert q.load_library().qcd_set_boundary(None, 1) == q.QCD_ERR_ARG
