@@ -389,7 +389,8 @@ int qcd_learned_evaluate(qcd_ctx *ctx, const double *b, int nrhs, const qcd_para
 /* Kernel classes timed when profiling is on. */
 enum {
     QCD_K_DSLASH32 = 0, /* full operator D in FP32 (inner solver)     */
-    QCD_K_DSLASH64 = 1, /* full operator D in FP64 (outer solver)     */
+    QCD_K_DSLASH64 = 1, /* full operator D of the outer solver: FP64,
+                           or pair-of-FP32 arithmetic (QCD_F32X2)     */
     QCD_K_SSOR = 2,     /* SAP block SSOR (A_EE / A_OO)              */
     QCD_K_SAPHOP = 3,   /* SAP block / cross-block hop updates       */
     QCD_K_BLAS = 4,     /* BiCGStab vector updates and reductions    */
